@@ -1,0 +1,310 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU, no CUDA library).
+
+Each test checks the oracle against something other than itself: a textbook identity, a closed form, a printed
+number, a physical limit, an independent discretisation of the same operator, or the same computation in extended
+precision.  A dropped term, a wrong sign, index or normalisation, or a transposed operand fails at least one.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+from oracle import seas_oracle as O
+from paper_2603_00383_gb300 import synth
+
+CS = 3464.0
+MU = 32e9
+
+
+# ---------------------------------------------------------------- spectral kernel K(n, t) and its weights ------
+
+@pytest.mark.parametrize("n", [1, 3, 17])
+def test_K_before_cs_t_eq_L_is_J1_over_a(n):
+    """P1: for c_s t < L, Eq. (non_replicant_kernel_a) equals J_1(a)/a, a = n pi c_s t / L (textbook integral)."""
+    L = 1000.0
+    t = np.linspace(0.02, 0.98, 25) * L / CS
+    a = n * np.pi * CS * t / L
+    np.testing.assert_allclose(O.kernel_K(n, t, L, CS), special.j1(a) / a, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [1, 4, 9])
+def test_K_branches_meet_at_cs_t_eq_L(n):
+    """P2: the two branches of Eq. (non_replicant_kernel) join continuously at c_s t = L."""
+    L = 700.0
+    lo = O.kernel_K(n, L / CS * (1 - 1e-9), L, CS)
+    hi = O.kernel_K(n, L / CS * (1 + 1e-9), L, CS)
+    assert abs(lo - hi) < 1e-6 * max(1.0, abs(lo))
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 10, 40])
+def test_K_decays_monotonically_after_L_while_J1_oscillates(n):
+    """P4 (App. D): |K(n,t)| decreases monotonically for c_s t > L; the replicating J_1(a)/a keeps oscillating."""
+    L = 1000.0
+    t = np.linspace(1.0001, 30.0, 1500) * L / CS
+    K = O.kernel_K(n, t, L, CS)
+    assert np.all(np.diff(np.abs(K)) < 0)
+    assert np.all(np.sign(K) == np.sign(K[0]))
+    a = n * np.pi * CS * t / L
+    assert np.mean(np.diff(np.abs(special.j1(a) / a)) < 0) < 0.6
+
+
+@pytest.mark.parametrize("n", [1, 6, 25])
+def test_weights_equal_time_integral_of_J1_over_a(n):
+    """Weights for intervals with c_s t_1 < L against c_s k_n int J_1(a(t))/a(t) dt (independent closed form of K)."""
+    L, dt = 1000.0, 0.5 * 1000.0 / 64 / CS
+    kn = np.pi * n / L
+    T = np.array([0, 1, 7, 30, 100])
+    got = O.spectral_weights(n, T, dt, L, CS)
+    for Ti, g in zip(T, got):
+        f = lambda t: special.j1(kn * CS * t) / (kn * CS * t) if t > 0 else 0.5
+        ref = CS * kn * integrate.quad(f, Ti * dt, (Ti + 1) * dt, epsabs=1e-15, epsrel=1e-13)[0]
+        assert abs(g - ref) < 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 3])
+def test_weights_equal_time_integral_of_long_time_branch(n):
+    """Weights for c_s t_0 > L against nested quadrature of Eq. (non_replicant_kernel_b) over psi and t."""
+    L = 500.0
+    dt = 0.5 * L / 32 / CS
+    kn = np.pi * n / L
+
+    def Kb(t):
+        a = n * np.pi * CS * t / L
+        return 2 / np.pi * integrate.quad(lambda p: np.cos(p) ** 2 * np.cos(a * np.sin(p)), 0,
+                                          np.arcsin(L / (CS * t)), epsabs=1e-15, limit=200)[0]
+
+    for Ti in [70, 90, 200]:
+        assert CS * Ti * dt > L
+        ref = CS * kn * integrate.quad(Kb, Ti * dt, (Ti + 1) * dt, epsabs=1e-15, epsrel=1e-12)[0]
+        got = O.spectral_weights(n, np.array([Ti]), dt, L, CS)[0]
+        assert abs(got - ref) < 2e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_weight_sums_telescope_to_static_limit(n):
+    """P3: sum_{T<K} w^T = c_s k_n int_0^{K dt} K dt, which for rho = c_s K dt / L > 1 equals
+    (2/pi) int_0^1 sqrt(1 - x^2/rho^2) sin(n pi x)/x dx (substitution x = rho sin psi) and tends to (2/pi) Si(n pi),
+    the elastostatic limit, within 1/(pi rho^2)."""
+    nf = 4
+    L = 40.0
+    dt = 0.5 * (L / nf) / CS
+    K = 2400
+    rho = CS * K * dt / L
+    s = O.spectral_weights(n, np.arange(K), dt, L, CS).sum()
+    ref = 2 / np.pi * integrate.quad(lambda x: np.sqrt(1 - x * x / rho ** 2) * np.sin(n * np.pi * x) / x, 0, 1,
+                                     epsabs=1e-15, limit=200)[0]
+    assert abs(s - ref) < 1e-12
+    assert abs(s - 2 / np.pi * special.sici(n * np.pi)[0]) < 1.0 / (np.pi * rho ** 2)
+
+
+def test_dft_pair_reconstructs_zero_padded_slip():
+    """The mode range n = -N_f+1..N_f with F_{-n} = conj(F_n) and the 1/M normalisation invert exactly: the
+    identity mode operator maps slip back to itself on the physical fault."""
+    rng = np.random.default_rng(3)
+    for nf in (5, 16, 33):
+        d = rng.standard_normal((3, nf))
+        D = O.slip_modes(d, nf)
+        assert np.allclose(D[:, 0], d.sum(-1) / (2 * nf))
+        np.testing.assert_allclose(O.modes_to_space(D, nf), d, atol=1e-13)
+
+
+def test_mode_window_limits():
+    """Eq. (mode_dependent_truncation): q_w = n_max gives T_end(1) for all modes; q_w = 1 gives T_end(1)/n."""
+    nf, L, dt = 64, 1280.0, 0.5 * 20.0 / CS
+    W_all = O.mode_windows(nf, L, dt, CS, 1.5, 0, 10 ** 6)
+    W1 = math.ceil(1.5 * L / CS / dt - 1e-9)
+    assert np.all(W_all[1:] == W1)
+    W_q1 = O.mode_windows(nf, L, dt, CS, 1.5, 1, 10 ** 6)
+    for n in (1, 2, 5, 64):
+        assert W_q1[n] == math.ceil(1.5 * L / CS / n / dt - 1e-9)
+
+
+# ---------------------------------------------------------------- space-time interaction kernel -------------------
+
+def test_primitive_cross_derivatives_agree():
+    """P5: I_31 and I_32 derive from one potential off the cut: d I_31/d r2 = d I_32/d r1 (catches garbled terms
+    of Eq. primitives)."""
+    rng = np.random.default_rng(5)
+    for _ in range(40):
+        r1, r2 = rng.uniform(-400, 400), rng.uniform(-400, 400)
+        r = math.hypot(r1, r2)
+        t = r / CS * rng.uniform(1.1, 4.0)
+        h = 1e-3
+        a = (O.I31(r1, r2 + h, t, CS) - O.I31(r1, r2 - h, t, CS)) / (2 * h)
+        b = (O.I32(r1 + h, r2, t, CS) - O.I32(r1 - h, r2, t, CS)) / (2 * h)
+        assert abs(a - b) < 1e-6 * (abs(a) + 1e-3)
+
+
+def test_self_element_lag0_is_radiation_damping():
+    """P7: on its own element (r1 = r2 = 0) the lag-0 kernel is K_32 = 1, K_31 = 0, which reproduces the
+    instantaneous radiation damping -mu/(2 c_s) V of Eq. (superimposition2) (reading H(0) = 0)."""
+    for ds in (20.0, 78.125, 9.92757):
+        dt = 0.5 * ds / CS
+        k31, k32 = O.kernel_K3l(0.0, 0.0, 0, dt, ds, CS)
+        assert abs(k31) == 0.0
+        assert abs(k32 - 1.0) < 1e-6
+
+
+def _seg_dist(r1, r2, ds):
+    return np.where(np.abs(r1) <= ds / 2, np.abs(r2), np.hypot(np.abs(r1) - ds / 2, r2))
+
+
+def test_kernel_zero_exactly_before_arrival():
+    """P6: A_ij^T = 0 exactly iff the shear front from the nearest point of the source segment has not reached the
+    receiver by t = (T+1) dt; nonzero after."""
+    w = synth.tiny(2)
+    net = O.network(w.faults, MU, CS)
+    d = net.x[:, None, :] - net.x[None, :, :]
+    r1 = (d * net.e1[None]).sum(-1)
+    r2 = (d * net.nrm[None]).sum(-1)
+    dist = _seg_dist(r1, r2, net.ds[None, :])
+    other = net.fault_of[:, None] != net.fault_of[None, :]
+    checked = 0
+    for T in range(0, 160, 3):
+        A = O.interaction_slice(net, T)
+        front = CS * (T + 1) * net.dt
+        clear = np.abs(front - dist) > 1e-9 * dist
+        before = (front < dist) & other & clear
+        after = (front > dist) & other & clear
+        assert np.all(A[before] == 0.0)
+        assert np.all(A[after] != 0.0)
+        checked += after.sum()
+    assert checked > 100
+
+
+def test_late_time_kernel_tends_to_elastostatic_dislocation_stress():
+    """P8: K_3l^T / dt tends to the static anti-plane stress of a uniformly slipped segment (a pair of screw
+    dislocations): S_31 = -(c_s/pi)(r2/rho+^2 - r2/rho-^2), S_32 = (c_s/pi)(r1+/rho+^2 - r1-/rho-^2),
+    r1+- = r1 +- ds/2, with an error decaying like T^-2."""
+    ds = 20.0
+    dt = 0.5 * ds / CS
+    for r1, r2 in [(300.0, 200.0), (-1000.0, 50.0), (5.0, 400.0)]:
+        rp, rm = r1 + ds / 2, r1 - ds / 2
+        pp, pm = rp ** 2 + r2 ** 2, rm ** 2 + r2 ** 2
+        S31 = -(CS / np.pi) * (r2 / pp - r2 / pm)
+        S32 = (CS / np.pi) * (rp / pp - rm / pm)
+        errs = []
+        for T in (3000, 30000):
+            k31, k32 = O.kernel_K3l(r1, r2, T, dt, ds, CS)
+            errs.append(abs(k32 / dt - S32) / abs(S32))
+            assert abs(k31 / dt - S31) < 1e-4 * abs(S31)
+        assert errs[1] < errs[0] / 50 and errs[1] < 2e-5
+
+
+def test_reciprocity_of_far_field_kernel():
+    """Source/receiver reciprocity of the anti-plane Green's function: for well-separated elements,
+    A_ij^T / ds_j ~ A_ji^T / ds_i (error O((ds/r)^2)).  Faults of different element sizes make a transposed
+    operand, a wrong frame or a receiver/source normal swap fail."""
+    faults = np.array([[0.0, 0.0, 0.2, 200.0, 10], [100.0, -900.0, 1.1, 400.0, 10]])
+    net = O.network(faults, MU, CS)
+    nA = 10
+    for T in (300, 500, 800):
+        A = O.interaction_slice(net, T)
+        ab = A[:nA, nA:] / net.ds[None, nA:]
+        ba = A[nA:, :nA].T / net.ds[:nA, None]
+        r = np.linalg.norm(net.x[:nA, None, :] - net.x[None, nA:, :], axis=-1)
+        assert np.all(CS * T * net.dt > 1.5 * r)
+        np.testing.assert_allclose(ab, ba, rtol=3e-3)
+
+
+# ---------------------------------------------------------------- windows and printed numbers --------------------
+
+def test_printed_two_fault_and_x_fault_numbers(golden_printed):
+    """P9: the printed geometry of Sec. 3.1 reproduces the printed dt_min, cell sizes and T_end; Table 2's dt."""
+    w = synth.paper_two_fault()
+    net = O.network(w.faults, 30e9, CS)
+    g = golden_printed
+    assert abs(net.dt - g["two_fault.dt_min"][0]) <= g["two_fault.dt_min"][1]
+    assert abs(net.ds[0] - g["two_fault.dx_1"][0]) <= g["two_fault.dx_1"][1]
+    assert abs(net.ds[-1] - g["two_fault.dx_2"][0]) <= g["two_fault.dx_2"][1]
+    _, t_end, _ = O.pair_windows(net, 0.01, 0.01, 10 ** 6)
+    assert abs(t_end.max() - g["two_fault.T_end"][0]) <= g["two_fault.T_end"][1]
+    xf = O.network(np.array([[0, 0, 0.6, 1000.0, 510], [0, 0, -0.6, 1000.0, 510]]), 30e9, CS)
+    assert abs(xf.dt - g["x_fault.dt_min"][0]) <= g["x_fault.dt_min"][1]
+
+
+def test_exact_first_lag_and_centroid_arrival_time():
+    """Window start reading: the first nonzero lag of a fault pair is floor(min segment distance / (c_s dt)) (from
+    P6), while the centroid-based T_earl of Eq. (early_time) can come after the true first arrival (a source element
+    radiates from its nearest point, so for a receiver just beyond an element end the centroid distance overstates it
+    by up to ds/2).  The operator therefore starts each block at its exact first nonzero lag and reports T_init only;
+    on this network the paper's T_init = (1 - eta_Tmin) T_earl does include that first lag."""
+    w = synth.two_fault_128()
+    net = O.network(w.faults, MU, CS)
+    t_init, _, _ = O.pair_windows(net, 0.01, 0.01, 400)
+    d = net.x[:, None, :] - net.x[None, :, :]
+    r1 = (d * net.e1[None]).sum(-1)
+    r2 = (d * net.nrm[None]).sum(-1)
+    dist = _seg_dist(r1, r2, net.ds[None, :])
+    for a, b in [(0, 1), (1, 0)]:
+        ra, rb = slice(128 * a, 128 * a + 128), slice(128 * b, 128 * b + 128)
+        dmin = dist[ra, rb].min()
+        first = next(T for T in range(60) if np.any(O.interaction_slice(net, T)[ra, rb] != 0))
+        assert first == math.floor(dmin / (CS * net.dt))
+        assert t_init[a, b] / net.dt <= first + 1
+
+
+# ---------------------------------------------------------------- the whole functional ---------------------------
+
+def test_linearity_and_time_shift_invariance():
+    """P10: the functional is linear in the history and Toeplitz in time (pushing one zero step first delays the
+    output by one step)."""
+    w = synth.tiny(1, steps=24)
+    net = O.network(w.faults, MU, CS)
+    hp = dict(w.hparams, max_steps=25)
+    V1 = w.slip_rate(0, 0, 24)
+    V2 = w.slip_rate(1, 0, 24)
+    t1 = O.stress_history(net, V1, hp)[0]
+    t2 = O.stress_history(net, V2, hp)[0]
+    t12 = O.stress_history(net, 2.0 * V1 - 0.5 * V2, hp)[0]
+    np.testing.assert_allclose(t12, 2.0 * t1 - 0.5 * t2, rtol=1e-11, atol=1e-9 * np.abs(t1).max())
+    Vs = np.vstack([np.zeros((1, net.N)), V1[:-1]])
+    ts = O.stress_history(net, Vs, hp)[0]
+    np.testing.assert_allclose(ts[1:], t1[:-1], rtol=1e-11, atol=1e-9 * np.abs(t1).max())
+    assert np.all(ts[0] == 0.0)
+
+
+def test_spectral_self_converges_to_space_time_self_sum():
+    """P12: on one fault, radiation damping + the non-replicating spectral term and the space-time self sum of the
+    same primitives (r2 = 0, K_32 only) are two discretisations of one operator; they agree at O(ds)."""
+    L = 1000.0
+    errs = []
+    for N in (16, 32):
+        net = O.network(np.array([[0.0, 0.0, 0.3, L, N]]), MU, CS)
+        steps = int(round(3 * L / (CS * net.dt)))
+        t = np.arange(steps) * net.dt
+        xi = (np.arange(N) + 0.5) / N
+        V = np.outer(np.sin(np.pi * CS * t / L) ** 2 * (t < L / CS), np.sin(np.pi * xi) ** 2)
+        tab = O.SelfTables(N, L, net.dt, CS, np.full(N + 1, steps - 1))
+        spectral = O.self_history(net, 0, O.slip_from_rate(V, net.dt), tab) - MU / (2 * CS) * V
+        d = net.x[:, None, :] - net.x[None, :, :]
+        r1 = (d * net.e1[None]).sum(-1)
+        r2 = (d * net.nrm[None]).sum(-1)
+        A = np.stack([O.kernel_K3l(r1, r2, T, net.dt, net.ds[None, :], CS)[1] for T in range(steps)])
+        st = np.array([-(MU / (2 * CS)) * np.einsum("tij,tj->i", A[: n + 1], V[n::-1]) for n in range(steps)])
+        errs.append(np.linalg.norm(spectral - st) / np.linalg.norm(st))
+    assert errs[0] < 0.03 and errs[1] < 0.6 * errs[0]
+
+
+@pytest.mark.skipif(np.finfo(np.longdouble).eps > 1e-18, reason="no extended precision long double here")
+def test_oracle_rounding_is_far_below_parity_tolerance():
+    """P13: the FP64 interaction sum agrees with the same sum in extended precision to << 1e-10 (rel-L2)."""
+    w = synth.tiny(3, steps=150)
+    net = O.network(w.faults, MU, CS)
+    V = w.slip_rate(0, 0, 150)
+    f64 = O.interaction_history(net, V)
+    fld = O.interaction_history(net, V, dtype=np.longdouble).astype(np.float64)
+    assert np.linalg.norm(fld) > 0
+    assert np.linalg.norm(f64 - fld) / np.linalg.norm(fld) < 1e-13
+
+
+def test_normal_stress_change_vanishes_and_parts_add_up():
+    """Sec. 2.1: in mode III the elastodynamic normal-stress change is identically zero; tau is the sum of the
+    three parts of Eq. (superimposition2) and the radiation part is exactly -mu/(2 c_s) V."""
+    w = synth.tiny(1, steps=10)
+    net = O.network(w.faults, MU, CS)
+    V = w.slip_rate(0, 0, 10)
+    tau, rad, fs, fi = O.stress_history(net, V, dict(w.hparams, max_steps=10))
+    np.testing.assert_array_equal(rad, -(MU / (2 * CS)) * V)
+    np.testing.assert_allclose(tau, rad + fs + fi, rtol=0, atol=0)
