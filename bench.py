@@ -1,0 +1,387 @@
+"""Benchmark of the per-step stress-transfer functional on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload six_fault_3072]
+
+A step is one push of the slip rate plus one seas_stress_step (all hot-path stages: push, forward FFT, mode
+convolution, H-matrix interaction, inverse FFT + assembly) on the six-fault, 3072-element network with the
+selective H-matrix (leaf 32, eta_H 2, ACA 1e-6) and causal / spectral windows; the timed K steps are the first K
+steps of a fresh scenario (K = 2000 is the whole workload).  Prints one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+if "--impl" in sys.argv and "reference" in sys.argv:      # the oracle arm runs single-threaded on the host
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(var, "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2603_00383_gb300 import synth  # noqa: E402
+
+METRIC = "element-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="six_fault_3072")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 dense comparison run")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=48, help="oracle element-steps in the CPU baseline")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------ oracle sample --
+
+def oracle_sample(w, K, count, seed=11):
+    """(element, step) pairs of the CPU-baseline / reference sample: elements of fault 0 (whose spectral tables the
+    oracle builds once, untimed), steps spread over the run so the mean history depth is that of the workload."""
+    n0 = int(w.faults[0, 4])
+    k = np.arange(count)
+    elems = (k * 97 + seed) % n0
+    steps = (k * 7919 + 13 * seed) % K
+    return elems, steps
+
+
+class OracleStepper:
+    """Evaluates tau at single (element, step) pairs with the CPU oracle (interaction row + spectral self term of
+    fault 0 + radiation damping), with the workload's windows."""
+
+    def __init__(self, w, K, tables=None):
+        from oracle import seas_oracle as O
+        self.O = O
+        self.w = w
+        self.net = O.network(w.faults, w.mu, w.cs)
+        hp = w.hparams
+        self.V = w.slip_rate(0, 0, K)
+        self.delta = O.slip_from_rate(self.V, self.net.dt)
+        no_trunc = bool(hp.get("flags", 0) & 2)
+        _, _, self.last = O.pair_windows(self.net, hp["eta_tmin"], hp["eta_tmax"], hp["max_steps"], no_trunc)
+        n0 = int(self.net.n_elem[0])
+        if tables is None:
+            W0 = O.mode_windows(n0, self.net.length[0], self.net.dt, self.net.cs, hp["eta_w"], hp["q_w"],
+                                hp["max_steps"], no_trunc)
+            tables = O.SelfTables(n0, self.net.length[0], self.net.dt, self.net.cs, W0)
+        self.tab0 = tables
+        self.n0 = n0
+
+    def tau(self, i, n):
+        O = self.O
+        fi = O.interaction_rows(self.net, self.V, int(n), [int(i)], pair_hi=self.last)[0]
+        fs = O.self_rows(self.net, 0, self.delta[: n + 1, : self.n0], int(n), self.tab0, [int(i)])[0]
+        return -(self.w.mu / (2 * self.w.cs)) * self.V[n, i] + fs + fi
+
+
+_WORKER = None
+
+
+def _worker_init(name, K, tables):
+    global _WORKER
+    _WORKER = OracleStepper(synth.WORKLOADS[name](), K, tables)
+
+
+def _worker_tau(pair):
+    return _WORKER.tau(pair[0], pair[1])
+
+
+def run_reference(args, w, K, W):
+    """The oracle arm: each step evaluates one (element, step) sample of the workload on the host; the samples are
+    spread over the host cores by a spawn process pool (tables built once, shipped to the workers)."""
+    import multiprocessing as mp
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    cores = max(1, (os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    st = OracleStepper(w, K)
+    setup = time.perf_counter() - t0
+    elems, steps = oracle_sample(w, K, K + W)
+    pairs = list(zip(elems.tolist(), steps.tolist()))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_worker_init, initargs=(w.name, K, st.tab0)) as pool:
+        pool.map(_worker_tau, pairs[:max(W, cores)], chunksize=1)          # warm-up: every worker initialised
+        t0 = time.perf_counter()
+        pool.map(_worker_tau, pairs[W:], chunksize=4)
+        T = time.perf_counter() - t0
+    value = K / T
+    sample = (f"{K} oracle element-steps (one receiver of fault 0 at a step drawn uniformly from the {K}-step run, "
+              f"all lags of every source, NumPy FP64) over a {cores}-process spawn pool; spectral tables of fault 0 "
+              f"built once untimed ({setup:.1f} s)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * T / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, K),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+def config_of(w, K):
+    hp = w.hparams
+    return {"workload": w.name, "faults": w.n_faults, "elements": w.N, "steps": K, "batch": 1,
+            "leaf": hp["leaf"], "eta_h": hp["eta_h"], "aca_tol": hp["aca_tol"], "eta_tmax": hp["eta_tmax"],
+            "eta_w": hp["eta_w"], "q_w": "n_max" if hp["q_w"] <= 0 else hp["q_w"],
+            "parallelism": "replicas (independent scenarios per GPU)",
+            "l2": "operator larger than L2 (no flush between steps)"}
+
+
+# ---------------------------------------------------------------------------------------------------- GPU arm ------
+
+class Clocks:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        return dist, int(os.environ["RANK"]), world, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x, device):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def timed_run(seas, torch, s, Vd, K, dist, device, out_tau=None):
+    """K steps with device-resident inputs; per-step CUDA events on the library's stream."""
+    N = Vd.shape[1]
+    tau = out_tau if out_tau is not None else torch.zeros((K, N), dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    torch.cuda.synchronize(device)
+    start.record(stream)
+    for n in range(K):
+        ev[n][0].record(stream)
+        seas.seas_push_slip_rate(s.scn, Vd[n])
+        seas.seas_stress_step(s.scn, tau[n])
+        ev[n][1].record(stream)
+    stop.record(stream)
+    torch.cuda.synchronize(device)
+    barrier(dist)
+    total_ms = start.elapsed_time(stop)
+    per = np.array([a.elapsed_time(b) for a, b in ev])
+    return total_ms, per, tau
+
+
+def run_ours(args, w, K, W):
+    import torch
+    from paper_2603_00383_gb300 import seas
+    dist, rank, world, local = dist_setup(args)
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    stream = torch.cuda.current_stream(device)
+    wr = synth.six_fault_3072(steps=K) if w.name == "six_fault_3072" else w
+    wr.seed = synth.SEED + rank                          # independent scenario per rank
+    V = wr.slip_rate(0, 0, K)
+    Vd = torch.from_numpy(V).to(device)
+    peak, peak_kind = load_peaks()
+
+    s = seas.Session(wr, device=local, stream=stream.cuda_stream)
+    stats = s.stats
+    # warm-up on a scratch scenario, then a fresh one for the timed run
+    warm = seas.seas_scenario_create(s.op, 1)
+    tw = torch.zeros(wr.N, dtype=torch.float64, device=device)
+    for n in range(W):
+        seas.seas_push_slip_rate(warm, Vd[n % K])
+        seas.seas_stress_step(warm, tw)
+    torch.cuda.synchronize(device)
+    seas.seas_destroy_scn(warm)
+    seas.seas_scenario_set_timing(s.scn, True)
+    with Clocks(local) as clk:
+        total_ms, per, tau = timed_run(seas, torch, s, Vd, K, dist, device)
+    timing = seas.seas_scenario_get_timing(s.scn)
+    clocks = clk.summary()
+    total_ms = max_over_ranks(dist, total_ms, device)
+    value = wr.N * K * world / (total_ms / 1e3)
+
+    # plain FP64 GPU path: every fault pair one dense block, no compression, same windows
+    plain = None
+    if not args.no_plain:
+        p = seas.Session(wr, device=local, stream=stream.cuda_stream, flags=seas.SEAS_FLAG_DENSE, leaf=1024)
+        pm, pper, ptau = timed_run(seas, torch, p, Vd, K, dist, device)
+        pm = max_over_ranks(dist, pm, device)
+        pv = wr.N * K * world / (pm / 1e3)
+        diff = (ptau - tau).norm().item() / ptau.norm().item()
+        plain = {"value": pv, "unit": METRIC, "ms_per_step": pm / K, "p50_ms": float(np.percentile(pper, 50)),
+                 "p99_ms": float(np.percentile(pper, 99)), "speedup": value / pv,
+                 "bytes_interaction": p.stats["bytes_interaction"], "rel_l2_tau_vs_hmatrix": diff}
+        p.close()
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        s2 = seas.seas_scenario_create(s.op, 1)
+        Vh = torch.from_numpy(V).pin_memory().numpy()
+        th = torch.zeros(wr.N, dtype=torch.float64).pin_memory().numpy()
+        barrier(dist)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        for n in range(K):
+            seas.seas_push_slip_rate(s2, Vh[n])
+            seas.seas_stress_step(s2, th)
+        torch.cuda.synchronize(device)
+        barrier(dist)
+        e2e_s = max_over_ranks(dist, time.perf_counter() - t0, device)
+        seas.seas_destroy_scn(s2)
+        e2e = {"value": wr.N * K * world / e2e_s, "unit": METRIC, "h2d_bytes_per_step": wr.N * 8,
+               "d2h_bytes_per_step": wr.N * 8}
+
+    # roofline of the dominant kernel (the interaction): algorithmic bytes / live event time
+    ms = timing["ms"]
+    dominant = max(ms, key=ms.get)
+    inter_ms = ms["interaction"]
+    launches = timing["launches"]
+    achieved = timing["interaction_bytes"] / (inter_ms / 1e3) / 1e9 if inter_ms > 0 else 0.0
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "interaction_traffic.json")
+    if os.path.exists(tf):
+        with open(tf) as fh:
+            tr = json.load(fh)
+        if tr.get("kernel_version") == seas_kernel_version():
+            traffic = tr.get("dram_bytes_per_launch")
+    n_launch = launches["interaction"]
+    roofline = {"bound": "hbm", "kernel": "k_interaction", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": traffic, "algorithmic_bytes_per_launch": timing["interaction_bytes"] / max(1, n_launch),
+                "mean_launch_ms": inter_ms / max(1, n_launch), "dominant_by_time": dominant,
+                "kernel_ms": ms}
+
+    line = None
+    if rank == 0:
+        tau_h = tau.cpu().numpy()
+        cpu = None
+        err = None
+        if args.cpu_sample > 0:
+            st = OracleStepper(wr, K)
+            elems, steps = oracle_sample(wr, K, args.cpu_sample)
+            t0 = time.perf_counter()
+            ref = np.array([st.tau(i, n) for i, n in zip(elems, steps)])
+            T = time.perf_counter() - t0
+            got = tau_h[steps, elems]
+            err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            cpu = {"value": args.cpu_sample / T, "unit": METRIC, "cores": 1, "kind": "oracle",
+                   "sample": f"{args.cpu_sample} element-steps (receivers of fault 0 at steps spread over the run, "
+                             f"all lags of all sources, NumPy FP64), {T:.1f} s"}
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": total_ms / K, "p50_ms": float(np.percentile(per, 50)),
+                "p99_ms": float(np.percentile(per, 99)), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(wr, K),
+                "rel_l2_vs_oracle": err, "operator": {k: stats[k] for k in (
+                    "n_blocks_far", "n_blocks_near", "compression_ratio", "bytes_interaction", "mean_rank",
+                    "max_rank", "build_seconds", "n_tasks")},
+                "vs_plain_fp64_gpu": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+                "clocks": clocks, "gpu_launches": int(sum(launches.values()))}
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
+def seas_kernel_version():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("seas_step.cu", "seas_internal.h"):
+        with open(os.path.join(ROOT, "paper_2603_00383_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    args = parse()
+    w = synth.WORKLOADS[args.workload]()
+    K = args.steps if args.steps is not None else w.steps
+    W = max(3, args.warmup)
+    if args.impl == "reference":
+        line = run_reference(args, w, K, W)
+    else:
+        from paper_2603_00383_gb300 import build
+        build.build()
+        line = run_ours(args, w, K, W)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

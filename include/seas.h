@@ -1,0 +1,203 @@
+/*
+ * seas.h -- C ABI of the GB300 engine for the per-time-step elastodynamic stress-transfer functional of
+ * Ciardo & Romanet, "A divide-and-conquer strategy for fast elastodynamic simulation of earthquakes and aseismic
+ * slip on fault networks" (arXiv 2603.00383), anti-plane (mode III) setting.
+ *
+ * At step n (t_n = n dt) the library returns, for every element i of a network of planar faults,
+ *
+ *     tau_i^n = -(mu / 2 c_s) V_i^n  +  f_self,i^n  +  f_int,i^n                           (Eq. superimposition2)
+ *
+ *   * f_self: the non-replicating spectral self effect of the element's own fault (Sec. 2.3.1): slip zero-padded
+ *     to a 2 L_f domain, D_n = FFT, F_n = -(mu k_n / 2) sum_{T=0}^{W_f(n)} w_n^T D_n^{t-T}
+ *     (Eq. funcational_discretized_form, Eq. mode_dependent_truncation), then the inverse FFT;
+ *   * f_int: the fault-to-fault space-time convolution f_i = -(mu/2c_s) n_l^i sum_j sum_T K_3l^{ijT} V_j^{t-T}
+ *     (Eq. fault-to-fault_interactions_discretized) with kernels from the primitives of Eq. (primitives) and
+ *     Eq. (kernel_interactions), evaluated through a selective H-matrix stack (Sec. 2.3.2): one binary cluster
+ *     tree per fault, self blocks excluded, dual-tree traversal with the admissibility test of
+ *     Eq. (admissibility_condition), low-rank far blocks (adaptive cross approximation), dense near blocks, and
+ *     causal windows per block (exact first nonzero lag; end at (1 + eta_Tmax) T_max, Sec. 2.3.2).
+ *   * the elastodynamic normal-stress change is identically zero in mode III (Sec. 2.1).
+ *
+ * Conventions
+ *   * Fault f: centre (cx, cy), strike phi, e'_1 = (cos phi, sin phi), normal n = e'_2 = (sin phi, -cos phi)
+ *     (e'_1 = e'_3 x e'_2, Sec. 3.1).  Element j (0-based) of fault f has centroid c + (-L/2 + (j + 1/2) ds) e'_1,
+ *     ds = L / N_f.  Elements are numbered fault after fault in the order given.
+ *   * dt = beta * min_f ds_f / c_s (Sec. 2.3.1, Sec. 3.1; beta = 1/2 in the paper).
+ *   * Push n (n = 0, 1, ...) supplies V^n, the slip rate on (t_{n-1}, t_n]; slip delta^n = delta^{n-1} + dt V^n
+ *     (delta^{-1} = 0) unless the caller passes delta^n.  seas_stress_step after push n returns tau at t_n,
+ *     including lag 0 (the instantaneous part).
+ *   * Vectors are [batch][N] row-major float64 (scenario-major), N = total number of elements.
+ *
+ * Ownership and errors
+ *   * The library owns every buffer it allocates; handles are freed child first (destroying a parent with live
+ *     children returns SEAS_EBUSY).  The caller owns V / slip / tau buffers.
+ *   * Device work is asynchronous on the context's stream; host outputs (mem = SEAS_MEM_HOST) are complete when
+ *     the call returns, device outputs after seas_sync() or any later stream-ordered operation.
+ *   * Every call returns a status (< 0 on error) and never aborts or exits.  A failed call leaves its handles
+ *     usable unless it returned SEAS_ECUDA (a CUDA error; the context should then be destroyed).
+ *   * Thread safety: one context per host thread; handles of one context must not be used concurrently.
+ */
+#ifndef SEAS_H
+#define SEAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int seas_status;
+
+#define SEAS_OK 0
+#define SEAS_EINVAL (-1)       /* bad argument or geometry (non-finite input, size limits, touching faults) */
+#define SEAS_ENOMEM (-2)       /* device allocation failed or the context's HBM budget would be exceeded */
+#define SEAS_ECUDA (-3)        /* a CUDA runtime error; the message is in seas_last_error() */
+#define SEAS_ESTATE (-4)       /* call out of order: stress_step before a push, push past max_steps, ... */
+#define SEAS_EBUSY (-5)        /* destroying a handle that still has live children */
+#define SEAS_ETIMEOUT (-6)     /* a bounded device wait ran out */
+#define SEAS_EIO (-7)          /* checkpoint file could not be written / read or is malformed */
+
+#define SEAS_MEM_HOST 0
+#define SEAS_MEM_DEVICE 1
+
+/* operator flags */
+#define SEAS_FLAG_DENSE 1        /* admissibility never satisfied: every block dense (the plain space-time sum) */
+#define SEAS_FLAG_NO_TRUNC 2     /* no causal end truncation; full-length spectral windows (exact operator) */
+#define SEAS_FLAG_STATIC_TAIL 4  /* reserved: elastostatic response of truncated history (not implemented) */
+
+/* storage precision of the interaction operator */
+#define SEAS_PREC_FP64 0
+
+typedef struct seas_ctx seas_ctx;
+typedef struct seas_net seas_net;
+typedef struct seas_op seas_op;
+typedef struct seas_scn seas_scn;
+
+/* One planar fault: centre (m), strike phi (rad), length L (m), number of elements N_f (>= 1). */
+typedef struct {
+    double cx, cy, strike_rad, length;
+    int32_t n_elem;
+    int32_t reserved;
+} seas_fault;
+
+/* Homogeneous medium: shear modulus mu (Pa), shear speed c_s (m/s), P speed c_p (recorded; unused in mode III),
+ * and beta in dt = beta * min ds / c_s (the paper uses 1/2). */
+typedef struct {
+    double mu, cs, cp, beta;
+} seas_medium;
+
+/* Operator parameters (Table 1 names): leaf = eta_leaf (max elements in a leaf cluster), eta_h = eta_H of
+ * Eq. (admissibility_condition), aca_tol = relative Frobenius tolerance per (block, lag) slice (the paper's
+ * eps_SVD with ACA in place of SVD), eta_tmin (reported only: windows start at the exact first nonzero lag),
+ * eta_tmax, eta_w, q_w (<= 0: q_w = N_f, i.e. no mode-dependent shortening), max_steps = largest number of pushes
+ * the operator serves (lags 0 .. max_steps - 1), precision = SEAS_PREC_*, flags = SEAS_FLAG_*. */
+typedef struct {
+    int32_t leaf;
+    int32_t q_w;
+    double eta_h, aca_tol, eta_tmin, eta_tmax, eta_w;
+    int32_t max_steps;
+    int32_t precision;
+    int32_t flags;
+    int32_t max_block;   /* largest cluster side of an admissible block (0: 1024) */
+} seas_hparams;
+
+typedef struct {
+    double dt;
+    int32_t n_faults;
+    int32_t n_elem;      /* N */
+} seas_net_info;
+
+typedef struct {
+    int64_t n_blocks_near, n_blocks_far;
+    int64_t n_slices_dense, n_slices_lowrank, n_slices_zero;
+    int64_t bytes_interaction;      /* stored interaction operator (all lags) */
+    int64_t bytes_dense_causal;     /* the same slices stored dense (rank-0 slices excluded) */
+    double compression_ratio;       /* bytes_interaction / bytes_dense_causal, in percent */
+    int64_t bytes_self;             /* spectral weight tables */
+    int32_t max_rank;
+    int32_t ring_depth;             /* slip-rate history slots kept per scenario */
+    double mean_rank;
+    double build_seconds;
+    int64_t n_tasks;                /* interaction work units */
+} seas_op_stats;
+
+/* Creates a context on CUDA device `device`.  hbm_budget: bytes the library may allocate (0: no limit).
+ * cuda_stream: a cudaStream_t the library issues all work on (NULL: the library creates and owns one). */
+seas_status seas_create(seas_ctx **ctx, int device, size_t hbm_budget, void *cuda_stream);
+
+/* Builds the discretised network (Sec. 2.3.1 "Discretization", Sec. 3.1 frames).  Rejects non-finite or
+ * non-positive sizes, N_f whose 2,3,5-free part is not 1, N_f > 7168, and receiver centroids lying on another
+ * fault (within 1e-6 ds of one of its elements, where the kernel is singular). */
+seas_status seas_build_network(seas_ctx *ctx, const seas_fault *faults, int n_faults, const seas_medium *medium,
+                               seas_net **net);
+seas_status seas_net_get_info(const seas_net *net, seas_net_info *info);
+/* Element centroids [N][2] and normals [N][2] (host buffers of the caller). */
+seas_status seas_net_get_elements(const seas_net *net, double *centroids, double *normals);
+
+/* Builds the selective H-matrix stack and the spectral tables on the device (Sec. 2.3.1, Sec. 2.3.2).
+ * stats may be NULL. */
+seas_status seas_build_hmatrix(seas_net *net, const seas_hparams *hp, seas_op **op, seas_op_stats *stats);
+/* Per ordered fault pair (receiver a, source b): last lag of the window, [F][F] int32, -1 on the diagonal. */
+seas_status seas_op_pair_windows(const seas_op *op, int32_t *last_lag);
+/* Per fault f and mode n = 0..N_f: last lag W_f(n) of the spectral window (flattened fault after fault). */
+seas_status seas_op_mode_windows(const seas_op *op, int32_t *w);
+
+/* Allocates the history ring buffers of `batch` independent scenarios sharing the operator. */
+seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **scn);
+
+/* Pushes V^n ([batch][N] float64) and optionally delta^n (same layout; NULL: integrate).  mem: where V and slip
+ * live.  replace_last != 0 overwrites the previous push instead (the corrector of Sec. 2.4 step 3).
+ * SEAS_ESTATE after max_steps pushes.  Host inputs are checked for finiteness (SEAS_EINVAL). */
+seas_status seas_push_slip_rate(seas_scn *scn, const double *V, const double *slip, int mem, int replace_last);
+
+/* tau at the last pushed step into tau ([batch][N]); sigma_n (nullable) receives zeros; parts (nullable,
+ * [3][batch][N]) receives radiation damping, f_self and f_int separately. */
+seas_status seas_stress_step(seas_scn *scn, double *tau, double *sigma_n, double *parts, int mem);
+
+/* Number of pushes so far. */
+seas_status seas_scenario_step(const seas_scn *scn, int64_t *n);
+
+seas_status seas_sync(seas_ctx *ctx);
+const char *seas_strerror(seas_status s);
+/* Thread-local description of the last error of this thread (empty when none). */
+const char *seas_last_error(void);
+
+/* Host-only planning (no device work): the block partition, windows and time step the operator build would use.
+ * blocks (nullable): [cap][6] int32 rows (r0, p, c0, q, far, first_lag) -- receiver rows [r0, r0 + p), source
+ * columns [c0, c0 + q), far = 1 for an admissible (low-rank) block, first_lag = conservative first nonzero lag;
+ * *n_blocks receives the total count even when it exceeds cap.  pair_last (nullable): [F][F] last lags.
+ * mode_windows (nullable): W_f(n), n = 0..N_f, fault after fault.  dt (nullable). */
+seas_status seas_plan_hmatrix(const seas_fault *faults, int n_faults, const seas_medium *medium,
+                              const seas_hparams *hp, int32_t *blocks, int64_t cap, int64_t *n_blocks,
+                              int32_t *pair_last, int32_t *mode_windows, double *dt);
+
+/* Kernel timing on the context stream (tracing).  set_timing(1) resets and starts recording a CUDA event pair
+ * around every kernel the scenario launches; get_timing synchronises and returns, per kernel class (0 push,
+ * 1 forward FFT, 2 mode convolution, 3 interaction, 4 inverse FFT + assembly), the launch count and the summed
+ * device time, plus the algorithmic bytes the interaction kernel streamed (stored operator slices with
+ * lag <= step, summed over the timed steps). */
+typedef struct {
+    int64_t launches[5];
+    double ms[5];
+    int64_t interaction_bytes;
+    int64_t steps;
+} seas_timing;
+seas_status seas_scenario_set_timing(seas_scn *scn, int enable);
+seas_status seas_scenario_get_timing(seas_scn *scn, seas_timing *out);
+/* Stored interaction-operator bytes that step `step` reads (slices with lag <= step). */
+seas_status seas_op_step_bytes(const seas_op *op, int64_t step, int64_t *bytes);
+
+/* Checkpoint/resume of a scenario: the step counter, slip-rate ring, slip and spectral ring. */
+seas_status seas_scenario_save(seas_scn *scn, const char *path);
+seas_status seas_scenario_load(seas_op *op, const char *path, seas_scn **scn);
+
+seas_status seas_destroy_scn(seas_scn *scn);
+seas_status seas_destroy_op(seas_op *op);
+seas_status seas_destroy_net(seas_net *net);
+seas_status seas_destroy_ctx(seas_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEAS_H */

@@ -131,10 +131,11 @@ def kernel_K3l(r1, r2, T, dt, ds, cs):
     return out[0], out[1]
 
 
-def interaction_slice(net: Network, T: int, rows=None, cols=None, dtype=np.float64) -> np.ndarray:
+def interaction_slice(net: Network, T, rows=None, cols=None, dtype=np.float64) -> np.ndarray:
     """A_ij^T = n'_1 K_31 + n'_2 K_32 for receivers ``rows`` and sources ``cols`` (default: all).  (r1, r2) are the
     receiver's coordinates in the source element's frame, n' the receiver normal in that frame (Eq.
-    fault-to-fault_interactions_discretized).  Same-fault entries are zero: self effects are spectral (Sec. 2.3.2)."""
+    fault-to-fault_interactions_discretized).  Same-fault entries are zero: self effects are spectral (Sec. 2.3.2).
+    T may be a 1-D array of lags; the result then has a leading lag axis."""
     rows = np.arange(net.N) if rows is None else np.asarray(rows)
     cols = np.arange(net.N) if cols is None else np.asarray(cols)
     x = net.x.astype(dtype)
@@ -147,7 +148,9 @@ def interaction_slice(net: Network, T: int, rows=None, cols=None, dtype=np.float
     n1 = (nr * e1).sum(-1)
     n2 = (nr * e2).sum(-1)
     cs = dtype(net.cs)
-    k31, k32 = kernel_K3l(r1, r2, dtype(T), dtype(net.dt), net.ds[cols].astype(dtype)[None, :], cs)
+    Ta = np.asarray(T)
+    Tb = Ta.astype(dtype)[:, None, None] if Ta.ndim == 1 else dtype(Ta)
+    k31, k32 = kernel_K3l(r1, r2, Tb, dtype(net.dt), net.ds[cols].astype(dtype)[None, :], cs)
     A = n1 * k31 + n2 * k32
     same = net.fault_of[rows][:, None] == net.fault_of[cols][None, :]
     return np.where(same, dtype(0), A)
@@ -170,19 +173,18 @@ def interaction_history(net: Network, V: np.ndarray, pair_hi=None, dtype=np.floa
     return -(dtype(net.mu) / (2 * dtype(net.cs))) * out
 
 
-def interaction_rows(net: Network, V: np.ndarray, n: int, rows, pair_hi=None, chunk: int = 64) -> np.ndarray:
+def interaction_rows(net: Network, V: np.ndarray, n: int, rows, pair_hi=None, chunk: int = 128) -> np.ndarray:
     """f_int^n at receiver ``rows`` only, for one step n, from the slip-rate history V[0..n][N]."""
     rows = np.asarray(rows)
     acc = np.zeros(rows.shape[0])
     fo = net.fault_of
+    hi = None if pair_hi is None else np.asarray(pair_hi)[fo[rows]][:, fo]
     for T0 in range(0, n + 1, chunk):
-        Ts = range(T0, min(n + 1, T0 + chunk))
-        for T in Ts:
-            A = interaction_slice(net, T, rows=rows)
-            if pair_hi is not None:
-                hi = np.asarray(pair_hi)[fo[rows]][:, fo]
-                A = np.where(T <= hi, A, 0.0)
-            acc += A @ V[n - T]
+        Ts = np.arange(T0, min(n + 1, T0 + chunk))
+        A = interaction_slice(net, Ts, rows=rows)               # [lags, rows, N]
+        if hi is not None:
+            A = np.where(Ts[:, None, None] <= hi[None], A, 0.0)
+        acc += np.einsum("tij,tj->i", A, V[n - Ts])
     return -(net.mu / (2 * net.cs)) * acc
 
 

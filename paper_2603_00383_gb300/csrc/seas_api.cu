@@ -1,0 +1,1266 @@
+// Host side of the C ABI (include/seas.h): handles, validation, network geometry, fault-wise cluster trees and the
+// dual-tree traversal of the selective H-matrix (Sec. 2.3.2), causal windows, the device build of the operator, and
+// the per-step call sequence.
+#include "seas.h"
+#include "seas_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+using namespace seas;
+
+namespace {
+
+thread_local std::string g_err;
+
+seas_status fail(seas_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            cudaGetLastError();                                                               \
+            return fail(SEAS_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));          \
+        }                                                                                     \
+    } while (0)
+
+#define SEAS_TRY(expr)                 \
+    do {                               \
+        seas_status s_ = (expr);       \
+        if (s_ != SEAS_OK) return s_;  \
+    } while (0)
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr int64_t kItemBytes = 64 * 1024;     // target size of one work item
+constexpr int64_t kTaskBytes = 256 * 1024;    // target size of one task (one flush of partial sums)
+constexpr int64_t kChunkEntries = 48 << 20;   // kernel entries materialised per build chunk
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------------------
+// handles
+// ------------------------------------------------------------------------------------------------------------
+
+struct seas_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;
+    size_t used = 0;
+    int children = 0;
+};
+
+namespace {
+
+seas_status dev_alloc(seas_ctx *c, size_t bytes, void **p) {
+    *p = nullptr;
+    if (bytes == 0) return SEAS_OK;
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(SEAS_ENOMEM, "allocation of %zu bytes exceeds the HBM budget (%zu of %zu used)", bytes, c->used,
+                    c->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(SEAS_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    c->used += bytes;
+    return SEAS_OK;
+}
+
+void dev_free(seas_ctx *c, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    c->used -= bytes;
+}
+
+// Device array owned by a context.
+template <class T>
+struct DArr {
+    seas_ctx *ctx = nullptr;
+    T *p = nullptr;
+    size_t n = 0;
+    DArr() = default;
+    DArr(const DArr &) = delete;
+    DArr &operator=(const DArr &) = delete;
+    ~DArr() { release(); }
+    seas_status alloc(seas_ctx *c, size_t count) {
+        release();
+        ctx = c;
+        void *q = nullptr;
+        SEAS_TRY(dev_alloc(c, count * sizeof(T), &q));
+        p = static_cast<T *>(q);
+        n = count;
+        return SEAS_OK;
+    }
+    seas_status upload(seas_ctx *c, const std::vector<T> &v) {
+        SEAS_TRY(alloc(c, v.size()));
+        if (!v.empty()) CUDA_TRY(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return SEAS_OK;
+    }
+    seas_status zero(cudaStream_t s) {
+        if (n) CUDA_TRY(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+        return SEAS_OK;
+    }
+    void release() {
+        if (p && ctx) dev_free(ctx, p, n * sizeof(T));
+        p = nullptr;
+        n = 0;
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// Pinned host buffer.
+struct HostBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~HostBuf() {
+        if (p) cudaFreeHost(p);
+    }
+    seas_status alloc(size_t b) {
+        if (b == 0) return SEAS_OK;
+        CUDA_TRY(cudaMallocHost(&p, b));
+        bytes = b;
+        return SEAS_OK;
+    }
+};
+
+bool is_235_smooth(int n) {
+    if (n < 1) return false;
+    for (int f : {2, 3, 5})
+        while (n % f == 0) n /= f;
+    return n == 1;
+}
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+}  // namespace
+
+struct seas_net {
+    seas_ctx *ctx = nullptr;
+    std::vector<seas_fault> faults;
+    seas_medium med{};
+    double dt = 0.0;
+    int N = 0, F = 0;
+    std::vector<int> off;                       // F + 1
+    std::vector<double> x, y, e1x, e1y, nx, ny, ds;
+    std::vector<int> fault_of;
+    DArr<double2> d_x, d_e1, d_n;
+    DArr<double> d_ds;
+    int children = 0;
+};
+
+struct StoredSlice {                 // one nonzero (block, lag) slice of the operator
+    int32_t block, T, k;             // k < 0 dense, k > 0 rank
+    const double *data;
+};
+
+struct seas_op {
+    seas_net *net = nullptr;
+    seas_hparams hp{};
+    int children = 0;
+    // spectral self effect
+    std::vector<FaultDev> faults_h;
+    std::vector<ModeDev> modes_h;
+    std::vector<int32_t> mode_W;     // per fault, modes 0..N_f
+    DArr<FaultDev> d_faults;
+    DArr<ModeDev> d_modes;
+    DArr<double> d_w;
+    DArr<double2> d_tw;
+    int n_modes_total = 0, max_nf = 0;
+    // space-time interaction
+    std::vector<BlockDev> blocks_h;
+    std::vector<int32_t> block_far, block_pair;
+    DArr<BlockDev> d_blocks;
+    std::vector<std::unique_ptr<DArr<double>>> arena;
+    DArr<ItemDev> d_items;
+    DArr<TaskDev> d_tasks;
+    std::vector<int32_t> task_T;     // T_start of each task (ascending)
+    std::vector<int32_t> pair_last;  // [F][F]
+    std::vector<int64_t> bytes_upto; // stored interaction bytes with lag <= T
+    int ring = 1;
+    seas_op_stats stats{};
+};
+
+struct seas_scn {
+    seas_op *op = nullptr;
+    int B = 0;
+    int64_t n = 0;                   // pushes so far
+    DArr<double> vring, slip, slip_prev, fint, d_V, d_slip, d_tau, d_parts;
+    DArr<double2> dring, fmodes;
+    DArr<FaultDev> faults;           // fault table with spectral-ring offsets for this batch size
+    int64_t dring_len = 0;
+    HostBuf h_in, h_out;
+    // kernel timing (seas_scenario_set_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;     // pairs (start, stop)
+    std::vector<int> ev_class;
+    size_t ev_used = 0;
+    seas_timing acc{};
+    ~seas_scn() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
+// ------------------------------------------------------------------------------------------------------------
+// context
+// ------------------------------------------------------------------------------------------------------------
+
+extern "C" seas_status seas_create(seas_ctx **out, int device, size_t hbm_budget, void *cuda_stream) {
+    if (!out) return fail(SEAS_EINVAL, "ctx pointer is NULL");
+    *out = nullptr;
+    int count = 0;
+    CUDA_TRY(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) return fail(SEAS_EINVAL, "device %d out of range (%d devices)", device, count);
+    CUDA_TRY(cudaSetDevice(device));
+    auto c = std::make_unique<seas_ctx>();
+    c->device = device;
+    c->budget = hbm_budget;
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    *out = c.release();
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_sync(seas_ctx *c) {
+    if (!c) return fail(SEAS_EINVAL, "ctx is NULL");
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_destroy_ctx(seas_ctx *c) {
+    if (!c) return SEAS_OK;
+    if (c->children) return fail(SEAS_EBUSY, "context has %d live networks", c->children);
+    cudaSetDevice(c->device);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return SEAS_OK;
+}
+
+extern "C" const char *seas_strerror(seas_status s) {
+    switch (s) {
+        case SEAS_OK: return "ok";
+        case SEAS_EINVAL: return "invalid argument";
+        case SEAS_ENOMEM: return "out of device memory or over the HBM budget";
+        case SEAS_ECUDA: return "CUDA error";
+        case SEAS_ESTATE: return "call out of order";
+        case SEAS_EBUSY: return "handle has live children";
+        case SEAS_ETIMEOUT: return "device wait timed out";
+        case SEAS_EIO: return "checkpoint I/O error";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char *seas_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------------------------------------------------
+// network (Sec. 3.1 frames, Sec. 2.3.1 discretisation)
+// ------------------------------------------------------------------------------------------------------------
+
+namespace {
+
+double seg_point_dist(double px, double py, double ax, double ay, double bx, double by) {
+    const double ux = bx - ax, uy = by - ay;
+    const double L2 = ux * ux + uy * uy;
+    double t = L2 > 0 ? ((px - ax) * ux + (py - ay) * uy) / L2 : 0.0;
+    t = std::min(1.0, std::max(0.0, t));
+    return std::hypot(ax + t * ux - px, ay + t * uy - py);
+}
+
+}  // namespace
+
+namespace {
+
+// Host geometry of a network (validation, centroids, frames, dt); no device work.
+seas_status make_geometry(const seas_fault *faults, int n_faults, const seas_medium *med, seas_net &net) {
+    if (!faults || !med) return fail(SEAS_EINVAL, "NULL argument");
+    if (n_faults < 1) return fail(SEAS_EINVAL, "n_faults must be >= 1");
+    if (!(is_fin(med->mu) && med->mu > 0 && is_fin(med->cs) && med->cs > 0 && is_fin(med->beta) && med->beta > 0 &&
+          is_fin(med->cp)))
+        return fail(SEAS_EINVAL, "medium: mu, cs, beta must be finite and > 0");
+    int64_t N = 0;
+    for (int f = 0; f < n_faults; ++f) {
+        const seas_fault &F = faults[f];
+        if (!(is_fin(F.cx) && is_fin(F.cy) && is_fin(F.strike_rad) && is_fin(F.length) && F.length > 0))
+            return fail(SEAS_EINVAL, "fault %d: non-finite or non-positive geometry", f);
+        if (F.n_elem < 1 || F.n_elem > kMaxFFT)
+            return fail(SEAS_EINVAL, "fault %d: n_elem %d outside [1, %d]", f, F.n_elem, kMaxFFT);
+        if (!is_235_smooth(F.n_elem))
+            return fail(SEAS_EINVAL, "fault %d: n_elem %d has a prime factor > 5 (FFT radices are 2, 3, 5)", f,
+                        F.n_elem);
+        N += F.n_elem;
+    }
+    if (N > (1 << 24)) return fail(SEAS_EINVAL, "too many elements (%lld)", (long long)N);
+    net.faults.assign(faults, faults + n_faults);
+    net.med = *med;
+    net.F = n_faults;
+    net.N = (int)N;
+    net.off.assign(n_faults + 1, 0);
+    double min_ds = INFINITY;
+    for (int f = 0; f < n_faults; ++f) {
+        const seas_fault &F = faults[f];
+        const double ds = F.length / F.n_elem;
+        min_ds = std::min(min_ds, ds);
+        const double c1 = std::cos(F.strike_rad), s1 = std::sin(F.strike_rad);
+        for (int j = 0; j < F.n_elem; ++j) {
+            const double s = -0.5 * F.length + (j + 0.5) * ds;
+            net.x.push_back(F.cx + s * c1);
+            net.y.push_back(F.cy + s * s1);
+            net.e1x.push_back(c1);
+            net.e1y.push_back(s1);
+            net.nx.push_back(s1);
+            net.ny.push_back(-c1);
+            net.ds.push_back(ds);
+            net.fault_of.push_back(f);
+        }
+        net.off[f + 1] = net.off[f] + F.n_elem;
+    }
+    net.dt = med->beta * min_ds / med->cs;
+    // A receiver centroid on (or numerically at) another fault's element makes the kernel singular.
+    for (int a = 0; a < n_faults; ++a) {
+        for (int b = 0; b < n_faults; ++b) {
+            if (a == b) continue;
+            const seas_fault &Fb = faults[b];
+            const double hx = 0.5 * Fb.length * std::cos(Fb.strike_rad), hy = 0.5 * Fb.length * std::sin(Fb.strike_rad);
+            const double dsb = Fb.length / Fb.n_elem;
+            for (int i = net.off[a]; i < net.off[a + 1]; ++i) {
+                const double d = seg_point_dist(net.x[i], net.y[i], Fb.cx - hx, Fb.cy - hy, Fb.cx + hx, Fb.cy + hy);
+                if (d < 1e-6 * dsb)
+                    return fail(SEAS_EINVAL, "element %d of fault %d lies on fault %d (distance %g m)", i - net.off[a],
+                                a, b, d);
+            }
+        }
+    }
+    return SEAS_OK;
+}
+
+}  // namespace
+
+extern "C" seas_status seas_build_network(seas_ctx *c, const seas_fault *faults, int n_faults,
+                                          const seas_medium *med, seas_net **out) {
+    if (!c || !out) return fail(SEAS_EINVAL, "NULL argument");
+    *out = nullptr;
+    auto net = std::make_unique<seas_net>();
+    SEAS_TRY(make_geometry(faults, n_faults, med, *net));
+    CUDA_TRY(cudaSetDevice(c->device));
+    net->ctx = c;
+    const int64_t N = net->N;
+    std::vector<double2> hx(N), he(N), hn(N);
+    for (int64_t i = 0; i < N; ++i) {
+        hx[i] = make_double2(net->x[i], net->y[i]);
+        he[i] = make_double2(net->e1x[i], net->e1y[i]);
+        hn[i] = make_double2(net->nx[i], net->ny[i]);
+    }
+    SEAS_TRY(net->d_x.upload(c, hx));
+    SEAS_TRY(net->d_e1.upload(c, he));
+    SEAS_TRY(net->d_n.upload(c, hn));
+    SEAS_TRY(net->d_ds.upload(c, net->ds));
+    c->children++;
+    *out = net.release();
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_net_get_info(const seas_net *net, seas_net_info *info) {
+    if (!net || !info) return fail(SEAS_EINVAL, "NULL argument");
+    info->dt = net->dt;
+    info->n_faults = net->F;
+    info->n_elem = net->N;
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_net_get_elements(const seas_net *net, double *centroids, double *normals) {
+    if (!net) return fail(SEAS_EINVAL, "NULL network");
+    for (int i = 0; i < net->N; ++i) {
+        if (centroids) {
+            centroids[2 * i] = net->x[i];
+            centroids[2 * i + 1] = net->y[i];
+        }
+        if (normals) {
+            normals[2 * i] = net->nx[i];
+            normals[2 * i + 1] = net->ny[i];
+        }
+    }
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_destroy_net(seas_net *net) {
+    if (!net) return SEAS_OK;
+    if (net->children) return fail(SEAS_EBUSY, "network has %d live operators", net->children);
+    cudaSetDevice(net->ctx->device);
+    net->ctx->children--;
+    delete net;
+    return SEAS_OK;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// operator build
+// ------------------------------------------------------------------------------------------------------------
+
+namespace {
+
+// Cluster of one fault-wise binary tree (Sec. 2.3.2): elements [a, b), bounding circle of centre c (mean of
+// the centroids) and radius max ||x - c|| + ds / 2.
+struct Cluster {
+    int a, b;
+    double cx, cy, r;
+    int left = -1, right = -1;
+    bool leaf() const { return left < 0; }
+};
+
+int build_tree(const seas_net &net, int f, int lo, int hi, int leaf, std::vector<Cluster> &t) {
+    Cluster c;
+    c.a = lo;
+    c.b = hi;
+    double sx = 0, sy = 0;
+    for (int i = lo; i < hi; ++i) {
+        sx += net.x[i];
+        sy += net.y[i];
+    }
+    c.cx = sx / (hi - lo);
+    c.cy = sy / (hi - lo);
+    double r = 0;
+    for (int i = lo; i < hi; ++i) r = std::max(r, std::hypot(net.x[i] - c.cx, net.y[i] - c.cy) + 0.5 * net.ds[i]);
+    c.r = r;
+    const int idx = (int)t.size();
+    t.push_back(c);
+    if (hi - lo > leaf) {
+        const int mid = lo + (hi - lo + 1) / 2;     // odd counts: the left child takes the extra element
+        const int l = build_tree(net, f, lo, mid, leaf, t);
+        const int rr = build_tree(net, f, mid, hi, leaf, t);
+        t[idx].left = l;
+        t[idx].right = rr;
+    }
+    return idx;
+}
+
+// Dual-tree traversal (Sec. 2.3.2): admissible pairs become far blocks; inadmissible leaf pairs near blocks;
+// otherwise the cluster with the larger radius is split (the other one if it is a leaf; the receiver on a tie).
+void traverse(const std::vector<Cluster> &ta, const std::vector<Cluster> &tb, double eta, bool dense, int max_block,
+              int pair, std::vector<BlockDev> &blocks, std::vector<int32_t> &far, std::vector<int32_t> &pairs) {
+    std::vector<std::pair<int, int>> st{{0, 0}};
+    while (!st.empty()) {
+        auto [i, j] = st.back();
+        st.pop_back();
+        const Cluster &A = ta[i], &B = tb[j];
+        const int p = A.b - A.a, q = B.b - B.a;
+        const double d = std::hypot(A.cx - B.cx, A.cy - B.cy);
+        const bool adm = !dense && d > eta * (A.r + B.r) && p <= max_block && q <= max_block;
+        if (adm || (A.leaf() && B.leaf())) {
+            blocks.push_back(BlockDev{A.a, p, B.a, q});
+            far.push_back(adm ? 1 : 0);
+            pairs.push_back(pair);
+            continue;
+        }
+        bool split_recv;
+        if (A.leaf()) split_recv = false;
+        else if (B.leaf()) split_recv = true;
+        else if (std::fabs(A.r - B.r) <= 1e-12 * std::max(A.r, B.r)) split_recv = true;
+        else split_recv = A.r > B.r;
+        if (split_recv) {
+            st.push_back({A.right, j});
+            st.push_back({A.left, j});
+        } else {
+            st.push_back({i, B.right});
+            st.push_back({i, B.left});
+        }
+    }
+}
+
+// Points of one fault pair (receiver a, source b): last lag of the window.  T_max is the largest distance from the
+// far ends of the source elements to the two receiver-fault endpoints over c_s; T_end = (1 + eta_Tmax) T_max
+// (Sec. 2.3.2); last lag = ceil(T_end / dt - 1e-9), at most max_steps - 1.
+int32_t pair_last_lag(const seas_net &net, int a, int b, double eta_tmax, int max_steps, bool no_trunc) {
+    if (no_trunc) return max_steps - 1;
+    const seas_fault &Fa = net.faults[a];
+    const double c1 = std::cos(Fa.strike_rad), s1 = std::sin(Fa.strike_rad);
+    const double h = 0.5 * Fa.length;
+    const double ex[2] = {Fa.cx - h * c1, Fa.cx + h * c1}, ey[2] = {Fa.cy - h * s1, Fa.cy + h * s1};
+    double dmax = 0.0;
+    for (int j = net.off[b]; j < net.off[b + 1]; ++j) {
+        const double hb = 0.5 * net.ds[j];
+        const double sx[2] = {net.x[j] - hb * net.e1x[j], net.x[j] + hb * net.e1x[j]};
+        const double sy[2] = {net.y[j] - hb * net.e1y[j], net.y[j] + hb * net.e1y[j]};
+        for (int u = 0; u < 2; ++u)
+            for (int v = 0; v < 2; ++v) dmax = std::max(dmax, std::hypot(ex[u] - sx[v], ey[u] - sy[v]));
+    }
+    const double tmax = dmax / net.med.cs;
+    const double tend = (1.0 + eta_tmax) * tmax;
+    const double lag = std::ceil(tend / net.dt - 1e-9);
+    return (int32_t)std::min<double>(lag, max_steps - 1);
+}
+
+// Conservative first lag of a block: one less than floor(min segment distance / (c_s dt)).  Exactly-zero slices
+// found while building are dropped as well, so the stored window starts at the exact first nonzero lag.
+int32_t block_first_lag(const seas_net &net, const BlockDev &b) {
+    double dmin = INFINITY;
+    for (int i = b.r0; i < b.r0 + b.p; ++i)
+        for (int j = b.c0; j < b.c0 + b.q; ++j) {
+            const double dx = net.x[i] - net.x[j], dy = net.y[i] - net.y[j];
+            const double r1 = dx * net.e1x[j] + dy * net.e1y[j];
+            const double r2 = dx * net.nx[j] + dy * net.ny[j];
+            const double h = 0.5 * net.ds[j];
+            const double d = std::fabs(r1) <= h ? std::fabs(r2) : std::hypot(std::fabs(r1) - h, r2);
+            dmin = std::min(dmin, d);
+        }
+    const double lag = std::floor(dmin / (net.med.cs * net.dt)) - 1.0;
+    return (int32_t)std::max(0.0, lag);
+}
+
+// Last lag W_f(n) of the spectral window of mode n >= 1 (Eq. mode_dependent_truncation):
+// T_end(n) = eta_w L / c_s * Lcal(n), Lcal(n) = 1/n + (q_w - 1)/(n_max - 1) (1 - 1/n), n_max = N_f.
+int32_t mode_window(const seas_net &net, int f, int n, const seas_hparams &hp, bool no_trunc) {
+    if (no_trunc) return hp.max_steps - 1;
+    const int nf = net.faults[f].n_elem;
+    const double qw = hp.q_w <= 0 ? (double)nf : (double)hp.q_w;
+    const double lcal = nf == 1 ? 1.0 : 1.0 / n + (qw - 1.0) / (nf - 1.0) * (1.0 - 1.0 / n);
+    const double tend = hp.eta_w * net.faults[f].length / net.med.cs * lcal;
+    const double lag = std::ceil(tend / net.dt - 1e-9);
+    return (int32_t)std::min<double>(lag, hp.max_steps - 1);
+}
+
+std::vector<int> radix_plan(int n) {
+    std::vector<int> r;
+    for (int R : {4, 2, 3, 5})
+        while (n % R == 0 && !(R == 2 && n % 4 == 0)) {
+            r.push_back(R);
+            n /= R;
+        }
+    return r;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n (in long double).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i < n; ++i) {
+        long double z = cosl(pi * (i + 0.75L) / (n + 0.5L)), pp = 0;
+        for (int it = 0; it < 100; ++it) {
+            long double p0 = 1, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            pp = n * (z * p1 - p0) / (z * z - 1);
+            const long double dz = p1 / pp;
+            z -= dz;
+            if (fabsl(dz) < 1e-30L) break;
+        }
+        x[i] = (double)z;
+        w[i] = (double)(2 / ((1 - z * z) * pp * pp));
+    }
+}
+
+seas_status build_self(seas_op &op) {
+    seas_net &net = *op.net;
+    seas_ctx *c = net.ctx;
+    const bool no_trunc = op.hp.flags & SEAS_FLAG_NO_TRUNC;
+    std::vector<double2> tw;
+    std::vector<int64_t> g_prefix;
+    std::vector<double> mode_L;
+    int64_t w_total = 0, g_total = 0, dring = 0;
+    op.n_modes_total = 0;
+    op.max_nf = 0;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int f = 0; f < net.F; ++f) {
+        const int nf = net.faults[f].n_elem;
+        FaultDev fd{};
+        fd.off = net.off[f];
+        fd.nf = nf;
+        fd.mode_off = op.n_modes_total;
+        std::vector<int> rp = radix_plan(nf);
+        if ((int)rp.size() > kMaxStages) return fail(SEAS_EINVAL, "fault %d: FFT plan too deep", f);
+        fd.nstages = (int)rp.size();
+        for (size_t s = 0; s < rp.size(); ++s) fd.radix[s] = rp[s];
+        fd.tw_off = (int64_t)tw.size();
+        for (int k = 0; k < nf; ++k) {
+            const long double ang = -2 * pi * k / nf;
+            tw.push_back(make_double2((double)cosl(ang), (double)sinl(ang)));
+        }
+        for (int k = 0; k <= nf; ++k) {
+            const long double ang = -pi * k / nf;
+            tw.push_back(make_double2((double)cosl(ang), (double)sinl(ang)));
+        }
+        fd.kfac = -(net.med.mu / 2.0) * kPi / net.faults[f].length;
+        int32_t wmax = 0;
+        op.mode_W.push_back(0);
+        for (int n = 1; n <= nf; ++n) {
+            const int32_t W = mode_window(net, f, n, op.hp, no_trunc);
+            op.mode_W.push_back(W);
+            wmax = std::max(wmax, W);
+            ModeDev md{};
+            md.w_off = w_total;
+            md.W = W;
+            md.fault = f;
+            md.n = n;
+            op.modes_h.push_back(md);
+            g_prefix.push_back(g_total);
+            mode_L.push_back(net.faults[f].length);
+            w_total += W + 1;
+            g_total += W + 2;
+        }
+        fd.ring = wmax + 1;
+        fd.dring_off = dring;        // batch-1 layout; scenarios derive their own table
+        dring += (int64_t)(nf + 1) * fd.ring;
+        op.faults_h.push_back(fd);
+        op.n_modes_total += nf + 1;
+        op.max_nf = std::max(op.max_nf, nf);
+    }
+    SEAS_TRY(op.d_faults.upload(c, op.faults_h));
+    SEAS_TRY(op.d_modes.upload(c, op.modes_h));
+    SEAS_TRY(op.d_tw.upload(c, tw));
+    SEAS_TRY(op.d_w.alloc(c, (size_t)w_total));
+    DArr<int64_t> d_gp;
+    DArr<double> d_L, d_G, d_glx, d_glw;
+    std::vector<double> glx, glw;
+    gauss_legendre(10, glx, glw);
+    SEAS_TRY(d_gp.upload(c, g_prefix));
+    SEAS_TRY(d_L.upload(c, mode_L));
+    SEAS_TRY(d_glx.upload(c, glx));
+    SEAS_TRY(d_glw.upload(c, glw));
+    SEAS_TRY(d_G.alloc(c, (size_t)g_total));
+    CUDA_TRY(launch_spectral_tables(op.d_modes.p, (int)op.modes_h.size(), d_gp.p, g_total, d_L.p,
+                                    net.med.cs * net.dt, d_glx.p, d_glw.p, (int)glx.size(), d_G.p, op.d_w.p,
+                                    c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    op.stats.bytes_self = w_total * (int64_t)sizeof(double);
+    return SEAS_OK;
+}
+
+seas_status build_interaction(seas_op &op) {
+    seas_net &net = *op.net;
+    seas_ctx *c = net.ctx;
+    const seas_hparams &hp = op.hp;
+    const bool dense = hp.flags & SEAS_FLAG_DENSE;
+    const bool no_trunc = hp.flags & SEAS_FLAG_NO_TRUNC;
+    const int max_block = hp.max_block > 0 ? std::min(hp.max_block, kMaxBlockSide) : kMaxBlockSide;
+
+    // fault-wise cluster trees and per-pair block partitions
+    std::vector<std::vector<Cluster>> trees(net.F);
+    for (int f = 0; f < net.F; ++f) build_tree(net, f, net.off[f], net.off[f + 1], hp.leaf, trees[f]);
+    op.pair_last.assign((size_t)net.F * net.F, -1);
+    for (int a = 0; a < net.F; ++a)
+        for (int b = 0; b < net.F; ++b) {
+            if (a == b) continue;
+            op.pair_last[(size_t)a * net.F + b] = pair_last_lag(net, a, b, hp.eta_tmax, hp.max_steps, no_trunc);
+            traverse(trees[a], trees[b], hp.eta_h, dense, max_block, a * net.F + b, op.blocks_h, op.block_far,
+                     op.block_pair);
+        }
+    const int nb = (int)op.blocks_h.size();
+    std::vector<int32_t> lo(nb), hi(nb);
+    int32_t Tmin = INT32_MAX, Tmax = -1;
+    for (int b = 0; b < nb; ++b) {
+        lo[b] = block_first_lag(net, op.blocks_h[b]);
+        hi[b] = op.pair_last[op.block_pair[b]];
+        if (lo[b] <= hi[b]) {
+            Tmin = std::min(Tmin, lo[b]);
+            Tmax = std::max(Tmax, hi[b]);
+        }
+        if (op.block_far[b]) op.stats.n_blocks_far++;
+        else op.stats.n_blocks_near++;
+    }
+    op.ring = std::max<int32_t>(1, Tmax + 1);
+    SEAS_TRY(op.d_blocks.upload(c, op.blocks_h));
+
+    GeomDev g{net.d_x.p, net.d_e1.p, net.d_n.p, net.d_ds.p, net.med.cs, net.dt, -net.med.mu / (2.0 * net.med.cs)};
+    std::vector<StoredSlice> stored;
+    int64_t max_block_entries = 1;
+    for (auto &b : op.blocks_h) max_block_entries = std::max<int64_t>(max_block_entries, (int64_t)b.p * b.q);
+    const int64_t cap = std::max(kChunkEntries, max_block_entries);
+    bool any_far = false;
+    for (int b = 0; b < nb; ++b) any_far |= op.block_far[b] != 0;
+    DArr<double> scratch, resid, factors;
+    if (Tmax >= 0) {
+        SEAS_TRY(scratch.alloc(c, (size_t)cap));
+        if (any_far) {
+            SEAS_TRY(resid.alloc(c, (size_t)cap));
+            SEAS_TRY(factors.alloc(c, (size_t)cap));
+        }
+    }
+    int64_t bytes_dense = 0, bytes_stored = 0, rank_sum = 0;
+    int32_t T = Tmin;
+    int cb = 0;                       // next block of lag T (a lag larger than one chunk spans several)
+    while (Tmax >= 0 && T <= Tmax) {
+        std::vector<SliceGen> sl;
+        std::vector<int64_t> prefix;
+        int64_t entries = 0;
+        bool full = false;
+        while (T <= Tmax && !full) {
+            for (; cb < nb; ++cb) {
+                if (T < lo[cb] || T > hi[cb]) continue;
+                const int64_t pq = (int64_t)op.blocks_h[cb].p * op.blocks_h[cb].q;
+                if (entries + pq > cap) {
+                    full = true;
+                    break;
+                }
+                sl.push_back(SliceGen{cb, T, op.block_far[cb], 0, entries});
+                prefix.push_back(entries);
+                entries += pq;
+            }
+            if (!full) {
+                cb = 0;
+                ++T;
+            }
+        }
+        if (sl.empty()) continue;
+        DArr<SliceGen> d_sl;
+        DArr<int64_t> d_pref, d_off;
+        DArr<SliceOut> d_out;
+        SEAS_TRY(d_sl.upload(c, sl));
+        SEAS_TRY(d_pref.upload(c, prefix));
+        SEAS_TRY(d_out.alloc(c, sl.size()));
+        CUDA_TRY(launch_gen_slices(g, op.d_blocks.p, d_sl.p, (int)sl.size(), d_pref.p, entries, scratch.p,
+                                   c->stream));
+        CUDA_TRY(launch_compress(op.d_blocks.p, d_sl.p, (int)sl.size(), scratch.p, resid.p, factors.p, d_out.p,
+                                 hp.aca_tol, c->stream));
+        std::vector<SliceOut> so(sl.size());
+        CUDA_TRY(cudaMemcpyAsync(so.data(), d_out.p, so.size() * sizeof(SliceOut), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        std::vector<int64_t> dst(sl.size());
+        int64_t total = 0;
+        for (size_t s = 0; s < sl.size(); ++s) {
+            const BlockDev &b = op.blocks_h[sl[s].block];
+            dst[s] = total;
+            if (so[s].k == 0) {
+                op.stats.n_slices_zero++;
+                continue;
+            }
+            const int64_t pq = (int64_t)b.p * b.q;
+            bytes_dense += pq * 8;
+            const int64_t n = so[s].k < 0 ? pq : (int64_t)so[s].k * (b.p + b.q);
+            if (so[s].k < 0) op.stats.n_slices_dense++;
+            else {
+                op.stats.n_slices_lowrank++;
+                rank_sum += so[s].k;
+                op.stats.max_rank = std::max(op.stats.max_rank, so[s].k);
+            }
+            total += n;
+        }
+        if (total == 0) continue;
+        auto buf = std::make_unique<DArr<double>>();
+        SEAS_TRY(buf->alloc(c, (size_t)total));
+        SEAS_TRY(d_off.upload(c, dst));
+        CUDA_TRY(launch_pack(op.d_blocks.p, d_sl.p, d_out.p, (int)sl.size(), scratch.p, factors.p, d_off.p, buf->p,
+                             c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        for (size_t s = 0; s < sl.size(); ++s)
+            if (so[s].k != 0) stored.push_back(StoredSlice{sl[s].block, sl[s].T, so[s].k, buf->p + dst[s]});
+        bytes_stored += total * 8;
+        op.arena.push_back(std::move(buf));
+    }
+    scratch.release();
+    resid.release();
+    factors.release();
+
+    // work items (inner ranges of one slice) and tasks (runs of items of one block), tasks sorted by first lag
+    std::stable_sort(stored.begin(), stored.end(), [](const StoredSlice &x, const StoredSlice &y) {
+        return x.block != y.block ? x.block < y.block : x.T < y.T;
+    });
+    std::vector<ItemDev> items;
+    std::vector<TaskDev> tasks;
+    size_t s = 0;
+    while (s < stored.size()) {
+        const int blk = stored[s].block;
+        const BlockDev &b = op.blocks_h[blk];
+        TaskDev task{blk, (int32_t)items.size(), 0, stored[s].T};
+        int64_t task_bytes = 0;
+        for (; s < stored.size() && stored[s].block == blk; ++s) {
+            const StoredSlice &x = stored[s];
+            if (task_bytes >= kTaskBytes) {
+                task.item_end = (int32_t)items.size();
+                tasks.push_back(task);
+                task = TaskDev{blk, (int32_t)items.size(), 0, x.T};
+                task_bytes = 0;
+            }
+            if (x.k < 0) {
+                const int rows = (int)std::max<int64_t>(1, kItemBytes / (8 * (int64_t)b.p));
+                for (int j = 0; j < b.q; j += rows) {
+                    const int j1 = std::min(b.q, j + rows);
+                    items.push_back(ItemDev{x.T, -1, j, j1, x.data + (int64_t)j * b.p, nullptr});
+                }
+                task_bytes += (int64_t)b.p * b.q * 8;
+            } else {
+                const int per = (int)std::min<int64_t>(kMaxItemRank,
+                                                       std::max<int64_t>(1, kItemBytes / (8 * (int64_t)(b.p + b.q))));
+                const double *Vt = x.data, *Ut = x.data + (int64_t)x.k * b.q;
+                for (int l = 0; l < x.k; l += per) {
+                    const int l1 = std::min(x.k, l + per);
+                    items.push_back(ItemDev{x.T, l1 - l, l, l1, Vt + (int64_t)l * b.q, Ut + (int64_t)l * b.p});
+                }
+                task_bytes += (int64_t)x.k * (b.p + b.q) * 8;
+            }
+        }
+        task.item_end = (int32_t)items.size();
+        tasks.push_back(task);
+    }
+    std::stable_sort(tasks.begin(), tasks.end(), [](const TaskDev &x, const TaskDev &y) { return x.T_start < y.T_start; });
+    op.bytes_upto.assign((size_t)op.ring, 0);
+    for (const StoredSlice &x : stored) {
+        const BlockDev &b = op.blocks_h[x.block];
+        op.bytes_upto[x.T] += 8 * (x.k < 0 ? (int64_t)b.p * b.q : (int64_t)x.k * (b.p + b.q));
+    }
+    for (size_t T = 1; T < op.bytes_upto.size(); ++T) op.bytes_upto[T] += op.bytes_upto[T - 1];
+    for (auto &t : tasks) op.task_T.push_back(t.T_start);
+    SEAS_TRY(op.d_items.upload(c, items));
+    SEAS_TRY(op.d_tasks.upload(c, tasks));
+    op.stats.n_tasks = (int64_t)tasks.size();
+    op.stats.bytes_interaction = bytes_stored;
+    op.stats.bytes_dense_causal = bytes_dense;
+    op.stats.compression_ratio = bytes_dense ? 100.0 * (double)bytes_stored / (double)bytes_dense : 0.0;
+    op.stats.mean_rank = op.stats.n_slices_lowrank ? (double)rank_sum / op.stats.n_slices_lowrank : 0.0;
+    op.stats.ring_depth = op.ring;
+    return SEAS_OK;
+}
+
+}  // namespace
+
+extern "C" seas_status seas_build_hmatrix(seas_net *net, const seas_hparams *hp, seas_op **out,
+                                          seas_op_stats *stats) {
+    if (!net || !hp || !out) return fail(SEAS_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (hp->leaf < 1 || hp->leaf > kMaxBlockSide) return fail(SEAS_EINVAL, "leaf must be in [1, %d]", kMaxBlockSide);
+    if (!(hp->eta_h > 0)) return fail(SEAS_EINVAL, "eta_h must be > 0");
+    if (!(is_fin(hp->aca_tol) && hp->aca_tol >= 0 && hp->aca_tol < 1)) return fail(SEAS_EINVAL, "aca_tol in [0, 1)");
+    if (!(is_fin(hp->eta_tmax) && hp->eta_tmax >= 0)) return fail(SEAS_EINVAL, "eta_tmax must be >= 0");
+    if (!(is_fin(hp->eta_w) && hp->eta_w > 0)) return fail(SEAS_EINVAL, "eta_w must be > 0");
+    if (hp->max_steps < 1 || hp->max_steps > (1 << 22)) return fail(SEAS_EINVAL, "max_steps in [1, 2^22]");
+    if (hp->precision != SEAS_PREC_FP64) return fail(SEAS_EINVAL, "precision %d not available", hp->precision);
+    if (hp->flags & ~(SEAS_FLAG_DENSE | SEAS_FLAG_NO_TRUNC))
+        return fail(SEAS_EINVAL, "unsupported flags 0x%x", hp->flags);
+    if (hp->max_block != 0 && hp->max_block < hp->leaf) return fail(SEAS_EINVAL, "max_block must be >= leaf");
+    seas_ctx *c = net->ctx;
+    CUDA_TRY(cudaSetDevice(c->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    auto op = std::make_unique<seas_op>();
+    op->net = net;
+    op->hp = *hp;
+    SEAS_TRY(build_self(*op));
+    SEAS_TRY(build_interaction(*op));
+    op->stats.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = op->stats;
+    net->children++;
+    *out = op.release();
+    return SEAS_OK;
+}
+
+
+extern "C" seas_status seas_plan_hmatrix(const seas_fault *faults, int n_faults, const seas_medium *med,
+                                         const seas_hparams *hp, int32_t *blocks, int64_t cap, int64_t *n_blocks,
+                                         int32_t *pair_last, int32_t *mode_windows, double *dt) {
+    if (!hp) return fail(SEAS_EINVAL, "NULL hparams");
+    seas_net net;
+    SEAS_TRY(make_geometry(faults, n_faults, med, net));
+    if (hp->leaf < 1 || hp->leaf > kMaxBlockSide) return fail(SEAS_EINVAL, "leaf must be in [1, %d]", kMaxBlockSide);
+    if (hp->max_steps < 1) return fail(SEAS_EINVAL, "max_steps must be >= 1");
+    const bool dense = hp->flags & SEAS_FLAG_DENSE;
+    const bool no_trunc = hp->flags & SEAS_FLAG_NO_TRUNC;
+    const int max_block = hp->max_block > 0 ? std::min(hp->max_block, kMaxBlockSide) : kMaxBlockSide;
+    std::vector<std::vector<Cluster>> trees(net.F);
+    for (int f = 0; f < net.F; ++f) build_tree(net, f, net.off[f], net.off[f + 1], hp->leaf, trees[f]);
+    std::vector<BlockDev> bl;
+    std::vector<int32_t> far, pairs;
+    for (int a = 0; a < net.F; ++a)
+        for (int b = 0; b < net.F; ++b) {
+            if (a == b) continue;
+            if (pair_last)
+                pair_last[a * net.F + b] = pair_last_lag(net, a, b, hp->eta_tmax, hp->max_steps, no_trunc);
+            traverse(trees[a], trees[b], hp->eta_h, dense, max_block, a * net.F + b, bl, far, pairs);
+        }
+    if (pair_last)
+        for (int a = 0; a < net.F; ++a) pair_last[a * net.F + a] = -1;
+    if (n_blocks) *n_blocks = (int64_t)bl.size();
+    if (blocks)
+        for (int64_t i = 0; i < std::min<int64_t>(cap, (int64_t)bl.size()); ++i) {
+            int32_t *r = blocks + 6 * i;
+            r[0] = bl[i].r0;
+            r[1] = bl[i].p;
+            r[2] = bl[i].c0;
+            r[3] = bl[i].q;
+            r[4] = far[i];
+            r[5] = block_first_lag(net, bl[i]);
+        }
+    if (mode_windows) {
+        int64_t o = 0;
+        for (int f = 0; f < net.F; ++f) {
+            mode_windows[o++] = 0;
+            for (int n = 1; n <= net.faults[f].n_elem; ++n) mode_windows[o++] = mode_window(net, f, n, *hp, no_trunc);
+        }
+    }
+    if (dt) *dt = net.dt;
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_op_pair_windows(const seas_op *op, int32_t *last_lag) {
+    if (!op || !last_lag) return fail(SEAS_EINVAL, "NULL argument");
+    std::copy(op->pair_last.begin(), op->pair_last.end(), last_lag);
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_op_mode_windows(const seas_op *op, int32_t *w) {
+    if (!op || !w) return fail(SEAS_EINVAL, "NULL argument");
+    std::copy(op->mode_W.begin(), op->mode_W.end(), w);
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_destroy_op(seas_op *op) {
+    if (!op) return SEAS_OK;
+    if (op->children) return fail(SEAS_EBUSY, "operator has %d live scenarios", op->children);
+    cudaSetDevice(op->net->ctx->device);
+    op->net->children--;
+    delete op;
+    return SEAS_OK;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// scenarios and the per-step calls
+// ------------------------------------------------------------------------------------------------------------
+
+namespace {
+
+StepArgs step_args(seas_scn &s, int64_t step) {
+    seas_op &op = *s.op;
+    seas_net &net = *op.net;
+    StepArgs a{};
+    a.N = net.N;
+    a.F = net.F;
+    a.B = s.B;
+    a.n_modes_total = op.n_modes_total;
+    a.max_nf = op.max_nf;
+    a.step = step;
+    a.ring = op.ring;
+    a.dt = net.dt;
+    a.rad = -net.med.mu / (2.0 * net.med.cs);
+    a.faults = s.faults.p;
+    a.modes = op.d_modes.p;
+    a.n_modes = (int)op.modes_h.size();
+    a.w = op.d_w.p;
+    a.tw = op.d_tw.p;
+    a.vring = s.vring.p;
+    a.slip = s.slip.p;
+    a.slip_prev = s.slip_prev.p;
+    a.dring = s.dring.p;
+    a.fmodes = s.fmodes.p;
+    a.fint = s.fint.p;
+    a.blocks = op.d_blocks.p;
+    a.items = op.d_items.p;
+    a.tasks = op.d_tasks.p;
+    a.n_tasks_active =
+        (int)(std::upper_bound(op.task_T.begin(), op.task_T.end(), (int32_t)std::min<int64_t>(step, INT32_MAX)) -
+              op.task_T.begin());
+    return a;
+}
+
+seas_status scenario_alloc(seas_op *op, int batch, std::unique_ptr<seas_scn> &s) {
+    seas_ctx *c = op->net->ctx;
+    const int64_t N = op->net->N;
+    s = std::make_unique<seas_scn>();
+    s->op = op;
+    s->B = batch;
+    const int64_t BN = N * batch;
+    // spectral rings: per fault [batch][N_f + 1][R_f], faults one after the other
+    std::vector<FaultDev> ft = op->faults_h;
+    int64_t dr = 0;
+    for (auto &f : ft) {
+        f.dring_off = dr;
+        dr += (int64_t)batch * (f.nf + 1) * f.ring;
+    }
+    s->dring_len = dr;
+    SEAS_TRY(s->faults.upload(c, ft));
+    SEAS_TRY(s->vring.alloc(c, (size_t)(op->ring * BN)));
+    SEAS_TRY(s->slip.alloc(c, (size_t)BN));
+    SEAS_TRY(s->slip_prev.alloc(c, (size_t)BN));
+    SEAS_TRY(s->fint.alloc(c, (size_t)BN));
+    SEAS_TRY(s->d_V.alloc(c, (size_t)BN));
+    SEAS_TRY(s->d_slip.alloc(c, (size_t)BN));
+    SEAS_TRY(s->d_tau.alloc(c, (size_t)BN));
+    SEAS_TRY(s->d_parts.alloc(c, (size_t)(3 * BN)));
+    SEAS_TRY(s->dring.alloc(c, (size_t)s->dring_len));
+    SEAS_TRY(s->fmodes.alloc(c, (size_t)(op->n_modes_total * (int64_t)batch)));
+    SEAS_TRY(s->h_in.alloc((size_t)(2 * BN) * sizeof(double)));
+    SEAS_TRY(s->h_out.alloc((size_t)(4 * BN) * sizeof(double)));
+    for (DArr<double> *d : {&s->vring, &s->slip, &s->slip_prev, &s->fint}) SEAS_TRY(d->zero(c->stream));
+    SEAS_TRY(s->dring.zero(c->stream));
+    SEAS_TRY(s->fmodes.zero(c->stream));
+    return SEAS_OK;
+}
+
+}  // namespace
+
+extern "C" seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **out) {
+    if (!op || !out) return fail(SEAS_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (batch < 1 || batch > 4096) return fail(SEAS_EINVAL, "batch must be in [1, 4096]");
+    CUDA_TRY(cudaSetDevice(op->net->ctx->device));
+    std::unique_ptr<seas_scn> s;
+    SEAS_TRY(scenario_alloc(op, batch, s));
+    CUDA_TRY(cudaStreamSynchronize(op->net->ctx->stream));
+    op->children++;
+    *out = s.release();
+    return SEAS_OK;
+}
+
+
+
+namespace {
+
+constexpr size_t kEventPairs = 8192;
+
+seas_status timing_resolve(seas_scn &s) {
+    if (s.ev_used == 0) return SEAS_OK;
+    CUDA_TRY(cudaEventSynchronize(s.ev[2 * s.ev_used - 1]));
+    for (size_t i = 0; i < s.ev_used; ++i) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, s.ev[2 * i], s.ev[2 * i + 1]));
+        s.acc.ms[s.ev_class[i]] += ms;
+        s.acc.launches[s.ev_class[i]] += 1;
+    }
+    s.ev_used = 0;
+    return SEAS_OK;
+}
+
+// Runs one launch, bracketed by an event pair of class `cls` when timing is on.
+template <class F>
+seas_status timed(seas_scn &s, int cls, F &&launch) {
+    cudaStream_t st = s.op->net->ctx->stream;
+    if (!s.timing) {
+        CUDA_TRY(launch());
+        return SEAS_OK;
+    }
+    if (s.ev.empty()) {
+        s.ev.resize(2 * kEventPairs);
+        s.ev_class.resize(kEventPairs);
+        for (cudaEvent_t &e : s.ev) CUDA_TRY(cudaEventCreate(&e));
+    }
+    if (s.ev_used == kEventPairs) SEAS_TRY(timing_resolve(s));
+    CUDA_TRY(cudaEventRecord(s.ev[2 * s.ev_used], st));
+    CUDA_TRY(launch());
+    CUDA_TRY(cudaEventRecord(s.ev[2 * s.ev_used + 1], st));
+    s.ev_class[s.ev_used++] = cls;
+    return SEAS_OK;
+}
+
+}  // namespace
+
+extern "C" seas_status seas_scenario_set_timing(seas_scn *s, int enable) {
+    if (!s) return fail(SEAS_EINVAL, "NULL scenario");
+    CUDA_TRY(cudaSetDevice(s->op->net->ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(s->op->net->ctx->stream));
+    s->ev_used = 0;
+    s->acc = seas_timing{};
+    s->timing = enable != 0;
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_scenario_get_timing(seas_scn *s, seas_timing *out) {
+    if (!s || !out) return fail(SEAS_EINVAL, "NULL argument");
+    CUDA_TRY(cudaSetDevice(s->op->net->ctx->device));
+    SEAS_TRY(timing_resolve(*s));
+    *out = s->acc;
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_op_step_bytes(const seas_op *op, int64_t step, int64_t *bytes) {
+    if (!op || !bytes || step < 0) return fail(SEAS_EINVAL, "bad argument");
+    if (op->bytes_upto.empty()) {
+        *bytes = 0;
+        return SEAS_OK;
+    }
+    *bytes = op->bytes_upto[(size_t)std::min<int64_t>(step, (int64_t)op->bytes_upto.size() - 1)];
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_push_slip_rate(seas_scn *s, const double *V, const double *slip, int mem,
+                                           int replace_last) {
+    if (!s || !V) return fail(SEAS_EINVAL, "NULL argument");
+    if (mem != SEAS_MEM_HOST && mem != SEAS_MEM_DEVICE) return fail(SEAS_EINVAL, "mem must be HOST or DEVICE");
+    seas_op &op = *s->op;
+    seas_ctx *c = op.net->ctx;
+    if (replace_last && s->n == 0) return fail(SEAS_ESTATE, "replace_last before the first push");
+    if (!replace_last && s->n >= op.hp.max_steps)
+        return fail(SEAS_ESTATE, "push %lld beyond max_steps %d", (long long)s->n, op.hp.max_steps);
+    CUDA_TRY(cudaSetDevice(c->device));
+    const int64_t BN = (int64_t)s->B * op.net->N;
+    const double *dV = V, *dS = slip;
+    if (mem == SEAS_MEM_HOST) {
+        for (int64_t i = 0; i < BN; ++i)
+            if (!std::isfinite(V[i])) return fail(SEAS_EINVAL, "non-finite slip rate at index %lld", (long long)i);
+        if (slip)
+            for (int64_t i = 0; i < BN; ++i)
+                if (!std::isfinite(slip[i])) return fail(SEAS_EINVAL, "non-finite slip at index %lld", (long long)i);
+        double *hin = static_cast<double *>(s->h_in.p);
+        CUDA_TRY(cudaStreamSynchronize(c->stream));   // the staging buffer may still feed a previous copy
+        std::memcpy(hin, V, BN * sizeof(double));
+        CUDA_TRY(cudaMemcpyAsync(s->d_V.p, hin, BN * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        dV = s->d_V.p;
+        if (slip) {
+            std::memcpy(hin + BN, slip, BN * sizeof(double));
+            CUDA_TRY(cudaMemcpyAsync(s->d_slip.p, hin + BN, BN * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            dS = s->d_slip.p;
+        }
+    }
+    const int64_t step = replace_last ? s->n - 1 : s->n;
+    StepArgs a = step_args(*s, step);
+    SEAS_TRY(timed(*s, 0, [&] { return launch_push(a, dV, dS, replace_last, c->stream); }));
+    SEAS_TRY(timed(*s, 1, [&] { return launch_fft_forward(a, c->stream); }));
+    if (!replace_last) s->n++;
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_stress_step(seas_scn *s, double *tau, double *sigma_n, double *parts, int mem) {
+    if (!s || !tau) return fail(SEAS_EINVAL, "NULL argument");
+    if (mem != SEAS_MEM_HOST && mem != SEAS_MEM_DEVICE) return fail(SEAS_EINVAL, "mem must be HOST or DEVICE");
+    if (s->n == 0) return fail(SEAS_ESTATE, "stress_step before the first push");
+    seas_op &op = *s->op;
+    seas_ctx *c = op.net->ctx;
+    CUDA_TRY(cudaSetDevice(c->device));
+    const int64_t BN = (int64_t)s->B * op.net->N;
+    StepArgs a = step_args(*s, s->n - 1);
+    double *dtau = mem == SEAS_MEM_DEVICE ? tau : s->d_tau.p;
+    double *dparts = parts ? (mem == SEAS_MEM_DEVICE ? parts : s->d_parts.p) : nullptr;
+    CUDA_TRY(cudaMemsetAsync(s->fint.p, 0, BN * sizeof(double), c->stream));
+    SEAS_TRY(timed(*s, 2, [&] { return launch_modeconv(a, c->stream); }));
+    SEAS_TRY(timed(*s, 3, [&] { return launch_interaction(a, c->stream); }));
+    SEAS_TRY(timed(*s, 4, [&] { return launch_ifft_assemble(a, dtau, dparts, c->stream); }));
+    if (s->timing) {
+        int64_t b = 0;
+        SEAS_TRY(seas_op_step_bytes(&op, s->n - 1, &b));
+        s->acc.interaction_bytes += b;
+        s->acc.steps += 1;
+    }
+    if (mem == SEAS_MEM_DEVICE) {
+        if (sigma_n) CUDA_TRY(cudaMemsetAsync(sigma_n, 0, BN * sizeof(double), c->stream));
+        return SEAS_OK;
+    }
+    double *hout = static_cast<double *>(s->h_out.p);
+    CUDA_TRY(cudaMemcpyAsync(hout, dtau, BN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (parts)
+        CUDA_TRY(cudaMemcpyAsync(hout + BN, dparts, 3 * BN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    std::memcpy(tau, hout, BN * sizeof(double));
+    if (parts) std::memcpy(parts, hout + BN, 3 * BN * sizeof(double));
+    if (sigma_n) std::memset(sigma_n, 0, BN * sizeof(double));
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_scenario_step(const seas_scn *s, int64_t *n) {
+    if (!s || !n) return fail(SEAS_EINVAL, "NULL argument");
+    *n = s->n;
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_destroy_scn(seas_scn *s) {
+    if (!s) return SEAS_OK;
+    cudaSetDevice(s->op->net->ctx->device);
+    cudaStreamSynchronize(s->op->net->ctx->stream);
+    s->op->children--;
+    delete s;
+    return SEAS_OK;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// checkpoint / resume
+// ------------------------------------------------------------------------------------------------------------
+
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    int32_t version, B, N, F;
+    int64_t n, ring, dring_len, n_modes_total;
+};
+
+seas_status dump(FILE *fp, const void *dev, size_t bytes) {
+    std::vector<char> h(bytes);
+    if (bytes) CUDA_TRY(cudaMemcpy(h.data(), dev, bytes, cudaMemcpyDeviceToHost));
+    if (bytes && fwrite(h.data(), 1, bytes, fp) != bytes) return fail(SEAS_EIO, "short write");
+    return SEAS_OK;
+}
+
+seas_status slurp(FILE *fp, void *dev, size_t bytes) {
+    std::vector<char> h(bytes);
+    if (bytes && fread(h.data(), 1, bytes, fp) != bytes) return fail(SEAS_EIO, "short read");
+    if (bytes) CUDA_TRY(cudaMemcpy(dev, h.data(), bytes, cudaMemcpyHostToDevice));
+    return SEAS_OK;
+}
+
+}  // namespace
+
+extern "C" seas_status seas_scenario_save(seas_scn *s, const char *path) {
+    if (!s || !path) return fail(SEAS_EINVAL, "NULL argument");
+    seas_op &op = *s->op;
+    CUDA_TRY(cudaSetDevice(op.net->ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(op.net->ctx->stream));
+    FILE *fp = fopen(path, "wb");
+    if (!fp) return fail(SEAS_EIO, "cannot open %s for writing", path);
+    CkptHeader h{};
+    std::memcpy(h.magic, "SEASCKP1", 8);
+    h.version = 1;
+    h.B = s->B;
+    h.N = op.net->N;
+    h.F = op.net->F;
+    h.n = s->n;
+    h.ring = op.ring;
+    h.dring_len = s->dring_len;
+    h.n_modes_total = op.n_modes_total;
+    seas_status st = SEAS_OK;
+    if (fwrite(&h, sizeof h, 1, fp) != 1) st = fail(SEAS_EIO, "short write");
+    if (st == SEAS_OK) st = dump(fp, s->vring.p, s->vring.bytes());
+    if (st == SEAS_OK) st = dump(fp, s->slip.p, s->slip.bytes());
+    if (st == SEAS_OK) st = dump(fp, s->slip_prev.p, s->slip_prev.bytes());
+    if (st == SEAS_OK) st = dump(fp, s->dring.p, s->dring.bytes());
+    if (fclose(fp) != 0 && st == SEAS_OK) st = fail(SEAS_EIO, "close failed");
+    return st;
+}
+
+extern "C" seas_status seas_scenario_load(seas_op *op, const char *path, seas_scn **out) {
+    if (!op || !path || !out) return fail(SEAS_EINVAL, "NULL argument");
+    *out = nullptr;
+    CUDA_TRY(cudaSetDevice(op->net->ctx->device));
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return fail(SEAS_EIO, "cannot open %s", path);
+    CkptHeader h{};
+    if (fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "SEASCKP1", 8) != 0 || h.version != 1) {
+        fclose(fp);
+        return fail(SEAS_EIO, "%s is not a scenario checkpoint", path);
+    }
+    if (h.N != op->net->N || h.F != op->net->F || h.ring != op->ring || h.n_modes_total != op->n_modes_total ||
+        h.B < 1 || h.n < 0 || h.n > op->hp.max_steps) {
+        fclose(fp);
+        return fail(SEAS_EIO, "checkpoint does not match this operator");
+    }
+    std::unique_ptr<seas_scn> s;
+    seas_status st = scenario_alloc(op, h.B, s);
+    if (st == SEAS_OK && h.dring_len != s->dring_len) st = fail(SEAS_EIO, "checkpoint spectral ring size mismatch");
+    if (st == SEAS_OK) st = slurp(fp, s->vring.p, s->vring.bytes());
+    if (st == SEAS_OK) st = slurp(fp, s->slip.p, s->slip.bytes());
+    if (st == SEAS_OK) st = slurp(fp, s->slip_prev.p, s->slip_prev.bytes());
+    if (st == SEAS_OK) st = slurp(fp, s->dring.p, s->dring.bytes());
+    fclose(fp);
+    if (st != SEAS_OK) return st;
+    s->n = h.n;
+    op->children++;
+    *out = s.release();
+    return SEAS_OK;
+}

@@ -1,0 +1,132 @@
+// Internal declarations shared by the host orchestration (seas_api.cu), the operator-build kernels
+// (seas_build.cu) and the per-step kernels (seas_step.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace seas {
+
+constexpr int kThreads = 256;       // threads per CTA of every kernel
+constexpr int kMaxFFT = 7168;       // largest N_f: two N_f-point complex buffers fit in shared memory
+constexpr int kMaxStages = 16;      // radix stages of one FFT plan
+constexpr int kMaxBlockSide = 1024; // rows / columns of one H-matrix block (4 accumulator rows per thread)
+constexpr int kRowsPerThread = kMaxBlockSide / kThreads;
+constexpr int kMaxItemRank = 128;   // rank-1 terms of one low-rank work item (shared-memory z buffer)
+
+// One fault of the spectral self-effect path.
+struct FaultDev {
+    int32_t off;        // first element (global index)
+    int32_t nf;         // N_f (complex FFT size); the padded real transform has M = 2 N_f points
+    int32_t mode_off;   // first entry of this fault in the per-mode arrays (N_f + 1 entries, modes 0..N_f)
+    int32_t ring;       // R_f: slots of the spectral history ring
+    int64_t dring_off;  // first double2 of this fault's ring: [batch][N_f + 1][R_f]
+    int64_t tw_off;     // first double2 of the twiddles: N_f entries e^{-2 pi i k/N_f}, then N_f + 1 entries
+                        // e^{-2 pi i k/(2 N_f)}
+    int32_t nstages;
+    int32_t radix[kMaxStages];
+    double kfac;        // -(mu / 2) * pi / L_f, so that F_n = kfac * n * sum_T w_n^T D_n^{t-T}
+};
+
+// One spectral mode n >= 1 of one fault.
+struct ModeDev {
+    int64_t w_off;      // first weight of w_n^0..w_n^W
+    int32_t W;          // last lag of the window
+    int32_t fault;
+    int32_t n;
+    int32_t pad;
+};
+
+// One H-matrix block: receiver rows [r0, r0 + p), source columns [c0, c0 + q) (global element indices).
+struct BlockDev {
+    int32_t r0, p, c0, q;
+};
+
+// One unit of interaction work: the inner range [i0, i1) of one (block, lag) slice.
+//   dense   (k < 0): a points at rows i0..i1-1 of A^T (each p doubles): y += sum_j A^T[j][:] x_{c0+j}
+//   lowrank (k > 0): a points at rows i0..i1-1 of V^T (each q doubles), b at rows i0..i1-1 of U^T (each p
+//                    doubles): y += sum_l U^T[l][:] (V^T[l][:] . x)
+struct ItemDev {
+    int32_t T;
+    int32_t k;
+    int32_t i0, i1;
+    const double *a;
+    const double *b;
+};
+
+// A run of items of one block (sorted by lag) whose partial sums are flushed together.
+struct TaskDev {
+    int32_t block;
+    int32_t item_begin;
+    int32_t item_end;
+    int32_t T_start;
+};
+
+// One (block, lag) slice produced during the build.
+struct SliceGen {
+    int32_t block;
+    int32_t T;
+    int32_t far;        // 1: admissible (compress), 0: near (store dense)
+    int32_t pad;
+    int64_t scratch;    // first double of its p*q entries (layout A^T: q rows of p) in the scratch buffers
+};
+
+// Result of compressing one slice.
+struct SliceOut {
+    int32_t k;          // 0: zero slice, -1: dense, > 0: rank
+    int32_t pad;
+    double norm;        // Frobenius norm of the slice
+    double resid;       // Frobenius norm of the residual (low rank) or 0
+};
+
+// ---- build kernels (seas_build.cu) ----
+struct GeomDev {
+    const double2 *x;     // centroids
+    const double2 *e1;    // along-fault unit vectors
+    const double2 *nrm;   // normals
+    const double *ds;     // element lengths
+    double cs, dt, scale; // scale = -mu / (2 c_s)
+};
+
+cudaError_t launch_gen_slices(const GeomDev &g, const BlockDev *blocks, const SliceGen *slices, int n_slices,
+                              const int64_t *entry_prefix, int64_t n_entries, double *scratch, cudaStream_t s);
+cudaError_t launch_compress(const BlockDev *blocks, const SliceGen *slices, int n_slices, const double *scratch,
+                            double *resid, double *factors, SliceOut *out, double tol, cudaStream_t s);
+cudaError_t launch_pack(const BlockDev *blocks, const SliceGen *slices, const SliceOut *out, int n_slices,
+                        const double *scratch, const double *factors, const int64_t *dst_off, double *dst,
+                        cudaStream_t s);
+cudaError_t launch_spectral_tables(const ModeDev *modes, int n_modes, const int64_t *g_prefix, int64_t n_g,
+                                   const double *mode_L, double cs_dt, const double *gl_x, const double *gl_w,
+                                   int gl_n, double *G, double *w, cudaStream_t s);
+
+// ---- step kernels (seas_step.cu) ----
+struct StepArgs {
+    int N, F, B, n_modes_total;   // elements, faults, batch, sum over faults of (N_f + 1)
+    int max_nf;                   // largest N_f (shared memory of the FFT kernels)
+    int64_t step;                 // index of the step being evaluated
+    int ring;                     // slip-rate ring depth R
+    double dt, rad;               // rad = -mu / (2 c_s)
+    const FaultDev *faults;
+    const ModeDev *modes;         // modes n >= 1 of all faults
+    int n_modes;
+    const double *w;              // spectral weights
+    const double2 *tw;            // FFT twiddles
+    double *vring;                // [R][B][N]
+    double *slip, *slip_prev;     // [B][N]
+    double2 *dring;               // spectral rings
+    double2 *fmodes;              // [B][n_modes_total]
+    double *fint;                 // [B][N]
+    const BlockDev *blocks;
+    const ItemDev *items;
+    const TaskDev *tasks;
+    int n_tasks_active;
+};
+
+cudaError_t launch_push(const StepArgs &a, const double *V, const double *slip_in, int replace_last,
+                        cudaStream_t s);
+cudaError_t launch_fft_forward(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_ifft_assemble(const StepArgs &a, double *tau, double *parts, cudaStream_t s);
+
+}  // namespace seas

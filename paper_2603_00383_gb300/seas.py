@@ -1,0 +1,364 @@
+"""Thin Python binding of the C ABI in include/seas.h (ctypes; argument marshalling only).
+
+Every function has the C name and returns Python values instead of out-parameters; a negative status raises
+``SeasError``.  Host arrays are float64 C-contiguous NumPy arrays (``SEAS_MEM_HOST``); device arrays are float64
+contiguous CUDA tensors (anything with ``data_ptr()`` and ``is_cuda``), passed as raw pointers (``SEAS_MEM_DEVICE``).
+All computation happens in libseas.so; if the library is missing this module raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libseas.so")
+
+SEAS_OK = 0
+SEAS_EINVAL, SEAS_ENOMEM, SEAS_ECUDA, SEAS_ESTATE, SEAS_EBUSY, SEAS_ETIMEOUT, SEAS_EIO = -1, -2, -3, -4, -5, -6, -7
+SEAS_MEM_HOST, SEAS_MEM_DEVICE = 0, 1
+SEAS_FLAG_DENSE, SEAS_FLAG_NO_TRUNC, SEAS_FLAG_STATIC_TAIL = 1, 2, 4
+SEAS_PREC_FP64 = 0
+
+EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_get_elements", "seas_build_hmatrix",
+            "seas_op_pair_windows", "seas_op_mode_windows", "seas_scenario_create", "seas_push_slip_rate",
+            "seas_stress_step", "seas_scenario_step", "seas_sync", "seas_strerror", "seas_last_error",
+            "seas_scenario_save", "seas_scenario_load", "seas_destroy_scn", "seas_destroy_op", "seas_destroy_net",
+            "seas_destroy_ctx", "seas_plan_hmatrix", "seas_scenario_set_timing", "seas_scenario_get_timing",
+            "seas_op_step_bytes"]
+
+
+class SeasError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class seas_fault(C.Structure):
+    _fields_ = [("cx", C.c_double), ("cy", C.c_double), ("strike_rad", C.c_double), ("length", C.c_double),
+                ("n_elem", C.c_int32), ("reserved", C.c_int32)]
+
+
+class seas_medium(C.Structure):
+    _fields_ = [("mu", C.c_double), ("cs", C.c_double), ("cp", C.c_double), ("beta", C.c_double)]
+
+
+class seas_hparams(C.Structure):
+    _fields_ = [("leaf", C.c_int32), ("q_w", C.c_int32), ("eta_h", C.c_double), ("aca_tol", C.c_double),
+                ("eta_tmin", C.c_double), ("eta_tmax", C.c_double), ("eta_w", C.c_double),
+                ("max_steps", C.c_int32), ("precision", C.c_int32), ("flags", C.c_int32), ("max_block", C.c_int32)]
+
+
+class seas_net_info(C.Structure):
+    _fields_ = [("dt", C.c_double), ("n_faults", C.c_int32), ("n_elem", C.c_int32)]
+
+
+class seas_op_stats(C.Structure):
+    _fields_ = [("n_blocks_near", C.c_int64), ("n_blocks_far", C.c_int64), ("n_slices_dense", C.c_int64),
+                ("n_slices_lowrank", C.c_int64), ("n_slices_zero", C.c_int64), ("bytes_interaction", C.c_int64),
+                ("bytes_dense_causal", C.c_int64), ("compression_ratio", C.c_double), ("bytes_self", C.c_int64),
+                ("max_rank", C.c_int32), ("ring_depth", C.c_int32), ("mean_rank", C.c_double),
+                ("build_seconds", C.c_double), ("n_tasks", C.c_int64)]
+
+
+class seas_timing(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5), ("interaction_bytes", C.c_int64),
+                ("steps", C.c_int64)]
+
+
+KERNEL_CLASSES = ["push", "fft_forward", "modeconv", "interaction", "ifft_assemble"]
+
+_lib = None
+_VP, _PP = C.c_void_p, C.POINTER(C.c_void_p)
+_SIGS = {
+    "seas_create": ([_PP, C.c_int, C.c_size_t, _VP], C.c_int),
+    "seas_build_network": ([_VP, C.POINTER(seas_fault), C.c_int, C.POINTER(seas_medium), _PP], C.c_int),
+    "seas_net_get_info": ([_VP, C.POINTER(seas_net_info)], C.c_int),
+    "seas_net_get_elements": ([_VP, _VP, _VP], C.c_int),
+    "seas_build_hmatrix": ([_VP, C.POINTER(seas_hparams), _PP, C.POINTER(seas_op_stats)], C.c_int),
+    "seas_op_pair_windows": ([_VP, _VP], C.c_int),
+    "seas_op_mode_windows": ([_VP, _VP], C.c_int),
+    "seas_scenario_create": ([_VP, C.c_int, _PP], C.c_int),
+    "seas_push_slip_rate": ([_VP, _VP, _VP, C.c_int, C.c_int], C.c_int),
+    "seas_stress_step": ([_VP, _VP, _VP, _VP, C.c_int], C.c_int),
+    "seas_scenario_step": ([_VP, C.POINTER(C.c_int64)], C.c_int),
+    "seas_sync": ([_VP], C.c_int),
+    "seas_strerror": ([C.c_int], C.c_char_p),
+    "seas_last_error": ([], C.c_char_p),
+    "seas_scenario_save": ([_VP, C.c_char_p], C.c_int),
+    "seas_scenario_load": ([_VP, C.c_char_p, _PP], C.c_int),
+    "seas_destroy_scn": ([_VP], C.c_int),
+    "seas_destroy_op": ([_VP], C.c_int),
+    "seas_destroy_net": ([_VP], C.c_int),
+    "seas_destroy_ctx": ([_VP], C.c_int),
+    "seas_plan_hmatrix": ([C.POINTER(seas_fault), C.c_int, C.POINTER(seas_medium), C.POINTER(seas_hparams), _VP,
+                           C.c_int64, C.POINTER(C.c_int64), _VP, _VP, C.POINTER(C.c_double)], C.c_int),
+    "seas_scenario_set_timing": ([_VP, C.c_int], C.c_int),
+    "seas_scenario_get_timing": ([_VP, C.POINTER(seas_timing)], C.c_int),
+    "seas_op_step_bytes": ([_VP, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
+}
+
+
+def lib(path: str = LIB_PATH) -> C.CDLL:
+    """Loads libseas.so (built in-tree by ``paper_2603_00383_gb300.build``).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise FileNotFoundError(f"{path} is missing: build it with `python -m paper_2603_00383_gb300.build`")
+        L = C.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status < 0:
+        raise SeasError(status, f"{seas_strerror(status)}: {lib().seas_last_error().decode()}")
+
+
+class Handle:
+    """An opaque library handle plus the sizes the binding needs to check buffers."""
+
+    def __init__(self, ptr, kind, **meta):
+        self.ptr = ptr
+        self.kind = kind
+        self.__dict__.update(meta)
+
+
+def _buf(x, n: int, what: str):
+    """(pointer, mem) of a float64 buffer of n elements: NumPy -> host, CUDA tensor -> device."""
+    if x is None:
+        return None, None
+    if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
+        if str(x.dtype) != "torch.float64" or not x.is_contiguous() or x.numel() != n:
+            raise ValueError(f"{what}: need a contiguous float64 CUDA tensor of {n} elements")
+        return C.c_void_p(x.data_ptr()), SEAS_MEM_DEVICE
+    if not isinstance(x, np.ndarray) or x.dtype != np.float64 or not x.flags.c_contiguous or x.size != n:
+        raise ValueError(f"{what}: need a C-contiguous float64 array of {n} elements")
+    return C.c_void_p(x.ctypes.data), SEAS_MEM_HOST
+
+
+def seas_strerror(status: int) -> str:
+    return lib().seas_strerror(status).decode()
+
+
+def seas_last_error() -> str:
+    return lib().seas_last_error().decode()
+
+
+def seas_create(device: int = 0, hbm_budget: int = 0, stream=None) -> Handle:
+    h = C.c_void_p()
+    st = stream if stream is None or isinstance(stream, int) else int(stream)
+    _check(lib().seas_create(C.byref(h), device, hbm_budget, C.c_void_p(st) if st else None))
+    return Handle(h, "ctx", device=device)
+
+
+def _faults(faults):
+    faults = np.asarray(faults, dtype=np.float64)
+    arr = (seas_fault * len(faults))()
+    for i, (cx, cy, s, L, n) in enumerate(faults):
+        arr[i] = seas_fault(cx, cy, s, L, int(n), 0)
+    return faults, arr
+
+
+def _hparams(hp: dict) -> seas_hparams:
+    return seas_hparams(int(hp.get("leaf", 32)), int(hp.get("q_w", 0)), float(hp.get("eta_h", 2.0)),
+                        float(hp.get("aca_tol", 1e-6)), float(hp.get("eta_tmin", 0.01)),
+                        float(hp.get("eta_tmax", 0.01)), float(hp.get("eta_w", 1.5)), int(hp["max_steps"]),
+                        int(hp.get("precision", SEAS_PREC_FP64)), int(hp.get("flags", 0)),
+                        int(hp.get("max_block", 0)))
+
+
+def seas_plan_hmatrix(faults, mu: float, cs: float, cp: float, beta: float, hp: dict) -> dict:
+    """Host-only plan: blocks [n, 6] (r0, p, c0, q, far, first_lag), pair_last [F, F], mode windows per fault, dt."""
+    faults, arr = _faults(faults)
+    med = seas_medium(mu, cs, cp, beta)
+    p = _hparams(hp)
+    nb = C.c_int64()
+    dt = C.c_double()
+    F = len(faults)
+    _check(lib().seas_plan_hmatrix(arr, F, C.byref(med), C.byref(p), None, 0, C.byref(nb), None, None,
+                                   C.byref(dt)))
+    blocks = np.zeros((nb.value, 6), dtype=np.int32)
+    last = np.zeros((F, F), dtype=np.int32)
+    nel = [int(n) for n in faults[:, 4]]
+    mw = np.zeros(sum(n + 1 for n in nel), dtype=np.int32)
+    _check(lib().seas_plan_hmatrix(arr, F, C.byref(med), C.byref(p), blocks.ctypes.data, nb.value, C.byref(nb),
+                                   last.ctypes.data, mw.ctypes.data, C.byref(dt)))
+    windows, o = [], 0
+    for n in nel:
+        windows.append(mw[o:o + n + 1].copy())
+        o += n + 1
+    return dict(blocks=blocks, pair_last=last, mode_windows=windows, dt=dt.value)
+
+
+def seas_build_network(ctx: Handle, faults, mu: float, cs: float, cp: float = 6000.0, beta: float = 0.5) -> Handle:
+    """faults: [F, 5] array (cx, cy, strike_rad, length, n_elem)."""
+    faults, arr = _faults(faults)
+    med = seas_medium(mu, cs, cp, beta)
+    h = C.c_void_p()
+    _check(lib().seas_build_network(ctx.ptr, arr, len(faults), C.byref(med), C.byref(h)))
+    info = seas_net_info()
+    _check(lib().seas_net_get_info(h, C.byref(info)))
+    return Handle(h, "net", ctx=ctx, N=info.n_elem, F=info.n_faults, dt=info.dt,
+                  n_elem=[int(n) for n in faults[:, 4]])
+
+
+def seas_net_get_info(net: Handle) -> dict:
+    info = seas_net_info()
+    _check(lib().seas_net_get_info(net.ptr, C.byref(info)))
+    return dict(dt=info.dt, n_faults=info.n_faults, n_elem=info.n_elem)
+
+
+def seas_net_get_elements(net: Handle):
+    c = np.zeros((net.N, 2))
+    n = np.zeros((net.N, 2))
+    _check(lib().seas_net_get_elements(net.ptr, c.ctypes.data, n.ctypes.data))
+    return c, n
+
+
+def seas_build_hmatrix(net: Handle, hp: dict):
+    """hp keys: leaf, q_w, eta_h, aca_tol, eta_tmin, eta_tmax, eta_w, max_steps, precision, flags, max_block.
+    Returns (op handle, stats dict)."""
+    p = _hparams(hp)
+    h = C.c_void_p()
+    st = seas_op_stats()
+    _check(lib().seas_build_hmatrix(net.ptr, C.byref(p), C.byref(h), C.byref(st)))
+    stats = {name: getattr(st, name) for name, _ in seas_op_stats._fields_}
+    return Handle(h, "op", net=net, N=net.N, F=net.F, max_steps=p.max_steps), stats
+
+
+def seas_op_pair_windows(op: Handle) -> np.ndarray:
+    out = np.zeros((op.F, op.F), dtype=np.int32)
+    _check(lib().seas_op_pair_windows(op.ptr, out.ctypes.data))
+    return out
+
+
+def seas_op_mode_windows(op: Handle) -> list:
+    n_elem = op.net.n_elem
+    flat = np.zeros(sum(n + 1 for n in n_elem), dtype=np.int32)
+    _check(lib().seas_op_mode_windows(op.ptr, flat.ctypes.data))
+    out, o = [], 0
+    for n in n_elem:
+        out.append(flat[o:o + n + 1].copy())
+        o += n + 1
+    return out
+
+
+def seas_scenario_create(op: Handle, batch: int = 1) -> Handle:
+    h = C.c_void_p()
+    _check(lib().seas_scenario_create(op.ptr, batch, C.byref(h)))
+    return Handle(h, "scn", op=op, N=op.N, B=batch)
+
+
+def seas_push_slip_rate(scn: Handle, V, slip=None, replace_last: bool = False):
+    n = scn.B * scn.N
+    pv, mem = _buf(V, n, "V")
+    ps, mem_s = _buf(slip, n, "slip")
+    if slip is not None and mem_s != mem:
+        raise ValueError("V and slip must live in the same memory")
+    _check(lib().seas_push_slip_rate(scn.ptr, pv, ps, mem, 1 if replace_last else 0))
+
+
+def seas_stress_step(scn: Handle, tau, sigma_n=None, parts=None):
+    n = scn.B * scn.N
+    pt, mem = _buf(tau, n, "tau")
+    pn, mn = _buf(sigma_n, n, "sigma_n")
+    pp, mp = _buf(parts, 3 * n, "parts")
+    for m in (mn, mp):
+        if m is not None and m != mem:
+            raise ValueError("tau, sigma_n and parts must live in the same memory")
+    _check(lib().seas_stress_step(scn.ptr, pt, pn, pp, mem))
+
+
+def seas_scenario_step(scn: Handle) -> int:
+    n = C.c_int64()
+    _check(lib().seas_scenario_step(scn.ptr, C.byref(n)))
+    return n.value
+
+
+def seas_scenario_set_timing(scn: Handle, enable: bool = True):
+    _check(lib().seas_scenario_set_timing(scn.ptr, 1 if enable else 0))
+
+
+def seas_scenario_get_timing(scn: Handle) -> dict:
+    t = seas_timing()
+    _check(lib().seas_scenario_get_timing(scn.ptr, C.byref(t)))
+    return dict(launches={k: t.launches[i] for i, k in enumerate(KERNEL_CLASSES)},
+                ms={k: t.ms[i] for i, k in enumerate(KERNEL_CLASSES)},
+                interaction_bytes=t.interaction_bytes, steps=t.steps)
+
+
+def seas_op_step_bytes(op: Handle, step: int) -> int:
+    b = C.c_int64()
+    _check(lib().seas_op_step_bytes(op.ptr, step, C.byref(b)))
+    return b.value
+
+
+def seas_sync(ctx: Handle):
+    _check(lib().seas_sync(ctx.ptr))
+
+
+def seas_scenario_save(scn: Handle, path: str):
+    _check(lib().seas_scenario_save(scn.ptr, path.encode()))
+
+
+def seas_scenario_load(op: Handle, path: str) -> Handle:
+    h = C.c_void_p()
+    _check(lib().seas_scenario_load(op.ptr, path.encode(), C.byref(h)))
+    with open(path, "rb") as fh:
+        hdr = fh.read(24)
+    B = int(np.frombuffer(hdr[12:16], dtype=np.int32)[0])
+    return Handle(h, "scn", op=op, N=op.N, B=B)
+
+
+def _destroy(fn, h: Handle):
+    if h is not None and h.ptr:
+        _check(fn(h.ptr))
+        h.ptr = None
+
+
+def seas_destroy_scn(h: Handle):
+    _destroy(lib().seas_destroy_scn, h)
+
+
+def seas_destroy_op(h: Handle):
+    _destroy(lib().seas_destroy_op, h)
+
+
+def seas_destroy_net(h: Handle):
+    _destroy(lib().seas_destroy_net, h)
+
+
+def seas_destroy_ctx(h: Handle):
+    _destroy(lib().seas_destroy_ctx, h)
+
+
+class Session:
+    """Convenience owner of ctx -> net -> op -> scn for one workload; frees child first."""
+
+    def __init__(self, workload, batch: int = 1, device: int = 0, stream=None, hbm_budget: int = 0, **hp):
+        self.ctx = seas_create(device, hbm_budget, stream)
+        self.net = seas_build_network(self.ctx, workload.faults, workload.mu, workload.cs, workload.cp,
+                                      workload.beta)
+        params = dict(workload.hparams)
+        params.update(hp)
+        self.op, self.stats = seas_build_hmatrix(self.net, params)
+        self.scn = seas_scenario_create(self.op, batch)
+
+    def close(self):
+        for fn, h in ((seas_destroy_scn, "scn"), (seas_destroy_op, "op"), (seas_destroy_net, "net"),
+                      (seas_destroy_ctx, "ctx")):
+            if getattr(self, h, None) is not None:
+                fn(getattr(self, h))
+                setattr(self, h, None)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -202,9 +202,10 @@ def six_fault_3072(steps: int = 2000) -> Workload:
 
 
 def tiny(seed: int = 1, n_faults: int = 2, steps: int = 30) -> Workload:
-    """2..3 faults of 4..16 elements (even counts) in a 600 m box, 40 m gaps."""
+    """2..3 faults of 4..16 elements (2,3,5-smooth counts) in a 600 m box, 40 m gaps."""
     u = uniform01(seed ^ 0x71E1, np.arange(n_faults, dtype=np.uint64))
-    n_elem = [int(4 + 2 * math.floor(6 * x)) for x in u]
+    sizes = [4, 5, 6, 8, 9, 10, 12, 15, 16]
+    n_elem = [sizes[int(math.floor(len(sizes) * x))] for x in u]
     faults = place_faults(n_elem, 10.0, 600.0, 40.0, seed)
     return Workload(f"tiny{seed}", faults, steps=steps, seed=SEED + 1000 * seed,
                     hparams=_hp(leaf=4, eta_h=1.0, aca_tol=1e-8, max_steps=steps, flags=FLAG_NO_TRUNC))

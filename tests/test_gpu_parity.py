@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+Exact mode (every block dense, no truncation beyond exact causality) must match the FP64 oracle to rel-L2 <= 1e-10
+on tau and on each part (radiation damping, self, interaction) separately, so the radiation term cannot mask
+convolution errors.  Compressed modes are compared with the oracle run with the same windows (isolating the
+compression error, bounded by the per-slice ACA tolerance) and against the untruncated oracle (truncation error,
+reported).
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import seas_oracle as O
+from paper_2603_00383_gb300 import seas, synth
+
+pytestmark = pytest.mark.gpu
+
+EXACT = 1e-10
+DENSE_EXACT = dict(flags=seas.SEAS_FLAG_DENSE | seas.SEAS_FLAG_NO_TRUNC)
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+def run_host(session, V, parts=True):
+    """Pushes V[steps][B*N] through the C ABI with host buffers; returns tau and parts per step."""
+    steps, BN = V.shape
+    tau = np.zeros((steps, BN))
+    P = np.zeros((steps, 3, BN))
+    t = np.zeros(BN)
+    p = np.zeros(3 * BN)
+    for n in range(steps):
+        seas.seas_push_slip_rate(session.scn, np.ascontiguousarray(V[n]))
+        seas.seas_stress_step(session.scn, t, parts=p if parts else None)
+        tau[n] = t
+        P[n] = p.reshape(3, BN)
+    return tau, P
+
+
+@pytest.fixture(scope="module")
+def two_fault_oracle():
+    w = synth.two_fault_128()
+    net = O.network(w.faults, w.mu, w.cs)
+    V = w.slip_rate(0, 0, w.steps)
+    return w, V, O.stress_history(net, V, w.hparams)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+@pytest.mark.parametrize("mode", ["dense", "hmatrix"])
+def test_tiny_networks_match_oracle(seed, mode):
+    w = synth.tiny(seed, n_faults=2 + seed % 2, steps=160)
+    hp = DENSE_EXACT if mode == "dense" else dict(leaf=2, eta_h=0.8, aca_tol=1e-13, flags=seas.SEAS_FLAG_NO_TRUNC)
+    net = O.network(w.faults, w.mu, w.cs)
+    V = w.slip_rate(0, 0, w.steps)
+    ref = O.stress_history(net, V, dict(w.hparams, flags=seas.SEAS_FLAG_NO_TRUNC))
+    with seas.Session(w, **hp) as s:
+        tau, P = run_host(s, V)
+        if mode == "hmatrix":
+            assert s.stats["n_blocks_far"] > 0
+    assert rel(tau, ref[0]) <= EXACT
+    for k in range(3):
+        assert rel(P[:, k], ref[k + 1]) <= EXACT, ["rad", "self", "int"][k]
+
+
+def test_two_fault_128_exact_parity(two_fault_oracle):
+    """The small two-fault workload, full 400-step history, every element and step."""
+    w, V, ref = two_fault_oracle
+    with seas.Session(w) as s:
+        tau, P = run_host(s, V)
+        st = s.stats
+    assert st["n_blocks_far"] == 0 and st["n_slices_dense"] > 0
+    errs = [rel(tau, ref[0])] + [rel(P[:, k], ref[k + 1]) for k in range(3)]
+    print("two_fault_128 exact rel-L2 tau/rad/self/int:", errs)
+    assert max(errs) <= EXACT
+    np.testing.assert_allclose(P.sum(1), tau, rtol=1e-14, atol=1e-14 * np.abs(tau).max())
+
+
+def test_two_fault_128_hmatrix_error_within_aca_tolerance(two_fault_oracle):
+    """Same workload through the compressed operator (leaf 32, eta_H 2, ACA 1e-6): the self and radiation parts
+    stay exact, the interaction error is of the order of the per-slice tolerance."""
+    w, V, ref = two_fault_oracle
+    with seas.Session(w, flags=seas.SEAS_FLAG_NO_TRUNC, eta_h=2.0, leaf=32, aca_tol=1e-6) as s:
+        tau, P = run_host(s, V)
+        st = s.stats
+    assert st["n_blocks_far"] > 0
+    e_int = rel(P[:, 2], ref[3])
+    print("two_fault_128 hmatrix: compression %.1f%%, rel-L2 int %.2e tau %.2e" %
+          (st["compression_ratio"], e_int, rel(tau, ref[0])))
+    assert rel(P[:, 0], ref[1]) <= EXACT and rel(P[:, 1], ref[2]) <= EXACT
+    assert e_int <= 1e-5
+
+
+def test_six_fault_3072_full_size_sampled_rows():
+    """The paper-scale network at full size (3072 elements, 2000 steps, H-matrix leaf 32 / eta 2 / ACA 1e-6, causal
+    and spectral windows), run as the bench runs it (device-resident inputs), checked on sampled rows and steps
+    against the oracle evaluated one row at a time with the same windows."""
+    torch = pytest.importorskip("torch")
+    w = synth.six_fault_3072()
+    net = O.network(w.faults, w.mu, w.cs)
+    V = w.slip_rate(0, 0, w.steps)
+    hp = w.hparams
+    check_steps = [401, 1999]
+    rng = np.random.default_rng(7)
+    rows = np.sort(rng.choice(net.N, 6, replace=False))
+    rows0 = np.arange(0, 256, 51)                    # rows of fault 0 for the self term
+    out = {}
+    with seas.Session(w) as s:
+        Vd = torch.from_numpy(V).cuda()
+        tau = torch.zeros(net.N, dtype=torch.float64, device="cuda")
+        parts = torch.zeros(3 * net.N, dtype=torch.float64, device="cuda")
+        wins = seas.seas_op_pair_windows(s.op)
+        for n in range(w.steps):
+            seas.seas_push_slip_rate(s.scn, Vd[n])
+            seas.seas_stress_step(s.scn, tau, parts=parts)
+            if n in check_steps:
+                torch.cuda.synchronize()
+                out[n] = (tau.cpu().numpy().copy(), parts.cpu().numpy().reshape(3, net.N).copy())
+        stats = s.stats
+    _, _, last = O.pair_windows(net, hp["eta_tmin"], hp["eta_tmax"], hp["max_steps"])
+    np.testing.assert_array_equal(wins, last)
+    W0 = O.mode_windows(256, net.length[0], net.dt, net.cs, hp["eta_w"], hp["q_w"], hp["max_steps"])
+    tab0 = O.SelfTables(256, net.length[0], net.dt, net.cs, W0)
+    delta = O.slip_from_rate(V, net.dt)
+    for n in check_steps:
+        t_gpu, p_gpu = out[n]
+        f_int = O.interaction_rows(net, V, n, rows, pair_hi=last)
+        f_int_untrunc = O.interaction_rows(net, V, n, rows)
+        f_self = O.self_rows(net, 0, delta[: n + 1, :256], n, tab0, rows0)
+        e_int = rel(p_gpu[2, rows], f_int)
+        e_trunc = rel(f_int, f_int_untrunc)
+        e_self = rel(p_gpu[1, rows0], f_self)
+        print(f"six_fault_3072 step {n}: compression {stats['compression_ratio']:.1f}%, rel int {e_int:.2e} "
+              f"(truncation vs untruncated {e_trunc:.2e}), rel self {e_self:.2e}")
+        assert e_self <= EXACT
+        assert e_int <= 1e-5
+        np.testing.assert_array_equal(p_gpu[0], -(w.mu / (2 * w.cs)) * V[n])
+
+
+def test_batch_members_are_independent():
+    w = synth.tiny(5, n_faults=3, steps=60)
+    w.batch = 3
+    Vb = w.slip_rate_batch(0, w.steps).reshape(w.steps, -1)
+    with seas.Session(w, batch=3, **DENSE_EXACT) as s:
+        tb, _ = run_host(s, Vb, parts=False)
+    for b in range(3):
+        with seas.Session(w, batch=1, **DENSE_EXACT) as s:
+            ta, _ = run_host(s, np.ascontiguousarray(Vb[:, b * w.N:(b + 1) * w.N]), parts=False)
+        assert rel(tb[:, b * w.N:(b + 1) * w.N], ta) <= 1e-13
+
+
+def test_replace_last_equals_pushing_the_corrected_rate():
+    """The corrector re-push (Sec. 2.4 step 3) overwrites the last slot and slip."""
+    w = synth.tiny(6, steps=40)
+    V = w.slip_rate(0, 0, w.steps)
+    V2 = w.slip_rate(1, 0, w.steps)
+    with seas.Session(w, **DENSE_EXACT) as s:
+        ref, _ = run_host(s, V, parts=False)
+    with seas.Session(w, **DENSE_EXACT) as s:
+        out = np.zeros_like(ref)
+        t = np.zeros(w.N)
+        for n in range(w.steps):
+            seas.seas_push_slip_rate(s.scn, np.ascontiguousarray(V2[n]))
+            seas.seas_push_slip_rate(s.scn, np.ascontiguousarray(V[n]), replace_last=True)
+            seas.seas_stress_step(s.scn, t)
+            out[n] = t
+    assert rel(out, ref) <= 1e-14
+
+
+def test_caller_slip_and_device_buffers():
+    torch = pytest.importorskip("torch")
+    w = synth.tiny(2, steps=50)
+    V = w.slip_rate(0, 0, w.steps)
+    net = O.network(w.faults, w.mu, w.cs)
+    slip = O.slip_from_rate(V, net.dt) * 1.5            # any caller-supplied slip history
+    ref = O.stress_history(net, V, dict(w.hparams, flags=seas.SEAS_FLAG_NO_TRUNC), slip=slip)[0]
+    with seas.Session(w, **DENSE_EXACT) as s:
+        Vd = torch.from_numpy(V).cuda()
+        Sd = torch.from_numpy(slip).cuda()
+        t = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+        sig = torch.ones(w.N, dtype=torch.float64, device="cuda")
+        out = []
+        for n in range(w.steps):
+            seas.seas_push_slip_rate(s.scn, Vd[n], slip=Sd[n])
+            seas.seas_stress_step(s.scn, t, sigma_n=sig)
+            out.append(t.cpu().numpy().copy())
+        assert torch.all(sig == 0)
+    assert rel(np.array(out), ref) <= EXACT
+
+
+def test_checkpoint_resume_is_bitwise():
+    w = synth.tiny(3, n_faults=3, steps=80)
+    V = w.slip_rate(0, 0, w.steps)
+    with seas.Session(w, **DENSE_EXACT) as s:
+        full, _ = run_host(s, V, parts=False)
+    with seas.Session(w, **DENSE_EXACT) as s:
+        run_host(s, V[:37], parts=False)
+        with tempfile.TemporaryDirectory() as d:
+            path = os.path.join(d, "scn.ckpt")
+            seas.seas_scenario_save(s.scn, path)
+            seas.seas_destroy_scn(s.scn)
+            s.scn = seas.seas_scenario_load(s.op, path)
+        assert seas.seas_scenario_step(s.scn) == 37
+        rest, _ = run_host(s, V[37:], parts=False)
+    np.testing.assert_array_equal(rest, full[37:])
+
+
+def test_single_fault_and_single_element_networks():
+    w = synth.Workload("one", np.array([[0.0, 0.0, 0.4, 300.0, 12]]), steps=30,
+                       hparams=dict(max_steps=30, leaf=4, flags=seas.SEAS_FLAG_NO_TRUNC))
+    net = O.network(w.faults, w.mu, w.cs)
+    V = w.slip_rate(0, 0, 30)
+    ref = O.stress_history(net, V, w.hparams)[0]
+    with seas.Session(w) as s:
+        tau, _ = run_host(s, V, parts=False)
+    assert rel(tau, ref) <= EXACT
+    w1 = synth.Workload("two1", np.array([[0.0, 0.0, 0.0, 20.0, 1], [0.0, 30.0, 0.3, 20.0, 2]]), steps=40,
+                        hparams=dict(max_steps=40, leaf=1, flags=seas.SEAS_FLAG_NO_TRUNC | seas.SEAS_FLAG_DENSE))
+    net1 = O.network(w1.faults, w1.mu, w1.cs)
+    V1 = w1.slip_rate(0, 0, 40)
+    ref1 = O.stress_history(net1, V1, w1.hparams)[0]
+    with seas.Session(w1) as s:
+        tau1, _ = run_host(s, V1, parts=False)
+    assert rel(tau1, ref1) <= EXACT
+
+
+def test_error_statuses():
+    w = synth.tiny(1, steps=3)
+    with seas.Session(w, **DENSE_EXACT) as s:
+        t = np.zeros(w.N)
+        with pytest.raises(seas.SeasError) as e:
+            seas.seas_stress_step(s.scn, t)
+        assert e.value.status == seas.SEAS_ESTATE
+        with pytest.raises(seas.SeasError) as e:
+            seas.seas_push_slip_rate(s.scn, np.zeros(w.N), replace_last=True)
+        assert e.value.status == seas.SEAS_ESTATE
+        bad = np.zeros(w.N)
+        bad[1] = np.nan
+        with pytest.raises(seas.SeasError) as e:
+            seas.seas_push_slip_rate(s.scn, bad)
+        assert e.value.status == seas.SEAS_EINVAL
+        for _ in range(3):
+            seas.seas_push_slip_rate(s.scn, np.full(w.N, 1e-9))
+        with pytest.raises(seas.SeasError) as e:
+            seas.seas_push_slip_rate(s.scn, np.full(w.N, 1e-9))
+        assert e.value.status == seas.SEAS_ESTATE
+        with pytest.raises(seas.SeasError) as e:
+            seas.seas_destroy_op(s.op)
+        assert e.value.status == seas.SEAS_EBUSY
+    with pytest.raises(seas.SeasError) as e:
+        seas.Session(synth.six_fault_3072(), hbm_budget=1 << 20)
+    assert e.value.status == seas.SEAS_ENOMEM
+
+
+def test_linearity_at_full_size():
+    """A property that holds at any size: the functional is linear in the pushed history."""
+    torch = pytest.importorskip("torch")
+    w = synth.six_fault_3072(steps=60)
+    V1 = torch.from_numpy(w.slip_rate(0, 0, 60)).cuda()
+    V2 = torch.from_numpy(w.slip_rate(1, 0, 60)).cuda()
+    res = []
+    for V in (V1, V2, 2.0 * V1 - 3.0 * V2):
+        with seas.Session(w) as s:
+            t = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+            for n in range(60):
+                seas.seas_push_slip_rate(s.scn, V[n].contiguous())
+                seas.seas_stress_step(s.scn, t)
+            res.append(t.cpu().numpy().copy())
+    assert rel(res[2], 2.0 * res[0] - 3.0 * res[1]) <= 1e-12

@@ -1,0 +1,101 @@
+"""Host logic of the operator plan (no GPU): block partition of the selective H-matrix (Sec. 2.3.2), causal windows
+and spectral windows, checked against the definitions and against the oracle's own window arithmetic."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import seas_oracle as O
+from paper_2603_00383_gb300 import seas, synth
+
+
+def plan(w, **hp):
+    p = dict(w.hparams)
+    p.update(hp)
+    return seas.seas_plan_hmatrix(w.faults, w.mu, w.cs, w.cp, w.beta, p), p
+
+
+def circle(net, a, b):
+    xs = net.x[a:b]
+    c = xs.mean(0)
+    return c, np.max(np.hypot(*(xs - c).T)) + net.ds[a] / 2
+
+
+@pytest.mark.parametrize("make,hp", [(synth.six_fault_3072, {}), (synth.two_fault_128, {"flags": 0}),
+                                     (synth.two_fault_128, {}), (lambda: synth.tiny(2), {"leaf": 2, "eta_h": 1.0})])
+def test_partition_covers_every_cross_fault_pair_once(make, hp):
+    w = make()
+    pl, p = plan(w, **hp)
+    net = O.network(w.faults, w.mu, w.cs)
+    cover = np.zeros((net.N, net.N), dtype=np.int32)
+    for r0, pp, c0, q, far, _ in pl["blocks"]:
+        cover[r0:r0 + pp, c0:c0 + q] += 1
+        assert net.fault_of[r0] == net.fault_of[r0 + pp - 1] != net.fault_of[c0] == net.fault_of[c0 + q - 1]
+        ca, ra = circle(net, r0, r0 + pp)
+        cb, rb = circle(net, c0, c0 + q)
+        adm = np.hypot(*(ca - cb)) > p["eta_h"] * (ra + rb)
+        if far:
+            assert adm and not (p["flags"] & seas.SEAS_FLAG_DENSE)
+        else:
+            assert pp <= p["leaf"] and q <= p["leaf"]
+            assert not adm or (p["flags"] & seas.SEAS_FLAG_DENSE)
+    other = net.fault_of[:, None] != net.fault_of[None, :]
+    assert np.all(cover[other] == 1) and np.all(cover[~other] == 0)
+
+
+def test_dense_flag_gives_only_near_leaf_blocks():
+    w = synth.two_fault_128()
+    pl, _ = plan(w)
+    assert pl["blocks"][:, 4].sum() == 0
+    assert pl["blocks"][:, 1].max() <= 32 and pl["blocks"][:, 3].max() <= 32
+
+
+@pytest.mark.parametrize("make", [synth.two_fault_128, synth.six_fault_3072, synth.paper_two_fault])
+def test_windows_and_dt_equal_the_oracle(make):
+    w = make()
+    pl, p = plan(w, flags=0)
+    net = O.network(w.faults, w.mu, w.cs)
+    assert abs(pl["dt"] - net.dt) <= 2e-16 * net.dt
+    _, _, last = O.pair_windows(net, p["eta_tmin"], p["eta_tmax"], p["max_steps"])
+    np.testing.assert_array_equal(pl["pair_last"], last)
+    for f in range(net.F):
+        W = O.mode_windows(int(net.n_elem[f]), net.length[f], net.dt, net.cs, p["eta_w"], p["q_w"], p["max_steps"])
+        np.testing.assert_array_equal(pl["mode_windows"][f][1:], W[1:])
+
+
+def test_no_trunc_windows_are_the_whole_history():
+    w = synth.six_fault_3072(steps=700)
+    pl, p = plan(w, flags=seas.SEAS_FLAG_NO_TRUNC)
+    off = ~np.eye(w.n_faults, dtype=bool)
+    assert np.all(pl["pair_last"][off] == 699)
+    assert all(np.all(m[1:] == 699) for m in pl["mode_windows"])
+
+
+def test_block_first_lag_never_after_the_first_nonzero_lag():
+    w = synth.tiny(3, steps=200)
+    pl, _ = plan(w, leaf=2, eta_h=1.0, flags=0)
+    net = O.network(w.faults, w.mu, w.cs)
+    A = np.stack([O.interaction_slice(net, T) for T in range(200)])
+    for r0, pp, c0, q, far, first in pl["blocks"]:
+        nz = np.nonzero(np.any(A[:, r0:r0 + pp, c0:c0 + q] != 0, axis=(1, 2)))[0]
+        if len(nz):
+            assert first <= nz[0] <= first + 2
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n=7), dict(n=0), dict(length=-1.0), dict(cx=float("nan")), dict(n=7168 * 2)])
+def test_invalid_geometry_is_rejected(bad):
+    f = dict(cx=0.0, cy=0.0, strike=0.0, length=100.0, n=8)
+    f.update(bad)
+    faults = np.array([[f["cx"], f["cy"], f["strike"], f["length"], f["n"]],
+                       [0.0, 500.0, 0.0, 100.0, 8]])
+    with pytest.raises(seas.SeasError) as e:
+        seas.seas_plan_hmatrix(faults, 32e9, 3464.0, 6000.0, 0.5, dict(max_steps=10, leaf=4))
+    assert e.value.status == seas.SEAS_EINVAL
+
+
+def test_receiver_on_another_fault_is_rejected():
+    faults = np.array([[0.0, 0.0, 0.0, 100.0, 10], [5.0, 0.0, 0.0, 100.0, 10]])   # collinear, overlapping
+    with pytest.raises(seas.SeasError) as e:
+        seas.seas_plan_hmatrix(faults, 32e9, 3464.0, 6000.0, 0.5, dict(max_steps=10, leaf=4))
+    assert e.value.status == seas.SEAS_EINVAL
