@@ -99,7 +99,9 @@ typedef struct {
     int32_t max_steps;
     int32_t precision;
     int32_t flags;
-    int32_t max_block;   /* largest cluster side of an admissible block (0: 1024) */
+    int32_t max_block;   /* largest cluster side of an admissible block (0: 64; at most 1024).  Large admissible
+                          * blocks are split further: the wavefront cuts a smaller block for fewer lags, which
+                          * keeps more of its slices low rank. */
 } seas_hparams;
 
 typedef struct {
@@ -123,7 +125,9 @@ typedef struct {
 } seas_op_stats;
 
 /* Creates a context on CUDA device `device`.  hbm_budget: bytes the library may allocate (0: no limit).
- * cuda_stream: a cudaStream_t the library issues all work on (NULL: the library creates and owns one). */
+ * cuda_stream: a cudaStream_t the library issues all work on (NULL: the library creates and owns one; the
+ * legacy default stream is passed as cudaStreamLegacy, (void *)1).  Device buffers the caller passes must be
+ * ready in this stream's order. */
 seas_status seas_create(seas_ctx **ctx, int device, size_t hbm_budget, void *cuda_stream);
 
 /* Builds the discretised network (Sec. 2.3.1 "Discretization", Sec. 3.1 frames).  Rejects non-finite or
@@ -143,7 +147,7 @@ seas_status seas_op_pair_windows(const seas_op *op, int32_t *last_lag);
 /* Per fault f and mode n = 0..N_f: last lag W_f(n) of the spectral window (flattened fault after fault). */
 seas_status seas_op_mode_windows(const seas_op *op, int32_t *w);
 
-/* Allocates the history ring buffers of `batch` independent scenarios sharing the operator. */
+/* Allocates the history ring buffers of `batch` (1..8) independent scenarios sharing the operator. */
 seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **scn);
 
 /* Pushes V^n ([batch][N] float64) and optionally delta^n (same layout; NULL: integrate).  mem: where V and slip
@@ -159,6 +163,9 @@ seas_status seas_stress_step(seas_scn *scn, double *tau, double *sigma_n, double
 seas_status seas_scenario_step(const seas_scn *scn, int64_t *n);
 
 seas_status seas_sync(seas_ctx *ctx);
+/* Synchronises the scenario's stream and reports SEAS_ETIMEOUT if a bounded device wait of its kernels ran out
+ * (host-output stress_step calls check this themselves). */
+seas_status seas_scenario_check(seas_scn *scn);
 const char *seas_strerror(seas_status s);
 /* Thread-local description of the last error of this thread (empty when none). */
 const char *seas_last_error(void);
@@ -174,12 +181,12 @@ seas_status seas_plan_hmatrix(const seas_fault *faults, int n_faults, const seas
 
 /* Kernel timing on the context stream (tracing).  set_timing(1) resets and starts recording a CUDA event pair
  * around every kernel the scenario launches; get_timing synchronises and returns, per kernel class (0 push,
- * 1 forward FFT, 2 mode convolution, 3 interaction, 4 inverse FFT + assembly), the launch count and the summed
- * device time, plus the algorithmic bytes the interaction kernel streamed (stored operator slices with
- * lag <= step, summed over the timed steps). */
+ * 1 forward FFT, 2 mode convolution, 3 interaction, 4 interaction reduction, 5 inverse FFT + assembly), the
+ * launch count and the summed device time, plus the algorithmic bytes the interaction kernel streamed (stored
+ * operator slices with lag <= step, summed over the timed steps). */
 typedef struct {
-    int64_t launches[5];
-    double ms[5];
+    int64_t launches[6];
+    double ms[6];
     int64_t interaction_bytes;
     int64_t steps;
 } seas_timing;

@@ -46,9 +46,8 @@ seas_status fail(seas_status s, const char *fmt, ...) {
     } while (0)
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
-constexpr int64_t kItemBytes = 64 * 1024;     // target size of one work item
-constexpr int64_t kTaskBytes = 256 * 1024;    // target size of one task (one flush of partial sums)
 constexpr int64_t kChunkEntries = 48 << 20;   // kernel entries materialised per build chunk
+constexpr int kDefaultMaxBlock = 64;          // largest side of an admissible block when hp->max_block == 0
 
 }  // namespace
 
@@ -58,6 +57,7 @@ constexpr int64_t kChunkEntries = 48 << 20;   // kernel entries materialised per
 
 struct seas_ctx {
     int device = 0;
+    int n_sms = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t budget = 0;
@@ -191,6 +191,10 @@ struct seas_op {
     DArr<ItemDev> d_items;
     DArr<TaskDev> d_tasks;
     std::vector<int32_t> task_T;     // T_start of each task (ascending)
+    int64_t n_partial = 0;           // partial-sum slots (rows) over all tasks
+    int max_q = 0;                   // widest block (source columns)
+    DArr<int32_t> d_cover_ptr, d_cover_blk, d_blk_task_ptr, d_blk_task_T;
+    DArr<int64_t> d_blk_part;
     std::vector<int32_t> pair_last;  // [F][F]
     std::vector<int64_t> bytes_upto; // stored interaction bytes with lag <= T
     int ring = 1;
@@ -201,8 +205,10 @@ struct seas_scn {
     seas_op *op = nullptr;
     int B = 0;
     int64_t n = 0;                   // pushes so far
-    DArr<double> vring, slip, slip_prev, fint, d_V, d_slip, d_tau, d_parts;
+    DArr<double> vring, slip, slip_prev, fint, d_V, d_slip, d_tau, d_parts, partial;
     DArr<double2> dring, fmodes;
+    DArr<int> counter_err;           // [0]: interaction task counter, [1]: device error word
+    int64_t ring_stride = 0;
     DArr<FaultDev> faults;           // fault table with spectral-ring offsets for this batch size
     int64_t dring_len = 0;
     HostBuf h_in, h_out;
@@ -231,6 +237,7 @@ extern "C" seas_status seas_create(seas_ctx **out, int device, size_t hbm_budget
     auto c = std::make_unique<seas_ctx>();
     c->device = device;
     c->budget = hbm_budget;
+    CUDA_TRY(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device));
     if (cuda_stream) {
         c->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -245,6 +252,16 @@ extern "C" seas_status seas_sync(seas_ctx *c) {
     if (!c) return fail(SEAS_EINVAL, "ctx is NULL");
     CUDA_TRY(cudaSetDevice(c->device));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_scenario_check(seas_scn *s) {
+    if (!s) return fail(SEAS_EINVAL, "NULL scenario");
+    CUDA_TRY(cudaSetDevice(s->op->net->ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(s->op->net->ctx->stream));
+    int err = 0;
+    CUDA_TRY(cudaMemcpy(&err, s->counter_err.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return fail(SEAS_ETIMEOUT, "a bounded device wait ran out in the interaction kernel");
     return SEAS_OK;
 }
 
@@ -654,7 +671,7 @@ seas_status build_interaction(seas_op &op) {
     const seas_hparams &hp = op.hp;
     const bool dense = hp.flags & SEAS_FLAG_DENSE;
     const bool no_trunc = hp.flags & SEAS_FLAG_NO_TRUNC;
-    const int max_block = hp.max_block > 0 ? std::min(hp.max_block, kMaxBlockSide) : kMaxBlockSide;
+    const int max_block = hp.max_block > 0 ? std::min(hp.max_block, kMaxBlockSide) : kDefaultMaxBlock;
 
     // fault-wise cluster trees and per-pair block partitions
     std::vector<std::vector<Cluster>> trees(net.F);
@@ -684,9 +701,18 @@ seas_status build_interaction(seas_op &op) {
     SEAS_TRY(op.d_blocks.upload(c, op.blocks_h));
 
     GeomDev g{net.d_x.p, net.d_e1.p, net.d_n.p, net.d_ds.p, net.med.cs, net.dt, -net.med.mu / (2.0 * net.med.cs)};
-    std::vector<StoredSlice> stored;
     int64_t max_block_entries = 1;
-    for (auto &b : op.blocks_h) max_block_entries = std::max<int64_t>(max_block_entries, (int64_t)b.p * b.q);
+    for (auto &b : op.blocks_h) {
+        max_block_entries = std::max<int64_t>(max_block_entries, (int64_t)b.p * b.q);
+        op.max_q = std::max(op.max_q, b.q);
+    }
+    // rank-1 terms per low-rank item and rows per dense item of each block (items <= kItemBytes)
+    std::vector<int32_t> group(nb), drows(nb);
+    for (int b = 0; b < nb; ++b) {
+        const int p2 = pad2(op.blocks_h[b].p), q2 = pad2(op.blocks_h[b].q);
+        group[b] = (int32_t)std::min<int64_t>(kMaxItemRank, std::max<int64_t>(1, kItemBytes / (8 * (p2 + q2))));
+        drows[b] = (int32_t)std::max<int64_t>(1, kItemBytes / (8 * p2));
+    }
     const int64_t cap = std::max(kChunkEntries, max_block_entries);
     bool any_far = false;
     for (int b = 0; b < nb; ++b) any_far |= op.block_far[b] != 0;
@@ -698,32 +724,40 @@ seas_status build_interaction(seas_op &op) {
             SEAS_TRY(factors.alloc(c, (size_t)cap));
         }
     }
+    // Slices in block-major, lag-minor order, so that each block's slices are adjacent in the arena.
+    struct Stored {
+        int32_t block, T, k;
+        const double *data;
+        int chunk;
+    };
+    std::vector<Stored> stored;
     int64_t bytes_dense = 0, bytes_stored = 0, rank_sum = 0;
-    int32_t T = Tmin;
-    int cb = 0;                       // next block of lag T (a lag larger than one chunk spans several)
-    while (Tmax >= 0 && T <= Tmax) {
+    int cb = 0;
+    int32_t cT = nb ? lo[0] : 0;
+    auto advance = [&]() {            // next (block, lag) of the cursor
+        ++cT;
+        while (cb < nb && cT > hi[cb]) {
+            ++cb;
+            if (cb < nb) cT = lo[cb];
+        }
+    };
+    while (cb < nb && cT > hi[cb]) {
+        ++cb;
+        if (cb < nb) cT = lo[cb];
+    }
+    int chunk_id = 0;
+    while (cb < nb) {
         std::vector<SliceGen> sl;
         std::vector<int64_t> prefix;
         int64_t entries = 0;
-        bool full = false;
-        while (T <= Tmax && !full) {
-            for (; cb < nb; ++cb) {
-                if (T < lo[cb] || T > hi[cb]) continue;
-                const int64_t pq = (int64_t)op.blocks_h[cb].p * op.blocks_h[cb].q;
-                if (entries + pq > cap) {
-                    full = true;
-                    break;
-                }
-                sl.push_back(SliceGen{cb, T, op.block_far[cb], 0, entries});
-                prefix.push_back(entries);
-                entries += pq;
-            }
-            if (!full) {
-                cb = 0;
-                ++T;
-            }
+        while (cb < nb) {
+            const int64_t pq = (int64_t)op.blocks_h[cb].p * op.blocks_h[cb].q;
+            if (entries + pq > cap) break;
+            sl.push_back(SliceGen{cb, cT, op.block_far[cb], group[cb], entries});
+            prefix.push_back(entries);
+            entries += pq;
+            advance();
         }
-        if (sl.empty()) continue;
         DArr<SliceGen> d_sl;
         DArr<int64_t> d_pref, d_off;
         DArr<SliceOut> d_out;
@@ -740,91 +774,128 @@ seas_status build_interaction(seas_op &op) {
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         std::vector<int64_t> dst(sl.size());
         int64_t total = 0;
-        for (size_t s = 0; s < sl.size(); ++s) {
-            const BlockDev &b = op.blocks_h[sl[s].block];
-            dst[s] = total;
-            if (so[s].k == 0) {
+        for (size_t k = 0; k < sl.size(); ++k) {
+            const BlockDev &b = op.blocks_h[sl[k].block];
+            dst[k] = total;
+            if (so[k].k == 0) {
                 op.stats.n_slices_zero++;
                 continue;
             }
-            const int64_t pq = (int64_t)b.p * b.q;
-            bytes_dense += pq * 8;
-            const int64_t n = so[s].k < 0 ? pq : (int64_t)so[s].k * (b.p + b.q);
-            if (so[s].k < 0) op.stats.n_slices_dense++;
+            const int p2 = pad2(b.p), q2 = pad2(b.q);
+            bytes_dense += (int64_t)b.p * b.q * 8;
+            const int64_t n = so[k].k < 0 ? (int64_t)b.q * p2 : (int64_t)so[k].k * (p2 + q2);
+            if (so[k].k < 0) op.stats.n_slices_dense++;
             else {
                 op.stats.n_slices_lowrank++;
-                rank_sum += so[s].k;
-                op.stats.max_rank = std::max(op.stats.max_rank, so[s].k);
+                rank_sum += so[k].k;
+                op.stats.max_rank = std::max(op.stats.max_rank, so[k].k);
             }
             total += n;
         }
-        if (total == 0) continue;
-        auto buf = std::make_unique<DArr<double>>();
-        SEAS_TRY(buf->alloc(c, (size_t)total));
-        SEAS_TRY(d_off.upload(c, dst));
-        CUDA_TRY(launch_pack(op.d_blocks.p, d_sl.p, d_out.p, (int)sl.size(), scratch.p, factors.p, d_off.p, buf->p,
-                             c->stream));
-        CUDA_TRY(cudaStreamSynchronize(c->stream));
-        for (size_t s = 0; s < sl.size(); ++s)
-            if (so[s].k != 0) stored.push_back(StoredSlice{sl[s].block, sl[s].T, so[s].k, buf->p + dst[s]});
-        bytes_stored += total * 8;
-        op.arena.push_back(std::move(buf));
+        if (total > 0) {
+            auto buf = std::make_unique<DArr<double>>();
+            SEAS_TRY(buf->alloc(c, (size_t)total));
+            SEAS_TRY(d_off.upload(c, dst));
+            CUDA_TRY(launch_pack(op.d_blocks.p, d_sl.p, d_out.p, (int)sl.size(), scratch.p, factors.p, d_off.p,
+                                 buf->p, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            for (size_t k = 0; k < sl.size(); ++k)
+                if (so[k].k != 0) stored.push_back(Stored{sl[k].block, sl[k].T, so[k].k, buf->p + dst[k], chunk_id});
+            bytes_stored += total * 8;
+            op.arena.push_back(std::move(buf));
+        }
+        ++chunk_id;
     }
     scratch.release();
     resid.release();
     factors.release();
 
-    // work items (inner ranges of one slice) and tasks (runs of items of one block), tasks sorted by first lag
-    std::stable_sort(stored.begin(), stored.end(), [](const StoredSlice &x, const StoredSlice &y) {
-        return x.block != y.block ? x.block < y.block : x.T < y.T;
-    });
+    // Work items (<= kItemBytes, adjacent in memory) and tasks (runs of items of one block within one arena
+    // chunk, <= kTaskBytes); each task owns p partial-sum rows, the k-th task of block b at
+    // blk_part[b] + k * p.
     std::vector<ItemDev> items;
     std::vector<TaskDev> tasks;
     size_t s = 0;
     while (s < stored.size()) {
         const int blk = stored[s].block;
         const BlockDev &b = op.blocks_h[blk];
-        TaskDev task{blk, (int32_t)items.size(), 0, stored[s].T};
+        const int p2 = pad2(b.p), q2 = pad2(b.q);
+        TaskDev task{blk, (int32_t)items.size(), 0, stored[s].T, 0};
         int64_t task_bytes = 0;
+        int chunk = stored[s].chunk;
         for (; s < stored.size() && stored[s].block == blk; ++s) {
-            const StoredSlice &x = stored[s];
-            if (task_bytes >= kTaskBytes) {
+            const Stored &x = stored[s];
+            if (task_bytes >= kTaskBytes || x.chunk != chunk) {
                 task.item_end = (int32_t)items.size();
                 tasks.push_back(task);
-                task = TaskDev{blk, (int32_t)items.size(), 0, x.T};
+                task = TaskDev{blk, (int32_t)items.size(), 0, x.T, 0};
                 task_bytes = 0;
+                chunk = x.chunk;
             }
             if (x.k < 0) {
-                const int rows = (int)std::max<int64_t>(1, kItemBytes / (8 * (int64_t)b.p));
-                for (int j = 0; j < b.q; j += rows) {
-                    const int j1 = std::min(b.q, j + rows);
-                    items.push_back(ItemDev{x.T, -1, j, j1, x.data + (int64_t)j * b.p, nullptr});
+                for (int j = 0; j < b.q; j += drows[blk]) {
+                    const int j1 = std::min(b.q, j + drows[blk]);
+                    items.push_back(ItemDev{x.T, -1, j, j1, x.data + (int64_t)j * p2});
                 }
-                task_bytes += (int64_t)b.p * b.q * 8;
+                task_bytes += (int64_t)b.q * p2 * 8;
             } else {
-                const int per = (int)std::min<int64_t>(kMaxItemRank,
-                                                       std::max<int64_t>(1, kItemBytes / (8 * (int64_t)(b.p + b.q))));
-                const double *Vt = x.data, *Ut = x.data + (int64_t)x.k * b.q;
-                for (int l = 0; l < x.k; l += per) {
-                    const int l1 = std::min(x.k, l + per);
-                    items.push_back(ItemDev{x.T, l1 - l, l, l1, Vt + (int64_t)l * b.q, Ut + (int64_t)l * b.p});
+                for (int l = 0; l < x.k; l += group[blk]) {
+                    const int l1 = std::min(x.k, l + group[blk]);
+                    items.push_back(ItemDev{x.T, l1 - l, l, l1, x.data + (int64_t)l * (p2 + q2)});
                 }
-                task_bytes += (int64_t)x.k * (b.p + b.q) * 8;
+                task_bytes += (int64_t)x.k * (p2 + q2) * 8;
             }
         }
         task.item_end = (int32_t)items.size();
         tasks.push_back(task);
     }
+    // per-block task lists (in lag order) and partial-sum slots
+    std::vector<int32_t> blk_task_ptr(nb + 1, 0), blk_task_T;
+    std::vector<int64_t> blk_part(nb, 0);
+    for (const TaskDev &t : tasks) blk_task_ptr[t.block + 1]++;
+    for (int b = 0; b < nb; ++b) blk_task_ptr[b + 1] += blk_task_ptr[b];
+    blk_task_T.assign(tasks.size(), 0);
+    {
+        int64_t part = 0;
+        for (int b = 0; b < nb; ++b) {
+            blk_part[b] = part;
+            part += (int64_t)(blk_task_ptr[b + 1] - blk_task_ptr[b]) * op.blocks_h[b].p;
+        }
+        op.n_partial = part;
+        std::vector<int32_t> fill(nb, 0);
+        for (TaskDev &t : tasks) {            // tasks are in block order, lag order within a block
+            const int k = fill[t.block]++;
+            blk_task_T[blk_task_ptr[t.block] + k] = t.T_start;
+            t.part_off = blk_part[t.block] + (int64_t)k * op.blocks_h[t.block].p;
+        }
+    }
+    // receiver cover lists: for each element, the blocks whose rows contain it
+    std::vector<int32_t> cover_ptr(net.N + 1, 0), cover_blk;
+    for (int b = 0; b < nb; ++b)
+        for (int i = op.blocks_h[b].r0; i < op.blocks_h[b].r0 + op.blocks_h[b].p; ++i) cover_ptr[i + 1]++;
+    for (int i = 0; i < net.N; ++i) cover_ptr[i + 1] += cover_ptr[i];
+    cover_blk.assign(cover_ptr[net.N], 0);
+    {
+        std::vector<int32_t> fill(cover_ptr.begin(), cover_ptr.end() - 1);
+        for (int b = 0; b < nb; ++b)
+            for (int i = op.blocks_h[b].r0; i < op.blocks_h[b].r0 + op.blocks_h[b].p; ++i) cover_blk[fill[i]++] = b;
+    }
     std::stable_sort(tasks.begin(), tasks.end(), [](const TaskDev &x, const TaskDev &y) { return x.T_start < y.T_start; });
+    for (auto &t : tasks) op.task_T.push_back(t.T_start);
     op.bytes_upto.assign((size_t)op.ring, 0);
-    for (const StoredSlice &x : stored) {
+    for (const Stored &x : stored) {
         const BlockDev &b = op.blocks_h[x.block];
-        op.bytes_upto[x.T] += 8 * (x.k < 0 ? (int64_t)b.p * b.q : (int64_t)x.k * (b.p + b.q));
+        const int p2 = pad2(b.p), q2 = pad2(b.q);
+        op.bytes_upto[x.T] += 8 * (x.k < 0 ? (int64_t)b.q * p2 : (int64_t)x.k * (p2 + q2));
     }
     for (size_t T = 1; T < op.bytes_upto.size(); ++T) op.bytes_upto[T] += op.bytes_upto[T - 1];
-    for (auto &t : tasks) op.task_T.push_back(t.T_start);
     SEAS_TRY(op.d_items.upload(c, items));
     SEAS_TRY(op.d_tasks.upload(c, tasks));
+    SEAS_TRY(op.d_cover_ptr.upload(c, cover_ptr));
+    SEAS_TRY(op.d_cover_blk.upload(c, cover_blk));
+    SEAS_TRY(op.d_blk_task_ptr.upload(c, blk_task_ptr));
+    SEAS_TRY(op.d_blk_task_T.upload(c, blk_task_T));
+    SEAS_TRY(op.d_blk_part.upload(c, blk_part));
     op.stats.n_tasks = (int64_t)tasks.size();
     op.stats.bytes_interaction = bytes_stored;
     op.stats.bytes_dense_causal = bytes_dense;
@@ -876,7 +947,7 @@ extern "C" seas_status seas_plan_hmatrix(const seas_fault *faults, int n_faults,
     if (hp->max_steps < 1) return fail(SEAS_EINVAL, "max_steps must be >= 1");
     const bool dense = hp->flags & SEAS_FLAG_DENSE;
     const bool no_trunc = hp->flags & SEAS_FLAG_NO_TRUNC;
-    const int max_block = hp->max_block > 0 ? std::min(hp->max_block, kMaxBlockSide) : kMaxBlockSide;
+    const int max_block = hp->max_block > 0 ? std::min(hp->max_block, kMaxBlockSide) : kDefaultMaxBlock;
     std::vector<std::vector<Cluster>> trees(net.F);
     for (int f = 0; f < net.F; ++f) build_tree(net, f, net.off[f], net.off[f + 1], hp->leaf, trees[f]);
     std::vector<BlockDev> bl;
@@ -950,6 +1021,7 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     a.max_nf = op.max_nf;
     a.step = step;
     a.ring = op.ring;
+    a.ring_stride = s.ring_stride;
     a.dt = net.dt;
     a.rad = -net.med.mu / (2.0 * net.med.cs);
     a.faults = s.faults.p;
@@ -969,6 +1041,16 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     a.n_tasks_active =
         (int)(std::upper_bound(op.task_T.begin(), op.task_T.end(), (int32_t)std::min<int64_t>(step, INT32_MAX)) -
               op.task_T.begin());
+    a.partial = s.partial.p;
+    a.n_partial = op.n_partial;
+    a.counter = s.counter_err.p;
+    a.err = s.counter_err.p + 1;
+    a.cover_ptr = op.d_cover_ptr.p;
+    a.cover_blk = op.d_cover_blk.p;
+    a.blk_task_ptr = op.d_blk_task_ptr.p;
+    a.blk_task_T = op.d_blk_task_T.p;
+    a.blk_part = op.d_blk_part.p;
+    a.n_sms = net.ctx->n_sms > 0 ? net.ctx->n_sms : 1;
     return a;
 }
 
@@ -988,7 +1070,11 @@ seas_status scenario_alloc(seas_op *op, int batch, std::unique_ptr<seas_scn> &s)
     }
     s->dring_len = dr;
     SEAS_TRY(s->faults.upload(c, ft));
-    SEAS_TRY(s->vring.alloc(c, (size_t)(op->ring * BN)));
+    s->ring_stride = BN + (BN & 1) + 2;    // even, with room for the 16-byte round-up of history slices
+    SEAS_TRY(s->vring.alloc(c, (size_t)(op->ring * s->ring_stride)));
+    SEAS_TRY(s->partial.alloc(c, (size_t)(op->n_partial * batch)));
+    SEAS_TRY(s->counter_err.alloc(c, 2));
+    SEAS_TRY(s->counter_err.zero(c->stream));
     SEAS_TRY(s->slip.alloc(c, (size_t)BN));
     SEAS_TRY(s->slip_prev.alloc(c, (size_t)BN));
     SEAS_TRY(s->fint.alloc(c, (size_t)BN));
@@ -1011,7 +1097,10 @@ seas_status scenario_alloc(seas_op *op, int batch, std::unique_ptr<seas_scn> &s)
 extern "C" seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **out) {
     if (!op || !out) return fail(SEAS_EINVAL, "NULL argument");
     *out = nullptr;
-    if (batch < 1 || batch > 4096) return fail(SEAS_EINVAL, "batch must be in [1, 4096]");
+    if (batch < 1 || batch > kMaxBatch) return fail(SEAS_EINVAL, "batch must be in [1, %d]", kMaxBatch);
+    if ((int64_t)op->max_q * batch * 8 + 16 + kItemBytes > kStageBytes)
+        return fail(SEAS_EINVAL, "batch %d too large for blocks of %d columns (stage of %d bytes)", batch, op->max_q,
+                    kStageBytes);
     CUDA_TRY(cudaSetDevice(op->net->ctx->device));
     std::unique_ptr<seas_scn> s;
     SEAS_TRY(scenario_alloc(op, batch, s));
@@ -1024,6 +1113,14 @@ extern "C" seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **o
 
 
 namespace {
+
+// Reads the device error word (set by a bounded wait that ran out); the stream must be synchronised.
+seas_status check_device_error(seas_scn &s) {
+    int err = 0;
+    CUDA_TRY(cudaMemcpy(&err, s.counter_err.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return fail(SEAS_ETIMEOUT, "a bounded device wait ran out in the interaction kernel");
+    return SEAS_OK;
+}
 
 constexpr size_t kEventPairs = 8192;
 
@@ -1139,10 +1236,10 @@ extern "C" seas_status seas_stress_step(seas_scn *s, double *tau, double *sigma_
     StepArgs a = step_args(*s, s->n - 1);
     double *dtau = mem == SEAS_MEM_DEVICE ? tau : s->d_tau.p;
     double *dparts = parts ? (mem == SEAS_MEM_DEVICE ? parts : s->d_parts.p) : nullptr;
-    CUDA_TRY(cudaMemsetAsync(s->fint.p, 0, BN * sizeof(double), c->stream));
     SEAS_TRY(timed(*s, 2, [&] { return launch_modeconv(a, c->stream); }));
     SEAS_TRY(timed(*s, 3, [&] { return launch_interaction(a, c->stream); }));
-    SEAS_TRY(timed(*s, 4, [&] { return launch_ifft_assemble(a, dtau, dparts, c->stream); }));
+    SEAS_TRY(timed(*s, 4, [&] { return launch_reduce(a, c->stream); }));
+    SEAS_TRY(timed(*s, 5, [&] { return launch_ifft_assemble(a, dtau, dparts, c->stream); }));
     if (s->timing) {
         int64_t b = 0;
         SEAS_TRY(seas_op_step_bytes(&op, s->n - 1, &b));
@@ -1158,6 +1255,7 @@ extern "C" seas_status seas_stress_step(seas_scn *s, double *tau, double *sigma_
     if (parts)
         CUDA_TRY(cudaMemcpyAsync(hout + BN, dparts, 3 * BN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    SEAS_TRY(check_device_error(*s));
     std::memcpy(tau, hout, BN * sizeof(double));
     if (parts) std::memcpy(parts, hout + BN, 3 * BN * sizeof(double));
     if (sigma_n) std::memset(sigma_n, 0, BN * sizeof(double));
@@ -1216,7 +1314,7 @@ extern "C" seas_status seas_scenario_save(seas_scn *s, const char *path) {
     if (!fp) return fail(SEAS_EIO, "cannot open %s for writing", path);
     CkptHeader h{};
     std::memcpy(h.magic, "SEASCKP1", 8);
-    h.version = 1;
+    h.version = 2;
     h.B = s->B;
     h.N = op.net->N;
     h.F = op.net->F;
@@ -1241,7 +1339,7 @@ extern "C" seas_status seas_scenario_load(seas_op *op, const char *path, seas_sc
     FILE *fp = fopen(path, "rb");
     if (!fp) return fail(SEAS_EIO, "cannot open %s", path);
     CkptHeader h{};
-    if (fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "SEASCKP1", 8) != 0 || h.version != 1) {
+    if (fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "SEASCKP1", 8) != 0 || h.version != 2) {
         fclose(fp);
         return fail(SEAS_EIO, "%s is not a scenario checkpoint", path);
     }
@@ -1253,6 +1351,7 @@ extern "C" seas_status seas_scenario_load(seas_op *op, const char *path, seas_sc
     std::unique_ptr<seas_scn> s;
     seas_status st = scenario_alloc(op, h.B, s);
     if (st == SEAS_OK && h.dring_len != s->dring_len) st = fail(SEAS_EIO, "checkpoint spectral ring size mismatch");
+    if (st == SEAS_OK) CUDA_TRY(cudaStreamSynchronize(op->net->ctx->stream));
     if (st == SEAS_OK) st = slurp(fp, s->vring.p, s->vring.bytes());
     if (st == SEAS_OK) st = slurp(fp, s->slip.p, s->slip.bytes());
     if (st == SEAS_OK) st = slurp(fp, s->slip_prev.p, s->slip_prev.bytes());

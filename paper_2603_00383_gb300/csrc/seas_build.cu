@@ -201,8 +201,10 @@ __global__ void __launch_bounds__(kThreads) k_compress(const BlockDev *__restric
     }
 }
 
-// Copies each stored slice into the operator arena: dense -> A^T (q rows of p); low rank -> V^T (k rows of q)
-// followed by U^T (k rows of p).
+// Copies each stored slice into the operator arena, rows padded to an even number of doubles (p2 = pad2(p),
+// q2 = pad2(q)) so that every work item starts on a 16-byte boundary:
+//   dense   -> A^T, q rows of p2;
+//   lowrank -> groups of `group` rank-1 terms l0..l1-1, each group [V^T rows (q2 each)][U^T rows (p2 each)].
 __global__ void k_pack(const BlockDev *__restrict__ blocks, const SliceGen *__restrict__ slices,
                        const SliceOut *__restrict__ out, const double *__restrict__ scratch,
                        const double *__restrict__ factors, const int64_t *__restrict__ dst_off,
@@ -211,20 +213,38 @@ __global__ void k_pack(const BlockDev *__restrict__ blocks, const SliceGen *__re
     const SliceOut o = out[blockIdx.x];
     if (o.k == 0) return;
     const BlockDev b = blocks[s.block];
-    const int p = b.p, q = b.q;
+    const int p = b.p, q = b.q, p2 = pad2(p), q2 = pad2(q);
     const int64_t pq = (int64_t)p * q;
     double *d = dst + dst_off[blockIdx.x];
     if (o.k < 0) {
         const double *S = scratch + s.scratch;
-        for (int64_t e = threadIdx.x; e < pq; e += blockDim.x) d[e] = S[e];
+        const int64_t n = (int64_t)q * p2;
+        for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+            const int j = (int)(e / p2), i = (int)(e - (int64_t)j * p2);
+            d[e] = i < p ? S[(int64_t)j * p + i] : 0.0;
+        }
         return;
     }
     const int kmax = (int)((pq - 1) / (p + q));
     const double *Ut = factors + s.scratch;
     const double *Vt = factors + s.scratch + (int64_t)kmax * p;
-    const int64_t nv = (int64_t)o.k * q, nu = (int64_t)o.k * p;
-    for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) d[e] = Vt[e];
-    for (int64_t e = threadIdx.x; e < nu; e += blockDim.x) d[nv + e] = Ut[e];
+    const int64_t n = (int64_t)o.k * (p2 + q2);
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const int g = (int)(e / ((int64_t)s.group * (p2 + q2)));     // group index
+        const int l0 = g * s.group;
+        const int nl = min(s.group, o.k - l0);
+        const int64_t r = e - (int64_t)l0 * (p2 + q2);               // offset inside the group
+        double v;
+        if (r < (int64_t)nl * q2) {
+            const int l = l0 + (int)(r / q2), j = (int)(r % q2);
+            v = j < q ? Vt[(int64_t)l * q + j] : 0.0;
+        } else {
+            const int64_t r2 = r - (int64_t)nl * q2;
+            const int l = l0 + (int)(r2 / p2), i = (int)(r2 % p2);
+            v = i < p ? Ut[(int64_t)l * p + i] : 0.0;
+        }
+        d[e] = v;
+    }
 }
 
 // ------------------------------------------------------------------------------------------------------------

@@ -13,6 +13,14 @@ constexpr int kMaxStages = 16;      // radix stages of one FFT plan
 constexpr int kMaxBlockSide = 1024; // rows / columns of one H-matrix block (4 accumulator rows per thread)
 constexpr int kRowsPerThread = kMaxBlockSide / kThreads;
 constexpr int kMaxItemRank = 128;   // rank-1 terms of one low-rank work item (shared-memory z buffer)
+constexpr int kMaxBatch = 8;        // scenarios per scenario handle (one pass of the interaction kernel)
+constexpr int kItemBytes = 24 * 1024;   // largest work item (operator bytes)
+constexpr int kStageBytes = 64 * 1024;  // one shared-memory stage of the interaction pipeline
+constexpr int kStages = 3;              // stages in flight per CTA
+constexpr int kStageItems = 31;         // work items per stage
+constexpr int64_t kTaskBytes = 1 << 20; // operator bytes per task (one deterministic partial sum)
+
+__host__ __device__ inline int pad2(int n) { return n + (n & 1); }
 
 // One fault of the spectral self-effect path.
 struct FaultDev {
@@ -42,24 +50,27 @@ struct BlockDev {
     int32_t r0, p, c0, q;
 };
 
-// One unit of interaction work: the inner range [i0, i1) of one (block, lag) slice.
-//   dense   (k < 0): a points at rows i0..i1-1 of A^T (each p doubles): y += sum_j A^T[j][:] x_{c0+j}
-//   lowrank (k > 0): a points at rows i0..i1-1 of V^T (each q doubles), b at rows i0..i1-1 of U^T (each p
-//                    doubles): y += sum_l U^T[l][:] (V^T[l][:] . x)
+// One unit of interaction work: the inner range [i0, i1) of one (block, lag) slice, stored contiguously at `a`
+// (rows padded to an even number of doubles: p2 = pad2(p), q2 = pad2(q)):
+//   dense   (k < 0): rows i0..i1-1 of A^T, each p2 doubles:  y += sum_j A^T[j][:] x_{c0+j}
+//   lowrank (k > 0): k = i1 - i0 rows of V^T (each q2 doubles) followed by k rows of U^T (each p2 doubles):
+//                    y += sum_l U^T[l][:] (V^T[l][:] . x)
+// Consecutive items of a task are adjacent in memory.
 struct ItemDev {
     int32_t T;
     int32_t k;
     int32_t i0, i1;
     const double *a;
-    const double *b;
 };
 
-// A run of items of one block (sorted by lag) whose partial sums are flushed together.
+// A run of items of one block (sorted by lag, adjacent in memory) whose partial sums land in one slot:
+// partial[b * n_partial + part_off + row].
 struct TaskDev {
     int32_t block;
     int32_t item_begin;
     int32_t item_end;
     int32_t T_start;
+    int64_t part_off;
 };
 
 // One (block, lag) slice produced during the build.
@@ -67,7 +78,7 @@ struct SliceGen {
     int32_t block;
     int32_t T;
     int32_t far;        // 1: admissible (compress), 0: near (store dense)
-    int32_t pad;
+    int32_t group;      // rank-1 terms per stored low-rank item (packing layout)
     int64_t scratch;    // first double of its p*q entries (layout A^T: q rows of p) in the scratch buffers
 };
 
@@ -105,21 +116,32 @@ struct StepArgs {
     int max_nf;                   // largest N_f (shared memory of the FFT kernels)
     int64_t step;                 // index of the step being evaluated
     int ring;                     // slip-rate ring depth R
+    int64_t ring_stride;          // doubles per ring slot: layout [slot][element][scenario], padded to even + 2
     double dt, rad;               // rad = -mu / (2 c_s)
     const FaultDev *faults;
     const ModeDev *modes;         // modes n >= 1 of all faults
     int n_modes;
     const double *w;              // spectral weights
     const double2 *tw;            // FFT twiddles
-    double *vring;                // [R][B][N]
+    double *vring;                // [R][ring_stride]
     double *slip, *slip_prev;     // [B][N]
     double2 *dring;               // spectral rings
     double2 *fmodes;              // [B][n_modes_total]
     double *fint;                 // [B][N]
+    // interaction
     const BlockDev *blocks;
     const ItemDev *items;
     const TaskDev *tasks;
-    int n_tasks_active;
+    int n_tasks_active;           // tasks with T_start <= step (a prefix of the T_start-sorted list)
+    double *partial;              // [B][n_partial]
+    int64_t n_partial;
+    int *counter;                 // dynamic task counter (reset by the reduction)
+    int *err;                     // device error word (bounded waits that ran out)
+    // reduction: per element the blocks it receives from; per block its tasks' first lags
+    const int32_t *cover_ptr, *cover_blk;
+    const int32_t *blk_task_ptr, *blk_task_T;
+    const int64_t *blk_part;      // first partial of each block
+    int n_sms;
 };
 
 cudaError_t launch_push(const StepArgs &a, const double *V, const double *slip_in, int replace_last,
@@ -127,6 +149,7 @@ cudaError_t launch_push(const StepArgs &a, const double *V, const double *slip_i
 cudaError_t launch_fft_forward(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_reduce(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_ifft_assemble(const StepArgs &a, double *tau, double *parts, cudaStream_t s);
 
 }  // namespace seas

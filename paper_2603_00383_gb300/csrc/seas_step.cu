@@ -72,10 +72,11 @@ __global__ void k_push(StepArgs a, const double *__restrict__ V, const double *_
                        int replace_last) {
     const int64_t BN = (int64_t)a.B * a.N;
     const int slot = (int)(a.step % a.ring);
-    double *vr = a.vring + (int64_t)slot * BN;
+    double *vr = a.vring + (int64_t)slot * a.ring_stride;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < BN; e += (int64_t)gridDim.x * blockDim.x) {
         const double v = V[e];
-        vr[e] = v;
+        const int64_t b = e / a.N, i = e - b * a.N;
+        vr[i * a.B + b] = v;                           // ring layout [slot][element][scenario]
         double s;
         if (slip_in) {
             s = slip_in[e];
@@ -180,13 +181,13 @@ __global__ void __launch_bounds__(kThreads) k_ifft_assemble(StepArgs a, double *
     const double2 *z = fft_stockham(b0, b1, N, fd.radix, fd.nstages, tw, true);
     const int64_t BN = (int64_t)a.B * a.N;
     const int slot = (int)(a.step % a.ring);
-    const double *V = a.vring + (int64_t)slot * BN + (int64_t)b * a.N + fd.off;
+    const double *V = a.vring + (int64_t)slot * a.ring_stride;
     const double *fi = a.fint + (int64_t)b * a.N + fd.off;
     double *t = tau + (int64_t)b * a.N + fd.off;
     for (int m = threadIdx.x; m < N; m += blockDim.x) {
         const double2 zz = z[m >> 1];
         const double fs = 2.0 * ((m & 1) ? zz.y : zz.x);
-        const double rad = a.rad * V[m];
+        const double rad = a.rad * V[(int64_t)(fd.off + m) * a.B + b];
         const double f = fi[m];
         t[m] = rad + fs + f;
         if (parts) {
@@ -199,116 +200,384 @@ __global__ void __launch_bounds__(kThreads) k_ifft_assemble(StepArgs a, double *
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Space-time interaction (Eq. fault-to-fault_interactions_discretized) through the H-matrix stack: one CTA per
-// task (a run of work items of one block, sorted by lag); items with lag > step are not yet causal.  Thread t owns
-// receiver rows t, t + 256, ... of the block and accumulates over all items of the task; the sum is flushed with
-// one atomic add per row and scenario.  BT scenarios per CTA share every operator load.
+// Space-time interaction (Eq. fault-to-fault_interactions_discretized) through the H-matrix stack.
+//
+// Persistent kernel, one CTA per SM: warp 8 produces, warps 0-7 consume.  The producer takes tasks from a
+// dynamic counter (tasks with T_start <= step form a prefix of the task list), packs consecutive causal items
+// (lag <= step) of the task into a shared-memory stage and issues one 1-D bulk copy (cp.async.bulk) for their
+// operator bytes plus one per item for the slip-rate history slice x^{step - T} it multiplies (taken from the
+// ring row, start rounded down to 16 bytes).  Each stage completes on an mbarrier (transaction bytes); consumers
+// release it on a second mbarrier.  Consumer thread t owns receiver row t mod P (P = 32, 64, 128 or 256) in
+// group t / P; groups split the inner dimension, and the task's partial sum is written, reduced over the groups
+// in a fixed order, to its own slot of the partial buffer.  No atomics: the result is bitwise reproducible.
+// Every wait is bounded; a wait that runs out sets the error word and the CTA stops.
 // ------------------------------------------------------------------------------------------------------------
-template <int BT>
-__global__ void __launch_bounds__(kThreads) k_interaction(StepArgs a) {
-    extern __shared__ double sh[];
-    double *xs = sh;                                  // [BT][kMaxBlockSide]
-    double *zs = sh + BT * kMaxBlockSide;             // [BT][kMaxItemRank]
-    const TaskDev task = a.tasks[blockIdx.x];
-    const BlockDev blk = a.blocks[task.block];
-    const int b0 = blockIdx.y * BT;
-    const int p = blk.p, q = blk.q;
-    const int64_t BN = (int64_t)a.B * a.N;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double acc[kRowsPerThread][BT];
-#pragma unroll
-    for (int s = 0; s < kRowsPerThread; ++s)
-#pragma unroll
-        for (int bb = 0; bb < BT; ++bb) acc[s][bb] = 0.0;
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumers = kConsumerWarps * 32;
+constexpr int kInterThreads = kConsumers + 32;
+constexpr uint32_t kSpinLimit = 1u << 22;
 
-    for (int it = task.item_begin; it < task.item_end; ++it) {
-        const ItemDev item = a.items[it];
-        if (item.T > a.step) break;
-        const int slot = (int)((a.step - item.T) % a.ring);
-        const double *vsrc = a.vring + (int64_t)slot * BN + blk.c0;
-        const int j0 = item.k < 0 ? item.i0 : 0;
-        const int j1 = item.k < 0 ? item.i1 : q;
+struct StageItem {
+    int32_t T, k, i0, i1;
+    int32_t data_off, x_off;     // byte offsets in the stage (x_off already includes the 16-byte round-down)
+};
+
+struct StageInfo {
+    int32_t task;                // -1: no more work
+    int32_t n;                   // items in the stage
+    int32_t flush;               // last stage of the task
+    int32_t p, q, r0, c0;
+    int64_t part_off;
+    StageItem it[kStageItems];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile(
+        "{\n"
+        " .reg .b64 st;\n"
+        " mbarrier.arrive.shared::cta.b64 st, [%0];\n"
+        "}\n" ::"r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "{\n"
+        " .reg .b64 st;\n"
+        " mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n"
+        "}\n" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false (and the error word set) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicExch(err, 1);
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
+
+template <int BT>
+__global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *stage_mem = smem_raw;                                            // kStages x kStageBytes
+    StageInfo *info = reinterpret_cast<StageInfo *>(smem_raw + kStages * kStageBytes);
+    double *zs = reinterpret_cast<double *>(info + kStages);                          // [kMaxItemRank][BT]
+    double *red = zs + kMaxItemRank * BT;                                             // [kConsumers][BT]
+    uint64_t *full = reinterpret_cast<uint64_t *>(red + kConsumers * BT);
+    uint64_t *empty = full + kStages;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kConsumerWarps) {
+        // ------------------------------------------------------------------ producer warp
+        int task = -1, it = 0, ie = 0;
+        TaskDev td{};
+        BlockDev bd{};
+        for (int g = 0;; ++g) {
+            const int slot = g % kStages;
+            if (g >= kStages && !mbar_wait(&empty[slot], ((g / kStages) - 1) & 1, a.err)) return;
+            if (it >= ie) {                        // next task
+                int t = 0;
+                if (lane == 0) t = atomicAdd(a.counter, 1);
+                t = __shfl_sync(0xffffffffu, t, 0);
+                if (t >= a.n_tasks_active) {
+                    if (lane == 0) {
+                        info[slot].task = -1;
+                        mbar_arrive(&full[slot]);
+                    }
+                    return;
+                }
+                task = t;
+                td = a.tasks[t];
+                bd = a.blocks[td.block];
+                it = td.item_begin;
+                ie = td.item_end;
+            }
+            // lane k looks at item it + k
+            const int idx = it + lane;
+            ItemDev item{};
+            bool valid = idx < ie;
+            if (valid) {
+                item = a.items[idx];
+                valid = item.T <= a.step;
+            }
+            const int p2 = pad2(bd.p), q2 = pad2(bd.q);
+            int data_bytes = 0, x_bytes = 0;
+            int64_t xs_start = 0;
+            if (valid) {
+                const int rows = item.i1 - item.i0;
+                data_bytes = 8 * rows * (item.k < 0 ? p2 : p2 + q2);
+                const int e0 = bd.c0 + (item.k < 0 ? item.i0 : 0);
+                const int e1 = bd.c0 + (item.k < 0 ? item.i1 : bd.q);
+                const int64_t s0 = (int64_t)e0 * a.B, s1 = (int64_t)e1 * a.B;
+                xs_start = s0 & ~(int64_t)1;
+                x_bytes = 8 * (int)(((s1 + 1) & ~(int64_t)1) - xs_start);
+            }
+            // items in the stage: the longest prefix of valid lanes (at most kStageItems) whose bytes fit
+            const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+            const int nvalid = __ffs(~vmask) - 1 < 0 ? 32 : __ffs(~vmask) - 1;      // leading run of valid lanes
+            int incl = data_bytes + x_bytes;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const unsigned fit = __ballot_sync(0xffffffffu, lane < nvalid && lane < kStageItems && incl <= kStageBytes);
+            const int n = __ffs(~fit) - 1 < 0 ? 32 : __ffs(~fit) - 1;
+            // data bytes of the n items (they are adjacent) and the x area offsets after them
+            int dincl = data_bytes;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, dincl, o);
+                if (lane >= o) dincl += v;
+            }
+            const int total_data = n > 0 ? __shfl_sync(0xffffffffu, dincl, n > 0 ? n - 1 : 0) : 0;
+            int xincl = lane < n ? x_bytes : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, xincl, o);
+                if (lane >= o) xincl += v;
+            }
+            const int total_x = __shfl_sync(0xffffffffu, xincl, 31);
+            // the task is finished when the next item is missing or not yet causal
+            const bool next_valid = __shfl_sync(0xffffffffu, (int)valid, n < 32 ? n : 31) != 0 && n < 32;
+            StageInfo *si = &info[slot];
+            if (lane == 0) {
+                si->task = task;
+                si->n = n;
+                si->flush = next_valid ? 0 : 1;
+                si->p = bd.p;
+                si->q = bd.q;
+                si->r0 = bd.r0;
+                si->c0 = bd.c0;
+                si->part_off = td.part_off;
+            }
+            const int data_off = dincl - data_bytes;
+            const int x_off = total_data + xincl - (lane < n ? x_bytes : 0);
+            if (lane < n) {
+                si->it[lane] = StageItem{item.T, item.k, item.i0, item.i1, data_off, x_off};
+            }
+            __syncwarp();
+            unsigned char *dst = stage_mem + (size_t)slot * kStageBytes;
+            if (lane == 0) mbar_arrive_tx(&full[slot], (uint32_t)(total_data + total_x));
+            __syncwarp();
+            if (n > 0) {
+                // lane 0 holds item `it`, the first of the n adjacent items
+                if (lane == 0 && total_data > 0) bulk_g2s(dst, item.a, (uint32_t)total_data, &full[slot]);
+                if (lane < n) {
+                    const int slot_v = (int)((a.step - item.T) % a.ring);
+                    const double *src = a.vring + (int64_t)slot_v * a.ring_stride + xs_start;
+                    bulk_g2s(dst + x_off, src, (uint32_t)x_bytes, &full[slot]);
+                }
+            }
+            it += n;
+            if (!next_valid) it = ie;              // remaining items are not causal yet: task done
+        }
+    }
+
+    // ---------------------------------------------------------------------- consumer warps
+    const int t = threadIdx.x;
+    int cur = -1, P = 32, G = 8, row = 0, grp = 0, nrow_thr = 1;
+    double acc[kRowsPerThread][BT];
+    for (int g = 0;; ++g) {
+        const int slot = g % kStages;
+        if (!mbar_wait(&full[slot], (g / kStages) & 1, a.err)) return;
+        const StageInfo &si = info[slot];
+        const int task = si.task;
+        if (task < 0) break;
+        const int p = si.p, q = si.q, p2 = pad2(p), q2 = pad2(q);
+        if (task != cur) {
+            cur = task;
+            P = p <= 32 ? 32 : p <= 64 ? 64 : p <= 128 ? 128 : 256;
+            G = kConsumers / P;
+            row = t % P;
+            grp = t / P;
+            nrow_thr = (p + P - 1) / P;
 #pragma unroll
-        for (int bb = 0; bb < BT; ++bb) {
-            if (b0 + bb < a.B) {
-                for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x)
-                    xs[bb * kMaxBlockSide + j] = vsrc[(int64_t)(b0 + bb) * a.N + j];
+            for (int s = 0; s < kRowsPerThread; ++s)
+#pragma unroll
+                for (int bb = 0; bb < BT; ++bb) acc[s][bb] = 0.0;
+        }
+        const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
+        const int n = si.n;
+        for (int k = 0; k < n; ++k) {
+            const StageItem itm = si.it[k];
+            const double *d = reinterpret_cast<const double *>(base + itm.data_off);
+            const double *x = reinterpret_cast<const double *>(base + itm.x_off);
+            const int e0 = si.c0 + (itm.k < 0 ? itm.i0 : 0);
+            x += ((int64_t)e0 * a.B) & 1;                 // undo the 16-byte round-down
+            const int rows = itm.i1 - itm.i0;
+            if (itm.k < 0) {
+                for (int j = grp; j < rows; j += G) {
+                    const double *ar = d + (int64_t)j * p2;
+                    double xv[BT];
+#pragma unroll
+                    for (int bb = 0; bb < BT; ++bb) xv[bb] = x[j * a.B + (bb < a.B ? bb : 0)];
+#pragma unroll
+                    for (int s = 0; s < kRowsPerThread; ++s) {
+                        if (s < nrow_thr) {
+                            const int i = row + s * P;
+                            if (i < p) {
+                                const double v = ar[i];
+#pragma unroll
+                                for (int bb = 0; bb < BT; ++bb) acc[s][bb] += v * xv[bb];
+                            }
+                        }
+                    }
+                }
             } else {
-                for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) xs[bb * kMaxBlockSide + j] = 0.0;
-            }
-        }
-        __syncthreads();
-        if (item.k < 0) {
-            const double *rows = item.a;
-#pragma unroll 4
-            for (int j = j0; j < j1; ++j) {
-                const double *row = rows + (int64_t)(j - j0) * p;
+                const double *Vt = d;
+                const double *Ut = d + (int64_t)rows * q2;
+                for (int l = warp; l < rows; l += kConsumerWarps) {
+                    const double *vr = Vt + (int64_t)l * q2;
+                    double z[BT];
 #pragma unroll
-                for (int s = 0; s < kRowsPerThread; ++s) {
-                    const int i = threadIdx.x + s * kThreads;
-                    if (i < p) {
-                        const double v = row[i];
+                    for (int bb = 0; bb < BT; ++bb) z[bb] = 0.0;
+                    for (int j = lane; j < q; j += 32) {
+                        const double v = vr[j];
 #pragma unroll
-                        for (int bb = 0; bb < BT; ++bb) acc[s][bb] += v * xs[bb * kMaxBlockSide + j];
+                        for (int bb = 0; bb < BT; ++bb) z[bb] += v * x[j * a.B + (bb < a.B ? bb : 0)];
+                    }
+#pragma unroll
+                    for (int bb = 0; bb < BT; ++bb) {
+                        for (int o = 16; o > 0; o >>= 1) z[bb] += __shfl_xor_sync(0xffffffffu, z[bb], o);
+                        if (lane == 0) zs[l * BT + bb] = z[bb];
                     }
                 }
-            }
-        } else {
-            const int nl = item.i1 - item.i0;
-            for (int l = warp; l < nl; l += kThreads / 32) {
-                const double *row = item.a + (int64_t)l * q;
-                double z[BT];
+                consumer_sync();
+                for (int l = grp; l < rows; l += G) {
+                    const double *ur = Ut + (int64_t)l * p2;
 #pragma unroll
-                for (int bb = 0; bb < BT; ++bb) z[bb] = 0.0;
-                for (int j = lane; j < q; j += 32) {
-                    const double v = row[j];
+                    for (int s = 0; s < kRowsPerThread; ++s) {
+                        if (s < nrow_thr) {
+                            const int i = row + s * P;
+                            if (i < p) {
+                                const double v = ur[i];
 #pragma unroll
-                    for (int bb = 0; bb < BT; ++bb) z[bb] += v * xs[bb * kMaxBlockSide + j];
-                }
-#pragma unroll
-                for (int bb = 0; bb < BT; ++bb) {
-                    for (int o = 16; o > 0; o >>= 1) z[bb] += __shfl_xor_sync(0xffffffffu, z[bb], o);
-                    if (lane == 0) zs[bb * kMaxItemRank + l] = z[bb];
-                }
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int l = 0; l < nl; ++l) {
-                const double *row = item.b + (int64_t)l * p;
-#pragma unroll
-                for (int s = 0; s < kRowsPerThread; ++s) {
-                    const int i = threadIdx.x + s * kThreads;
-                    if (i < p) {
-                        const double v = row[i];
-#pragma unroll
-                        for (int bb = 0; bb < BT; ++bb) acc[s][bb] += v * zs[bb * kMaxItemRank + l];
+                                for (int bb = 0; bb < BT; ++bb) acc[s][bb] += v * zs[l * BT + bb];
+                            }
+                        }
                     }
                 }
+                consumer_sync();
             }
         }
-        __syncthreads();
+        const bool flush = si.flush != 0;
+        const int64_t part_off = si.part_off;
+        consumer_sync();                                   // every consumer is done with the stage
+        if (t == 0) mbar_arrive(&empty[slot]);
+        if (flush) {
+            if (G == 1) {
+#pragma unroll
+                for (int s = 0; s < kRowsPerThread; ++s) {
+                    const int i = row + s * P;
+                    if (s < nrow_thr && i < p)
+#pragma unroll
+                        for (int bb = 0; bb < BT; ++bb)
+                            if (bb < a.B) a.partial[(int64_t)bb * a.n_partial + part_off + i] = acc[s][bb];
+                }
+            } else {
+#pragma unroll
+                for (int bb = 0; bb < BT; ++bb) red[t * BT + bb] = acc[0][bb];
+                consumer_sync();
+                if (grp == 0 && row < p) {
+#pragma unroll
+                    for (int bb = 0; bb < BT; ++bb) {
+                        double sum = 0.0;
+                        for (int gg = 0; gg < G; ++gg) sum += red[(gg * P + row) * BT + bb];
+                        if (bb < a.B) a.partial[(int64_t)bb * a.n_partial + part_off + row] = sum;
+                    }
+                }
+                consumer_sync();
+            }
+            cur = -1;
+        }
+    }
+}
+
+// f_int[b][e] = sum over the blocks that element e receives from, and over their causal tasks, of the tasks'
+// partial sums; one warp per element, fixed order (lane k takes tasks k, k + 32, ...; then a fixed tree).
+// Also resets the task counter for the next step.
+__global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
+    const int64_t e = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.counter = 0;
+    if (e >= a.N) return;
+    double sum[kMaxBatch];
+#pragma unroll
+    for (int bb = 0; bb < kMaxBatch; ++bb) sum[bb] = 0.0;
+    for (int c = a.cover_ptr[e]; c < a.cover_ptr[e + 1]; ++c) {
+        const int blk = a.cover_blk[c];
+        const BlockDev bd = a.blocks[blk];
+        const int t0 = a.blk_task_ptr[blk], t1 = a.blk_task_ptr[blk + 1];
+        int lo = t0, hi = t1;                               // causal tasks: T_start <= step
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (a.blk_task_T[mid] <= a.step) lo = mid + 1; else hi = mid;
+        }
+        const int64_t base = a.blk_part[blk] + (e - bd.r0);
+        for (int k = lane; k < lo - t0; k += 32) {
+            const int64_t o = base + (int64_t)k * bd.p;
+#pragma unroll
+            for (int bb = 0; bb < kMaxBatch; ++bb)
+                if (bb < a.B) sum[bb] += a.partial[(int64_t)bb * a.n_partial + o];
+        }
     }
 #pragma unroll
-    for (int s = 0; s < kRowsPerThread; ++s) {
-        const int i = threadIdx.x + s * kThreads;
-        if (i < p) {
-#pragma unroll
-            for (int bb = 0; bb < BT; ++bb)
-                if (b0 + bb < a.B) atomicAdd(a.fint + (int64_t)(b0 + bb) * a.N + blk.r0 + i, acc[s][bb]);
+    for (int bb = 0; bb < kMaxBatch; ++bb) {
+        if (bb < a.B) {
+            double v = sum[bb];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) a.fint[(int64_t)bb * a.N + e] = v;
         }
     }
 }
 
 template <int BT>
 cudaError_t launch_interaction_bt(const StepArgs &a, cudaStream_t s) {
-    const size_t smem = (size_t)BT * (kMaxBlockSide + kMaxItemRank) * sizeof(double);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_interaction<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    dim3 grid(a.n_tasks_active, (a.B + BT - 1) / BT);
-    k_interaction<BT><<<grid, kThreads, smem, s>>>(a);
+    const size_t smem = (size_t)kStages * kStageBytes + kStages * sizeof(StageInfo) +
+                        (size_t)(kMaxItemRank + kConsumers) * BT * sizeof(double) + 2 * kStages * sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(k_interaction<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = a.n_tasks_active < a.n_sms ? a.n_tasks_active : a.n_sms;
+    k_interaction<BT><<<grid, kInterThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -345,10 +614,16 @@ cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s) {
 
 cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s) {
     if (a.n_tasks_active <= 0) return cudaSuccess;
-    if (a.B >= 8) return launch_interaction_bt<8>(a, s);
-    if (a.B >= 4) return launch_interaction_bt<4>(a, s);
-    if (a.B >= 2) return launch_interaction_bt<2>(a, s);
+    if (a.B > 4) return launch_interaction_bt<8>(a, s);
+    if (a.B > 2) return launch_interaction_bt<4>(a, s);
+    if (a.B > 1) return launch_interaction_bt<2>(a, s);
     return launch_interaction_bt<1>(a, s);
+}
+
+cudaError_t launch_reduce(const StepArgs &a, cudaStream_t s) {
+    const int grid = (a.N + kThreads / 32 - 1) / (kThreads / 32);
+    k_reduce<<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ifft_assemble(const StepArgs &a, double *tau, double *parts, cudaStream_t s) {

@@ -26,7 +26,7 @@ EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_
             "seas_stress_step", "seas_scenario_step", "seas_sync", "seas_strerror", "seas_last_error",
             "seas_scenario_save", "seas_scenario_load", "seas_destroy_scn", "seas_destroy_op", "seas_destroy_net",
             "seas_destroy_ctx", "seas_plan_hmatrix", "seas_scenario_set_timing", "seas_scenario_get_timing",
-            "seas_op_step_bytes"]
+            "seas_op_step_bytes", "seas_scenario_check"]
 
 
 class SeasError(RuntimeError):
@@ -63,11 +63,11 @@ class seas_op_stats(C.Structure):
 
 
 class seas_timing(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5), ("interaction_bytes", C.c_int64),
+    _fields_ = [("launches", C.c_int64 * 6), ("ms", C.c_double * 6), ("interaction_bytes", C.c_int64),
                 ("steps", C.c_int64)]
 
 
-KERNEL_CLASSES = ["push", "fft_forward", "modeconv", "interaction", "ifft_assemble"]
+KERNEL_CLASSES = ["push", "fft_forward", "modeconv", "interaction", "reduce", "ifft_assemble"]
 
 _lib = None
 _VP, _PP = C.c_void_p, C.POINTER(C.c_void_p)
@@ -97,6 +97,7 @@ _SIGS = {
     "seas_scenario_set_timing": ([_VP, C.c_int], C.c_int),
     "seas_scenario_get_timing": ([_VP, C.POINTER(seas_timing)], C.c_int),
     "seas_op_step_bytes": ([_VP, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
+    "seas_scenario_check": ([_VP], C.c_int),
 }
 
 
@@ -150,9 +151,20 @@ def seas_last_error() -> str:
     return lib().seas_last_error().decode()
 
 
+CUDA_STREAM_LEGACY = 1     # cudaStreamLegacy: the legacy default stream
+
+
+def stream_handle(stream) -> int:
+    """A cudaStream_t value for the library from a torch stream (or raw handle); the legacy default stream, whose
+    handle is 0, becomes cudaStreamLegacy."""
+    h = stream if isinstance(stream, int) else int(stream.cuda_stream)
+    return h if h != 0 else CUDA_STREAM_LEGACY
+
+
 def seas_create(device: int = 0, hbm_budget: int = 0, stream=None) -> Handle:
+    """stream: None (the library owns a stream), a raw cudaStream_t value, or a torch.cuda.Stream."""
     h = C.c_void_p()
-    st = stream if stream is None or isinstance(stream, int) else int(stream)
+    st = None if stream is None else stream_handle(stream)
     _check(lib().seas_create(C.byref(h), device, hbm_budget, C.c_void_p(st) if st else None))
     return Handle(h, "ctx", device=device)
 
@@ -299,6 +311,10 @@ def seas_op_step_bytes(op: Handle, step: int) -> int:
     return b.value
 
 
+def seas_scenario_check(scn: Handle):
+    _check(lib().seas_scenario_check(scn.ptr))
+
+
 def seas_sync(ctx: Handle):
     _check(lib().seas_sync(ctx.ptr))
 
@@ -339,9 +355,16 @@ def seas_destroy_ctx(h: Handle):
 
 
 class Session:
-    """Convenience owner of ctx -> net -> op -> scn for one workload; frees child first."""
+    """Convenience owner of ctx -> net -> op -> scn for one workload; frees child first.  Without an explicit
+    stream the library works on torch's current stream of `device` when torch is loaded (so that tensors the
+    caller passes are ordered with the library's kernels), else on a stream of its own."""
 
     def __init__(self, workload, batch: int = 1, device: int = 0, stream=None, hbm_budget: int = 0, **hp):
+        if stream is None:
+            import sys
+            torch = sys.modules.get("torch")
+            if torch is not None and torch.cuda.is_available():
+                stream = torch.cuda.current_stream(device)
         self.ctx = seas_create(device, hbm_budget, stream)
         self.net = seas_build_network(self.ctx, workload.faults, workload.mu, workload.cs, workload.cp,
                                       workload.beta)
