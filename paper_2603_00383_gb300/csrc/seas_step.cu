@@ -20,44 +20,65 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 // tw[k] = e^{-2 pi i k / N}; the inverse (unnormalised) uses conjugate twiddles.  Returns the buffer holding the
 // result.  All threads of the CTA must call it.
 // ------------------------------------------------------------------------------------------------------------
+template <int R>
+__device__ __forceinline__ void fft_stage(const double2 *__restrict__ src, double2 *__restrict__ dst, int N, int Ns,
+                                          const double2 *__restrict__ tw, bool inverse) {
+    const int NR = N / R;
+    const int tstride = N / (Ns * R);
+    // R-point DFT constants W_R^m, m < R (conjugated for the inverse)
+    double2 wr[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        double2 w = tw[m * NR];
+        wr[m] = inverse ? cconj(w) : w;
+    }
+    for (int j = threadIdx.x; j < NR; j += blockDim.x) {
+        const int k = j % Ns;
+        double2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            double2 x = src[j + r * NR];
+            if (r > 0) {
+                double2 w = tw[k * r * tstride];
+                x = cmul(x, inverse ? cconj(w) : w);
+            }
+            v[r] = x;
+        }
+        const int d = (j / Ns) * Ns * R + k;
+        if (R == 2) {
+            dst[d] = cadd(v[0], v[1]);
+            dst[d + Ns] = csub(v[0], v[1]);
+        } else if (R == 4) {
+            // W_4 = -i (forward), +i (inverse)
+            const double2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+            const double2 b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
+            const double2 jb1 = inverse ? make_double2(-b1.y, b1.x) : make_double2(b1.y, -b1.x);
+            dst[d] = cadd(a0, b0);
+            dst[d + Ns] = cadd(a1, jb1);
+            dst[d + 2 * Ns] = csub(a0, b0);
+            dst[d + 3 * Ns] = csub(a1, jb1);
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                double2 acc = v[0];
+#pragma unroll
+                for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], wr[(r * t) % R]));
+                dst[d + t * Ns] = acc;
+            }
+        }
+    }
+}
+
 __device__ double2 *fft_stockham(double2 *src, double2 *dst, int N, const int *radix, int nstages,
                                  const double2 *__restrict__ tw, bool inverse) {
     int Ns = 1;
     for (int st = 0; st < nstages; ++st) {
         const int R = radix[st];
-        const int NR = N / R;
-        const int tstride = N / (Ns * R);
-        for (int j = threadIdx.x; j < NR; j += blockDim.x) {
-            const int k = j % Ns;
-            double2 v[5];
-#pragma unroll
-            for (int r = 0; r < 5; ++r) {
-                if (r < R) {
-                    double2 x = src[j + r * NR];
-                    if (r > 0) {
-                        double2 w = tw[k * r * tstride];
-                        if (inverse) w = cconj(w);
-                        x = cmul(x, w);
-                    }
-                    v[r] = x;
-                }
-            }
-            const int d = (j / Ns) * Ns * R + k;
-#pragma unroll
-            for (int t = 0; t < 5; ++t) {
-                if (t < R) {
-                    double2 acc = v[0];
-#pragma unroll
-                    for (int r = 1; r < 5; ++r) {
-                        if (r < R) {
-                            double2 w = tw[((r * t) % R) * NR];
-                            if (inverse) w = cconj(w);
-                            acc = cadd(acc, cmul(v[r], w));
-                        }
-                    }
-                    dst[d + t * Ns] = acc;
-                }
-            }
+        switch (R) {
+            case 2: fft_stage<2>(src, dst, N, Ns, tw, inverse); break;
+            case 3: fft_stage<3>(src, dst, N, Ns, tw, inverse); break;
+            case 4: fft_stage<4>(src, dst, N, Ns, tw, inverse); break;
+            default: fft_stage<5>(src, dst, N, Ns, tw, inverse); break;
         }
         __syncthreads();
         double2 *tmp = src;
@@ -95,7 +116,7 @@ __global__ void k_push(StepArgs a, const double *__restrict__ V, const double *_
 // O_k = (Z_k - conj Z_{N-k})/(2i).  One CTA per (fault, scenario); D^n goes to ring slot n mod R_f.
 __global__ void __launch_bounds__(kThreads) k_fft_forward(StepArgs a) {
     extern __shared__ double2 smem[];
-    const FaultDev fd = a.faults[blockIdx.x];
+    const FaultDev &fd = a.faults[blockIdx.x];
     const int b = blockIdx.y;
     const int N = fd.nf;
     double2 *b0 = smem, *b1 = smem + N;
@@ -162,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) k_modeconv(StepArgs a) {
 __global__ void __launch_bounds__(kThreads) k_ifft_assemble(StepArgs a, double *__restrict__ tau,
                                                             double *__restrict__ parts) {
     extern __shared__ double2 smem[];
-    const FaultDev fd = a.faults[blockIdx.x];
+    const FaultDev &fd = a.faults[blockIdx.x];
     const int b = blockIdx.y;
     const int N = fd.nf;
     double2 *b0 = smem, *b1 = smem + N;
@@ -216,6 +237,7 @@ constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kInterThreads = kConsumers + 32;
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kMaxStageRanks = 256;     // rank-1 terms of all low-rank items of one stage (z buffer)
 
 struct StageItem {
     int32_t T, k, i0, i1;
@@ -293,8 +315,8 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *stage_mem = smem_raw;                                            // kStages x kStageBytes
     StageInfo *info = reinterpret_cast<StageInfo *>(smem_raw + kStages * kStageBytes);
-    double *zs = reinterpret_cast<double *>(info + kStages);                          // [kMaxItemRank][BT]
-    double *red = zs + kMaxItemRank * BT;                                             // [kConsumers][BT]
+    double *zs = reinterpret_cast<double *>(info + kStages);                          // [kMaxStageRanks][BT]
+    double *red = zs + kMaxStageRanks * BT;                                           // [kConsumers][BT]
     uint64_t *full = reinterpret_cast<uint64_t *>(red + kConsumers * BT);
     uint64_t *empty = full + kStages;
 
@@ -357,11 +379,17 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             const unsigned vmask = __ballot_sync(0xffffffffu, valid);
             const int nvalid = __ffs(~vmask) - 1 < 0 ? 32 : __ffs(~vmask) - 1;      // leading run of valid lanes
             int incl = data_bytes + x_bytes;
+            int rincl = valid && item.k > 0 ? item.i1 - item.i0 : 0;
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
+                const int r = __shfl_up_sync(0xffffffffu, rincl, o);
+                if (lane >= o) {
+                    incl += v;
+                    rincl += r;
+                }
             }
-            const unsigned fit = __ballot_sync(0xffffffffu, lane < nvalid && lane < kStageItems && incl <= kStageBytes);
+            const unsigned fit = __ballot_sync(0xffffffffu, lane < nvalid && lane < kStageItems &&
+                                                                incl <= kStageBytes && rincl <= kMaxStageRanks);
             const int n = __ffs(~fit) - 1 < 0 ? 32 : __ffs(~fit) - 1;
             // data bytes of the n items (they are adjacent) and the x area offsets after them
             int dincl = data_bytes;
@@ -413,6 +441,9 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     }
 
     // ---------------------------------------------------------------------- consumer warps
+    // Per stage: phase A computes every V^T x dot product of the stage's low-rank items (lane groups of
+    // L = 8, 16 or 32 lanes per rank row), one barrier, phase B runs every row update of the stage
+    // (rows of A^T times x_j, rows of U^T times z_l) with no barrier between items.
     const int t = threadIdx.x;
     int cur = -1, P = 32, G = 8, row = 0, grp = 0, nrow_thr = 1;
     double acc[kRowsPerThread][BT];
@@ -437,71 +468,94 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         }
         const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
         const int n = si.n;
-        for (int k = 0; k < n; ++k) {
-            const StageItem itm = si.it[k];
-            const double *d = reinterpret_cast<const double *>(base + itm.data_off);
-            const double *x = reinterpret_cast<const double *>(base + itm.x_off);
-            const int e0 = si.c0 + (itm.k < 0 ? itm.i0 : 0);
-            x += ((int64_t)e0 * a.B) & 1;                 // undo the 16-byte round-down
-            const int rows = itm.i1 - itm.i0;
-            if (itm.k < 0) {
-                for (int j = grp; j < rows; j += G) {
-                    const double *ar = d + (int64_t)j * p2;
-                    double xv[BT];
-#pragma unroll
-                    for (int bb = 0; bb < BT; ++bb) xv[bb] = x[j * a.B + (bb < a.B ? bb : 0)];
-#pragma unroll
-                    for (int s = 0; s < kRowsPerThread; ++s) {
-                        if (s < nrow_thr) {
-                            const int i = row + s * P;
-                            if (i < p) {
-                                const double v = ar[i];
-#pragma unroll
-                                for (int bb = 0; bb < BT; ++bb) acc[s][bb] += v * xv[bb];
-                            }
-                        }
-                    }
-                }
-            } else {
-                const double *Vt = d;
-                const double *Ut = d + (int64_t)rows * q2;
-                for (int l = warp; l < rows; l += kConsumerWarps) {
+        // phase A: z for every rank row of the stage; zs index = running rank count over the stage's items
+        const int L = q <= 64 ? 8 : q <= 128 ? 16 : 32;
+        const int sub = lane / L, subs = 32 / L, sl = lane % L;
+        bool any_lr = false;
+        {
+            int zbase = 0;
+            for (int k = 0; k < n; ++k) {
+                const StageItem itm = si.it[k];
+                if (itm.k < 0) continue;
+                any_lr = true;
+                const int rows = itm.i1 - itm.i0;
+                const double *Vt = reinterpret_cast<const double *>(base + itm.data_off);
+                const double *x = reinterpret_cast<const double *>(base + itm.x_off) + (((int64_t)si.c0 * a.B) & 1);
+                for (int l = warp * subs + sub; l < rows; l += kConsumerWarps * subs) {
                     const double *vr = Vt + (int64_t)l * q2;
                     double z[BT];
 #pragma unroll
                     for (int bb = 0; bb < BT; ++bb) z[bb] = 0.0;
-                    for (int j = lane; j < q; j += 32) {
+                    for (int j = sl; j < q; j += L) {
                         const double v = vr[j];
 #pragma unroll
                         for (int bb = 0; bb < BT; ++bb) z[bb] += v * x[j * a.B + (bb < a.B ? bb : 0)];
                     }
 #pragma unroll
                     for (int bb = 0; bb < BT; ++bb) {
-                        for (int o = 16; o > 0; o >>= 1) z[bb] += __shfl_xor_sync(0xffffffffu, z[bb], o);
-                        if (lane == 0) zs[l * BT + bb] = z[bb];
+                        for (int o = L / 2; o > 0; o >>= 1) z[bb] += __shfl_xor_sync(0xffffffffu, z[bb], o, L);
+                        if (sl == 0) zs[(zbase + l) * BT + bb] = z[bb];
                     }
                 }
-                consumer_sync();
-                for (int l = grp; l < rows; l += G) {
-                    const double *ur = Ut + (int64_t)l * p2;
+                zbase += rows;
+            }
+        }
+        if (any_lr) consumer_sync();
+        // phase B: row updates
+        {
+            int zbase = 0;
+            for (int k = 0; k < n; ++k) {
+                const StageItem itm = si.it[k];
+                const double *d = reinterpret_cast<const double *>(base + itm.data_off);
+                const int rows = itm.i1 - itm.i0;
+                if (itm.k < 0) {
+                    const double *x = reinterpret_cast<const double *>(base + itm.x_off) +
+                                      (((int64_t)(si.c0 + itm.i0) * a.B) & 1);
+#pragma unroll 4
+                    for (int j = grp; j < rows; j += G) {
+                        const double *ar = d + (int64_t)j * p2;
+                        double xv[BT];
 #pragma unroll
-                    for (int s = 0; s < kRowsPerThread; ++s) {
-                        if (s < nrow_thr) {
-                            const int i = row + s * P;
-                            if (i < p) {
-                                const double v = ur[i];
+                        for (int bb = 0; bb < BT; ++bb) xv[bb] = x[j * a.B + (bb < a.B ? bb : 0)];
 #pragma unroll
-                                for (int bb = 0; bb < BT; ++bb) acc[s][bb] += v * zs[l * BT + bb];
+                        for (int s = 0; s < kRowsPerThread; ++s) {
+                            if (s < nrow_thr) {
+                                const int i = row + s * P;
+                                if (i < p) {
+                                    const double v = ar[i];
+#pragma unroll
+                                    for (int bb = 0; bb < BT; ++bb) acc[s][bb] += v * xv[bb];
+                                }
                             }
                         }
                     }
+                } else {
+                    const double *Ut = d + (int64_t)rows * q2;
+#pragma unroll 4
+                    for (int l = grp; l < rows; l += G) {
+                        const double *ur = Ut + (int64_t)l * p2;
+                        double zv[BT];
+#pragma unroll
+                        for (int bb = 0; bb < BT; ++bb) zv[bb] = zs[(zbase + l) * BT + bb];
+#pragma unroll
+                        for (int s = 0; s < kRowsPerThread; ++s) {
+                            if (s < nrow_thr) {
+                                const int i = row + s * P;
+                                if (i < p) {
+                                    const double v = ur[i];
+#pragma unroll
+                                    for (int bb = 0; bb < BT; ++bb) acc[s][bb] += v * zv[bb];
+                                }
+                            }
+                        }
+                    }
+                    zbase += rows;
                 }
-                consumer_sync();
             }
         }
         const bool flush = si.flush != 0;
         const int64_t part_off = si.part_off;
-        consumer_sync();                                   // every consumer is done with the stage
+        consumer_sync();                                   // every consumer is done with the stage (and zs)
         if (t == 0) mbar_arrive(&empty[slot]);
         if (flush) {
             if (G == 1) {
@@ -533,8 +587,8 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
 }
 
 // f_int[b][e] = sum over the blocks that element e receives from, and over their causal tasks, of the tasks'
-// partial sums; one warp per element, fixed order (lane k takes tasks k, k + 32, ...; then a fixed tree).
-// Also resets the task counter for the next step.
+// partial sums; one warp per element, lane c takes covering blocks c, c + 32, ... (its tasks in lag order), then
+// a fixed tree: the summation order never depends on timing.  Also resets the task counter for the next step.
 __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
     const int64_t e = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -543,7 +597,8 @@ __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
     double sum[kMaxBatch];
 #pragma unroll
     for (int bb = 0; bb < kMaxBatch; ++bb) sum[bb] = 0.0;
-    for (int c = a.cover_ptr[e]; c < a.cover_ptr[e + 1]; ++c) {
+    const int c1 = a.cover_ptr[e + 1];
+    for (int c = a.cover_ptr[e] + lane; c < c1; c += 32) {
         const int blk = a.cover_blk[c];
         const BlockDev bd = a.blocks[blk];
         const int t0 = a.blk_task_ptr[blk], t1 = a.blk_task_ptr[blk + 1];
@@ -553,7 +608,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
             if (a.blk_task_T[mid] <= a.step) lo = mid + 1; else hi = mid;
         }
         const int64_t base = a.blk_part[blk] + (e - bd.r0);
-        for (int k = lane; k < lo - t0; k += 32) {
+        for (int k = 0; k < lo - t0; ++k) {
             const int64_t o = base + (int64_t)k * bd.p;
 #pragma unroll
             for (int bb = 0; bb < kMaxBatch; ++bb)
@@ -573,7 +628,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
 template <int BT>
 cudaError_t launch_interaction_bt(const StepArgs &a, cudaStream_t s) {
     const size_t smem = (size_t)kStages * kStageBytes + kStages * sizeof(StageInfo) +
-                        (size_t)(kMaxItemRank + kConsumers) * BT * sizeof(double) + 2 * kStages * sizeof(uint64_t);
+                        (size_t)(kMaxStageRanks + kConsumers) * BT * sizeof(double) + 2 * kStages * sizeof(uint64_t);
     cudaError_t e = cudaFuncSetAttribute(k_interaction<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = a.n_tasks_active < a.n_sms ? a.n_tasks_active : a.n_sms;
