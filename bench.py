@@ -271,6 +271,7 @@ def run_ours(args, w, K, W):
     seas.seas_scenario_set_timing(s.scn, True)
     with Clocks(local) as clk:
         total_ms, per, tau = timed_run(seas, torch, s, Vd, K, dist, device)
+    seas.seas_scenario_check(s.scn)                      # raises if a bounded device wait ran out
     timing = seas.seas_scenario_get_timing(s.scn)
     clocks = clk.summary()
     total_ms = max_over_ranks(dist, total_ms, device)
@@ -281,6 +282,7 @@ def run_ours(args, w, K, W):
     if not args.no_plain:
         p = seas.Session(wr, device=local, stream=stream.cuda_stream, flags=seas.SEAS_FLAG_DENSE, leaf=1024)
         pm, pper, ptau = timed_run(seas, torch, p, Vd, K, dist, device)
+        seas.seas_scenario_check(p.scn)
         pm = max_over_ranks(dist, pm, device)
         pv = wr.N * K * world / (pm / 1e3)
         diff = (ptau - tau).norm().item() / ptau.norm().item()

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_ifft_assemble(StepArgs a, double *
 constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kInterThreads = kConsumers + 32;
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint64_t kWaitNs = 2000000000ull;   // bound of one mbarrier wait
 constexpr int kMaxStageRanks = 256;     // rank-1 terms of all low-rank items of one stage (z buffer)
 
 struct StageItem {
@@ -292,10 +292,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; false (and the error word set) if the phase never completes.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait (about 2 s of wall time, and at most 2^30 polls); false, with the error word set, if the phase
+// never completes.  Called by one thread per role, which then shares the outcome, so an abort is uniform.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0; i < (1u << 30); ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 0 && global_ns() - t0 > kWaitNs) break;
+    }
     atomicExch(err, 1);
     return false;
 }
@@ -319,6 +330,7 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     double *red = zs + kMaxStageRanks * BT;                                           // [kConsumers][BT]
     uint64_t *full = reinterpret_cast<uint64_t *>(red + kConsumers * BT);
     uint64_t *empty = full + kStages;
+    __shared__ int sh_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -327,8 +339,10 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             mbar_init(&empty[s], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sh_flag = *(volatile int *)a.err;          // an earlier launch already failed: do nothing
     }
     __syncthreads();
+    if (sh_flag) return;
 
     if (warp == kConsumerWarps) {
         // ------------------------------------------------------------------ producer warp
@@ -337,7 +351,11 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         BlockDev bd{};
         for (int g = 0;; ++g) {
             const int slot = g % kStages;
-            if (g >= kStages && !mbar_wait(&empty[slot], ((g / kStages) - 1) & 1, a.err)) return;
+            if (g >= kStages) {
+                int ok = 1;
+                if (lane == 0) ok = mbar_wait(&empty[slot], ((g / kStages) - 1) & 1, a.err);
+                if (!__shfl_sync(0xffffffffu, ok, 0)) return;
+            }
             if (it >= ie) {                        // next task
                 int t = 0;
                 if (lane == 0) t = atomicAdd(a.counter, 1);
@@ -449,7 +467,9 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     double acc[kRowsPerThread][BT];
     for (int g = 0;; ++g) {
         const int slot = g % kStages;
-        if (!mbar_wait(&full[slot], (g / kStages) & 1, a.err)) return;
+        if (t == 0) sh_flag = mbar_wait(&full[slot], (g / kStages) & 1, a.err) ? 0 : 1;
+        consumer_sync();
+        if (sh_flag) return;
         const StageInfo &si = info[slot];
         const int task = si.task;
         if (task < 0) break;
@@ -481,20 +501,25 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 const int rows = itm.i1 - itm.i0;
                 const double *Vt = reinterpret_cast<const double *>(base + itm.data_off);
                 const double *x = reinterpret_cast<const double *>(base + itm.x_off) + (((int64_t)si.c0 * a.B) & 1);
-                for (int l = warp * subs + sub; l < rows; l += kConsumerWarps * subs) {
-                    const double *vr = Vt + (int64_t)l * q2;
+                // warp-uniform rounds: every lane of the warp reaches the shuffles
+                for (int l0 = warp * subs; l0 < rows; l0 += kConsumerWarps * subs) {
+                    const int l = l0 + sub;
+                    const bool act = l < rows;
+                    const double *vr = Vt + (int64_t)(act ? l : 0) * q2;
                     double z[BT];
 #pragma unroll
                     for (int bb = 0; bb < BT; ++bb) z[bb] = 0.0;
-                    for (int j = sl; j < q; j += L) {
-                        const double v = vr[j];
+                    if (act) {
+                        for (int j = sl; j < q; j += L) {
+                            const double v = vr[j];
 #pragma unroll
-                        for (int bb = 0; bb < BT; ++bb) z[bb] += v * x[j * a.B + (bb < a.B ? bb : 0)];
+                            for (int bb = 0; bb < BT; ++bb) z[bb] += v * x[j * a.B + (bb < a.B ? bb : 0)];
+                        }
                     }
 #pragma unroll
                     for (int bb = 0; bb < BT; ++bb) {
                         for (int o = L / 2; o > 0; o >>= 1) z[bb] += __shfl_xor_sync(0xffffffffu, z[bb], o, L);
-                        if (sl == 0) zs[(zbase + l) * BT + bb] = z[bb];
+                        if (act && sl == 0) zs[(zbase + l) * BT + bb] = z[bb];
                     }
                 }
                 zbase += rows;

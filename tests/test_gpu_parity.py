@@ -117,7 +117,7 @@ def test_six_fault_3072_full_size_sampled_rows():
             seas.seas_push_slip_rate(s.scn, Vd[n])
             seas.seas_stress_step(s.scn, tau, parts=parts)
             if n in check_steps:
-                torch.cuda.synchronize()
+                seas.seas_scenario_check(s.scn)
                 out[n] = (tau.cpu().numpy().copy(), parts.cpu().numpy().reshape(3, net.N).copy())
         stats = s.stats
     _, _, last = O.pair_windows(net, hp["eta_tmin"], hp["eta_tmax"], hp["max_steps"])
