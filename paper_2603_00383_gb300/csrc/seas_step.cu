@@ -459,11 +459,12 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     }
 
     // ---------------------------------------------------------------------- consumer warps
-    // Per stage: phase A computes every V^T x dot product of the stage's low-rank items (lane groups of
-    // L = 8, 16 or 32 lanes per rank row), one barrier, phase B runs every row update of the stage
-    // (rows of A^T times x_j, rows of U^T times z_l) with no barrier between items.
+    // Thread t owns receiver row t mod P of group t / P, with P = p (p <= 256; G = 256 / p groups) or P = 256
+    // (larger blocks, several rows per thread).  Rows of the stage's items are dealt to groups (phase B) and
+    // rank rows to lane groups (phase A) with offsets running over the whole stage, so that small items still
+    // keep every warp busy.
     const int t = threadIdx.x;
-    int cur = -1, P = 32, G = 8, row = 0, grp = 0, nrow_thr = 1;
+    int cur = -1, P = 1, G = 1, row = 0, grp = 0, nrow_thr = 1;
     double acc[kRowsPerThread][BT];
     for (int g = 0;; ++g) {
         const int slot = g % kStages;
@@ -476,10 +477,10 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         const int p = si.p, q = si.q, p2 = pad2(p), q2 = pad2(q);
         if (task != cur) {
             cur = task;
-            P = p <= 32 ? 32 : p <= 64 ? 64 : p <= 128 ? 128 : 256;
+            P = p <= kConsumers ? p : kConsumers;
             G = kConsumers / P;
             row = t % P;
-            grp = t / P;
+            grp = t / P;                               // grp == G: idle thread (256 not a multiple of p)
             nrow_thr = (p + P - 1) / P;
 #pragma unroll
             for (int s = 0; s < kRowsPerThread; ++s)
@@ -488,12 +489,13 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         }
         const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
         const int n = si.n;
-        // phase A: z for every rank row of the stage; zs index = running rank count over the stage's items
+        // phase A: V^T x for every rank row of the stage
         const int L = q <= 64 ? 8 : q <= 128 ? 16 : 32;
-        const int sub = lane / L, subs = 32 / L, sl = lane % L;
+        const int subs = 32 / L, S = kConsumerWarps * subs;
+        const int sub = lane / L, sl = lane % L, slotA = warp * subs + sub;
         bool any_lr = false;
         {
-            int zbase = 0;
+            int zoff = 0;
             for (int k = 0; k < n; ++k) {
                 const StageItem itm = si.it[k];
                 if (itm.k < 0) continue;
@@ -501,9 +503,10 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 const int rows = itm.i1 - itm.i0;
                 const double *Vt = reinterpret_cast<const double *>(base + itm.data_off);
                 const double *x = reinterpret_cast<const double *>(base + itm.x_off) + (((int64_t)si.c0 * a.B) & 1);
-                // warp-uniform rounds: every lane of the warp reaches the shuffles
-                for (int l0 = warp * subs; l0 < rows; l0 += kConsumerWarps * subs) {
-                    const int l = l0 + sub;
+                const int l0 = ((slotA - zoff) % S + S) % S;
+                const int trips = (rows + S - 1) / S;          // uniform over the warp
+                for (int r = 0; r < trips; ++r) {
+                    const int l = l0 + r * S;
                     const bool act = l < rows;
                     const double *vr = Vt + (int64_t)(act ? l : 0) * q2;
                     double z[BT];
@@ -519,25 +522,26 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
 #pragma unroll
                     for (int bb = 0; bb < BT; ++bb) {
                         for (int o = L / 2; o > 0; o >>= 1) z[bb] += __shfl_xor_sync(0xffffffffu, z[bb], o, L);
-                        if (act && sl == 0) zs[(zbase + l) * BT + bb] = z[bb];
+                        if (act && sl == 0) zs[(zoff + l) * BT + bb] = z[bb];
                     }
                 }
-                zbase += rows;
+                zoff += rows;
             }
         }
         if (any_lr) consumer_sync();
-        // phase B: row updates
-        {
-            int zbase = 0;
+        // phase B: row updates, rows dealt round-robin to the groups across all items of the stage
+        if (grp < G) {
+            int roff = 0, zoff = 0;
             for (int k = 0; k < n; ++k) {
                 const StageItem itm = si.it[k];
                 const double *d = reinterpret_cast<const double *>(base + itm.data_off);
                 const int rows = itm.i1 - itm.i0;
+                const int r0 = ((grp - roff) % G + G) % G;
                 if (itm.k < 0) {
                     const double *x = reinterpret_cast<const double *>(base + itm.x_off) +
                                       (((int64_t)(si.c0 + itm.i0) * a.B) & 1);
 #pragma unroll 4
-                    for (int j = grp; j < rows; j += G) {
+                    for (int j = r0; j < rows; j += G) {
                         const double *ar = d + (int64_t)j * p2;
                         double xv[BT];
 #pragma unroll
@@ -557,11 +561,11 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 } else {
                     const double *Ut = d + (int64_t)rows * q2;
 #pragma unroll 4
-                    for (int l = grp; l < rows; l += G) {
+                    for (int l = r0; l < rows; l += G) {
                         const double *ur = Ut + (int64_t)l * p2;
                         double zv[BT];
 #pragma unroll
-                        for (int bb = 0; bb < BT; ++bb) zv[bb] = zs[(zbase + l) * BT + bb];
+                        for (int bb = 0; bb < BT; ++bb) zv[bb] = zs[(zoff + l) * BT + bb];
 #pragma unroll
                         for (int s = 0; s < kRowsPerThread; ++s) {
                             if (s < nrow_thr) {
@@ -574,8 +578,9 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                             }
                         }
                     }
-                    zbase += rows;
+                    zoff += rows;
                 }
+                roff += rows;
             }
         }
         const bool flush = si.flush != 0;
@@ -596,7 +601,7 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
 #pragma unroll
                 for (int bb = 0; bb < BT; ++bb) red[t * BT + bb] = acc[0][bb];
                 consumer_sync();
-                if (grp == 0 && row < p) {
+                if (grp == 0) {
 #pragma unroll
                     for (int bb = 0; bb < BT; ++bb) {
                         double sum = 0.0;
