@@ -39,7 +39,14 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 dense comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=48, help="oracle element-steps in the CPU baseline")
+    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS), help="headline storage precision")
+    ap.add_argument("--no-variants", action="store_true", help="skip the other storage precisions")
     return ap.parse_args()
+
+
+# name -> (seas precision code, dtype label of the arithmetic)
+PRECISIONS = {"fp64": (0, "f64"), "df64": (3, "df64 (fp32 pairs)"), "bf16": (1, "bf16 storage, f32 compensated"),
+              "fp16s": (2, "fp16 storage with per-slice scale, f32 compensated")}
 
 
 def load_peaks():
@@ -245,22 +252,9 @@ def timed_run(seas, torch, s, Vd, K, dist, device, out_tau=None):
     return total_ms, per, tau
 
 
-def run_ours(args, w, K, W):
-    import torch
-    from paper_2603_00383_gb300 import seas
-    dist, rank, world, local = dist_setup(args)
-    device = torch.device("cuda", local)
-    torch.cuda.set_device(device)
-    stream = torch.cuda.current_stream(device)
-    wr = synth.six_fault_3072(steps=K) if w.name == "six_fault_3072" else w
-    wr.seed = synth.SEED + rank                          # independent scenario per rank
-    V = wr.slip_rate(0, 0, K)
-    Vd = torch.from_numpy(V).to(device)
-    peak, peak_kind = load_peaks()
-
-    s = seas.Session(wr, device=local, stream=stream.cuda_stream)
-    stats = s.stats
-    # warm-up on a scratch scenario, then a fresh one for the timed run
+def run_precision(seas, torch, wr, prec, Vd, K, W, dist, device, stream, peak):
+    """Builds the operator in one storage precision and times K steps; returns the measurements and tau."""
+    s = seas.Session(wr, device=device.index, stream=stream.cuda_stream, precision=prec)
     warm = seas.seas_scenario_create(s.op, 1)
     tw = torch.zeros(wr.N, dtype=torch.float64, device=device)
     for n in range(W):
@@ -269,26 +263,88 @@ def run_ours(args, w, K, W):
     torch.cuda.synchronize(device)
     seas.seas_destroy_scn(warm)
     seas.seas_scenario_set_timing(s.scn, True)
-    with Clocks(local) as clk:
+    with Clocks(device.index) as clk:
         total_ms, per, tau = timed_run(seas, torch, s, Vd, K, dist, device)
     seas.seas_scenario_check(s.scn)                      # raises if a bounded device wait ran out
     timing = seas.seas_scenario_get_timing(s.scn)
-    clocks = clk.summary()
     total_ms = max_over_ranks(dist, total_ms, device)
-    value = wr.N * K * world / (total_ms / 1e3)
+    ms = timing["ms"]
+    launches = timing["launches"]
+    n_launch = max(1, launches["interaction"])
+    inter_ms = ms["interaction"]
+    achieved = timing["interaction_bytes"] / (inter_ms / 1e3) / 1e9 if inter_ms > 0 else 0.0
+    res = {"total_ms": total_ms, "per": per, "stats": s.stats, "timing": timing, "clocks": clk.summary(),
+           "roofline": {"bound": "hbm", "kernel": "k_interaction", "achieved": achieved, "peak": peak[0],
+                        "unit": "GB/s", "frac": achieved / peak[0], "peak_kind": peak[1],
+                        "algorithmic_bytes_per_launch": timing["interaction_bytes"] / n_launch,
+                        "mean_launch_ms": inter_ms / n_launch, "dominant_by_time": max(ms, key=ms.get),
+                        "kernel_ms": ms}}
+    s_keep = s
+    return res, tau, s_keep
 
-    # plain FP64 GPU path: every fault pair one dense block, no compression, same windows
+
+def run_ours(args, w, K, W):
+    import torch
+    from paper_2603_00383_gb300 import seas
+    dist, rank, world, local = dist_setup(args)
+    wr = synth.six_fault_3072(steps=K) if w.name == "six_fault_3072" else w
+    wr.seed = synth.SEED + rank                          # independent scenario per rank
+    # CPU oracle sample first (before any GPU work in this process)
+    oracle = None
+    if rank == 0 and args.cpu_sample > 0:
+        st = OracleStepper(wr, K)
+        elems, steps = oracle_sample(wr, K, args.cpu_sample)
+        t0 = time.perf_counter()
+        ref = np.array([st.tau(i, n) for i, n in zip(elems, steps)])
+        T = time.perf_counter() - t0
+        oracle = (elems, steps, ref, T)
+        del st
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    stream = torch.cuda.current_stream(device)
+    V = wr.slip_rate(0, 0, K)
+    Vd = torch.from_numpy(V).to(device)
+    peak = load_peaks()
+
+    def err_of(tau):
+        if oracle is None:
+            return None
+        elems, steps, ref, _ = oracle
+        got = tau.cpu().numpy()[steps, elems]
+        return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    head_code, head_dtype = PRECISIONS[args.precision]
+    res, tau, s = run_precision(seas, torch, wr, head_code, Vd, K, W, dist, device, stream, peak)
+    value = wr.N * K * world / (res["total_ms"] / 1e3)
+    err = err_of(tau)
+    stats = res["stats"]
+
+    variants = {}
+    if not args.no_variants:
+        for name, (code, dtype) in PRECISIONS.items():
+            if name == args.precision:
+                continue
+            r2, tau2, s2 = run_precision(seas, torch, wr, code, Vd, K, W, dist, device, stream, peak)
+            variants[name] = {"value": wr.N * K * world / (r2["total_ms"] / 1e3), "unit": METRIC, "dtype": dtype,
+                              "ms_per_step": r2["total_ms"] / K, "p50_ms": float(np.percentile(r2["per"], 50)),
+                              "p99_ms": float(np.percentile(r2["per"], 99)), "rel_l2_vs_oracle": err_of(tau2),
+                              "rel_l2_vs_headline": (tau2 - tau).norm().item() / tau.norm().item(),
+                              "bytes_interaction": r2["stats"]["bytes_interaction"],
+                              "roofline": {k: r2["roofline"][k] for k in ("achieved", "frac", "mean_launch_ms")}}
+            s2.close()
+
+    # plain FP64 GPU path: every block dense (leaf blocks, exact windows), no compression, FP64 arithmetic
     plain = None
     if not args.no_plain:
-        p = seas.Session(wr, device=local, stream=stream.cuda_stream, flags=seas.SEAS_FLAG_DENSE, leaf=1024)
+        p = seas.Session(wr, device=local, stream=stream.cuda_stream, flags=seas.SEAS_FLAG_DENSE)
         pm, pper, ptau = timed_run(seas, torch, p, Vd, K, dist, device)
         seas.seas_scenario_check(p.scn)
         pm = max_over_ranks(dist, pm, device)
         pv = wr.N * K * world / (pm / 1e3)
-        diff = (ptau - tau).norm().item() / ptau.norm().item()
         plain = {"value": pv, "unit": METRIC, "ms_per_step": pm / K, "p50_ms": float(np.percentile(pper, 50)),
                  "p99_ms": float(np.percentile(pper, 99)), "speedup": value / pv,
-                 "bytes_interaction": p.stats["bytes_interaction"], "rel_l2_tau_vs_hmatrix": diff}
+                 "bytes_interaction": p.stats["bytes_interaction"], "rel_l2_vs_oracle": err_of(ptau),
+                 "rel_l2_tau_vs_headline": (ptau - tau).norm().item() / ptau.norm().item()}
         p.close()
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
@@ -310,51 +366,33 @@ def run_ours(args, w, K, W):
         e2e = {"value": wr.N * K * world / e2e_s, "unit": METRIC, "h2d_bytes_per_step": wr.N * 8,
                "d2h_bytes_per_step": wr.N * 8}
 
-    # roofline of the dominant kernel (the interaction): algorithmic bytes / live event time
-    ms = timing["ms"]
-    dominant = max(ms, key=ms.get)
-    inter_ms = ms["interaction"]
-    launches = timing["launches"]
-    achieved = timing["interaction_bytes"] / (inter_ms / 1e3) / 1e9 if inter_ms > 0 else 0.0
-    traffic = None
+    roofline = res["roofline"]
+    roofline["traffic"] = None
     tf = os.path.join(ROOT, "profiles", "interaction_traffic.json")
     if os.path.exists(tf):
         with open(tf) as fh:
             tr = json.load(fh)
-        if tr.get("kernel_version") == seas_kernel_version():
-            traffic = tr.get("dram_bytes_per_launch")
-    n_launch = launches["interaction"]
-    roofline = {"bound": "hbm", "kernel": "k_interaction", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": traffic, "algorithmic_bytes_per_launch": timing["interaction_bytes"] / max(1, n_launch),
-                "mean_launch_ms": inter_ms / max(1, n_launch), "dominant_by_time": dominant,
-                "kernel_ms": ms}
+        if tr.get("kernel_version") == seas_kernel_version() and tr.get("precision") == args.precision:
+            roofline["traffic"] = tr.get("dram_bytes_per_launch")
 
     line = None
     if rank == 0:
-        tau_h = tau.cpu().numpy()
         cpu = None
-        err = None
-        if args.cpu_sample > 0:
-            st = OracleStepper(wr, K)
-            elems, steps = oracle_sample(wr, K, args.cpu_sample)
-            t0 = time.perf_counter()
-            ref = np.array([st.tau(i, n) for i, n in zip(elems, steps)])
-            T = time.perf_counter() - t0
-            got = tau_h[steps, elems]
-            err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-            cpu = {"value": args.cpu_sample / T, "unit": METRIC, "cores": 1, "kind": "oracle",
+        if oracle is not None:
+            cpu = {"value": args.cpu_sample / oracle[3], "unit": METRIC, "cores": 1, "kind": "oracle",
                    "sample": f"{args.cpu_sample} element-steps (receivers of fault 0 at steps spread over the run, "
-                             f"all lags of all sources, NumPy FP64), {T:.1f} s"}
+                             f"all lags of all sources, NumPy FP64), {oracle[3]:.1f} s"}
+        launches = res["timing"]["launches"]
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": W,
-                "ms_per_step": total_ms / K, "p50_ms": float(np.percentile(per, 50)),
-                "p99_ms": float(np.percentile(per, 99)), "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(wr, K),
+                "ms_per_step": res["total_ms"] / K, "p50_ms": float(np.percentile(res["per"], 50)),
+                "p99_ms": float(np.percentile(res["per"], 99)), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": head_dtype, "data": "synthetic",
+                "config": dict(config_of(wr, K), precision=args.precision),
                 "rel_l2_vs_oracle": err, "operator": {k: stats[k] for k in (
                     "n_blocks_far", "n_blocks_near", "compression_ratio", "bytes_interaction", "mean_rank",
                     "max_rank", "build_seconds", "n_tasks")},
-                "vs_plain_fp64_gpu": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
-                "clocks": clocks, "gpu_launches": int(sum(launches.values()))}
+                "vs_plain_fp64_gpu": plain, "variants": variants, "e2e": e2e, "roofline": roofline,
+                "cpu_baseline": cpu, "clocks": res["clocks"], "gpu_launches": int(sum(launches.values()))}
     s.close()
     if dist is not None:
         dist.destroy_process_group()

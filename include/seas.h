@@ -66,8 +66,12 @@ typedef int seas_status;
 #define SEAS_FLAG_NO_TRUNC 2     /* no causal end truncation; full-length spectral windows (exact operator) */
 #define SEAS_FLAG_STATIC_TAIL 4  /* reserved: elastostatic response of truncated history (not implemented) */
 
-/* storage precision of the interaction operator */
-#define SEAS_PREC_FP64 0
+/* storage precision and arithmetic of the interaction operator */
+#define SEAS_PREC_FP64 0   /* FP64 entries, FP64 arithmetic */
+#define SEAS_PREC_BF16 1   /* bfloat16 entries, FP32 arithmetic, Kahan-compensated accumulation over the history */
+#define SEAS_PREC_FP16S 2  /* float16 entries with a per-slice scale, FP32 compensated arithmetic */
+#define SEAS_PREC_DF64 3   /* FP32 (hi, lo) pairs per entry (8 bytes, ~48-bit significand), double-float arithmetic
+                            * on the FP32 pipes; the spectral path and assembly stay FP64 in every mode */
 
 typedef struct seas_ctx seas_ctx;
 typedef struct seas_net seas_net;

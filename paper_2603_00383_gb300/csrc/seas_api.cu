@@ -187,7 +187,7 @@ struct seas_op {
     std::vector<BlockDev> blocks_h;
     std::vector<int32_t> block_far, block_pair;
     DArr<BlockDev> d_blocks;
-    std::vector<std::unique_ptr<DArr<double>>> arena;
+    std::vector<std::unique_ptr<DArr<unsigned char>>> arena;
     DArr<ItemDev> d_items;
     DArr<TaskDev> d_tasks;
     std::vector<int32_t> task_T;     // T_start of each task (ascending)
@@ -206,6 +206,7 @@ struct seas_scn {
     int B = 0;
     int64_t n = 0;                   // pushes so far
     DArr<double> vring, slip, slip_prev, fint, d_V, d_slip, d_tau, d_parts, partial;
+    DArr<unsigned char> xring;       // history in the operator's arithmetic (DF64: float2, BF16/FP16: float)
     DArr<double2> dring, fmodes;
     DArr<int> counter_err;           // [0]: interaction task counter, [1]: device error word
     int64_t ring_stride = 0;
@@ -707,11 +708,13 @@ seas_status build_interaction(seas_op &op) {
         op.max_q = std::max(op.max_q, b.q);
     }
     // rank-1 terms per low-rank item and rows per dense item of each block (items <= kItemBytes)
+    const int prec = hp.precision;
+    const int eb = elem_bytes(prec);
     std::vector<int32_t> group(nb), drows(nb);
     for (int b = 0; b < nb; ++b) {
-        const int p2 = pad2(op.blocks_h[b].p), q2 = pad2(op.blocks_h[b].q);
-        group[b] = (int32_t)std::min<int64_t>(kMaxItemRank, std::max<int64_t>(1, kItemBytes / (8 * (p2 + q2))));
-        drows[b] = (int32_t)std::max<int64_t>(1, kItemBytes / (8 * p2));
+        const int p2 = pad_row(op.blocks_h[b].p, prec), q2 = pad_row(op.blocks_h[b].q, prec);
+        group[b] = (int32_t)std::min<int64_t>(kMaxItemRank, std::max<int64_t>(1, kItemBytes / (eb * (p2 + q2))));
+        drows[b] = (int32_t)std::max<int64_t>(1, kItemBytes / (eb * p2));
     }
     const int64_t cap = std::max(kChunkEntries, max_block_entries);
     bool any_far = false;
@@ -727,7 +730,8 @@ seas_status build_interaction(seas_op &op) {
     // Slices in block-major, lag-minor order, so that each block's slices are adjacent in the arena.
     struct Stored {
         int32_t block, T, k;
-        const double *data;
+        const unsigned char *data;
+        float scale;
         int chunk;
     };
     std::vector<Stored> stored;
@@ -781,7 +785,7 @@ seas_status build_interaction(seas_op &op) {
                 op.stats.n_slices_zero++;
                 continue;
             }
-            const int p2 = pad2(b.p), q2 = pad2(b.q);
+            const int p2 = pad_row(b.p, prec), q2 = pad_row(b.q, prec);
             bytes_dense += (int64_t)b.p * b.q * 8;
             const int64_t n = so[k].k < 0 ? (int64_t)b.q * p2 : (int64_t)so[k].k * (p2 + q2);
             if (so[k].k < 0) op.stats.n_slices_dense++;
@@ -793,15 +797,21 @@ seas_status build_interaction(seas_op &op) {
             total += n;
         }
         if (total > 0) {
-            auto buf = std::make_unique<DArr<double>>();
-            SEAS_TRY(buf->alloc(c, (size_t)total));
+            auto buf = std::make_unique<DArr<unsigned char>>();
+            SEAS_TRY(buf->alloc(c, (size_t)(total * eb)));
             SEAS_TRY(d_off.upload(c, dst));
+            DArr<float> d_scale;
+            SEAS_TRY(d_scale.alloc(c, sl.size()));
             CUDA_TRY(launch_pack(op.d_blocks.p, d_sl.p, d_out.p, (int)sl.size(), scratch.p, factors.p, d_off.p,
-                                 buf->p, c->stream));
+                                 buf->p, d_scale.p, prec, c->stream));
+            std::vector<float> scl(sl.size());
+            CUDA_TRY(cudaMemcpyAsync(scl.data(), d_scale.p, scl.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                                     c->stream));
             CUDA_TRY(cudaStreamSynchronize(c->stream));
             for (size_t k = 0; k < sl.size(); ++k)
-                if (so[k].k != 0) stored.push_back(Stored{sl[k].block, sl[k].T, so[k].k, buf->p + dst[k], chunk_id});
-            bytes_stored += total * 8;
+                if (so[k].k != 0)
+                    stored.push_back(Stored{sl[k].block, sl[k].T, so[k].k, buf->p + dst[k] * eb, scl[k], chunk_id});
+            bytes_stored += total * eb;
             op.arena.push_back(std::move(buf));
         }
         ++chunk_id;
@@ -819,7 +829,7 @@ seas_status build_interaction(seas_op &op) {
     while (s < stored.size()) {
         const int blk = stored[s].block;
         const BlockDev &b = op.blocks_h[blk];
-        const int p2 = pad2(b.p), q2 = pad2(b.q);
+        const int p2 = pad_row(b.p, prec), q2 = pad_row(b.q, prec);
         TaskDev task{blk, (int32_t)items.size(), 0, stored[s].T, 0};
         int64_t task_bytes = 0;
         int chunk = stored[s].chunk;
@@ -835,15 +845,15 @@ seas_status build_interaction(seas_op &op) {
             if (x.k < 0) {
                 for (int j = 0; j < b.q; j += drows[blk]) {
                     const int j1 = std::min(b.q, j + drows[blk]);
-                    items.push_back(ItemDev{x.T, -1, j, j1, x.data + (int64_t)j * p2});
+                    items.push_back(ItemDev{x.T, -1, j, j1, x.data + (int64_t)j * p2 * eb, x.scale, 0});
                 }
-                task_bytes += (int64_t)b.q * p2 * 8;
+                task_bytes += (int64_t)b.q * p2 * eb;
             } else {
                 for (int l = 0; l < x.k; l += group[blk]) {
                     const int l1 = std::min(x.k, l + group[blk]);
-                    items.push_back(ItemDev{x.T, l1 - l, l, l1, x.data + (int64_t)l * (p2 + q2)});
+                    items.push_back(ItemDev{x.T, l1 - l, l, l1, x.data + (int64_t)l * (p2 + q2) * eb, x.scale, 0});
                 }
-                task_bytes += (int64_t)x.k * (p2 + q2) * 8;
+                task_bytes += (int64_t)x.k * (p2 + q2) * eb;
             }
         }
         task.item_end = (int32_t)items.size();
@@ -885,8 +895,8 @@ seas_status build_interaction(seas_op &op) {
     op.bytes_upto.assign((size_t)op.ring, 0);
     for (const Stored &x : stored) {
         const BlockDev &b = op.blocks_h[x.block];
-        const int p2 = pad2(b.p), q2 = pad2(b.q);
-        op.bytes_upto[x.T] += 8 * (x.k < 0 ? (int64_t)b.q * p2 : (int64_t)x.k * (p2 + q2));
+        const int p2 = pad_row(b.p, prec), q2 = pad_row(b.q, prec);
+        op.bytes_upto[x.T] += eb * (x.k < 0 ? (int64_t)b.q * p2 : (int64_t)x.k * (p2 + q2));
     }
     for (size_t T = 1; T < op.bytes_upto.size(); ++T) op.bytes_upto[T] += op.bytes_upto[T - 1];
     SEAS_TRY(op.d_items.upload(c, items));
@@ -917,7 +927,8 @@ extern "C" seas_status seas_build_hmatrix(seas_net *net, const seas_hparams *hp,
     if (!(is_fin(hp->eta_tmax) && hp->eta_tmax >= 0)) return fail(SEAS_EINVAL, "eta_tmax must be >= 0");
     if (!(is_fin(hp->eta_w) && hp->eta_w > 0)) return fail(SEAS_EINVAL, "eta_w must be > 0");
     if (hp->max_steps < 1 || hp->max_steps > (1 << 22)) return fail(SEAS_EINVAL, "max_steps in [1, 2^22]");
-    if (hp->precision != SEAS_PREC_FP64) return fail(SEAS_EINVAL, "precision %d not available", hp->precision);
+    if (hp->precision < kPrecFP64 || hp->precision > kPrecDF64)
+        return fail(SEAS_EINVAL, "precision %d not available", hp->precision);
     if (hp->flags & ~(SEAS_FLAG_DENSE | SEAS_FLAG_NO_TRUNC))
         return fail(SEAS_EINVAL, "unsupported flags 0x%x", hp->flags);
     if (hp->max_block != 0 && hp->max_block < hp->leaf) return fail(SEAS_EINVAL, "max_block must be >= leaf");
@@ -1030,6 +1041,8 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     a.w = op.d_w.p;
     a.tw = op.d_tw.p;
     a.vring = s.vring.p;
+    a.xring = s.xring.p;
+    a.prec = op.hp.precision;
     a.slip = s.slip.p;
     a.slip_prev = s.slip_prev.p;
     a.dring = s.dring.p;
@@ -1070,8 +1083,15 @@ seas_status scenario_alloc(seas_op *op, int batch, std::unique_ptr<seas_scn> &s)
     }
     s->dring_len = dr;
     SEAS_TRY(s->faults.upload(c, ft));
-    s->ring_stride = BN + (BN & 1) + 2;    // even, with room for the 16-byte round-up of history slices
+    // a multiple of 4 elements (16-byte rows for 4- and 8-byte elements) with room for the 16-byte round-up of
+    // history slices
+    s->ring_stride = (BN + 3) / 4 * 4 + 4;
     SEAS_TRY(s->vring.alloc(c, (size_t)(op->ring * s->ring_stride)));
+    if (op->hp.precision != kPrecFP64) {
+        const int xb = op->hp.precision == kPrecDF64 ? 8 : 4;
+        SEAS_TRY(s->xring.alloc(c, (size_t)(op->ring * s->ring_stride * xb)));
+        SEAS_TRY(s->xring.zero(c->stream));
+    }
     SEAS_TRY(s->partial.alloc(c, (size_t)(op->n_partial * batch)));
     SEAS_TRY(s->counter_err.alloc(c, 2));
     SEAS_TRY(s->counter_err.zero(c->stream));
@@ -1098,7 +1118,8 @@ extern "C" seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **o
     if (!op || !out) return fail(SEAS_EINVAL, "NULL argument");
     *out = nullptr;
     if (batch < 1 || batch > kMaxBatch) return fail(SEAS_EINVAL, "batch must be in [1, %d]", kMaxBatch);
-    if ((int64_t)op->max_q * batch * 8 + 16 + kItemBytes > kStageBytes)
+    const int xb = op->hp.precision == kPrecBF16 || op->hp.precision == kPrecFP16 ? 4 : 8;
+    if ((int64_t)op->max_q * batch * xb + 16 + kItemBytes > kStageBytes)
         return fail(SEAS_EINVAL, "batch %d too large for blocks of %d columns (stage of %d bytes)", batch, op->max_q,
                     kStageBytes);
     CUDA_TRY(cudaSetDevice(op->net->ctx->device));
@@ -1328,6 +1349,7 @@ extern "C" seas_status seas_scenario_save(seas_scn *s, const char *path) {
     if (st == SEAS_OK) st = dump(fp, s->slip.p, s->slip.bytes());
     if (st == SEAS_OK) st = dump(fp, s->slip_prev.p, s->slip_prev.bytes());
     if (st == SEAS_OK) st = dump(fp, s->dring.p, s->dring.bytes());
+    if (st == SEAS_OK) st = dump(fp, s->xring.p, s->xring.bytes());
     if (fclose(fp) != 0 && st == SEAS_OK) st = fail(SEAS_EIO, "close failed");
     return st;
 }
@@ -1356,6 +1378,7 @@ extern "C" seas_status seas_scenario_load(seas_op *op, const char *path, seas_sc
     if (st == SEAS_OK) st = slurp(fp, s->slip.p, s->slip.bytes());
     if (st == SEAS_OK) st = slurp(fp, s->slip_prev.p, s->slip_prev.bytes());
     if (st == SEAS_OK) st = slurp(fp, s->dring.p, s->dring.bytes());
+    if (st == SEAS_OK) st = slurp(fp, s->xring.p, s->xring.bytes());
     fclose(fp);
     if (st != SEAS_OK) return st;
     s->n = h.n;

@@ -2,6 +2,8 @@
 // pre-integrated spectral self-effect weights (Sec. 2.3.1).  Run once per seas_build_hmatrix call.
 #include "seas_internal.h"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 namespace seas {
@@ -201,33 +203,97 @@ __global__ void __launch_bounds__(kThreads) k_compress(const BlockDev *__restric
     }
 }
 
-// Copies each stored slice into the operator arena, rows padded to an even number of doubles (p2 = pad2(p),
-// q2 = pad2(q)) so that every work item starts on a 16-byte boundary:
+// Storage conversion of one operator value.
+template <int PREC> struct Store;
+template <> struct Store<kPrecFP64> {
+    using T = double;
+    __device__ static T cv(double v) { return v; }
+};
+template <> struct Store<kPrecDF64> {
+    using T = float2;                                  // (hi, lo): hi = fl32(v), lo = fl32(v - hi)
+    __device__ static T cv(double v) {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    }
+};
+template <> struct Store<kPrecBF16> {
+    using T = __nv_bfloat16;
+    __device__ static T cv(double v) { return __float2bfloat16_rn((float)v); }
+};
+template <> struct Store<kPrecFP16> {
+    using T = __half;
+    __device__ static T cv(double v) { return __float2half_rn((float)v); }
+};
+
+// Largest |v| over n values (CTA reduction).
+__device__ double block_absmax(const double *v, int64_t n, int64_t stride_rows, int row_len, double *sh) {
+    double m = 0.0;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const int64_t r = e / row_len, c = e - r * row_len;
+        m = fmax(m, fabs(v[r * stride_rows + c]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    return m;
+}
+
+// Scale putting the largest value near 2^14, inside float16's range with room to spare.
+__device__ __forceinline__ double fp16_scale(double amax) { return amax > 0.0 ? amax / 16384.0 : 1.0; }
+
+// Copies each stored slice into the operator arena in the storage precision, rows padded to 16 bytes
+// (p2 = pad_row(p), q2 = pad_row(q) elements):
 //   dense   -> A^T, q rows of p2;
 //   lowrank -> groups of `group` rank-1 terms l0..l1-1, each group [V^T rows (q2 each)][U^T rows (p2 each)].
+// FP16 stores values divided by a per-slice scale (dense: one; low rank: one for U and one for V); the scale of
+// the product (1 for the other precisions) goes to scales[slice].
+template <int PREC>
 __global__ void k_pack(const BlockDev *__restrict__ blocks, const SliceGen *__restrict__ slices,
                        const SliceOut *__restrict__ out, const double *__restrict__ scratch,
                        const double *__restrict__ factors, const int64_t *__restrict__ dst_off,
-                       double *__restrict__ dst) {
+                       typename Store<PREC>::T *__restrict__ dst, float *__restrict__ scales) {
+    using T = typename Store<PREC>::T;
+    __shared__ double sh[32];
     const SliceGen s = slices[blockIdx.x];
     const SliceOut o = out[blockIdx.x];
     if (o.k == 0) return;
     const BlockDev b = blocks[s.block];
-    const int p = b.p, q = b.q, p2 = pad2(p), q2 = pad2(q);
+    const int p = b.p, q = b.q, p2 = pad_row(p, PREC), q2 = pad_row(q, PREC);
     const int64_t pq = (int64_t)p * q;
-    double *d = dst + dst_off[blockIdx.x];
+    T *d = dst + dst_off[blockIdx.x];
     if (o.k < 0) {
         const double *S = scratch + s.scratch;
+        double inv = 1.0;
+        if (PREC == kPrecFP16) {
+            const double sc = fp16_scale(block_absmax(S, pq, p, p, sh));
+            inv = 1.0 / sc;
+            if (threadIdx.x == 0) scales[blockIdx.x] = (float)sc;
+        } else if (threadIdx.x == 0) {
+            scales[blockIdx.x] = 1.0f;
+        }
         const int64_t n = (int64_t)q * p2;
         for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
             const int j = (int)(e / p2), i = (int)(e - (int64_t)j * p2);
-            d[e] = i < p ? S[(int64_t)j * p + i] : 0.0;
+            d[e] = Store<PREC>::cv(i < p ? S[(int64_t)j * p + i] * inv : 0.0);
         }
         return;
     }
     const int kmax = (int)((pq - 1) / (p + q));
     const double *Ut = factors + s.scratch;
     const double *Vt = factors + s.scratch + (int64_t)kmax * p;
+    double inv_u = 1.0, inv_v = 1.0;
+    if (PREC == kPrecFP16) {
+        const double su = fp16_scale(block_absmax(Ut, (int64_t)o.k * p, p, p, sh));
+        const double sv = fp16_scale(block_absmax(Vt, (int64_t)o.k * q, q, q, sh));
+        inv_u = 1.0 / su;
+        inv_v = 1.0 / sv;
+        if (threadIdx.x == 0) scales[blockIdx.x] = (float)(su * sv);
+    } else if (threadIdx.x == 0) {
+        scales[blockIdx.x] = 1.0f;
+    }
     const int64_t n = (int64_t)o.k * (p2 + q2);
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
         const int g = (int)(e / ((int64_t)s.group * (p2 + q2)));     // group index
@@ -237,13 +303,13 @@ __global__ void k_pack(const BlockDev *__restrict__ blocks, const SliceGen *__re
         double v;
         if (r < (int64_t)nl * q2) {
             const int l = l0 + (int)(r / q2), j = (int)(r % q2);
-            v = j < q ? Vt[(int64_t)l * q + j] : 0.0;
+            v = j < q ? Vt[(int64_t)l * q + j] * inv_v : 0.0;
         } else {
             const int64_t r2 = r - (int64_t)nl * q2;
             const int l = l0 + (int)(r2 / p2), i = (int)(r2 % p2);
-            v = i < p ? Ut[(int64_t)l * p + i] : 0.0;
+            v = i < p ? Ut[(int64_t)l * p + i] * inv_u : 0.0;
         }
-        d[e] = v;
+        d[e] = Store<PREC>::cv(v);
     }
 }
 
@@ -333,10 +399,27 @@ cudaError_t launch_compress(const BlockDev *blocks, const SliceGen *slices, int 
 }
 
 cudaError_t launch_pack(const BlockDev *blocks, const SliceGen *slices, const SliceOut *out, int n_slices,
-                        const double *scratch, const double *factors, const int64_t *dst_off, double *dst,
-                        cudaStream_t s) {
+                        const double *scratch, const double *factors, const int64_t *dst_off, void *dst,
+                        float *scales, int prec, cudaStream_t s) {
     if (n_slices <= 0) return cudaSuccess;
-    k_pack<<<n_slices, kThreads, 0, s>>>(blocks, slices, out, scratch, factors, dst_off, dst);
+    switch (prec) {
+        case kPrecFP64:
+            k_pack<kPrecFP64><<<n_slices, kThreads, 0, s>>>(blocks, slices, out, scratch, factors, dst_off,
+                                                            static_cast<double *>(dst), scales);
+            break;
+        case kPrecDF64:
+            k_pack<kPrecDF64><<<n_slices, kThreads, 0, s>>>(blocks, slices, out, scratch, factors, dst_off,
+                                                            static_cast<float2 *>(dst), scales);
+            break;
+        case kPrecBF16:
+            k_pack<kPrecBF16><<<n_slices, kThreads, 0, s>>>(blocks, slices, out, scratch, factors, dst_off,
+                                                            static_cast<__nv_bfloat16 *>(dst), scales);
+            break;
+        default:
+            k_pack<kPrecFP16><<<n_slices, kThreads, 0, s>>>(blocks, slices, out, scratch, factors, dst_off,
+                                                            static_cast<__half *>(dst), scales);
+            break;
+    }
     return cudaGetLastError();
 }
 

@@ -22,6 +22,19 @@ constexpr int64_t kTaskBytes = 1 << 20; // operator bytes per task (one determin
 
 __host__ __device__ inline int pad2(int n) { return n + (n & 1); }
 
+// Storage precision of the interaction operator (values of seas_hparams::precision).
+constexpr int kPrecFP64 = 0;   // double entries, FP64 arithmetic
+constexpr int kPrecBF16 = 1;   // bfloat16 entries, FP32 arithmetic with compensated accumulation
+constexpr int kPrecFP16 = 2;   // float16 entries with a per-slice scale, FP32 compensated accumulation
+constexpr int kPrecDF64 = 3;   // FP32 (hi, lo) pairs, double-float arithmetic on the FP32 pipes
+
+__host__ __device__ inline int elem_bytes(int prec) { return prec == kPrecBF16 || prec == kPrecFP16 ? 2 : 8; }
+// Row length padded so that every row starts on a 16-byte boundary.
+__host__ __device__ inline int pad_row(int n, int prec) {
+    const int e = 16 / elem_bytes(prec);
+    return (n + e - 1) / e * e;
+}
+
 // One fault of the spectral self-effect path.
 struct FaultDev {
     int32_t off;        // first element (global index)
@@ -51,16 +64,18 @@ struct BlockDev {
 };
 
 // One unit of interaction work: the inner range [i0, i1) of one (block, lag) slice, stored contiguously at `a`
-// (rows padded to an even number of doubles: p2 = pad2(p), q2 = pad2(q)):
-//   dense   (k < 0): rows i0..i1-1 of A^T, each p2 doubles:  y += sum_j A^T[j][:] x_{c0+j}
-//   lowrank (k > 0): k = i1 - i0 rows of V^T (each q2 doubles) followed by k rows of U^T (each p2 doubles):
+// (rows padded to 16 bytes: p2 = pad_row(p), q2 = pad_row(q) elements of the storage precision):
+//   dense   (k < 0): rows i0..i1-1 of A^T, each p2 elements:  y += sum_j A^T[j][:] x_{c0+j}
+//   lowrank (k > 0): k = i1 - i0 rows of V^T (each q2 elements) followed by k rows of U^T (each p2 elements):
 //                    y += sum_l U^T[l][:] (V^T[l][:] . x)
 // Consecutive items of a task are adjacent in memory.
 struct ItemDev {
     int32_t T;
     int32_t k;
     int32_t i0, i1;
-    const double *a;
+    const void *a;
+    float scale;        // stored values times scale = operator values (1 except FP16)
+    int32_t pad;
 };
 
 // A run of items of one block (sorted by lag, adjacent in memory) whose partial sums land in one slot:
@@ -104,8 +119,8 @@ cudaError_t launch_gen_slices(const GeomDev &g, const BlockDev *blocks, const Sl
 cudaError_t launch_compress(const BlockDev *blocks, const SliceGen *slices, int n_slices, const double *scratch,
                             double *resid, double *factors, SliceOut *out, double tol, cudaStream_t s);
 cudaError_t launch_pack(const BlockDev *blocks, const SliceGen *slices, const SliceOut *out, int n_slices,
-                        const double *scratch, const double *factors, const int64_t *dst_off, double *dst,
-                        cudaStream_t s);
+                        const double *scratch, const double *factors, const int64_t *dst_off, void *dst,
+                        float *scales, int prec, cudaStream_t s);
 cudaError_t launch_spectral_tables(const ModeDev *modes, int n_modes, const int64_t *g_prefix, int64_t n_g,
                                    const double *mode_L, double cs_dt, const double *gl_x, const double *gl_w,
                                    int gl_n, double *G, double *w, cudaStream_t s);
@@ -124,6 +139,9 @@ struct StepArgs {
     const double *w;              // spectral weights
     const double2 *tw;            // FFT twiddles
     double *vring;                // [R][ring_stride]
+    void *xring;                  // history in the operator's arithmetic: float2 (DF64) or float (BF16/FP16), same
+                                  // layout; NULL for FP64
+    int prec;
     double *slip, *slip_prev;     // [B][N]
     double2 *dring;               // spectral rings
     double2 *fmodes;              // [B][n_modes_total]

@@ -3,6 +3,9 @@
 // interaction (Sec. 2.3.2), then assembly with the radiation-damping term.
 #include "seas_internal.h"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 namespace seas {
 namespace {
 
@@ -98,6 +101,13 @@ __global__ void k_push(StepArgs a, const double *__restrict__ V, const double *_
         const double v = V[e];
         const int64_t b = e / a.N, i = e - b * a.N;
         vr[i * a.B + b] = v;                           // ring layout [slot][element][scenario]
+        if (a.prec == kPrecDF64) {
+            const float hi = (float)v;
+            reinterpret_cast<float2 *>(a.xring)[(int64_t)slot * a.ring_stride + i * a.B + b] =
+                make_float2(hi, (float)(v - (double)hi));
+        } else if (a.prec != kPrecFP64) {
+            reinterpret_cast<float *>(a.xring)[(int64_t)slot * a.ring_stride + i * a.B + b] = (float)v;
+        }
         double s;
         if (slip_in) {
             s = slip_in[e];
@@ -242,6 +252,7 @@ constexpr int kMaxStageRanks = 256;     // rank-1 terms of all low-rank items of
 struct StageItem {
     int32_t T, k, i0, i1;
     int32_t data_off, x_off;     // byte offsets in the stage (x_off already includes the 16-byte round-down)
+    float scale;
 };
 
 struct StageInfo {
@@ -321,16 +332,133 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
 
-template <int BT>
+// ------------------------------------------------------------------------------------------------------------
+// Arithmetic of each storage precision: stored element S, history element X, dot-product value Z, accumulator
+// Acc; mac = acc += s * x; dot = z += s * x.
+//   FP64: FP64 FMA.
+//   DF64: double-float (FP32 pairs): products by FMA-based TwoProd, sums by TwoSum, the low parts carried along;
+//         about 2^-48 relative per operation, on the FP32 pipes (GB300 runs FP64 at 1/58 of the FP32 rate).
+//   BF16 / FP16: FP32 products, Kahan-compensated accumulation along the history (the task's lags); the FP16
+//         per-slice scale is folded into x (dense) or z (low rank).
+// ------------------------------------------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_prod(float2 a, float2 x) {
+    const float p = a.x * x.x;
+    float e = fmaf(a.x, x.x, -p);
+    e = fmaf(a.x, x.y, e);
+    e = fmaf(a.y, x.x, e);
+    return DF{p, e};
+}
+
+__device__ __forceinline__ void df_add(DF &s, DF v) {
+    const float t = s.hi + v.hi;
+    const float bv = t - s.hi;
+    const float err = (s.hi - (t - bv)) + (v.hi - bv);
+    s.lo += err + v.lo;
+    s.hi = t;
+}
+
+__device__ __forceinline__ DF df_norm(DF s) {
+    const float t = s.hi + s.lo;
+    return DF{t, s.lo - (t - s.hi)};
+}
+
+template <int PREC> struct PT;
+
+template <> struct PT<kPrecFP64> {
+    using S = double;
+    using X = double;
+    using Z = double;
+    using Acc = double;
+    __device__ static Acc zero() { return 0.0; }
+    __device__ static void mac(Acc &a, S s, X x) { a = fma(s, x, a); }
+    __device__ static void macz(Acc &a, S s, Z z) { a = fma(s, z, a); }
+    __device__ static Z zz() { return 0.0; }
+    __device__ static void dot(Z &z, S s, X x) { z = fma(s, x, z); }
+    __device__ static Z shfl_add(Z z, int o, int w) { return z + __shfl_xor_sync(0xffffffffu, z, o, w); }
+    __device__ static X xscale(X x, float) { return x; }
+    __device__ static Z zscale(Z z, float) { return z; }
+    __device__ static double to_d(const Acc &a) { return a; }
+};
+
+template <> struct PT<kPrecDF64> {
+    using S = float2;
+    using X = float2;
+    using Z = float2;
+    using Acc = DF;
+    __device__ static Acc zero() { return DF{0.f, 0.f}; }
+    __device__ static void mac(Acc &a, S s, X x) { df_add(a, df_prod(s, x)); }
+    __device__ static void macz(Acc &a, S s, Z z) { df_add(a, df_prod(s, z)); }
+    __device__ static Z zz() { return make_float2(0.f, 0.f); }
+    __device__ static void dot(Z &z, S s, X x) {
+        DF d{z.x, z.y};
+        df_add(d, df_prod(s, x));
+        z = make_float2(d.hi, d.lo);
+    }
+    __device__ static Z shfl_add(Z z, int o, int w) {
+        DF d{z.x, z.y};
+        df_add(d, DF{__shfl_xor_sync(0xffffffffu, z.x, o, w), __shfl_xor_sync(0xffffffffu, z.y, o, w)});
+        d = df_norm(d);
+        return make_float2(d.hi, d.lo);
+    }
+    __device__ static X xscale(X x, float) { return x; }
+    __device__ static Z zscale(Z z, float) {
+        const DF d = df_norm(DF{z.x, z.y});
+        return make_float2(d.hi, d.lo);
+    }
+    __device__ static double to_d(const Acc &a) { return (double)a.hi + (double)a.lo; }
+};
+
+template <typename H> struct PTHalf {
+    using S = H;
+    using X = float;
+    using Z = float;
+    using Acc = float2;     // (sum, compensation)
+    __device__ static float f(S s);
+    __device__ static Acc zero() { return make_float2(0.f, 0.f); }
+    __device__ static void kahan(Acc &a, float v) {
+        const float y = v - a.y;
+        const float t = a.x + y;
+        a.y = (t - a.x) - y;
+        a.x = t;
+    }
+    __device__ static void mac(Acc &a, S s, X x) { kahan(a, f(s) * x); }
+    __device__ static void macz(Acc &a, S s, Z z) { kahan(a, f(s) * z); }
+    __device__ static Z zz() { return 0.f; }
+    __device__ static void dot(Z &z, S s, X x) { z = fmaf(f(s), x, z); }
+    __device__ static Z shfl_add(Z z, int o, int w) { return z + __shfl_xor_sync(0xffffffffu, z, o, w); }
+    __device__ static X xscale(X x, float sc) { return x * sc; }
+    __device__ static Z zscale(Z z, float sc) { return z * sc; }
+    __device__ static double to_d(const Acc &a) { return (double)a.x - (double)a.y; }
+};
+template <> __device__ __forceinline__ float PTHalf<__nv_bfloat16>::f(__nv_bfloat16 s) { return __bfloat162float(s); }
+template <> __device__ __forceinline__ float PTHalf<__half>::f(__half s) { return __half2float(s); }
+template <> struct PT<kPrecBF16> : PTHalf<__nv_bfloat16> {};
+template <> struct PT<kPrecFP16> : PTHalf<__half> {};
+
+template <int PREC, int BT>
 __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
+    using T = PT<PREC>;
+    using S = typename T::S;
+    using X = typename T::X;
+    using Z = typename T::Z;
+    using Acc = typename T::Acc;
+    constexpr int SB = (int)sizeof(S);
+    constexpr int XB = (int)sizeof(X);
+    constexpr int XA = 16 / XB;                     // history elements per 16 bytes
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *stage_mem = smem_raw;                                            // kStages x kStageBytes
     StageInfo *info = reinterpret_cast<StageInfo *>(smem_raw + kStages * kStageBytes);
-    double *zs = reinterpret_cast<double *>(info + kStages);                          // [kMaxStageRanks][BT]
-    double *red = zs + kMaxStageRanks * BT;                                           // [kConsumers][BT]
+    Z *zs = reinterpret_cast<Z *>(info + kStages);                                  // [kMaxStageRanks][BT]
+    double *red = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(info + kStages) +
+                                             (size_t)kMaxStageRanks * BT * 8);     // [kConsumers][BT]
     uint64_t *full = reinterpret_cast<uint64_t *>(red + kConsumers * BT);
     uint64_t *empty = full + kStages;
     __shared__ int sh_flag;
+    const X *xring = PREC == kPrecFP64 ? reinterpret_cast<const X *>(a.vring) : reinterpret_cast<const X *>(a.xring);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -381,19 +509,20 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 item = a.items[idx];
                 valid = item.T <= a.step;
             }
-            const int p2 = pad2(bd.p), q2 = pad2(bd.q);
+            const int p2 = pad_row(bd.p, PREC), q2 = pad_row(bd.q, PREC);
             int data_bytes = 0, x_bytes = 0;
             int64_t xs_start = 0;
             if (valid) {
                 const int rows = item.i1 - item.i0;
-                data_bytes = 8 * rows * (item.k < 0 ? p2 : p2 + q2);
+                data_bytes = SB * rows * (item.k < 0 ? p2 : p2 + q2);
                 const int e0 = bd.c0 + (item.k < 0 ? item.i0 : 0);
                 const int e1 = bd.c0 + (item.k < 0 ? item.i1 : bd.q);
                 const int64_t s0 = (int64_t)e0 * a.B, s1 = (int64_t)e1 * a.B;
-                xs_start = s0 & ~(int64_t)1;
-                x_bytes = 8 * (int)(((s1 + 1) & ~(int64_t)1) - xs_start);
+                xs_start = s0 / XA * XA;
+                x_bytes = XB * (int)((s1 + XA - 1) / XA * XA - xs_start);
             }
-            // items in the stage: the longest prefix of valid lanes (at most kStageItems) whose bytes fit
+            // items in the stage: the longest prefix of valid lanes (at most kStageItems) whose bytes and rank
+            // rows fit
             const unsigned vmask = __ballot_sync(0xffffffffu, valid);
             const int nvalid = __ffs(~vmask) - 1 < 0 ? 32 : __ffs(~vmask) - 1;      // leading run of valid lanes
             int incl = data_bytes + x_bytes;
@@ -409,7 +538,6 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             const unsigned fit = __ballot_sync(0xffffffffu, lane < nvalid && lane < kStageItems &&
                                                                 incl <= kStageBytes && rincl <= kMaxStageRanks);
             const int n = __ffs(~fit) - 1 < 0 ? 32 : __ffs(~fit) - 1;
-            // data bytes of the n items (they are adjacent) and the x area offsets after them
             int dincl = data_bytes;
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_up_sync(0xffffffffu, dincl, o);
@@ -437,9 +565,7 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             }
             const int data_off = dincl - data_bytes;
             const int x_off = total_data + xincl - (lane < n ? x_bytes : 0);
-            if (lane < n) {
-                si->it[lane] = StageItem{item.T, item.k, item.i0, item.i1, data_off, x_off};
-            }
+            if (lane < n) si->it[lane] = StageItem{item.T, item.k, item.i0, item.i1, data_off, x_off, item.scale};
             __syncwarp();
             unsigned char *dst = stage_mem + (size_t)slot * kStageBytes;
             if (lane == 0) mbar_arrive_tx(&full[slot], (uint32_t)(total_data + total_x));
@@ -449,7 +575,7 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 if (lane == 0 && total_data > 0) bulk_g2s(dst, item.a, (uint32_t)total_data, &full[slot]);
                 if (lane < n) {
                     const int slot_v = (int)((a.step - item.T) % a.ring);
-                    const double *src = a.vring + (int64_t)slot_v * a.ring_stride + xs_start;
+                    const X *src = xring + (int64_t)slot_v * a.ring_stride + xs_start;
                     bulk_g2s(dst + x_off, src, (uint32_t)x_bytes, &full[slot]);
                 }
             }
@@ -461,11 +587,10 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     // ---------------------------------------------------------------------- consumer warps
     // Thread t owns receiver row t mod P of group t / P, with P = p (p <= 256; G = 256 / p groups) or P = 256
     // (larger blocks, several rows per thread).  Rows of the stage's items are dealt to groups (phase B) and
-    // rank rows to lane groups (phase A) with offsets running over the whole stage, so that small items still
-    // keep every warp busy.
+    // rank rows to lane groups (phase A) with offsets running over the whole stage.
     const int t = threadIdx.x;
     int cur = -1, P = 1, G = 1, row = 0, grp = 0, nrow_thr = 1;
-    double acc[kRowsPerThread][BT];
+    Acc acc[kRowsPerThread][BT];
     for (int g = 0;; ++g) {
         const int slot = g % kStages;
         if (t == 0) sh_flag = mbar_wait(&full[slot], (g / kStages) & 1, a.err) ? 0 : 1;
@@ -474,7 +599,7 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         const StageInfo &si = info[slot];
         const int task = si.task;
         if (task < 0) break;
-        const int p = si.p, q = si.q, p2 = pad2(p), q2 = pad2(q);
+        const int p = si.p, q = si.q, p2 = pad_row(p, PREC), q2 = pad_row(q, PREC);
         if (task != cur) {
             cur = task;
             P = p <= kConsumers ? p : kConsumers;
@@ -485,13 +610,13 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
 #pragma unroll
             for (int s = 0; s < kRowsPerThread; ++s)
 #pragma unroll
-                for (int bb = 0; bb < BT; ++bb) acc[s][bb] = 0.0;
+                for (int bb = 0; bb < BT; ++bb) acc[s][bb] = T::zero();
         }
         const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
         const int n = si.n;
         // phase A: V^T x for every rank row of the stage
         const int L = q <= 64 ? 8 : q <= 128 ? 16 : 32;
-        const int subs = 32 / L, S = kConsumerWarps * subs;
+        const int subs = 32 / L, SA = kConsumerWarps * subs;
         const int sub = lane / L, sl = lane % L, slotA = warp * subs + sub;
         bool any_lr = false;
         {
@@ -501,28 +626,28 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 if (itm.k < 0) continue;
                 any_lr = true;
                 const int rows = itm.i1 - itm.i0;
-                const double *Vt = reinterpret_cast<const double *>(base + itm.data_off);
-                const double *x = reinterpret_cast<const double *>(base + itm.x_off) + (((int64_t)si.c0 * a.B) & 1);
-                const int l0 = ((slotA - zoff) % S + S) % S;
-                const int trips = (rows + S - 1) / S;          // uniform over the warp
+                const S *Vt = reinterpret_cast<const S *>(base + itm.data_off);
+                const X *x = reinterpret_cast<const X *>(base + itm.x_off) + (((int64_t)si.c0 * a.B) % XA);
+                const int l0 = ((slotA - zoff) % SA + SA) % SA;
+                const int trips = (rows + SA - 1) / SA;        // uniform over the warp
                 for (int r = 0; r < trips; ++r) {
-                    const int l = l0 + r * S;
+                    const int l = l0 + r * SA;
                     const bool act = l < rows;
-                    const double *vr = Vt + (int64_t)(act ? l : 0) * q2;
-                    double z[BT];
+                    const S *vr = Vt + (int64_t)(act ? l : 0) * q2;
+                    Z z[BT];
 #pragma unroll
-                    for (int bb = 0; bb < BT; ++bb) z[bb] = 0.0;
+                    for (int bb = 0; bb < BT; ++bb) z[bb] = T::zz();
                     if (act) {
                         for (int j = sl; j < q; j += L) {
-                            const double v = vr[j];
+                            const S v = vr[j];
 #pragma unroll
-                            for (int bb = 0; bb < BT; ++bb) z[bb] += v * x[j * a.B + (bb < a.B ? bb : 0)];
+                            for (int bb = 0; bb < BT; ++bb) T::dot(z[bb], v, x[j * a.B + (bb < a.B ? bb : 0)]);
                         }
                     }
 #pragma unroll
                     for (int bb = 0; bb < BT; ++bb) {
-                        for (int o = L / 2; o > 0; o >>= 1) z[bb] += __shfl_xor_sync(0xffffffffu, z[bb], o, L);
-                        if (act && sl == 0) zs[(zoff + l) * BT + bb] = z[bb];
+                        for (int o = L / 2; o > 0; o >>= 1) z[bb] = T::shfl_add(z[bb], o, L);
+                        if (act && sl == 0) zs[(zoff + l) * BT + bb] = T::zscale(z[bb], itm.scale);
                     }
                 }
                 zoff += rows;
@@ -534,36 +659,36 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             int roff = 0, zoff = 0;
             for (int k = 0; k < n; ++k) {
                 const StageItem itm = si.it[k];
-                const double *d = reinterpret_cast<const double *>(base + itm.data_off);
+                const S *d = reinterpret_cast<const S *>(base + itm.data_off);
                 const int rows = itm.i1 - itm.i0;
                 const int r0 = ((grp - roff) % G + G) % G;
                 if (itm.k < 0) {
-                    const double *x = reinterpret_cast<const double *>(base + itm.x_off) +
-                                      (((int64_t)(si.c0 + itm.i0) * a.B) & 1);
+                    const X *x = reinterpret_cast<const X *>(base + itm.x_off) +
+                                 (((int64_t)(si.c0 + itm.i0) * a.B) % XA);
 #pragma unroll 4
                     for (int j = r0; j < rows; j += G) {
-                        const double *ar = d + (int64_t)j * p2;
-                        double xv[BT];
+                        const S *ar = d + (int64_t)j * p2;
+                        X xv[BT];
 #pragma unroll
-                        for (int bb = 0; bb < BT; ++bb) xv[bb] = x[j * a.B + (bb < a.B ? bb : 0)];
+                        for (int bb = 0; bb < BT; ++bb) xv[bb] = T::xscale(x[j * a.B + (bb < a.B ? bb : 0)], itm.scale);
 #pragma unroll
                         for (int s = 0; s < kRowsPerThread; ++s) {
                             if (s < nrow_thr) {
                                 const int i = row + s * P;
                                 if (i < p) {
-                                    const double v = ar[i];
+                                    const S v = ar[i];
 #pragma unroll
-                                    for (int bb = 0; bb < BT; ++bb) acc[s][bb] += v * xv[bb];
+                                    for (int bb = 0; bb < BT; ++bb) T::mac(acc[s][bb], v, xv[bb]);
                                 }
                             }
                         }
                     }
                 } else {
-                    const double *Ut = d + (int64_t)rows * q2;
+                    const S *Ut = d + (int64_t)rows * q2;
 #pragma unroll 4
                     for (int l = r0; l < rows; l += G) {
-                        const double *ur = Ut + (int64_t)l * p2;
-                        double zv[BT];
+                        const S *ur = Ut + (int64_t)l * p2;
+                        Z zv[BT];
 #pragma unroll
                         for (int bb = 0; bb < BT; ++bb) zv[bb] = zs[(zoff + l) * BT + bb];
 #pragma unroll
@@ -571,9 +696,9 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                             if (s < nrow_thr) {
                                 const int i = row + s * P;
                                 if (i < p) {
-                                    const double v = ur[i];
+                                    const S v = ur[i];
 #pragma unroll
-                                    for (int bb = 0; bb < BT; ++bb) acc[s][bb] += v * zv[bb];
+                                    for (int bb = 0; bb < BT; ++bb) T::macz(acc[s][bb], v, zv[bb]);
                                 }
                             }
                         }
@@ -595,11 +720,11 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                     if (s < nrow_thr && i < p)
 #pragma unroll
                         for (int bb = 0; bb < BT; ++bb)
-                            if (bb < a.B) a.partial[(int64_t)bb * a.n_partial + part_off + i] = acc[s][bb];
+                            if (bb < a.B) a.partial[(int64_t)bb * a.n_partial + part_off + i] = T::to_d(acc[s][bb]);
                 }
             } else {
 #pragma unroll
-                for (int bb = 0; bb < BT; ++bb) red[t * BT + bb] = acc[0][bb];
+                for (int bb = 0; bb < BT; ++bb) red[t * BT + bb] = T::to_d(acc[0][bb]);
                 consumer_sync();
                 if (grp == 0) {
 #pragma unroll
@@ -655,15 +780,25 @@ __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
     }
 }
 
-template <int BT>
+template <int PREC, int BT>
 cudaError_t launch_interaction_bt(const StepArgs &a, cudaStream_t s) {
     const size_t smem = (size_t)kStages * kStageBytes + kStages * sizeof(StageInfo) +
-                        (size_t)(kMaxStageRanks + kConsumers) * BT * sizeof(double) + 2 * kStages * sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(k_interaction<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                        (size_t)kMaxStageRanks * BT * 8 + (size_t)kConsumers * BT * sizeof(double) +
+                        2 * kStages * sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(k_interaction<PREC, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = a.n_tasks_active < a.n_sms ? a.n_tasks_active : a.n_sms;
-    k_interaction<BT><<<grid, kInterThreads, smem, s>>>(a);
+    k_interaction<PREC, BT><<<grid, kInterThreads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_interaction_prec(const StepArgs &a, cudaStream_t s) {
+    if (a.B > 4) return launch_interaction_bt<PREC, 8>(a, s);
+    if (a.B > 2) return launch_interaction_bt<PREC, 4>(a, s);
+    if (a.B > 1) return launch_interaction_bt<PREC, 2>(a, s);
+    return launch_interaction_bt<PREC, 1>(a, s);
 }
 
 }  // namespace
@@ -699,10 +834,12 @@ cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s) {
 
 cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s) {
     if (a.n_tasks_active <= 0) return cudaSuccess;
-    if (a.B > 4) return launch_interaction_bt<8>(a, s);
-    if (a.B > 2) return launch_interaction_bt<4>(a, s);
-    if (a.B > 1) return launch_interaction_bt<2>(a, s);
-    return launch_interaction_bt<1>(a, s);
+    switch (a.prec) {
+        case kPrecDF64: return launch_interaction_prec<kPrecDF64>(a, s);
+        case kPrecBF16: return launch_interaction_prec<kPrecBF16>(a, s);
+        case kPrecFP16: return launch_interaction_prec<kPrecFP16>(a, s);
+        default: return launch_interaction_prec<kPrecFP64>(a, s);
+    }
 }
 
 cudaError_t launch_reduce(const StepArgs &a, cudaStream_t s) {

@@ -19,7 +19,7 @@ SEAS_OK = 0
 SEAS_EINVAL, SEAS_ENOMEM, SEAS_ECUDA, SEAS_ESTATE, SEAS_EBUSY, SEAS_ETIMEOUT, SEAS_EIO = -1, -2, -3, -4, -5, -6, -7
 SEAS_MEM_HOST, SEAS_MEM_DEVICE = 0, 1
 SEAS_FLAG_DENSE, SEAS_FLAG_NO_TRUNC, SEAS_FLAG_STATIC_TAIL = 1, 2, 4
-SEAS_PREC_FP64 = 0
+SEAS_PREC_FP64, SEAS_PREC_BF16, SEAS_PREC_FP16S, SEAS_PREC_DF64 = 0, 1, 2, 3
 
 EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_get_elements", "seas_build_hmatrix",
             "seas_op_pair_windows", "seas_op_mode_windows", "seas_scenario_create", "seas_push_slip_rate",

@@ -271,3 +271,64 @@ def test_linearity_at_full_size():
                 seas.seas_stress_step(s.scn, t)
             res.append(t.cpu().numpy().copy())
     assert rel(res[2], 2.0 * res[0] - 3.0 * res[1]) <= 1e-12
+
+
+# ---------------------------------------------------------------- storage precisions --------------------------------
+
+MP_BOUND = {seas.SEAS_PREC_BF16: 2e-2, seas.SEAS_PREC_FP16S: 2e-3}
+
+
+@pytest.mark.parametrize("seed", [1, 3])
+def test_tiny_networks_double_float_is_exact(seed):
+    """DF64 (FP32-pair double-float arithmetic) meets the FP64 parity bar on the H-matrix path."""
+    w = synth.tiny(seed, n_faults=2 + seed % 2, steps=160)
+    net = O.network(w.faults, w.mu, w.cs)
+    V = w.slip_rate(0, 0, w.steps)
+    ref = O.stress_history(net, V, dict(w.hparams, flags=seas.SEAS_FLAG_NO_TRUNC))
+    with seas.Session(w, leaf=2, eta_h=0.8, aca_tol=1e-13, flags=seas.SEAS_FLAG_NO_TRUNC,
+                      precision=seas.SEAS_PREC_DF64) as s:
+        tau, P = run_host(s, V)
+    for k in range(3):
+        assert rel(P[:, k], ref[k + 1]) <= EXACT
+    assert rel(tau, ref[0]) <= EXACT
+
+
+@pytest.mark.parametrize("prec", [seas.SEAS_PREC_DF64, seas.SEAS_PREC_BF16, seas.SEAS_PREC_FP16S])
+def test_two_fault_128_storage_precisions(two_fault_oracle, prec):
+    """The mixed-precision workload on the two-fault network: radiation damping and the spectral self term stay
+    FP64 (exact), the interaction error is stated per precision: DF64 within the FP64 bar, BF16 / FP16 with scale
+    within their storage rounding (2^-9 / 2^-12 per entry, averaged by the sums)."""
+    w, V, ref = two_fault_oracle
+    with seas.Session(w, precision=prec) as s:
+        tau, P = run_host(s, V)
+    e = [rel(P[:, k], ref[k + 1]) for k in range(3)]
+    e_tau = rel(tau, ref[0])
+    print(f"two_fault_128 precision {prec}: rel-L2 rad {e[0]:.2e} self {e[1]:.2e} int {e[2]:.2e} tau {e_tau:.2e}")
+    assert e[0] <= EXACT and e[1] <= EXACT
+    assert e[2] <= (EXACT if prec == seas.SEAS_PREC_DF64 else MP_BOUND[prec])
+
+
+@pytest.mark.parametrize("prec", [seas.SEAS_PREC_DF64, seas.SEAS_PREC_BF16])
+def test_six_fault_3072_precisions_sampled(prec):
+    """Full-size network (H-matrix, windows) in DF64 and BF16, device-resident inputs, sampled rows at the last
+    step against the oracle with the same windows."""
+    torch = pytest.importorskip("torch")
+    w = synth.six_fault_3072()
+    net = O.network(w.faults, w.mu, w.cs)
+    V = w.slip_rate(0, 0, w.steps)
+    hp = w.hparams
+    rows = np.sort(np.random.default_rng(7).choice(net.N, 6, replace=False))
+    with seas.Session(w, precision=prec) as s:
+        Vd = torch.from_numpy(V).cuda()
+        parts = torch.zeros(3 * net.N, dtype=torch.float64, device="cuda")
+        tau = torch.zeros(net.N, dtype=torch.float64, device="cuda")
+        for n in range(w.steps):
+            seas.seas_push_slip_rate(s.scn, Vd[n])
+            seas.seas_stress_step(s.scn, tau, parts=parts)
+        seas.seas_scenario_check(s.scn)
+        p_gpu = parts.cpu().numpy().reshape(3, net.N)
+    _, _, last = O.pair_windows(net, hp["eta_tmin"], hp["eta_tmax"], hp["max_steps"])
+    f_int = O.interaction_rows(net, V, w.steps - 1, rows, pair_hi=last)
+    e = rel(p_gpu[2, rows], f_int)
+    print(f"six_fault_3072 precision {prec}: rel int at step {w.steps - 1}: {e:.2e}")
+    assert e <= (1e-5 if prec == seas.SEAS_PREC_DF64 else MP_BOUND[prec])
