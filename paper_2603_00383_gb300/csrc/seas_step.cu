@@ -247,11 +247,13 @@ constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kInterThreads = kConsumers + 32;
 constexpr uint64_t kWaitNs = 2000000000ull;   // bound of one mbarrier wait
-constexpr int kMaxStageRanks = 256;     // rank-1 terms of all low-rank items of one stage (z buffer)
+constexpr int kMaxStageRanks = 192;     // rank-1 terms of all low-rank items of one stage (z buffer)
 
 struct StageItem {
-    int32_t T, k, i0, i1;
+    int32_t k, i0, i1;
     int32_t data_off, x_off;     // byte offsets in the stage (x_off already includes the 16-byte round-down)
+    int32_t row_end;             // running count of row updates (phase B) through this item
+    int32_t z_end;               // running count of rank rows (phase A) through this item
     float scale;
 };
 
@@ -260,6 +262,7 @@ struct StageInfo {
     int32_t n;                   // items in the stage
     int32_t flush;               // last stage of the task
     int32_t p, q, r0, c0;
+    int32_t n_rows, n_zrows;     // row updates and rank rows of the stage
     int64_t part_off;
     StageItem it[kStageItems];
 };
@@ -474,9 +477,13 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
 
     if (warp == kConsumerWarps) {
         // ------------------------------------------------------------------ producer warp
+        // Lane l holds the descriptor of item it + l; after a stage of n items the descriptors shift down by n
+        // and the tail is fetched at once, so its latency overlaps the wait for the next free stage.
         int task = -1, it = 0, ie = 0;
         TaskDev td{};
         BlockDev bd{};
+        ItemDev item{};
+        bool have = false;                          // descriptors of `it` are loaded
         for (int g = 0;; ++g) {
             const int slot = g % kStages;
             if (g >= kStages) {
@@ -500,17 +507,12 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 bd = a.blocks[td.block];
                 it = td.item_begin;
                 ie = td.item_end;
+                have = false;
             }
-            // lane k looks at item it + k
-            const int idx = it + lane;
-            ItemDev item{};
-            bool valid = idx < ie;
-            if (valid) {
-                item = a.items[idx];
-                valid = item.T <= a.step;
-            }
+            if (!have && it + lane < ie) item = a.items[it + lane];
+            const bool valid = it + lane < ie && item.T <= a.step;
             const int p2 = pad_row(bd.p, PREC), q2 = pad_row(bd.q, PREC);
-            int data_bytes = 0, x_bytes = 0;
+            int data_bytes = 0, x_bytes = 0, nrow = 0, nz = 0;
             int64_t xs_start = 0;
             if (valid) {
                 const int rows = item.i1 - item.i0;
@@ -520,38 +522,48 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 const int64_t s0 = (int64_t)e0 * a.B, s1 = (int64_t)e1 * a.B;
                 xs_start = s0 / XA * XA;
                 x_bytes = XB * (int)((s1 + XA - 1) / XA * XA - xs_start);
+                nrow = rows;
+                nz = item.k > 0 ? rows : 0;
             }
             // items in the stage: the longest prefix of valid lanes (at most kStageItems) whose bytes and rank
             // rows fit
             const unsigned vmask = __ballot_sync(0xffffffffu, valid);
             const int nvalid = __ffs(~vmask) - 1 < 0 ? 32 : __ffs(~vmask) - 1;      // leading run of valid lanes
-            int incl = data_bytes + x_bytes;
-            int rincl = valid && item.k > 0 ? item.i1 - item.i0 : 0;
+            int incl = data_bytes + x_bytes, zincl = nz;
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                const int r = __shfl_up_sync(0xffffffffu, rincl, o);
+                const int r = __shfl_up_sync(0xffffffffu, zincl, o);
                 if (lane >= o) {
                     incl += v;
-                    rincl += r;
+                    zincl += r;
                 }
             }
             const unsigned fit = __ballot_sync(0xffffffffu, lane < nvalid && lane < kStageItems &&
-                                                                incl <= kStageBytes && rincl <= kMaxStageRanks);
+                                                                incl <= kStageBytes && zincl <= kMaxStageRanks);
             const int n = __ffs(~fit) - 1 < 0 ? 32 : __ffs(~fit) - 1;
-            int dincl = data_bytes;
+            const bool in = lane < n;
+            int dincl = in ? data_bytes : 0, xincl = in ? x_bytes : 0, rincl = in ? nrow : 0;
+            zincl = in ? nz : 0;
             for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, dincl, o);
-                if (lane >= o) dincl += v;
+                const int d = __shfl_up_sync(0xffffffffu, dincl, o);
+                const int x = __shfl_up_sync(0xffffffffu, xincl, o);
+                const int r = __shfl_up_sync(0xffffffffu, rincl, o);
+                const int z = __shfl_up_sync(0xffffffffu, zincl, o);
+                if (lane >= o) {
+                    dincl += d;
+                    xincl += x;
+                    rincl += r;
+                    zincl += z;
+                }
             }
-            const int total_data = n > 0 ? __shfl_sync(0xffffffffu, dincl, n > 0 ? n - 1 : 0) : 0;
-            int xincl = lane < n ? x_bytes : 0;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, xincl, o);
-                if (lane >= o) xincl += v;
-            }
+            const int total_data = __shfl_sync(0xffffffffu, dincl, 31);
             const int total_x = __shfl_sync(0xffffffffu, xincl, 31);
-            // the task is finished when the next item is missing or not yet causal
-            const bool next_valid = __shfl_sync(0xffffffffu, (int)valid, n < 32 ? n : 31) != 0 && n < 32;
+            const int total_rows = __shfl_sync(0xffffffffu, rincl, 31);
+            const int total_z = __shfl_sync(0xffffffffu, zincl, 31);
+            // the task is finished when the next item is missing or not yet causal (or, defensively, when no
+            // item fits: the cursor must always advance)
+            const bool next_valid =
+                n > 0 && n < 32 && __shfl_sync(0xffffffffu, (int)valid, n < 32 ? n : 31) != 0;
             StageInfo *si = &info[slot];
             if (lane == 0) {
                 si->task = task;
@@ -561,11 +573,13 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 si->q = bd.q;
                 si->r0 = bd.r0;
                 si->c0 = bd.c0;
+                si->n_rows = total_rows;
+                si->n_zrows = total_z;
                 si->part_off = td.part_off;
             }
-            const int data_off = dincl - data_bytes;
-            const int x_off = total_data + xincl - (lane < n ? x_bytes : 0);
-            if (lane < n) si->it[lane] = StageItem{item.T, item.k, item.i0, item.i1, data_off, x_off, item.scale};
+            const int data_off = dincl - (in ? data_bytes : 0);
+            const int x_off = total_data + xincl - (in ? x_bytes : 0);
+            if (in) si->it[lane] = StageItem{item.k, item.i0, item.i1, data_off, x_off, rincl, zincl, item.scale};
             __syncwarp();
             unsigned char *dst = stage_mem + (size_t)slot * kStageBytes;
             if (lane == 0) mbar_arrive_tx(&full[slot], (uint32_t)(total_data + total_x));
@@ -573,7 +587,7 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             if (n > 0) {
                 // lane 0 holds item `it`, the first of the n adjacent items
                 if (lane == 0 && total_data > 0) bulk_g2s(dst, item.a, (uint32_t)total_data, &full[slot]);
-                if (lane < n) {
+                if (in) {
                     const int slot_v = (int)((a.step - item.T) % a.ring);
                     const X *src = xring + (int64_t)slot_v * a.ring_stride + xs_start;
                     bulk_g2s(dst + x_off, src, (uint32_t)x_bytes, &full[slot]);
@@ -581,21 +595,39 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             }
             it += n;
             if (!next_valid) it = ie;              // remaining items are not causal yet: task done
+            // shift the descriptors of items it .. it + 31 down and fetch the tail now
+            if (it < ie) {
+                ItemDev nxt;
+                nxt.T = __shfl_sync(0xffffffffu, item.T, (lane + n) & 31);
+                nxt.k = __shfl_sync(0xffffffffu, item.k, (lane + n) & 31);
+                nxt.i0 = __shfl_sync(0xffffffffu, item.i0, (lane + n) & 31);
+                nxt.i1 = __shfl_sync(0xffffffffu, item.i1, (lane + n) & 31);
+                nxt.scale = __shfl_sync(0xffffffffu, item.scale, (lane + n) & 31);
+                nxt.a = reinterpret_cast<const void *>(
+                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(item.a), (lane + n) & 31));
+                nxt.pad = 0;
+                if (lane + n < 32) item = nxt;
+                else if (it + lane < ie) item = a.items[it + lane];
+                have = true;
+            } else {
+                have = false;
+            }
         }
     }
 
     // ---------------------------------------------------------------------- consumer warps
     // Thread t owns receiver row t mod P of group t / P, with P = p (p <= 256; G = 256 / p groups) or P = 256
-    // (larger blocks, several rows per thread).  Rows of the stage's items are dealt to groups (phase B) and
-    // rank rows to lane groups (phase A) with offsets running over the whole stage.
+    // (larger blocks, several rows per thread).  The stage's row updates (rows of A^T times x_j, rows of U^T times
+    // z_l) form one flat list dealt round-robin to the groups; the rank rows of phase A one flat list dealt to lane
+    // groups of L lanes.  A monotone cursor maps a flat index to its item: no divisions per row.
     const int t = threadIdx.x;
     int cur = -1, P = 1, G = 1, row = 0, grp = 0, nrow_thr = 1;
     Acc acc[kRowsPerThread][BT];
+    if (t == 0) sh_flag = mbar_wait(&full[0], 0, a.err) ? 0 : 1;
+    consumer_sync();
     for (int g = 0;; ++g) {
-        const int slot = g % kStages;
-        if (t == 0) sh_flag = mbar_wait(&full[slot], (g / kStages) & 1, a.err) ? 0 : 1;
-        consumer_sync();
         if (sh_flag) return;
+        const int slot = g % kStages;
         const StageInfo &si = info[slot];
         const int task = si.task;
         if (task < 0) break;
@@ -614,103 +646,88 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         }
         const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
         const int n = si.n;
-        // phase A: V^T x for every rank row of the stage
-        const int L = q <= 64 ? 8 : q <= 128 ? 16 : 32;
-        const int subs = 32 / L, SA = kConsumerWarps * subs;
-        const int sub = lane / L, sl = lane % L, slotA = warp * subs + sub;
-        bool any_lr = false;
-        {
-            int zoff = 0;
-            for (int k = 0; k < n; ++k) {
-                const StageItem itm = si.it[k];
-                if (itm.k < 0) continue;
-                any_lr = true;
-                const int rows = itm.i1 - itm.i0;
-                const S *Vt = reinterpret_cast<const S *>(base + itm.data_off);
-                const X *x = reinterpret_cast<const X *>(base + itm.x_off) + (((int64_t)si.c0 * a.B) % XA);
-                const int l0 = ((slotA - zoff) % SA + SA) % SA;
-                const int trips = (rows + SA - 1) / SA;        // uniform over the warp
-                for (int r = 0; r < trips; ++r) {
-                    const int l = l0 + r * SA;
-                    const bool act = l < rows;
-                    const S *vr = Vt + (int64_t)(act ? l : 0) * q2;
-                    Z z[BT];
+        // phase A: z = V^T x for every rank row of the stage
+        const int nz = si.n_zrows;
+        if (nz > 0) {
+            const int L = q <= 64 ? 8 : q <= 128 ? 16 : 32;
+            const int subs = 32 / L, SA = kConsumerWarps * subs;
+            const int sl = lane % L, slotA = warp * subs + lane / L;
+            const int trips = (nz + SA - 1) / SA;              // uniform over the warp
+            int k = 0, zstart = 0;
+            for (int r = 0; r < trips; ++r) {
+                const int f = slotA + r * SA;
+                const bool act = f < nz;
+                Z z[BT];
 #pragma unroll
-                    for (int bb = 0; bb < BT; ++bb) z[bb] = T::zz();
-                    if (act) {
-                        for (int j = sl; j < q; j += L) {
-                            const S v = vr[j];
-#pragma unroll
-                            for (int bb = 0; bb < BT; ++bb) T::dot(z[bb], v, x[j * a.B + (bb < a.B ? bb : 0)]);
-                        }
+                for (int bb = 0; bb < BT; ++bb) z[bb] = T::zz();
+                float sc = 1.f;
+                if (act) {
+                    while (f >= si.it[k].z_end) {
+                        zstart = si.it[k].z_end;
+                        ++k;
                     }
+                    const StageItem &itm = si.it[k];
+                    const S *vr = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)(f - zstart) * q2;
+                    const X *x = reinterpret_cast<const X *>(base + itm.x_off) + (((int64_t)si.c0 * a.B) % XA);
+                    sc = itm.scale;
+                    for (int j = sl; j < q; j += L) {
+                        const S v = vr[j];
 #pragma unroll
-                    for (int bb = 0; bb < BT; ++bb) {
-                        for (int o = L / 2; o > 0; o >>= 1) z[bb] = T::shfl_add(z[bb], o, L);
-                        if (act && sl == 0) zs[(zoff + l) * BT + bb] = T::zscale(z[bb], itm.scale);
+                        for (int bb = 0; bb < BT; ++bb) T::dot(z[bb], v, x[j * a.B + (bb < a.B ? bb : 0)]);
                     }
                 }
-                zoff += rows;
+#pragma unroll
+                for (int bb = 0; bb < BT; ++bb) {
+                    for (int o = L / 2; o > 0; o >>= 1) z[bb] = T::shfl_add(z[bb], o, L);
+                    if (act && sl == 0) zs[f * BT + bb] = T::zscale(z[bb], sc);
+                }
             }
+            consumer_sync();
         }
-        if (any_lr) consumer_sync();
-        // phase B: row updates, rows dealt round-robin to the groups across all items of the stage
+        // phase B: row updates
         if (grp < G) {
-            int roff = 0, zoff = 0;
-            for (int k = 0; k < n; ++k) {
-                const StageItem itm = si.it[k];
-                const S *d = reinterpret_cast<const S *>(base + itm.data_off);
-                const int rows = itm.i1 - itm.i0;
-                const int r0 = ((grp - roff) % G + G) % G;
+            const int nr = si.n_rows;
+            int k = 0, rstart = 0, zbase = 0;
+            for (int f = grp; f < nr; f += G) {
+                while (f >= si.it[k].row_end) {
+                    rstart = si.it[k].row_end;
+                    zbase = si.it[k].z_end;
+                    ++k;
+                }
+                const StageItem &itm = si.it[k];
+                const int r = f - rstart;
+                const S *rowp;
+                X cv[BT];
                 if (itm.k < 0) {
+                    rowp = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)r * p2;
                     const X *x = reinterpret_cast<const X *>(base + itm.x_off) +
                                  (((int64_t)(si.c0 + itm.i0) * a.B) % XA);
-#pragma unroll 4
-                    for (int j = r0; j < rows; j += G) {
-                        const S *ar = d + (int64_t)j * p2;
-                        X xv[BT];
 #pragma unroll
-                        for (int bb = 0; bb < BT; ++bb) xv[bb] = T::xscale(x[j * a.B + (bb < a.B ? bb : 0)], itm.scale);
-#pragma unroll
-                        for (int s = 0; s < kRowsPerThread; ++s) {
-                            if (s < nrow_thr) {
-                                const int i = row + s * P;
-                                if (i < p) {
-                                    const S v = ar[i];
-#pragma unroll
-                                    for (int bb = 0; bb < BT; ++bb) T::mac(acc[s][bb], v, xv[bb]);
-                                }
-                            }
-                        }
-                    }
+                    for (int bb = 0; bb < BT; ++bb) cv[bb] = T::xscale(x[r * a.B + (bb < a.B ? bb : 0)], itm.scale);
                 } else {
-                    const S *Ut = d + (int64_t)rows * q2;
-#pragma unroll 4
-                    for (int l = r0; l < rows; l += G) {
-                        const S *ur = Ut + (int64_t)l * p2;
-                        Z zv[BT];
+                    const int rows = itm.i1 - itm.i0;
+                    rowp = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)rows * q2 + (int64_t)r * p2;
 #pragma unroll
-                        for (int bb = 0; bb < BT; ++bb) zv[bb] = zs[(zoff + l) * BT + bb];
+                    for (int bb = 0; bb < BT; ++bb) cv[bb] = zs[(zbase + r) * BT + bb];
+                }
 #pragma unroll
-                        for (int s = 0; s < kRowsPerThread; ++s) {
-                            if (s < nrow_thr) {
-                                const int i = row + s * P;
-                                if (i < p) {
-                                    const S v = ur[i];
+                for (int s = 0; s < kRowsPerThread; ++s) {
+                    if (s < nrow_thr) {
+                        const int i = row + s * P;
+                        if (i < p) {
+                            const S v = rowp[i];
 #pragma unroll
-                                    for (int bb = 0; bb < BT; ++bb) T::macz(acc[s][bb], v, zv[bb]);
-                                }
-                            }
+                            for (int bb = 0; bb < BT; ++bb) T::mac(acc[s][bb], v, cv[bb]);
                         }
                     }
-                    zoff += rows;
                 }
-                roff += rows;
             }
         }
         const bool flush = si.flush != 0;
         const int64_t part_off = si.part_off;
-        consumer_sync();                                   // every consumer is done with the stage (and zs)
+        // one barrier ends this stage and starts the next: thread 0 has seen the next stage land
+        if (t == 0) sh_flag = mbar_wait(&full[(g + 1) % kStages], ((g + 1) / kStages) & 1, a.err) ? 0 : 1;
+        consumer_sync();
         if (t == 0) mbar_arrive(&empty[slot]);
         if (flush) {
             if (G == 1) {
