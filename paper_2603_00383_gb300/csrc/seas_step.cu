@@ -333,6 +333,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared (L2 only), tracked by the issuing thread's cp.async group.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// Arrive on the mbarrier once all cp.async copies this thread issued so far have landed (count preset).
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -466,7 +476,7 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], 1 + 32);           // lane 0's arrive (with the bulk bytes) + 32 cp.async arrivals
             mbar_init(&empty[s], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -477,6 +487,8 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
 
     if (warp == kConsumerWarps) {
         // ------------------------------------------------------------------ producer warp
+        // Operator bytes of a stage: one bulk copy (lane 0).  History slices x: 16-byte cp.async over the 32
+        // lanes, each lane arriving on the stage barrier when its copies have landed.
         // Lane l holds the descriptor of item it + l; after a stage of n items the descriptors shift down by n
         // and the tail is fetched at once, so its latency overlaps the wait for the next free stage.
         int task = -1, it = 0, ie = 0;
@@ -496,10 +508,10 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 if (lane == 0) t = atomicAdd(a.counter, 1);
                 t = __shfl_sync(0xffffffffu, t, 0);
                 if (t >= a.n_tasks_active) {
-                    if (lane == 0) {
-                        info[slot].task = -1;
-                        mbar_arrive(&full[slot]);
-                    }
+                    if (lane == 0) info[slot].task = -1;
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full[slot]);
+                    cp_async_arrive(&full[slot]);
                     return;
                 }
                 task = t;
@@ -582,17 +594,23 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             if (in) si->it[lane] = StageItem{item.k, item.i0, item.i1, data_off, x_off, rincl, zincl, item.scale};
             __syncwarp();
             unsigned char *dst = stage_mem + (size_t)slot * kStageBytes;
-            if (lane == 0) mbar_arrive_tx(&full[slot], (uint32_t)(total_data + total_x));
+            if (lane == 0) mbar_arrive_tx(&full[slot], (uint32_t)total_data);
             __syncwarp();
-            if (n > 0) {
-                // lane 0 holds item `it`, the first of the n adjacent items
-                if (lane == 0 && total_data > 0) bulk_g2s(dst, item.a, (uint32_t)total_data, &full[slot]);
-                if (in) {
-                    const int slot_v = (int)((a.step - item.T) % a.ring);
-                    const X *src = xring + (int64_t)slot_v * a.ring_stride + xs_start;
-                    bulk_g2s(dst + x_off, src, (uint32_t)x_bytes, &full[slot]);
-                }
+            // lane 0 holds item `it`, the first of the n adjacent items
+            if (lane == 0 && total_data > 0) bulk_g2s(dst, item.a, (uint32_t)total_data, &full[slot]);
+            // history slices: item k's x (x_bytes, 16-byte multiple) from its ring row
+            const int slot_v = in ? (int)((a.step - item.T) % a.ring) : 0;
+            const unsigned char *xsrc =
+                reinterpret_cast<const unsigned char *>(xring + (int64_t)slot_v * a.ring_stride + xs_start);
+            for (int k = 0; k < n; ++k) {
+                const int xb = __shfl_sync(0xffffffffu, x_bytes, k);
+                const int xo = __shfl_sync(0xffffffffu, x_off, k);
+                const unsigned long long src =
+                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(xsrc), k);
+                for (int c = lane * 16; c < xb; c += 32 * 16)
+                    cp_async16(dst + xo + c, reinterpret_cast<const unsigned char *>(src) + c);
             }
+            cp_async_arrive(&full[slot]);
             it += n;
             if (!next_valid) it = ie;              // remaining items are not causal yet: task done
             // shift the descriptors of items it .. it + 31 down and fetch the tail now
@@ -645,7 +663,6 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 for (int bb = 0; bb < BT; ++bb) acc[s][bb] = T::zero();
         }
         const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
-        const int n = si.n;
         // phase A: z = V^T x for every rank row of the stage
         const int nz = si.n_zrows;
         if (nz > 0) {
