@@ -1119,7 +1119,7 @@ extern "C" seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **o
     *out = nullptr;
     if (batch < 1 || batch > kMaxBatch) return fail(SEAS_EINVAL, "batch must be in [1, %d]", kMaxBatch);
     const int xb = op->hp.precision == kPrecBF16 || op->hp.precision == kPrecFP16 ? 4 : 8;
-    if ((int64_t)op->max_q * batch * xb + 16 + kItemBytes > kStageBytes)
+    if ((int64_t)(op->max_q + 8) * batch * xb + 16 + kItemBytes > kStageBytes)
         return fail(SEAS_EINVAL, "batch %d too large for blocks of %d columns (stage of %d bytes)", batch, op->max_q,
                     kStageBytes);
     CUDA_TRY(cudaSetDevice(op->net->ctx->device));

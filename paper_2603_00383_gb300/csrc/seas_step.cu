@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 namespace seas {
 namespace {
 
@@ -338,6 +340,12 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
+// 4- or 8-byte asynchronous copy global -> shared (any element alignment).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+
 // Arrive on the mbarrier once all cp.async copies this thread issued so far have landed (count preset).
 __device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -452,6 +460,92 @@ template <> __device__ __forceinline__ float PTHalf<__half>::f(__half s) { retur
 template <> struct PT<kPrecBF16> : PTHalf<__nv_bfloat16> {};
 template <> struct PT<kPrecFP16> : PTHalf<__half> {};
 
+// Vector view of the stored operator: VE values of 16 or 8 bytes per load, converted to the arithmetic type E
+// (double, DF pair or float).
+template <int PREC, int VE> struct VecLoad;
+template <int VE> struct VecLoad<kPrecFP64, VE> {
+    using E = double;
+    __device__ static void ld(const double *p, E *o) {
+        if (VE == 2) {
+            const double2 v = *reinterpret_cast<const double2 *>(p);
+            o[0] = v.x;
+            o[VE > 1 ? 1 : 0] = v.y;
+        } else {
+            o[0] = p[0];
+        }
+    }
+};
+template <int VE> struct VecLoad<kPrecDF64, VE> {
+    using E = float2;
+    __device__ static void ld(const float2 *p, E *o) {
+        if (VE == 2) {
+            const float4 v = *reinterpret_cast<const float4 *>(p);
+            o[0] = make_float2(v.x, v.y);
+            o[VE > 1 ? 1 : 0] = make_float2(v.z, v.w);
+        } else {
+            o[0] = p[0];
+        }
+    }
+};
+template <typename H, int VE> struct VecLoadHalf {
+    using E = float;
+    __device__ static float2 pair(uint32_t w);
+    __device__ static void ld(const H *p, E *o) {
+        if (VE == 8) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(p);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f = pair(w[k]);
+                o[(2 * k) % VE] = f.x;
+                o[(2 * k + 1) % VE] = f.y;
+            }
+        } else {
+            const uint2 v = *reinterpret_cast<const uint2 *>(p);
+            const uint32_t w[2] = {v.x, v.y};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float2 f = pair(w[k]);
+                o[(2 * k) % VE] = f.x;
+                o[(2 * k + 1) % VE] = f.y;
+            }
+        }
+    }
+};
+template <> __device__ __forceinline__ float2 VecLoadHalf<__nv_bfloat16, 8>::pair(uint32_t w) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+}
+template <> __device__ __forceinline__ float2 VecLoadHalf<__nv_bfloat16, 4>::pair(uint32_t w) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+}
+template <> __device__ __forceinline__ float2 VecLoadHalf<__half, 8>::pair(uint32_t w) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
+template <> __device__ __forceinline__ float2 VecLoadHalf<__half, 4>::pair(uint32_t w) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
+template <int VE> struct VecLoad<kPrecBF16, VE> : VecLoadHalf<__nv_bfloat16, VE> {};
+template <int VE> struct VecLoad<kPrecFP16, VE> : VecLoadHalf<__half, VE> {};
+
+// Elements per vector load: 16 bytes, halved for larger batches to bound the accumulator registers.
+template <int PREC, int BT> struct VecWidth {
+    static constexpr int SB = PREC == kPrecBF16 || PREC == kPrecFP16 ? 2 : 8;
+    static constexpr int value = SB == 2 ? (BT <= 2 ? 8 : 4) : (BT <= 4 ? 2 : 1);
+};
+
+// Multiply-accumulate of one converted operator value with one coefficient.
+__device__ __forceinline__ void emac(double &acc, double v, double c) { acc = fma(v, c, acc); }
+__device__ __forceinline__ void emac(DF &acc, float2 v, float2 c) { df_add(acc, df_prod(v, c)); }
+__device__ __forceinline__ void emac(float &acc, float v, float c) { acc = fmaf(v, c, acc); }
+// Dot-product step z += v x in the dot type Z (double, (hi, lo) float2, float).
+__device__ __forceinline__ void edot(double &z, double v, double x) { z = fma(v, x, z); }
+__device__ __forceinline__ void edot(float2 &z, float2 v, float2 x) {
+    DF d{z.x, z.y};
+    df_add(d, df_prod(v, x));
+    z = make_float2(d.hi, d.lo);
+}
+__device__ __forceinline__ void edot(float &z, float v, float x) { z = fmaf(v, x, z); }
+
 template <int PREC, int BT>
 __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     using T = PT<PREC>;
@@ -467,8 +561,8 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     StageInfo *info = reinterpret_cast<StageInfo *>(smem_raw + kStages * kStageBytes);
     Z *zs = reinterpret_cast<Z *>(info + kStages);                                  // [kMaxStageRanks][BT]
     double *red = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(info + kStages) +
-                                             (size_t)kMaxStageRanks * BT * 8);     // [kConsumers][BT]
-    uint64_t *full = reinterpret_cast<uint64_t *>(red + kConsumers * BT);
+                                             (size_t)kMaxStageRanks * BT * 8);     // [kConsumers][8]
+    uint64_t *full = reinterpret_cast<uint64_t *>(red + kConsumers * 8);
     uint64_t *empty = full + kStages;
     __shared__ int sh_flag;
     const X *xring = PREC == kPrecFP64 ? reinterpret_cast<const X *>(a.vring) : reinterpret_cast<const X *>(a.xring);
@@ -526,14 +620,15 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             const int p2 = pad_row(bd.p, PREC), q2 = pad_row(bd.q, PREC);
             int data_bytes = 0, x_bytes = 0, nrow = 0, nz = 0;
             int64_t xs_start = 0;
+            int x_count = 0;
             if (valid) {
                 const int rows = item.i1 - item.i0;
                 data_bytes = SB * rows * (item.k < 0 ? p2 : p2 + q2);
                 const int e0 = bd.c0 + (item.k < 0 ? item.i0 : 0);
-                const int e1 = bd.c0 + (item.k < 0 ? item.i1 : bd.q);
-                const int64_t s0 = (int64_t)e0 * a.B, s1 = (int64_t)e1 * a.B;
-                xs_start = s0 / XA * XA;
-                x_bytes = XB * (int)((s1 + XA - 1) / XA * XA - xs_start);
+                xs_start = (int64_t)e0 * a.B;
+                x_count = (item.k < 0 ? rows : bd.q) * a.B;           // history values copied
+                const int x_span = (item.k < 0 ? rows : q2) * a.B;    // values the consumers read (zero tail)
+                x_bytes = (XB * x_span + 15) / 16 * 16;
                 nrow = rows;
                 nz = item.k > 0 ? rows : 0;
             }
@@ -592,23 +687,32 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             const int data_off = dincl - (in ? data_bytes : 0);
             const int x_off = total_data + xincl - (in ? x_bytes : 0);
             if (in) si->it[lane] = StageItem{item.k, item.i0, item.i1, data_off, x_off, rincl, zincl, item.scale};
-            __syncwarp();
             unsigned char *dst = stage_mem + (size_t)slot * kStageBytes;
+            // zero the part of each x area past the copied values (padding columns of V^T multiply it); plain
+            // shared stores, published by lane 0's arrive below
+            for (int k = 0; k < n; ++k) {
+                const int cnt = __shfl_sync(0xffffffffu, x_count, k);
+                const int span = __shfl_sync(0xffffffffu, x_bytes, k) / XB;
+                const int xo = __shfl_sync(0xffffffffu, x_off, k);
+                X *xd = reinterpret_cast<X *>(dst + xo);
+                for (int c = cnt + lane; c < span; c += 32) xd[c] = X{};
+            }
+            __syncwarp();
             if (lane == 0) mbar_arrive_tx(&full[slot], (uint32_t)total_data);
             __syncwarp();
-            // lane 0 holds item `it`, the first of the n adjacent items
+            // lane 0 holds item `it`, the first of the n adjacent items: their operator bytes in one bulk copy
             if (lane == 0 && total_data > 0) bulk_g2s(dst, item.a, (uint32_t)total_data, &full[slot]);
-            // history slices: item k's x (x_bytes, 16-byte multiple) from its ring row
+            // history slices: item k's x values from its ring row, element by element so that the slice starts
+            // on a 16-byte boundary of the stage
             const int slot_v = in ? (int)((a.step - item.T) % a.ring) : 0;
-            const unsigned char *xsrc =
-                reinterpret_cast<const unsigned char *>(xring + (int64_t)slot_v * a.ring_stride + xs_start);
+            const X *xsrc = xring + (int64_t)slot_v * a.ring_stride + xs_start;
             for (int k = 0; k < n; ++k) {
-                const int xb = __shfl_sync(0xffffffffu, x_bytes, k);
+                const int cnt = __shfl_sync(0xffffffffu, x_count, k);
                 const int xo = __shfl_sync(0xffffffffu, x_off, k);
-                const unsigned long long src =
-                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(xsrc), k);
-                for (int c = lane * 16; c < xb; c += 32 * 16)
-                    cp_async16(dst + xo + c, reinterpret_cast<const unsigned char *>(src) + c);
+                const X *src = reinterpret_cast<const X *>(
+                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(xsrc), k));
+                X *xd = reinterpret_cast<X *>(dst + xo);
+                for (int c = lane; c < cnt; c += 32) cp_async_elem<XB>(xd + c, src + c);
             }
             cp_async_arrive(&full[slot]);
             it += n;
@@ -634,13 +738,20 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     }
 
     // ---------------------------------------------------------------------- consumer warps
-    // Thread t owns receiver row t mod P of group t / P, with P = p (p <= 256; G = 256 / p groups) or P = 256
-    // (larger blocks, several rows per thread).  The stage's row updates (rows of A^T times x_j, rows of U^T times
-    // z_l) form one flat list dealt round-robin to the groups; the rank rows of phase A one flat list dealt to lane
-    // groups of L lanes.  A monotone cursor maps a flat index to its item: no divisions per row.
+    // Thread t owns the VE-wide column vector (t mod P) of the block's rows and works in group t / P: P = number
+    // of column vectors (p2 / VE, at most 256), G = 256 / P groups.  The stage's row updates (rows of A^T times
+    // x_j, rows of U^T times z_l) form one flat list dealt round-robin to the groups; the rank rows of phase A a
+    // flat list dealt to lane groups.  A monotone cursor maps a flat index to its item.  BF16/FP16: plain FP32
+    // partial sums inside a stage, added into the Kahan-compensated accumulator once per stage.
+    constexpr int VE = VecWidth<PREC, BT>::value;
+    constexpr int NVT = (kMaxBlockSide + VE * kConsumers - 1) / (VE * kConsumers);   // vectors per thread, max
+    constexpr bool MP = PREC == kPrecBF16 || PREC == kPrecFP16;
+    using E = typename VecLoad<PREC, VE>::E;
+    using PAcc = typename std::conditional<MP, float, Acc>::type;                     // per-stage partial
     const int t = threadIdx.x;
-    int cur = -1, P = 1, G = 1, row = 0, grp = 0, nrow_thr = 1;
-    Acc acc[kRowsPerThread][BT];
+    int cur = -1, P = 1, G = 1, vec = 0, grp = 0, nvt = 1;
+    Acc acc[NVT][VE][BT];
+    PAcc part[NVT][VE][BT];
     if (t == 0) sh_flag = mbar_wait(&full[0], 0, a.err) ? 0 : 1;
     consumer_sync();
     for (int g = 0;; ++g) {
@@ -652,21 +763,28 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         const int p = si.p, q = si.q, p2 = pad_row(p, PREC), q2 = pad_row(q, PREC);
         if (task != cur) {
             cur = task;
-            P = p <= kConsumers ? p : kConsumers;
+            const int pv = p2 / VE;
+            P = pv <= kConsumers ? pv : kConsumers;
             G = kConsumers / P;
-            row = t % P;
-            grp = t / P;                               // grp == G: idle thread (256 not a multiple of p)
-            nrow_thr = (p + P - 1) / P;
+            vec = t % P;
+            grp = t / P;                               // grp == G: idle thread
+            nvt = (pv + P - 1) / P;
 #pragma unroll
-            for (int s = 0; s < kRowsPerThread; ++s)
+            for (int s = 0; s < NVT; ++s)
 #pragma unroll
-                for (int bb = 0; bb < BT; ++bb) acc[s][bb] = T::zero();
+                for (int e = 0; e < VE; ++e)
+#pragma unroll
+                    for (int bb = 0; bb < BT; ++bb) {
+                        acc[s][e][bb] = T::zero();
+                        part[s][e][bb] = PAcc{};
+                    }
         }
         const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
         // phase A: z = V^T x for every rank row of the stage
         const int nz = si.n_zrows;
         if (nz > 0) {
-            const int L = q <= 64 ? 8 : q <= 128 ? 16 : 32;
+            const int qv = q2 / VE;
+            const int L = qv <= 1 ? 1 : qv <= 2 ? 2 : qv <= 4 ? 4 : qv <= 8 ? 8 : qv <= 16 ? 16 : 32;
             const int subs = 32 / L, SA = kConsumerWarps * subs;
             const int sl = lane % L, slotA = warp * subs + lane / L;
             const int trips = (nz + SA - 1) / SA;              // uniform over the warp
@@ -685,12 +803,16 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                     }
                     const StageItem &itm = si.it[k];
                     const S *vr = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)(f - zstart) * q2;
-                    const X *x = reinterpret_cast<const X *>(base + itm.x_off) + (((int64_t)si.c0 * a.B) % XA);
+                    const X *x = reinterpret_cast<const X *>(base + itm.x_off);
                     sc = itm.scale;
-                    for (int j = sl; j < q; j += L) {
-                        const S v = vr[j];
+                    for (int u = sl; u < qv; u += L) {
+                        E v[VE];
+                        VecLoad<PREC, VE>::ld(vr + u * VE, v);
 #pragma unroll
-                        for (int bb = 0; bb < BT; ++bb) T::dot(z[bb], v, x[j * a.B + (bb < a.B ? bb : 0)]);
+                        for (int e = 0; e < VE; ++e)
+#pragma unroll
+                            for (int bb = 0; bb < BT; ++bb)
+                                edot(z[bb], v[e], x[(u * VE + e) * a.B + (bb < a.B ? bb : 0)]);
                     }
                 }
 #pragma unroll
@@ -714,30 +836,52 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 const StageItem &itm = si.it[k];
                 const int r = f - rstart;
                 const S *rowp;
-                X cv[BT];
+                E cv[BT];
                 if (itm.k < 0) {
                     rowp = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)r * p2;
-                    const X *x = reinterpret_cast<const X *>(base + itm.x_off) +
-                                 (((int64_t)(si.c0 + itm.i0) * a.B) % XA);
+                    const X *x = reinterpret_cast<const X *>(base + itm.x_off);
 #pragma unroll
-                    for (int bb = 0; bb < BT; ++bb) cv[bb] = T::xscale(x[r * a.B + (bb < a.B ? bb : 0)], itm.scale);
+                    for (int bb = 0; bb < BT; ++bb) {
+                        const X xv = T::xscale(x[r * a.B + (bb < a.B ? bb : 0)], itm.scale);
+                        cv[bb] = *reinterpret_cast<const E *>(&xv);
+                    }
                 } else {
                     const int rows = itm.i1 - itm.i0;
                     rowp = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)rows * q2 + (int64_t)r * p2;
 #pragma unroll
-                    for (int bb = 0; bb < BT; ++bb) cv[bb] = zs[(zbase + r) * BT + bb];
+                    for (int bb = 0; bb < BT; ++bb) {
+                        const Z zv = zs[(zbase + r) * BT + bb];
+                        cv[bb] = *reinterpret_cast<const E *>(&zv);
+                    }
                 }
 #pragma unroll
-                for (int s = 0; s < kRowsPerThread; ++s) {
-                    if (s < nrow_thr) {
-                        const int i = row + s * P;
-                        if (i < p) {
-                            const S v = rowp[i];
+                for (int s = 0; s < NVT; ++s) {
+                    if (s < nvt) {
+                        const int u = vec + s * P;
+                        if (u * VE < p2) {
+                            E v[VE];
+                            VecLoad<PREC, VE>::ld(rowp + u * VE, v);
 #pragma unroll
-                            for (int bb = 0; bb < BT; ++bb) T::mac(acc[s][bb], v, cv[bb]);
+                            for (int e = 0; e < VE; ++e)
+#pragma unroll
+                                for (int bb = 0; bb < BT; ++bb) {
+                                    if constexpr (MP) emac(part[s][e][bb], v[e], cv[bb]);
+                                    else emac(acc[s][e][bb], v[e], cv[bb]);
+                                }
                         }
                     }
                 }
+            }
+            if constexpr (MP) {                                // compensated accumulation, once per stage
+#pragma unroll
+                for (int s = 0; s < NVT; ++s)
+#pragma unroll
+                    for (int e = 0; e < VE; ++e)
+#pragma unroll
+                        for (int bb = 0; bb < BT; ++bb) {
+                            PTHalf<__half>::kahan(acc[s][e][bb], part[s][e][bb]);
+                            part[s][e][bb] = PAcc{};
+                        }
             }
         }
         const bool flush = si.flush != 0;
@@ -747,28 +891,45 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         consumer_sync();
         if (t == 0) mbar_arrive(&empty[slot]);
         if (flush) {
+            // column c = (vec + s P) VE + e; groups reduced in a fixed order, 8 values per thread per round
+            constexpr int NV = NVT * VE * BT;
             if (G == 1) {
 #pragma unroll
-                for (int s = 0; s < kRowsPerThread; ++s) {
-                    const int i = row + s * P;
-                    if (s < nrow_thr && i < p)
+                for (int s = 0; s < NVT; ++s)
 #pragma unroll
-                        for (int bb = 0; bb < BT; ++bb)
-                            if (bb < a.B) a.partial[(int64_t)bb * a.n_partial + part_off + i] = T::to_d(acc[s][bb]);
-                }
+                    for (int e = 0; e < VE; ++e) {
+                        const int c = (vec + s * P) * VE + e;
+                        if (s < nvt && c < p)
+#pragma unroll
+                            for (int bb = 0; bb < BT; ++bb)
+                                if (bb < a.B)
+                                    a.partial[(int64_t)bb * a.n_partial + part_off + c] = T::to_d(acc[s][e][bb]);
+                    }
             } else {
 #pragma unroll
-                for (int bb = 0; bb < BT; ++bb) red[t * BT + bb] = T::to_d(acc[0][bb]);
-                consumer_sync();
-                if (grp == 0) {
+                for (int r0 = 0; r0 < VE * BT; r0 += 8) {      // NVT == 1 when G > 1
 #pragma unroll
-                    for (int bb = 0; bb < BT; ++bb) {
-                        double sum = 0.0;
-                        for (int gg = 0; gg < G; ++gg) sum += red[(gg * P + row) * BT + bb];
-                        if (bb < a.B) a.partial[(int64_t)bb * a.n_partial + part_off + row] = sum;
+                    for (int m = 0; m < 8; ++m) {
+                        const int v = r0 + m;
+                        if (v < VE * BT) red[t * 8 + m] = T::to_d(acc[0][v / BT][v % BT]);
                     }
+                    consumer_sync();
+                    if (grp == 0) {
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) {
+                            const int v = r0 + m;
+                            const int e = v / BT, bb = v % BT;
+                            const int c = vec * VE + e;
+                            if (v < VE * BT && c < p && bb < a.B) {
+                                double sum = 0.0;
+                                for (int gg = 0; gg < G; ++gg) sum += red[(gg * P + vec) * 8 + m];
+                                a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
+                            }
+                        }
+                    }
+                    consumer_sync();
                 }
-                consumer_sync();
+                (void)NV;
             }
             cur = -1;
         }
@@ -817,7 +978,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
 template <int PREC, int BT>
 cudaError_t launch_interaction_bt(const StepArgs &a, cudaStream_t s) {
     const size_t smem = (size_t)kStages * kStageBytes + kStages * sizeof(StageInfo) +
-                        (size_t)kMaxStageRanks * BT * 8 + (size_t)kConsumers * BT * sizeof(double) +
+                        (size_t)kMaxStageRanks * BT * 8 + (size_t)kConsumers * 8 * sizeof(double) +
                         2 * kStages * sizeof(uint64_t);
     cudaError_t e = cudaFuncSetAttribute(k_interaction<PREC, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
