@@ -688,31 +688,29 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             const int x_off = total_data + xincl - (in ? x_bytes : 0);
             if (in) si->it[lane] = StageItem{item.k, item.i0, item.i1, data_off, x_off, rincl, zincl, item.scale};
             unsigned char *dst = stage_mem + (size_t)slot * kStageBytes;
-            // zero the part of each x area past the copied values (padding columns of V^T multiply it); plain
-            // shared stores, published by lane 0's arrive below
-            for (int k = 0; k < n; ++k) {
-                const int cnt = __shfl_sync(0xffffffffu, x_count, k);
-                const int span = __shfl_sync(0xffffffffu, x_bytes, k) / XB;
-                const int xo = __shfl_sync(0xffffffffu, x_off, k);
-                X *xd = reinterpret_cast<X *>(dst + xo);
-                for (int c = cnt + lane; c < span; c += 32) xd[c] = X{};
+            // each lane stages its own item's history slice.  First the part of its x area past the copied
+            // values is zeroed (padding columns of V^T multiply it): plain shared stores, published by lane 0's
+            // arrive below.
+            X *xd = reinterpret_cast<X *>(dst + x_off);
+            if (in) {
+                const int span = x_bytes / XB;
+                for (int c = x_count; c < span; ++c) xd[c] = X{};
             }
             __syncwarp();
             if (lane == 0) mbar_arrive_tx(&full[slot], (uint32_t)total_data);
             __syncwarp();
             // lane 0 holds item `it`, the first of the n adjacent items: their operator bytes in one bulk copy
             if (lane == 0 && total_data > 0) bulk_g2s(dst, item.a, (uint32_t)total_data, &full[slot]);
-            // history slices: item k's x values from its ring row, element by element so that the slice starts
-            // on a 16-byte boundary of the stage
-            const int slot_v = in ? (int)((a.step - item.T) % a.ring) : 0;
-            const X *xsrc = xring + (int64_t)slot_v * a.ring_stride + xs_start;
-            for (int k = 0; k < n; ++k) {
-                const int cnt = __shfl_sync(0xffffffffu, x_count, k);
-                const int xo = __shfl_sync(0xffffffffu, x_off, k);
-                const X *src = reinterpret_cast<const X *>(
-                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(xsrc), k));
-                X *xd = reinterpret_cast<X *>(dst + xo);
-                for (int c = lane; c < cnt; c += 32) cp_async_elem<XB>(xd + c, src + c);
+            // history values from the item's ring row, landing on a 16-byte boundary of the stage: 16-byte copies
+            // when the source is 16-byte aligned too, element copies otherwise
+            if (in) {
+                const int slot_v = (int)((a.step - item.T) % a.ring);
+                const X *src = xring + (int64_t)slot_v * a.ring_stride + xs_start;
+                int c = 0;
+                if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+                    for (; c + XA <= x_count; c += XA) cp_async16(xd + c, src + c);
+                }
+                for (; c < x_count; ++c) cp_async_elem<XB>(xd + c, src + c);
             }
             cp_async_arrive(&full[slot]);
             it += n;
