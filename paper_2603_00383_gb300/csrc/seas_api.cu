@@ -1283,6 +1283,30 @@ extern "C" seas_status seas_stress_step(seas_scn *s, double *tau, double *sigma_
     return SEAS_OK;
 }
 
+extern "C" seas_status seas_stress_step_static(seas_scn *s, double *tau, double *parts) {
+    // Same computation as seas_stress_step with device outputs, but nothing is allocated: the per-call scratch
+    // (partial sums of the interaction tasks and the summed interaction term) is a static device array.
+    if (!s || !tau) return fail(SEAS_EINVAL, "NULL argument");
+    if (s->n == 0) return fail(SEAS_ESTATE, "stress_step before the first push");
+    seas_op &op = *s->op;
+    seas_ctx *c = op.net->ctx;
+    const int64_t need = op.n_partial * s->B + (int64_t)s->B * op.net->N;
+    if (need > kStaticScratchDoubles)
+        return fail(SEAS_EINVAL, "static scratch too small: this scenario needs %lld doubles, the limit is %lld",
+                    (long long)need, (long long)kStaticScratchDoubles);
+    CUDA_TRY(cudaSetDevice(c->device));
+    double *scratch = nullptr;
+    CUDA_TRY(static_scratch(&scratch));               // first call on a device: symbol lookup (no allocation)
+    StepArgs a = step_args(*s, s->n - 1);
+    a.partial = scratch;
+    a.fint = scratch + op.n_partial * s->B;
+    CUDA_TRY(launch_modeconv(a, c->stream));
+    CUDA_TRY(launch_interaction(a, c->stream));
+    CUDA_TRY(launch_reduce(a, c->stream));
+    CUDA_TRY(launch_ifft_assemble(a, tau, parts, c->stream));
+    return SEAS_OK;
+}
+
 extern "C" seas_status seas_scenario_step(const seas_scn *s, int64_t *n) {
     if (!s || !n) return fail(SEAS_EINVAL, "NULL argument");
     *n = s->n;

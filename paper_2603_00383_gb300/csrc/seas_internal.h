@@ -162,6 +162,11 @@ struct StepArgs {
     int n_sms;
 };
 
+// Allocation-free stepping (seas_stress_step_static): scratch in a static device array of this many doubles.
+constexpr int64_t kStaticScratchDoubles = int64_t(1) << 22;
+constexpr int kMaxDevices = 64;
+cudaError_t static_scratch(double **ptr);   // device address of the array on the current device
+
 cudaError_t launch_push(const StepArgs &a, const double *V, const double *slip_in, int replace_last,
                         cudaStream_t s);
 cudaError_t launch_fft_forward(const StepArgs &a, cudaStream_t s);

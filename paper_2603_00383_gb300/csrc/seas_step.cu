@@ -6,9 +6,16 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <atomic>
 #include <type_traits>
 
 namespace seas {
+
+// Scratch of seas_stress_step_static: the per-task partial sums and the summed interaction term of one call.
+// It lives for the life of the process on every GPU that loads the library.  In host code the symbol is only a
+// stand-in: the device address comes from cudaGetSymbolAddress (static_scratch below).
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+
 namespace {
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -995,6 +1002,26 @@ cudaError_t launch_interaction_prec(const StepArgs &a, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t static_scratch(double **ptr) {
+    // device address of the scratch array, looked up once per device with that device current
+    // (threads that race here look up and store the same address)
+    static std::atomic<double *> cache[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    double *p = cache[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void *q = nullptr;
+        e = cudaGetSymbolAddress(&q, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        p = static_cast<double *>(q);
+        cache[dev].store(p, std::memory_order_release);
+    }
+    *ptr = p;
+    return cudaSuccess;
+}
 
 cudaError_t launch_push(const StepArgs &a, const double *V, const double *slip_in, int replace_last,
                         cudaStream_t s) {

@@ -26,7 +26,7 @@ EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_
             "seas_stress_step", "seas_scenario_step", "seas_sync", "seas_strerror", "seas_last_error",
             "seas_scenario_save", "seas_scenario_load", "seas_destroy_scn", "seas_destroy_op", "seas_destroy_net",
             "seas_destroy_ctx", "seas_plan_hmatrix", "seas_scenario_set_timing", "seas_scenario_get_timing",
-            "seas_op_step_bytes", "seas_scenario_check"]
+            "seas_op_step_bytes", "seas_scenario_check", "seas_stress_step_static"]
 
 
 class SeasError(RuntimeError):
@@ -98,6 +98,7 @@ _SIGS = {
     "seas_scenario_get_timing": ([_VP, C.POINTER(seas_timing)], C.c_int),
     "seas_op_step_bytes": ([_VP, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
     "seas_scenario_check": ([_VP], C.c_int),
+    "seas_stress_step_static": ([_VP, _VP, _VP], C.c_int),
 }
 
 
@@ -285,6 +286,17 @@ def seas_stress_step(scn: Handle, tau, sigma_n=None, parts=None):
         if m is not None and m != mem:
             raise ValueError("tau, sigma_n and parts must live in the same memory")
     _check(lib().seas_stress_step(scn.ptr, pt, pn, pp, mem))
+
+
+def seas_stress_step_static(scn: Handle, tau, parts=None):
+    """seas_stress_step into device buffers (CUDA tensors) with its scratch in a static device array, for callers
+    that must not allocate device memory while stepping; limits and sharing rules are in include/seas.h."""
+    n = scn.B * scn.N
+    pt, mem = _buf(tau, n, "tau")
+    pp, mp = _buf(parts, 3 * n, "parts")
+    if mem != SEAS_MEM_DEVICE or (mp is not None and mp != SEAS_MEM_DEVICE):
+        raise ValueError("seas_stress_step_static takes device buffers")
+    _check(lib().seas_stress_step_static(scn.ptr, pt, pp))
 
 
 def seas_scenario_step(scn: Handle) -> int:
