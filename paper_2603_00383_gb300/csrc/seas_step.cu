@@ -553,6 +553,16 @@ __device__ __forceinline__ void edot(float2 &z, float2 v, float2 x) {
 }
 __device__ __forceinline__ void edot(float &z, float v, float x) { z = fmaf(v, x, z); }
 
+// N values of 4 to 16 bytes each, N * size a multiple of 16, from a 16-byte aligned shared-memory address.
+template <typename X, int N>
+__device__ __forceinline__ void ld16(const X *p, X (&o)[N]) {
+    static_assert((N * sizeof(X)) % 16 == 0, "whole 16-byte words");
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+    uint4 *d = reinterpret_cast<uint4 *>(o);
+#pragma unroll
+    for (int i = 0; i < (int)(N * sizeof(X) / 16); ++i) d[i] = q[i];
+}
+
 template <int PREC, int BT>
 __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     using T = PT<PREC>;
@@ -785,13 +795,20 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                     }
         }
         const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
-        // phase A: z = V^T x for every rank row of the stage
+        // phase A: z = V^T x for every rank row of the stage.  L lanes share a rank row, each summing at least
+        // four vectors before the shuffle tree (the tree's adds run on the same pipe as the products); the lanes
+        // of row slot rw start their sweep rw * L vectors further on, so the rows a warp reads fall in different
+        // shared-memory banks.  With a full batch (B == BT) the VE * BT history values of a vector are contiguous
+        // and are read with 16-byte loads.
         const int nz = si.n_zrows;
         if (nz > 0) {
             const int qv = q2 / VE;
-            const int L = qv <= 1 ? 1 : qv <= 2 ? 2 : qv <= 4 ? 4 : qv <= 8 ? 8 : qv <= 16 ? 16 : 32;
+            const int q4 = qv >> 2;
+            const int L = q4 >= 32 ? 32 : q4 >= 16 ? 16 : q4 >= 8 ? 8 : q4 >= 4 ? 4 : q4 >= 2 ? 2 : 1;
             const int subs = 32 / L, SA = kConsumerWarps * subs;
-            const int sl = lane % L, slotA = warp * subs + lane / L;
+            const int sl = lane % L, rw = lane / L, slotA = warp * subs + rw;
+            const int rot = (rw * L) % qv;
+            const bool xvec = a.B == BT;
             const int trips = (nz + SA - 1) / SA;              // uniform over the warp
             int k = 0, zstart = 0;
             for (int r = 0; r < trips; ++r) {
@@ -810,14 +827,25 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                     const S *vr = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)(f - zstart) * q2;
                     const X *x = reinterpret_cast<const X *>(base + itm.x_off);
                     sc = itm.scale;
-                    for (int u = sl; u < qv; u += L) {
+                    for (int i = sl; i < qv; i += L) {
+                        int u = i + rot;
+                        if (u >= qv) u -= qv;
                         E v[VE];
                         VecLoad<PREC, VE>::ld(vr + u * VE, v);
+                        if (xvec) {
+                            X xv[VE * BT];
+                            ld16(x + u * VE * BT, xv);
 #pragma unroll
-                        for (int e = 0; e < VE; ++e)
+                            for (int e = 0; e < VE; ++e)
 #pragma unroll
-                            for (int bb = 0; bb < BT; ++bb)
-                                edot(z[bb], v[e], x[(u * VE + e) * a.B + (bb < a.B ? bb : 0)]);
+                                for (int bb = 0; bb < BT; ++bb) edot(z[bb], v[e], xv[e * BT + bb]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < VE; ++e)
+#pragma unroll
+                                for (int bb = 0; bb < BT; ++bb)
+                                    edot(z[bb], v[e], x[(u * VE + e) * a.B + (bb < a.B ? bb : 0)]);
+                        }
                     }
                 }
 #pragma unroll
