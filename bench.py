@@ -41,10 +41,14 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=48, help="oracle element-steps in the CPU baseline")
     ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS), help="headline storage precision")
     ap.add_argument("--no-variants", action="store_true", help="skip the other storage precisions")
+    ap.add_argument("--dump-step-bytes", default=None, help="write the per-step algorithmic interaction bytes here")
     return ap.parse_args()
 
 
 # name -> (seas precision code, dtype label of the arithmetic)
+# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops at the 2070 MHz maximum SM clock
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
+FP64_PEAK_KIND = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"
 PRECISIONS = {"fp64": (0, "f64"), "df64": (3, "df64 (fp32 pairs)"), "bf16": (1, "bf16 storage, f32 compensated"),
               "fp16s": (2, "fp16 storage with per-slice scale, f32 compensated")}
 
@@ -272,13 +276,22 @@ def run_precision(seas, torch, wr, prec, Vd, K, W, dist, device, stream, peak):
     launches = timing["launches"]
     n_launch = max(1, launches["interaction"])
     inter_ms = ms["interaction"]
-    achieved = timing["interaction_bytes"] / (inter_ms / 1e3) / 1e9 if inter_ms > 0 else 0.0
+    secs = inter_ms / 1e3
+    achieved = timing["interaction_bytes"] / secs / 1e9 if inter_ms > 0 else 0.0
+    common = {"kernel": "k_interaction", "algorithmic_bytes_per_launch": timing["interaction_bytes"] / n_launch,
+              "mean_launch_ms": inter_ms / n_launch, "dominant_by_time": max(ms, key=ms.get), "kernel_ms": ms}
+    if prec == 0:
+        # FP64: one FMA per 8 algorithmic bytes per scenario; the FP64 pipe (2 FMA/clk/SM) is below the HBM rate
+        tflops = 2.0 * timing["interaction_bytes"] / 8 * s.scn.B / secs / 1e12 if inter_ms > 0 else 0.0
+        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / FP64_PEAK_TFLOPS, "peak_kind": FP64_PEAK_KIND,
+                "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak[0]}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak[0], "unit": "GB/s", "frac": achieved / peak[0],
+                "peak_kind": peak[1]}
+    roof.update(common)
     res = {"total_ms": total_ms, "per": per, "stats": s.stats, "timing": timing, "clocks": clk.summary(),
-           "roofline": {"bound": "hbm", "kernel": "k_interaction", "achieved": achieved, "peak": peak[0],
-                        "unit": "GB/s", "frac": achieved / peak[0], "peak_kind": peak[1],
-                        "algorithmic_bytes_per_launch": timing["interaction_bytes"] / n_launch,
-                        "mean_launch_ms": inter_ms / n_launch, "dominant_by_time": max(ms, key=ms.get),
-                        "kernel_ms": ms}}
+           "roofline": roof}
     s_keep = s
     return res, tau, s_keep
 
@@ -315,6 +328,11 @@ def run_ours(args, w, K, W):
 
     head_code, head_dtype = PRECISIONS[args.precision]
     res, tau, s = run_precision(seas, torch, wr, head_code, Vd, K, W, dist, device, stream, peak)
+    if args.dump_step_bytes and rank == 0:
+        # algorithmic interaction bytes of every step, to match profiled launches to steps
+        with open(args.dump_step_bytes, "w") as fh:
+            json.dump({"precision": args.precision, "steps": K,
+                       "bytes": [seas.seas_op_step_bytes(s.op, n) for n in range(K)]}, fh)
     value = wr.N * K * world / (res["total_ms"] / 1e3)
     err = err_of(tau)
     stats = res["stats"]
@@ -330,7 +348,8 @@ def run_ours(args, w, K, W):
                               "p99_ms": float(np.percentile(r2["per"], 99)), "rel_l2_vs_oracle": err_of(tau2),
                               "rel_l2_vs_headline": (tau2 - tau).norm().item() / tau.norm().item(),
                               "bytes_interaction": r2["stats"]["bytes_interaction"],
-                              "roofline": {k: r2["roofline"][k] for k in ("achieved", "frac", "mean_launch_ms")}}
+                              "roofline": {k: r2["roofline"][k] for k in (
+                                  "bound", "achieved", "peak", "unit", "frac", "mean_launch_ms")}}
             s2.close()
 
     # plain FP64 GPU path: every block dense (leaf blocks, exact windows), no compression, FP64 arithmetic
@@ -373,7 +392,9 @@ def run_ours(args, w, K, W):
         with open(tf) as fh:
             tr = json.load(fh)
         if tr.get("kernel_version") == seas_kernel_version() and tr.get("precision") == args.precision:
-            roofline["traffic"] = tr.get("dram_bytes_per_launch")
+            # DRAM bytes of the captured launches over their algorithmic bytes, scaled to this run's mean launch
+            roofline["traffic"] = tr["dram_over_algorithmic"] * roofline["algorithmic_bytes_per_launch"]
+            roofline["traffic_source"] = tr.get("source")
 
     line = None
     if rank == 0:

@@ -210,7 +210,8 @@ typedef struct {
 } seas_timing;
 seas_status seas_scenario_set_timing(seas_scn *scn, int enable);
 seas_status seas_scenario_get_timing(seas_scn *scn, seas_timing *out);
-/* Stored interaction-operator bytes that step `step` reads (slices with lag <= step). */
+/* Algorithmic interaction-operator bytes of step `step`: the values of every stored slice with lag <= step
+ * (p q near, k (p + q) far) times the storage element size; the 16-byte row padding is not counted. */
 seas_status seas_op_step_bytes(const seas_op *op, int64_t step, int64_t *bytes);
 
 /* Checkpoint/resume of a scenario: the step counter, slip-rate ring, slip and spectral ring. */

@@ -892,11 +892,11 @@ seas_status build_interaction(seas_op &op) {
     }
     std::stable_sort(tasks.begin(), tasks.end(), [](const TaskDev &x, const TaskDev &y) { return x.T_start < y.T_start; });
     for (auto &t : tasks) op.task_T.push_back(t.T_start);
+    // algorithmic bytes: the values each stored slice holds (p q near, k (p + q) far), row padding not counted
     op.bytes_upto.assign((size_t)op.ring, 0);
     for (const Stored &x : stored) {
         const BlockDev &b = op.blocks_h[x.block];
-        const int p2 = pad_row(b.p, prec), q2 = pad_row(b.q, prec);
-        op.bytes_upto[x.T] += eb * (x.k < 0 ? (int64_t)b.q * p2 : (int64_t)x.k * (p2 + q2));
+        op.bytes_upto[x.T] += eb * (x.k < 0 ? (int64_t)b.q * b.p : (int64_t)x.k * (b.p + b.q));
     }
     for (size_t T = 1; T < op.bytes_upto.size(); ++T) op.bytes_upto[T] += op.bytes_upto[T - 1];
     SEAS_TRY(op.d_items.upload(c, items));

@@ -759,7 +759,11 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     // flat list dealt to lane groups.  A monotone cursor maps a flat index to its item.  BF16/FP16: plain FP32
     // partial sums inside a stage, added into the Kahan-compensated accumulator once per stage.
     constexpr int VE = VecWidth<PREC, BT>::value;
-    constexpr int NVT = (kMaxBlockSide + VE * kConsumers - 1) / (VE * kConsumers);   // vectors per thread, max
+    // vectors per thread and row: aim at 8 multiply-adds per row (fewer index operations per product); at
+    // least enough vectors for the widest block when all 256 consumers share a row
+    constexpr int NVT_T = 8 / (VE * BT) > 1 ? 8 / (VE * BT) : 1;
+    constexpr int NVT_MIN = (kMaxBlockSide + VE * kConsumers - 1) / (VE * kConsumers);
+    constexpr int NVT = NVT_T > NVT_MIN ? NVT_T : NVT_MIN;
     constexpr bool MP = PREC == kPrecBF16 || PREC == kPrecFP16;
     using E = typename VecLoad<PREC, VE>::E;
     using PAcc = typename std::conditional<MP, float, Acc>::type;                     // per-stage partial
@@ -779,7 +783,8 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         if (task != cur) {
             cur = task;
             const int pv = p2 / VE;
-            P = pv <= kConsumers ? pv : kConsumers;
+            const int pn = (pv + NVT_T - 1) / NVT_T;
+            P = pn <= kConsumers ? pn : kConsumers;
             G = kConsumers / P;
             vec = t % P;
             grp = t / P;                               // grp == G: idle thread
@@ -924,36 +929,41 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         consumer_sync();
         if (t == 0) mbar_arrive(&empty[slot]);
         if (flush) {
-            // column c = (vec + s P) VE + e; groups reduced in a fixed order, 8 values per thread per round
-            constexpr int NV = NVT * VE * BT;
+            // column c = (vec + s P) VE + e; groups reduced in a fixed order.  With one group the threads past
+            // P are idle and hold zeros: only group 0 writes.
             if (G == 1) {
 #pragma unroll
                 for (int s = 0; s < NVT; ++s)
 #pragma unroll
                     for (int e = 0; e < VE; ++e) {
                         const int c = (vec + s * P) * VE + e;
-                        if (s < nvt && c < p)
+                        if (grp == 0 && s < nvt && c < p)
 #pragma unroll
                             for (int bb = 0; bb < BT; ++bb)
                                 if (bb < a.B)
                                     a.partial[(int64_t)bb * a.n_partial + part_off + c] = T::to_d(acc[s][e][bb]);
                     }
             } else {
+                // value v of a thread: vector s = v / (VE BT), element e, scenario bb; column (vec + s P) VE + e.
+                // Rounds of 8 values through shared memory; rounds past the task's vectors are skipped (uniform).
+                constexpr int NV = NVT * VE * BT;
+                const int nv = nvt * VE * BT;
 #pragma unroll
-                for (int r0 = 0; r0 < VE * BT; r0 += 8) {      // NVT == 1 when G > 1
+                for (int r0 = 0; r0 < NV; r0 += 8) {
+                    if (r0 >= nv) break;
 #pragma unroll
                     for (int m = 0; m < 8; ++m) {
                         const int v = r0 + m;
-                        if (v < VE * BT) red[t * 8 + m] = T::to_d(acc[0][v / BT][v % BT]);
+                        if (v < NV) red[t * 8 + m] = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
                     }
                     consumer_sync();
                     if (grp == 0) {
 #pragma unroll
                         for (int m = 0; m < 8; ++m) {
                             const int v = r0 + m;
-                            const int e = v / BT, bb = v % BT;
-                            const int c = vec * VE + e;
-                            if (v < VE * BT && c < p && bb < a.B) {
+                            const int sv = v / (VE * BT), e = (v / BT) % VE, bb = v % BT;
+                            const int c = (vec + sv * P) * VE + e;
+                            if (v < nv && c < p && bb < a.B) {
                                 double sum = 0.0;
                                 for (int gg = 0; gg < G; ++gg) sum += red[(gg * P + vec) * 8 + m];
                                 a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
@@ -962,7 +972,6 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                     }
                     consumer_sync();
                 }
-                (void)NV;
             }
             cur = -1;
         }
