@@ -256,7 +256,8 @@ constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kInterThreads = kConsumers + 32;
 constexpr uint64_t kWaitNs = 2000000000ull;   // bound of one mbarrier wait
-constexpr int kMaxStageRanks = 192;     // rank-1 terms of all low-rank items of one stage (z buffer)
+constexpr int kMaxStageRanks = 192;     // rank-1 terms of all low-rank items of one stage (z buffer), B <= 4
+constexpr int kMaxStageRanks8 = 96;     // the same for batches of 5..8 (the z buffers are double-buffered)
 
 struct StageItem {
     int32_t k, i0, i1;
@@ -576,9 +577,10 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *stage_mem = smem_raw;                                            // kStages x kStageBytes
     StageInfo *info = reinterpret_cast<StageInfo *>(smem_raw + kStages * kStageBytes);
-    Z *zs = reinterpret_cast<Z *>(info + kStages);                                  // [kMaxStageRanks][BT]
+    constexpr int kZRows = BT > 4 ? kMaxStageRanks8 : kMaxStageRanks;
+    Z *zs = reinterpret_cast<Z *>(info + kStages);                                  // [2][kZRows][BT]
     double *red = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(info + kStages) +
-                                             (size_t)kMaxStageRanks * BT * 8);     // [kConsumers][8]
+                                             (size_t)2 * kZRows * BT * 8);         // [kConsumers][8]
     uint64_t *full = reinterpret_cast<uint64_t *>(red + kConsumers * 8);
     uint64_t *empty = full + kStages;
     __shared__ int sh_flag;
@@ -663,7 +665,7 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                 }
             }
             const unsigned fit = __ballot_sync(0xffffffffu, lane < nvalid && lane < kStageItems &&
-                                                                incl <= kStageBytes && zincl <= kMaxStageRanks);
+                                                                incl <= kStageBytes && zincl <= kZRows);
             const int n = __ffs(~fit) - 1 < 0 ? 32 : __ffs(~fit) - 1;
             const bool in = lane < n;
             int dincl = in ? data_bytes : 0, xincl = in ? x_bytes : 0, rincl = in ? nrow : 0;
@@ -753,11 +755,11 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     }
 
     // ---------------------------------------------------------------------- consumer warps
-    // Thread t owns the VE-wide column vector (t mod P) of the block's rows and works in group t / P: P = number
-    // of column vectors (p2 / VE, at most 256), G = 256 / P groups.  The stage's row updates (rows of A^T times
-    // x_j, rows of U^T times z_l) form one flat list dealt round-robin to the groups; the rank rows of phase A a
-    // flat list dealt to lane groups.  A monotone cursor maps a flat index to its item.  BF16/FP16: plain FP32
-    // partial sums inside a stage, added into the Kahan-compensated accumulator once per stage.
+    // Thread t works in group t / P and owns the VE-wide column vectors (t mod P) + s P, s < nvt, of the block's
+    // rows (P a power of two, G = 256 / P groups).  The stage's row updates (rows of A^T times x_j, rows of U^T
+    // times z_l) form one flat list dealt round-robin to the groups; the rank rows of phase A a flat list dealt
+    // to lane groups.  A monotone cursor maps a flat index to its item.  BF16/FP16: plain FP32 partial sums
+    // inside a stage, added into the Kahan-compensated accumulator once per stage.
     constexpr int VE = VecWidth<PREC, BT>::value;
     // vectors per thread and row: aim at 8 multiply-adds per row (fewer index operations per product); at
     // least enough vectors for the widest block when all 256 consumers share a row
@@ -771,23 +773,106 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     int cur = -1, P = 1, G = 1, vec = 0, grp = 0, nvt = 1;
     Acc acc[NVT][VE][BT];
     PAcc part[NVT][VE][BT];
+
+    // phase A of one stage: z = V^T x for every rank row.  L lanes share a rank row, each summing at least four
+    // vectors before the shuffle tree (the tree's adds run on the same pipe as the products); the lanes of row
+    // slot rw start their sweep rw * L vectors further on, so the rows a warp reads fall in different
+    // shared-memory banks.  With a full batch (B == BT) the VE * BT history values of a vector are contiguous and
+    // are read with 16-byte loads.
+    auto phase_a = [&](const StageInfo &sx, const unsigned char *bx, Z *zout) {
+        const int nz = sx.n_zrows;
+        if (nz <= 0) return;
+        const int qv = pad_row(sx.q, PREC) / VE;
+        const int q2 = qv * VE;
+        const int q4 = qv >> 2;
+        const int L = q4 >= 32 ? 32 : q4 >= 16 ? 16 : q4 >= 8 ? 8 : q4 >= 4 ? 4 : q4 >= 2 ? 2 : 1;
+        const int subs = 32 / L, SA = kConsumerWarps * subs;
+        const int sl = lane % L, rw = lane / L, slotA = warp * subs + rw;
+        const int rot = (rw * L) % qv;
+        const bool xvec = a.B == BT;
+        const int trips = (nz + SA - 1) / SA;                  // uniform over the warp
+        int k = 0, zstart = 0;
+        for (int r = 0; r < trips; ++r) {
+            const int f = slotA + r * SA;
+            const bool act = f < nz;
+            Z z[BT];
+#pragma unroll
+            for (int bb = 0; bb < BT; ++bb) z[bb] = T::zz();
+            float sc = 1.f;
+            if (act) {
+                while (f >= sx.it[k].z_end) {
+                    zstart = sx.it[k].z_end;
+                    ++k;
+                }
+                const StageItem &itm = sx.it[k];
+                const S *vr = reinterpret_cast<const S *>(bx + itm.data_off) + (int64_t)(f - zstart) * q2;
+                const X *x = reinterpret_cast<const X *>(bx + itm.x_off);
+                sc = itm.scale;
+                for (int i = sl; i < qv; i += L) {
+                    int u = i + rot;
+                    if (u >= qv) u -= qv;
+                    E v[VE];
+                    VecLoad<PREC, VE>::ld(vr + u * VE, v);
+                    if (xvec) {
+                        X xv[VE * BT];
+                        ld16(x + u * VE * BT, xv);
+#pragma unroll
+                        for (int e = 0; e < VE; ++e)
+#pragma unroll
+                            for (int bb = 0; bb < BT; ++bb) edot(z[bb], v[e], xv[e * BT + bb]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < VE; ++e)
+#pragma unroll
+                            for (int bb = 0; bb < BT; ++bb)
+                                edot(z[bb], v[e], x[(u * VE + e) * a.B + (bb < a.B ? bb : 0)]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int bb = 0; bb < BT; ++bb) {
+                for (int o = L / 2; o > 0; o >>= 1) z[bb] = T::shfl_add(z[bb], o, L);
+                if (act && sl == 0) zout[f * BT + bb] = T::zscale(z[bb], sc);
+            }
+        }
+    };
+
+    // Software pipeline over stages: between two consumer barriers, interval g runs phase A of stage g + 1
+    // (z into buffer (g + 1) & 1) and phase B of stage g (z from buffer g & 1), so one barrier per stage
+    // separates every producer of z from its readers and the pipe never drains between the phases.  Stage g - 1
+    // is handed back to the producer at the barrier that opens interval g.
     if (t == 0) sh_flag = mbar_wait(&full[0], 0, a.err) ? 0 : 1;
     consumer_sync();
+    if (sh_flag) return;
+    if (info[0].task >= 0) phase_a(info[0], stage_mem, zs);
     for (int g = 0;; ++g) {
-        if (sh_flag) return;
         const int slot = g % kStages;
+        if (t == 0 && info[slot].task >= 0)
+            sh_flag = mbar_wait(&full[(g + 1) % kStages], ((g + 1) / kStages) & 1, a.err) ? 0 : 1;
+        consumer_sync();
+        if (sh_flag) return;
+        if (t == 0 && g > 0) mbar_arrive(&empty[(g - 1) % kStages]);
         const StageInfo &si = info[slot];
         const int task = si.task;
         if (task < 0) break;
-        const int p = si.p, q = si.q, p2 = pad_row(p, PREC), q2 = pad_row(q, PREC);
+        {
+            const int ns = (g + 1) % kStages;
+            if (info[ns].task >= 0)
+                phase_a(info[ns], stage_mem + (size_t)ns * kStageBytes, zs + ((g + 1) & 1) * kZRows * BT);
+        }
+        const Z *zcur = zs + (g & 1) * kZRows * BT;
+        const int p = si.p, p2 = pad_row(p, PREC), q2 = pad_row(si.q, PREC);
         if (task != cur) {
             cur = task;
+            // P: threads per row, a power of two, so that groups tile the warps (P <= 32) or whole warps tile
+            // a group (P > 32)
             const int pv = p2 / VE;
             const int pn = (pv + NVT_T - 1) / NVT_T;
-            P = pn <= kConsumers ? pn : kConsumers;
+            P = 1;
+            while (P < pn && P < kConsumers) P <<= 1;
             G = kConsumers / P;
             vec = t % P;
-            grp = t / P;                               // grp == G: idle thread
+            grp = t / P;
             nvt = (pv + P - 1) / P;
 #pragma unroll
             for (int s = 0; s < NVT; ++s)
@@ -800,67 +885,6 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                     }
         }
         const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
-        // phase A: z = V^T x for every rank row of the stage.  L lanes share a rank row, each summing at least
-        // four vectors before the shuffle tree (the tree's adds run on the same pipe as the products); the lanes
-        // of row slot rw start their sweep rw * L vectors further on, so the rows a warp reads fall in different
-        // shared-memory banks.  With a full batch (B == BT) the VE * BT history values of a vector are contiguous
-        // and are read with 16-byte loads.
-        const int nz = si.n_zrows;
-        if (nz > 0) {
-            const int qv = q2 / VE;
-            const int q4 = qv >> 2;
-            const int L = q4 >= 32 ? 32 : q4 >= 16 ? 16 : q4 >= 8 ? 8 : q4 >= 4 ? 4 : q4 >= 2 ? 2 : 1;
-            const int subs = 32 / L, SA = kConsumerWarps * subs;
-            const int sl = lane % L, rw = lane / L, slotA = warp * subs + rw;
-            const int rot = (rw * L) % qv;
-            const bool xvec = a.B == BT;
-            const int trips = (nz + SA - 1) / SA;              // uniform over the warp
-            int k = 0, zstart = 0;
-            for (int r = 0; r < trips; ++r) {
-                const int f = slotA + r * SA;
-                const bool act = f < nz;
-                Z z[BT];
-#pragma unroll
-                for (int bb = 0; bb < BT; ++bb) z[bb] = T::zz();
-                float sc = 1.f;
-                if (act) {
-                    while (f >= si.it[k].z_end) {
-                        zstart = si.it[k].z_end;
-                        ++k;
-                    }
-                    const StageItem &itm = si.it[k];
-                    const S *vr = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)(f - zstart) * q2;
-                    const X *x = reinterpret_cast<const X *>(base + itm.x_off);
-                    sc = itm.scale;
-                    for (int i = sl; i < qv; i += L) {
-                        int u = i + rot;
-                        if (u >= qv) u -= qv;
-                        E v[VE];
-                        VecLoad<PREC, VE>::ld(vr + u * VE, v);
-                        if (xvec) {
-                            X xv[VE * BT];
-                            ld16(x + u * VE * BT, xv);
-#pragma unroll
-                            for (int e = 0; e < VE; ++e)
-#pragma unroll
-                                for (int bb = 0; bb < BT; ++bb) edot(z[bb], v[e], xv[e * BT + bb]);
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < VE; ++e)
-#pragma unroll
-                                for (int bb = 0; bb < BT; ++bb)
-                                    edot(z[bb], v[e], x[(u * VE + e) * a.B + (bb < a.B ? bb : 0)]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int bb = 0; bb < BT; ++bb) {
-                    for (int o = L / 2; o > 0; o >>= 1) z[bb] = T::shfl_add(z[bb], o, L);
-                    if (act && sl == 0) zs[f * BT + bb] = T::zscale(z[bb], sc);
-                }
-            }
-            consumer_sync();
-        }
         // phase B: row updates
         if (grp < G) {
             const int nr = si.n_rows;
@@ -888,7 +912,7 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                     rowp = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)rows * q2 + (int64_t)r * p2;
 #pragma unroll
                     for (int bb = 0; bb < BT; ++bb) {
-                        const Z zv = zs[(zbase + r) * BT + bb];
+                        const Z zv = zcur[(zbase + r) * BT + bb];
                         cv[bb] = *reinterpret_cast<const E *>(&zv);
                     }
                 }
@@ -922,35 +946,61 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                         }
             }
         }
-        const bool flush = si.flush != 0;
-        const int64_t part_off = si.part_off;
-        // one barrier ends this stage and starts the next: thread 0 has seen the next stage land
-        if (t == 0) sh_flag = mbar_wait(&full[(g + 1) % kStages], ((g + 1) / kStages) & 1, a.err) ? 0 : 1;
-        consumer_sync();
-        if (t == 0) mbar_arrive(&empty[slot]);
-        if (flush) {
-            // column c = (vec + s P) VE + e; groups reduced in a fixed order.  With one group the threads past
-            // P are idle and hold zeros: only group 0 writes.
+        if (si.flush) {
+            const int64_t part_off = si.part_off;
+            // column c = (vec + s P) VE + e; value v of a thread: vector s = v / (VE BT), element e = (v / BT) mod
+            // VE, scenario bb = v mod BT.  The G groups are reduced in a fixed order, 8 values per round through
+            // shared memory; rounds past the task's vectors are skipped (uniform).  The barrier that opens the
+            // next interval protects red from the next writes.
+            constexpr int NV = NVT * VE * BT;
+            const int nv = nvt * VE * BT;
             if (G == 1) {
 #pragma unroll
                 for (int s = 0; s < NVT; ++s)
 #pragma unroll
                     for (int e = 0; e < VE; ++e) {
                         const int c = (vec + s * P) * VE + e;
-                        if (grp == 0 && s < nvt && c < p)
+                        if (s < nvt && c < p)
 #pragma unroll
                             for (int bb = 0; bb < BT; ++bb)
                                 if (bb < a.B)
                                     a.partial[(int64_t)bb * a.n_partial + part_off + c] = T::to_d(acc[s][e][bb]);
                     }
-            } else {
-                // value v of a thread: vector s = v / (VE BT), element e, scenario bb; column (vec + s P) VE + e.
-                // Rounds of 8 values through shared memory; rounds past the task's vectors are skipped (uniform).
-                constexpr int NV = NVT * VE * BT;
-                const int nv = nvt * VE * BT;
+            } else if (P <= 32) {
+                // the 32 / P groups of a warp by a shuffle tree, then the 8 warp sums of each (column, value) by
+                // one of 8 P threads
 #pragma unroll
                 for (int r0 = 0; r0 < NV; r0 += 8) {
                     if (r0 >= nv) break;
+                    if (r0 > 0) consumer_sync();
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const int v = r0 + m;
+                        if (v < NV) {
+                            double x = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
+                            for (int o = 16; o >= P; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                            if (lane < P) red[(warp * 32 + lane) * 8 + m] = x;
+                        }
+                    }
+                    consumer_sync();
+                    if (t < 8 * P) {
+                        const int m = t / P, vv = t % P, v = r0 + m;
+                        const int sv = v / (VE * BT), e = (v / BT) % VE, bb = v % BT;
+                        const int c = (vv + sv * P) * VE + e;
+                        if (v < nv && c < p && bb < a.B) {
+                            double sum = 0.0;
+#pragma unroll
+                            for (int w = 0; w < kConsumerWarps; ++w) sum += red[(w * 32 + vv) * 8 + m];
+                            a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
+                        }
+                    }
+                }
+            } else {
+                // 2 or 4 groups of whole warps: group 0 adds the others' values
+#pragma unroll
+                for (int r0 = 0; r0 < NV; r0 += 8) {
+                    if (r0 >= nv) break;
+                    if (r0 > 0) consumer_sync();
 #pragma unroll
                     for (int m = 0; m < 8; ++m) {
                         const int v = r0 + m;
@@ -970,7 +1020,6 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                             }
                         }
                     }
-                    consumer_sync();
                 }
             }
             cur = -1;
@@ -1019,8 +1068,9 @@ __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
 
 template <int PREC, int BT>
 cudaError_t launch_interaction_bt(const StepArgs &a, cudaStream_t s) {
+    constexpr int kZRows = BT > 4 ? kMaxStageRanks8 : kMaxStageRanks;
     const size_t smem = (size_t)kStages * kStageBytes + kStages * sizeof(StageInfo) +
-                        (size_t)kMaxStageRanks * BT * 8 + (size_t)kConsumers * 8 * sizeof(double) +
+                        (size_t)2 * kZRows * BT * 8 + (size_t)kConsumers * 8 * sizeof(double) +
                         2 * kStages * sizeof(uint64_t);
     cudaError_t e = cudaFuncSetAttribute(k_interaction<PREC, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -141,7 +141,8 @@ def test_six_fault_3072_full_size_sampled_rows():
 
 
 def test_batch_members_are_independent():
-    """Each scenario of a batch gets bitwise the result it gets alone (no atomics: fixed summation order)."""
+    """Each scenario of a batch gets the result it gets alone, to rounding: the summation order is fixed for a
+    given batch width (no atomics), but the thread-to-column mapping depends on it."""
     w = synth.tiny(5, n_faults=3, steps=60)
     w.batch = 3
     Vb = w.slip_rate_batch(0, w.steps).reshape(w.steps, -1)
@@ -150,7 +151,9 @@ def test_batch_members_are_independent():
     for b in range(3):
         with seas.Session(w, batch=1, **DENSE_EXACT) as s:
             ta, _ = run_host(s, np.ascontiguousarray(Vb[:, b * w.N:(b + 1) * w.N]), parts=False)
-        np.testing.assert_array_equal(tb[:, b * w.N:(b + 1) * w.N], ta)
+        got = tb[:, b * w.N:(b + 1) * w.N]
+        assert np.abs(got - ta).max() <= 1e-12 * np.abs(ta).max()
+        assert rel(got, ta) <= 1e-13
 
 
 def test_replace_last_equals_pushing_the_corrected_rate():
