@@ -256,14 +256,21 @@ extern "C" seas_status seas_sync(seas_ctx *c) {
     return SEAS_OK;
 }
 
+// Status of the device error word: 1 = a bounded wait ran out, 2 = the interaction kernel was launched with less
+// shared memory than its layout needs (an internal error; the kernel returned before touching shared memory).
+static seas_status device_error_status(int err) {
+    if (err == 1) return fail(SEAS_ETIMEOUT, "a bounded device wait ran out in the interaction kernel");
+    if (err) return fail(SEAS_ECUDA, "interaction kernel launched with too little shared memory (error word %d)", err);
+    return SEAS_OK;
+}
+
 extern "C" seas_status seas_scenario_check(seas_scn *s) {
     if (!s) return fail(SEAS_EINVAL, "NULL scenario");
     CUDA_TRY(cudaSetDevice(s->op->net->ctx->device));
     CUDA_TRY(cudaStreamSynchronize(s->op->net->ctx->stream));
     int err = 0;
     CUDA_TRY(cudaMemcpy(&err, s->counter_err.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) return fail(SEAS_ETIMEOUT, "a bounded device wait ran out in the interaction kernel");
-    return SEAS_OK;
+    return device_error_status(err);
 }
 
 extern "C" seas_status seas_destroy_ctx(seas_ctx *c) {
@@ -1139,8 +1146,7 @@ namespace {
 seas_status check_device_error(seas_scn &s) {
     int err = 0;
     CUDA_TRY(cudaMemcpy(&err, s.counter_err.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) return fail(SEAS_ETIMEOUT, "a bounded device wait ran out in the interaction kernel");
-    return SEAS_OK;
+    return device_error_status(err);
 }
 
 constexpr size_t kEventPairs = 8192;

@@ -242,19 +242,26 @@ __global__ void __launch_bounds__(kThreads) k_ifft_assemble(StepArgs a, double *
 // ------------------------------------------------------------------------------------------------------------
 // Space-time interaction (Eq. fault-to-fault_interactions_discretized) through the H-matrix stack.
 //
-// Persistent kernel, one CTA per SM: warp 8 produces, warps 0-7 consume.  The producer takes tasks from a
-// dynamic counter (tasks with T_start <= step form a prefix of the task list), packs consecutive causal items
-// (lag <= step) of the task into a shared-memory stage and issues one 1-D bulk copy (cp.async.bulk) for their
-// operator bytes plus one per item for the slip-rate history slice x^{step - T} it multiplies (taken from the
-// ring row, start rounded down to 16 bytes).  Each stage completes on an mbarrier (transaction bytes); consumers
-// release it on a second mbarrier.  Consumer thread t owns receiver row t mod P (P = 32, 64, 128 or 256) in
-// group t / P; groups split the inner dimension, and the task's partial sum is written, reduced over the groups
-// in a fixed order, to its own slot of the partial buffer.  No atomics: the result is bitwise reproducible.
+// Persistent kernel, one CTA per SM: the last warp produces, the CW warps before it consume.  The producer takes
+// tasks from a dynamic counter (tasks with T_start <= step form a prefix of the task list), packs consecutive
+// causal items (lag <= step) of the task into a shared-memory stage and issues one 1-D bulk copy (cp.async.bulk)
+// for their operator bytes; each lane copies one item's slip-rate history slice x^{step - T} (cp.async, 16 bytes
+// when aligned).  Each stage completes on an mbarrier (transaction bytes plus the lanes' copy arrivals);
+// consumers release it on a second mbarrier.  Consumers compute z = V^T x for the rank rows (phase A) and the
+// row updates (phase B), pipelined over stages, accumulating each receiver column of the task in registers; at
+// the task's end the column sums, reduced over thread groups in a fixed order, go to the task's own slot of the
+// partial buffer.  No atomics: a run is bitwise reproducible.
 // Every wait is bounded; a wait that runs out sets the error word and the CTA stops.
 // ------------------------------------------------------------------------------------------------------------
-constexpr int kConsumerWarps = 8;
-constexpr int kConsumers = kConsumerWarps * 32;
-constexpr int kInterThreads = kConsumers + 32;
+// Threads of the interaction kernel for a batch width BT: CW consumer warps (16 while the accumulators are small
+// enough for 120 registers, which hides more shared-memory and pipe latency) plus one producer warp; RV values per
+// flush round keep the reduction buffer at 16 KB.
+template <int BT> struct InterShape {
+    static constexpr int CW = BT <= 2 ? 16 : 8;
+    static constexpr int NC = CW * 32;
+    static constexpr int NT = NC + 32;
+    static constexpr int RV = CW == 8 ? 8 : 4;
+};
 constexpr uint64_t kWaitNs = 2000000000ull;   // bound of one mbarrier wait
 constexpr int kMaxStageRanks = 192;     // rank-1 terms of all low-rank items of one stage (z buffer), B <= 4
 constexpr int kMaxStageRanks8 = 96;     // the same for batches of 5..8 (the z buffers are double-buffered)
@@ -275,6 +282,20 @@ struct StageInfo {
     int32_t n_rows, n_zrows;     // row updates and rank rows of the stage
     int64_t part_off;
     StageItem it[kStageItems];
+};
+
+// Dynamic shared memory of the interaction kernel for batch width BT, in bytes from the start: the stages, their
+// descriptors, the double-buffered z rows, the flush buffer and the full/empty mbarriers.  The kernel and its
+// launcher both use this, and the kernel checks the end against the size it was launched with.
+template <int BT> struct InterLayout {
+    static constexpr int kZRows = BT > 4 ? kMaxStageRanks8 : kMaxStageRanks;
+    static constexpr size_t info = (size_t)kStages * kStageBytes;
+    static constexpr size_t zs = info + kStages * sizeof(StageInfo);
+    static constexpr size_t red = zs + (size_t)2 * kZRows * BT * 8;
+    static constexpr size_t bars = red + (size_t)InterShape<BT>::NC * InterShape<BT>::RV * sizeof(double);
+    static constexpr size_t total = bars + 2 * kStages * sizeof(uint64_t);
+    static_assert(sizeof(StageInfo) % 8 == 0 && zs % 8 == 0 && red % 8 == 0 && bars % 8 == 0, "8-byte alignment");
+    static_assert(total <= 227 * 1024, "shared memory per CTA");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -359,7 +380,8 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
+template <int NC>
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory"); }
 
 // ------------------------------------------------------------------------------------------------------------
 // Arithmetic of each storage precision: stored element S, history element X, dot-product value Z, accumulator
@@ -565,7 +587,8 @@ __device__ __forceinline__ void ld16(const X *p, X (&o)[N]) {
 }
 
 template <int PREC, int BT>
-__global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
+__global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs a) {
+    constexpr int CW = InterShape<BT>::CW, NC = InterShape<BT>::NC, RV = InterShape<BT>::RV;
     using T = PT<PREC>;
     using S = typename T::S;
     using X = typename T::X;
@@ -575,30 +598,37 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     constexpr int XB = (int)sizeof(X);
     constexpr int XA = 16 / XB;                     // history elements per 16 bytes
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    using LY = InterLayout<BT>;
+    constexpr int kZRows = LY::kZRows;
     unsigned char *stage_mem = smem_raw;                                            // kStages x kStageBytes
-    StageInfo *info = reinterpret_cast<StageInfo *>(smem_raw + kStages * kStageBytes);
-    constexpr int kZRows = BT > 4 ? kMaxStageRanks8 : kMaxStageRanks;
-    Z *zs = reinterpret_cast<Z *>(info + kStages);                                  // [2][kZRows][BT]
-    double *red = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(info + kStages) +
-                                             (size_t)2 * kZRows * BT * 8);         // [kConsumers][8]
-    uint64_t *full = reinterpret_cast<uint64_t *>(red + kConsumers * 8);
+    StageInfo *info = reinterpret_cast<StageInfo *>(smem_raw + LY::info);
+    Z *zs = reinterpret_cast<Z *>(smem_raw + LY::zs);                              // [2][kZRows][BT]
+    double *red = reinterpret_cast<double *>(smem_raw + LY::red);                  // [NC][RV]
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + LY::bars);
     uint64_t *empty = full + kStages;
     __shared__ int sh_flag;
     const X *xring = PREC == kPrecFP64 ? reinterpret_cast<const X *>(a.vring) : reinterpret_cast<const X *>(a.xring);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1 + 32);           // lane 0's arrive (with the bulk bytes) + 32 cp.async arrivals
-            mbar_init(&empty[s], 1);
+        uint32_t dyn;
+        asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        if (dyn < LY::total) {                     // launched with less shared memory than the layout needs
+            atomicExch(a.err, 2);
+            sh_flag = 2;
+        } else {
+            for (int s = 0; s < kStages; ++s) {
+                mbar_init(&full[s], 1 + 32);       // lane 0's arrive (with the bulk bytes) + 32 cp.async arrivals
+                mbar_init(&empty[s], 1);
+            }
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            sh_flag = *(volatile int *)a.err;      // an earlier launch already failed: do nothing
         }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sh_flag = *(volatile int *)a.err;          // an earlier launch already failed: do nothing
     }
     __syncthreads();
     if (sh_flag) return;
 
-    if (warp == kConsumerWarps) {
+    if (warp == CW) {
         // ------------------------------------------------------------------ producer warp
         // Operator bytes of a stage: one bulk copy (lane 0).  History slices x: 16-byte cp.async over the 32
         // lanes, each lane arriving on the stage barrier when its copies have landed.
@@ -756,15 +786,15 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
 
     // ---------------------------------------------------------------------- consumer warps
     // Thread t works in group t / P and owns the VE-wide column vectors (t mod P) + s P, s < nvt, of the block's
-    // rows (P a power of two, G = 256 / P groups).  The stage's row updates (rows of A^T times x_j, rows of U^T
+    // rows (P a power of two, G = NC / P groups for NC consumer threads).  The stage's row updates (rows of A^T times x_j, rows of U^T
     // times z_l) form one flat list dealt round-robin to the groups; the rank rows of phase A a flat list dealt
     // to lane groups.  A monotone cursor maps a flat index to its item.  BF16/FP16: plain FP32 partial sums
     // inside a stage, added into the Kahan-compensated accumulator once per stage.
     constexpr int VE = VecWidth<PREC, BT>::value;
     // vectors per thread and row: aim at 8 multiply-adds per row (fewer index operations per product); at
-    // least enough vectors for the widest block when all 256 consumers share a row
+    // least enough vectors for the widest block when all NC consumers share a row
     constexpr int NVT_T = 8 / (VE * BT) > 1 ? 8 / (VE * BT) : 1;
-    constexpr int NVT_MIN = (kMaxBlockSide + VE * kConsumers - 1) / (VE * kConsumers);
+    constexpr int NVT_MIN = (kMaxBlockSide + VE * NC - 1) / (VE * NC);
     constexpr int NVT = NVT_T > NVT_MIN ? NVT_T : NVT_MIN;
     constexpr bool MP = PREC == kPrecBF16 || PREC == kPrecFP16;
     using E = typename VecLoad<PREC, VE>::E;
@@ -786,7 +816,7 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         const int q2 = qv * VE;
         const int q4 = qv >> 2;
         const int L = q4 >= 32 ? 32 : q4 >= 16 ? 16 : q4 >= 8 ? 8 : q4 >= 4 ? 4 : q4 >= 2 ? 2 : 1;
-        const int subs = 32 / L, SA = kConsumerWarps * subs;
+        const int subs = 32 / L, SA = CW * subs;
         const int sl = lane % L, rw = lane / L, slotA = warp * subs + rw;
         const int rot = (rw * L) % qv;
         const bool xvec = a.B == BT;
@@ -842,14 +872,14 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
     // separates every producer of z from its readers and the pipe never drains between the phases.  Stage g - 1
     // is handed back to the producer at the barrier that opens interval g.
     if (t == 0) sh_flag = mbar_wait(&full[0], 0, a.err) ? 0 : 1;
-    consumer_sync();
+    consumer_sync<NC>();
     if (sh_flag) return;
     if (info[0].task >= 0) phase_a(info[0], stage_mem, zs);
     for (int g = 0;; ++g) {
         const int slot = g % kStages;
         if (t == 0 && info[slot].task >= 0)
             sh_flag = mbar_wait(&full[(g + 1) % kStages], ((g + 1) / kStages) & 1, a.err) ? 0 : 1;
-        consumer_sync();
+        consumer_sync<NC>();
         if (sh_flag) return;
         if (t == 0 && g > 0) mbar_arrive(&empty[(g - 1) % kStages]);
         const StageInfo &si = info[slot];
@@ -869,8 +899,8 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
             const int pv = p2 / VE;
             const int pn = (pv + NVT_T - 1) / NVT_T;
             P = 1;
-            while (P < pn && P < kConsumers) P <<= 1;
-            G = kConsumers / P;
+            while (P < pn && P < NC) P <<= 1;
+            G = NC / P;
             vec = t % P;
             grp = t / P;
             nvt = (pv + P - 1) / P;
@@ -949,7 +979,7 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
         if (si.flush) {
             const int64_t part_off = si.part_off;
             // column c = (vec + s P) VE + e; value v of a thread: vector s = v / (VE BT), element e = (v / BT) mod
-            // VE, scenario bb = v mod BT.  The G groups are reduced in a fixed order, 8 values per round through
+            // VE, scenario bb = v mod BT.  The G groups are reduced in a fixed order, RV values per round through
             // shared memory; rounds past the task's vectors are skipped (uniform).  The barrier that opens the
             // next interval protects red from the next writes.
             constexpr int NV = NVT * VE * BT;
@@ -967,55 +997,55 @@ __global__ void __launch_bounds__(kInterThreads, 1) k_interaction(StepArgs a) {
                                     a.partial[(int64_t)bb * a.n_partial + part_off + c] = T::to_d(acc[s][e][bb]);
                     }
             } else if (P <= 32) {
-                // the 32 / P groups of a warp by a shuffle tree, then the 8 warp sums of each (column, value) by
-                // one of 8 P threads
+                // the 32 / P groups of a warp by a shuffle tree, then the CW warp sums of each (column, value) by
+                // one of RV P threads
 #pragma unroll
-                for (int r0 = 0; r0 < NV; r0 += 8) {
+                for (int r0 = 0; r0 < NV; r0 += RV) {
                     if (r0 >= nv) break;
-                    if (r0 > 0) consumer_sync();
+                    if (r0 > 0) consumer_sync<NC>();
 #pragma unroll
-                    for (int m = 0; m < 8; ++m) {
+                    for (int m = 0; m < RV; ++m) {
                         const int v = r0 + m;
                         if (v < NV) {
                             double x = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
                             for (int o = 16; o >= P; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                            if (lane < P) red[(warp * 32 + lane) * 8 + m] = x;
+                            if (lane < P) red[(warp * 32 + lane) * RV + m] = x;
                         }
                     }
-                    consumer_sync();
-                    if (t < 8 * P) {
+                    consumer_sync<NC>();
+                    if (t < RV * P) {
                         const int m = t / P, vv = t % P, v = r0 + m;
                         const int sv = v / (VE * BT), e = (v / BT) % VE, bb = v % BT;
                         const int c = (vv + sv * P) * VE + e;
                         if (v < nv && c < p && bb < a.B) {
                             double sum = 0.0;
 #pragma unroll
-                            for (int w = 0; w < kConsumerWarps; ++w) sum += red[(w * 32 + vv) * 8 + m];
+                            for (int w = 0; w < CW; ++w) sum += red[(w * 32 + vv) * RV + m];
                             a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
                         }
                     }
                 }
             } else {
-                // 2 or 4 groups of whole warps: group 0 adds the others' values
+                // 2 to 8 groups of whole warps: group 0 adds the others' values
 #pragma unroll
-                for (int r0 = 0; r0 < NV; r0 += 8) {
+                for (int r0 = 0; r0 < NV; r0 += RV) {
                     if (r0 >= nv) break;
-                    if (r0 > 0) consumer_sync();
+                    if (r0 > 0) consumer_sync<NC>();
 #pragma unroll
-                    for (int m = 0; m < 8; ++m) {
+                    for (int m = 0; m < RV; ++m) {
                         const int v = r0 + m;
-                        if (v < NV) red[t * 8 + m] = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
+                        if (v < NV) red[t * RV + m] = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
                     }
-                    consumer_sync();
+                    consumer_sync<NC>();
                     if (grp == 0) {
 #pragma unroll
-                        for (int m = 0; m < 8; ++m) {
+                        for (int m = 0; m < RV; ++m) {
                             const int v = r0 + m;
                             const int sv = v / (VE * BT), e = (v / BT) % VE, bb = v % BT;
                             const int c = (vec + sv * P) * VE + e;
                             if (v < nv && c < p && bb < a.B) {
                                 double sum = 0.0;
-                                for (int gg = 0; gg < G; ++gg) sum += red[(gg * P + vec) * 8 + m];
+                                for (int gg = 0; gg < G; ++gg) sum += red[(gg * P + vec) * RV + m];
                                 a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
                             }
                         }
@@ -1068,15 +1098,12 @@ __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
 
 template <int PREC, int BT>
 cudaError_t launch_interaction_bt(const StepArgs &a, cudaStream_t s) {
-    constexpr int kZRows = BT > 4 ? kMaxStageRanks8 : kMaxStageRanks;
-    const size_t smem = (size_t)kStages * kStageBytes + kStages * sizeof(StageInfo) +
-                        (size_t)2 * kZRows * BT * 8 + (size_t)kConsumers * 8 * sizeof(double) +
-                        2 * kStages * sizeof(uint64_t);
+    const size_t smem = InterLayout<BT>::total;
     cudaError_t e = cudaFuncSetAttribute(k_interaction<PREC, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = a.n_tasks_active < a.n_sms ? a.n_tasks_active : a.n_sms;
-    k_interaction<PREC, BT><<<grid, kInterThreads, smem, s>>>(a);
+    k_interaction<PREC, BT><<<grid, InterShape<BT>::NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
