@@ -805,16 +805,17 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
     PAcc part[NVT][VE][BT];
 
     // phase A of one stage: z = V^T x for every rank row.  L lanes share a rank row, each summing at least four
-    // vectors before the shuffle tree (the tree's adds run on the same pipe as the products); the lanes of row
-    // slot rw start their sweep rw * L vectors further on, so the rows a warp reads fall in different
-    // shared-memory banks.  With a full batch (B == BT) the VE * BT history values of a vector are contiguous and
-    // are read with 16-byte loads.
+    // vectors before the shuffle tree (the tree's adds run on the same pipe as the products), which keeps every
+    // consumer warp busy; DF64 takes one lane per row, its shuffle adds costing a dozen FP32 operations each.
+    // The lanes of row slot rw start their sweep rw * L vectors further on, so the rows a warp reads fall in
+    // different shared-memory banks.  With a full batch (B == BT) the VE * BT history values of a vector are
+    // contiguous and are read with 16-byte loads.
     auto phase_a = [&](const StageInfo &sx, const unsigned char *bx, Z *zout) {
         const int nz = sx.n_zrows;
         if (nz <= 0) return;
         const int qv = pad_row(sx.q, PREC) / VE;
         const int q2 = qv * VE;
-        const int q4 = qv >> 2;
+        const int q4 = PREC == kPrecDF64 ? 0 : qv >> 2;
         const int L = q4 >= 32 ? 32 : q4 >= 16 ? 16 : q4 >= 8 ? 8 : q4 >= 4 ? 4 : q4 >= 2 ? 2 : 1;
         const int subs = 32 / L, SA = CW * subs;
         const int sl = lane % L, rw = lane / L, slotA = warp * subs + rw;
@@ -996,6 +997,57 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
                                 if (bb < a.B)
                                     a.partial[(int64_t)bb * a.n_partial + part_off + c] = T::to_d(acc[s][e][bb]);
                     }
+            } else if (NV <= 8 && P <= 16) {
+                // Reduce-scatter over the 32 / P groups of a warp: at the level with lane distance o a lane keeps
+                // the half of its values selected by lane bit o and adds its partner's copy of that half, so the
+                // values per lane halve at each level (plain adds once a single value is left).  Lane l then holds
+                // values base(l) .. base(l) + cnt - 1 of column vector l mod P, summed over the warp's groups.
+                // The CW warp sums of each (vector, value) are added by one of P NV threads.
+                double vals[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) vals[v] = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
+                int base = 0, cnt = NV;
+                bool writer = true;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const int o = 16 >> k;
+                    if (o < P) break;
+                    const bool upper = (lane & o) != 0;
+                    if ((NV >> k) >= 2) {
+                        const int half = (NV >> k) / 2;
+#pragma unroll
+                        for (int j = 0; j < NV / 2; ++j) {
+                            if (j < half) {
+                                const double send = upper ? vals[j] : vals[j + half];
+                                const double keep = upper ? vals[j + half] : vals[j];
+                                vals[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                            }
+                        }
+                        if (upper) base += half;
+                        cnt = half;
+                    } else {
+                        vals[0] += __shfl_xor_sync(0xffffffffu, vals[0], o);
+                        if (upper) writer = false;             // the partner holds the same sum
+                    }
+                }
+                const int vv = lane % P;
+                if (writer) {
+#pragma unroll
+                    for (int j = 0; j < NV; ++j)
+                        if (j < cnt) red[(warp * P + vv) * NV + base + j] = vals[j];
+                }
+                consumer_sync<NC>();
+                if (t < P * NV) {
+                    const int vt = t % P, v = t / P;
+                    const int sv = v / (VE * BT), e = (v / BT) % VE, bb = v % BT;
+                    const int c = (vt + sv * P) * VE + e;
+                    if (v < nv && c < p && bb < a.B) {
+                        double sum = 0.0;
+#pragma unroll
+                        for (int w = 0; w < CW; ++w) sum += red[(w * P + vt) * NV + v];
+                        a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
+                    }
+                }
             } else if (P <= 32) {
                 // the 32 / P groups of a warp by a shuffle tree, then the CW warp sums of each (column, value) by
                 // one of RV P threads
