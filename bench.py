@@ -391,9 +391,10 @@ def run_ours(args, w, K, W):
     if os.path.exists(tf):
         with open(tf) as fh:
             tr = json.load(fh)
-        if tr.get("kernel_version") == seas_kernel_version() and tr.get("precision") == args.precision:
-            # DRAM bytes of the captured launches over their algorithmic bytes, scaled to this run's mean launch
-            roofline["traffic"] = tr["dram_over_algorithmic"] * roofline["algorithmic_bytes_per_launch"]
+        ratio = tr.get("dram_over_algorithmic", {}).get(args.precision)
+        if tr.get("kernel_version") == seas_kernel_version() and ratio is not None:
+            # DRAM bytes of the captured launch over its algorithmic bytes, scaled to this run's mean launch
+            roofline["traffic"] = ratio * roofline["algorithmic_bytes_per_launch"]
             roofline["traffic_source"] = tr.get("source")
 
     line = None
