@@ -25,7 +25,9 @@ What it computes, step by step, in plain FP64 NumPy (no blocking, no compression
 
 Windows (optional, off by default): mode-dependent self windows W_f(n) = ceil(T_end(n)/dt) with
 T_end(n) = eta_w L_f / c_s * Lcal(n) (Eq. mode_dependent_truncation) and per fault-pair interaction windows ending at
-ceil((1 + eta_Tmax) T_max / dt) (Sec. 2.3.2, "Truncation of elastodynamic time-window").
+ceil((1 + eta_Tmax) T_max / dt) (Sec. 2.3.2, "Truncation of elastodynamic time-window").  Static tail (flag 4,
+not in the paper, off by default): the history a window drops is added back as an elastostatic response, per mode
+c_n D_n^{m - W - 1} with c_n = (2/pi) Si(n pi) - sum_{T <= W} w_n^T, per fault pair A^static delta^{m - T_last - 1}.
 
 Parity status: every function here is pinned by tests/test_oracle_pins.py (closed forms, special cases, printed
 numbers, brute force in extended precision).
@@ -154,6 +156,32 @@ def interaction_slice(net: Network, T, rows=None, cols=None, dtype=np.float64) -
     A = n1 * k31 + n2 * k32
     same = net.fault_of[rows][:, None] == net.fault_of[cols][None, :]
     return np.where(same, dtype(0), A)
+
+
+def static_slice(net: Network, rows=None, cols=None) -> np.ndarray:
+    """A_ij^static = lim_{T -> inf} A_ij^T / dt: the elastostatic stress at receiver i of unit slip on source element
+    j.  As t -> inf, dI_31/dt -> -(c_s / pi) r2 / r^2 and dI_32/dt -> (c_s / pi) r1 / r^2 (Eq. primitives), so the
+    element difference of Eq. kernel_interactions gives S_31 = -(c_s/pi)(r2/rho_+^2 - r2/rho_-^2),
+    S_32 = (c_s/pi)(r1_+/rho_+^2 - r1_-/rho_-^2), r1_+- = r1 +- ds/2, rho_+-^2 = r1_+-^2 + r2^2; projected like
+    interaction_slice.  Same-fault entries are zero."""
+    rows = np.arange(net.N) if rows is None else np.asarray(rows)
+    cols = np.arange(net.N) if cols is None else np.asarray(cols)
+    d = net.x[rows][:, None, :] - net.x[cols][None, :, :]
+    e1 = net.e1[cols][None, :, :]
+    e2 = net.nrm[cols][None, :, :]
+    r1 = (d * e1).sum(-1)
+    r2 = (d * e2).sum(-1)
+    nr = net.nrm[rows][:, None, :]
+    n1 = (nr * e1).sum(-1)
+    n2 = (nr * e2).sum(-1)
+    h = 0.5 * net.ds[cols][None, :]
+    rp, rm = r1 + h, r1 - h
+    pp, pm = rp * rp + r2 * r2, rm * rm + r2 * r2
+    s31 = -(net.cs / np.pi) * (r2 / pp - r2 / pm)
+    s32 = (net.cs / np.pi) * (rp / pp - rm / pm)
+    A = n1 * s31 + n2 * s32
+    same = net.fault_of[rows][:, None] == net.fault_of[cols][None, :]
+    return np.where(same, 0.0, A)
 
 
 def interaction_history(net: Network, V: np.ndarray, pair_hi=None, dtype=np.float64) -> np.ndarray:
@@ -340,11 +368,19 @@ def modes_to_space(F: np.ndarray, n_f: int, rows=None) -> np.ndarray:
 
 
 class SelfTables:
-    """Weights w_{f,n}^T for one fault, n = 1..N_f, T = 0..W_f(n)."""
+    """Weights w_{f,n}^T for one fault, n = 1..N_f, T = 0..W_f(n); with ``tail``, also the weight mass beyond the
+    window, c_n = S_n - sum_{T <= W_f(n)} w_n^T with the static limit S_n = sum_{T >= 0} w_n^T = (2/pi) Si(n pi)
+    (the t -> inf limit of Eq. non_replicant_kernel's time integral)."""
 
-    def __init__(self, n_f: int, L: float, dt: float, cs: float, W: np.ndarray):
+    def __init__(self, n_f: int, L: float, dt: float, cs: float, W: np.ndarray, tail: bool = False):
         self.n_f, self.L, self.W = n_f, L, W
         self.w = [np.zeros(0)] + [spectral_weights(n, np.arange(W[n] + 1), dt, L, cs) for n in range(1, n_f + 1)]
+        self.c = None
+        if tail:
+            from scipy.special import sici
+            self.c = np.zeros(n_f + 1)
+            for n in range(1, n_f + 1):
+                self.c[n] = (2.0 / np.pi) * sici(n * np.pi)[0] - self.w[n].sum()
 
 
 def self_history(net: Network, f: int, delta: np.ndarray, tables: SelfTables) -> np.ndarray:
@@ -356,7 +392,13 @@ def self_history(net: Network, f: int, delta: np.ndarray, tables: SelfTables) ->
     F = np.zeros_like(D)
     for n in range(1, n_f + 1):
         kn = np.pi * n / L
-        F[:, n] = -(net.mu * kn / 2.0) * np.convolve(tables.w[n], D[:, n])[:steps]
+        conv = np.convolve(tables.w[n], D[:, n])[:steps]
+        if tables.c is not None:
+            # static tail: the slip at the window's far edge, held since t = -inf, times the weight mass beyond
+            # the window
+            lag = int(tables.W[n]) + 1
+            conv[lag:] += tables.c[n] * D[: steps - lag, n]
+        F[:, n] = -(net.mu * kn / 2.0) * conv
     return modes_to_space(F, n_f)
 
 
@@ -388,9 +430,12 @@ def stress_history(net: Network, V: np.ndarray, hp: dict, slip=None):
     """tau^n for every step of V[steps][N]; returns (tau, rad, self, int), each [steps][N]  (Eq. superimposition2).
 
     hp: operator parameters (eta_tmin, eta_tmax, eta_w, q_w, max_steps, flags); windows are applied unless
-    flags has NO_TRUNC (2)."""
+    flags has NO_TRUNC (2).  With STATIC_TAIL (4) and windows, the history each window drops is added as a static
+    response: per mode, c_n D_n^{m - W_f(n) - 1} (SelfTables); per fault pair, A^static delta^{m - T_last - 1}, the
+    elastostatic stress of the slip reached when the pair's window starts (static_slice)."""
     steps = V.shape[0]
     no_trunc = bool(hp.get("flags", 0) & 2)
+    tail = bool(hp.get("flags", 0) & 4) and not no_trunc
     max_steps = int(hp.get("max_steps", steps))
     delta = slip_from_rate(V, net.dt) if slip is None else slip
     rad = -(net.mu / (2 * net.cs)) * V
@@ -400,7 +445,31 @@ def stress_history(net: Network, V: np.ndarray, hp: dict, slip=None):
         n_f = int(net.n_elem[f])
         W = mode_windows(n_f, net.length[f], net.dt, net.cs, hp.get("eta_w", 1.5), hp.get("q_w", 0), max_steps,
                          no_trunc)
-        fself[:, o0:o1] = self_history(net, f, delta[:, o0:o1], SelfTables(n_f, net.length[f], net.dt, net.cs, W))
+        fself[:, o0:o1] = self_history(net, f, delta[:, o0:o1],
+                                       SelfTables(n_f, net.length[f], net.dt, net.cs, W, tail=tail))
     _, _, last = pair_windows(net, hp.get("eta_tmin", 0.01), hp.get("eta_tmax", 0.01), max_steps, no_trunc)
     fint = interaction_history(net, V, pair_hi=last)
+    if tail:
+        fint += static_tail_history(net, delta, last)
     return rad + fself + fint, rad, fself, fint
+
+
+def static_tail_history(net: Network, delta: np.ndarray, last) -> np.ndarray:
+    """Interaction part of the static tail at every step m: -(mu / 2 c_s) sum over source faults b != fault(i) of
+    sum_{j in b} A_ij^static delta_j^{m - T_last(a, b) - 1}, where the pair's window still reaches back to step 0
+    nothing is added (the dropped lags T > T_last carry A^T ~ dt A^static, and dt sum_{T > T_last} V^{m-T} is that
+    slip)."""
+    steps = delta.shape[0]
+    As = static_slice(net)
+    out = np.zeros((steps, net.N))
+    for a in range(net.F):
+        ra = slice(net.offset[a], net.offset[a + 1])
+        for b in range(net.F):
+            if a == b:
+                continue
+            rb = slice(net.offset[b], net.offset[b + 1])
+            lag = int(last[a][b]) + 1
+            if lag >= steps:
+                continue
+            out[lag:, ra] += delta[: steps - lag, rb] @ As[ra, rb].T
+    return -(net.mu / (2 * net.cs)) * out

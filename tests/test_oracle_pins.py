@@ -308,3 +308,61 @@ def test_normal_stress_change_vanishes_and_parts_add_up():
     tau, rad, fs, fi = O.stress_history(net, V, dict(w.hparams, max_steps=10))
     np.testing.assert_array_equal(rad, -(MU / (2 * CS)) * V)
     np.testing.assert_allclose(tau, rad + fs + fi, rtol=0, atol=0)
+
+
+# ---------------------------------------------------------------- static tail (flag STATIC_TAIL) -------------------
+
+def _two_small_faults():
+    return O.network(np.array([[0.0, 0.0, 0.1, 80.0, 8], [60.0, -150.0, 0.7, 80.0, 8]]), MU, CS)
+
+
+def test_static_slice_is_the_late_time_limit_of_the_dynamic_slice():
+    """P14a: A^static equals lim A^T / dt of the dynamic kernel built from Eq. primitives (projection, frames and
+    signs included), with an error decaying like T^-2; same-fault entries are zero."""
+    net = _two_small_faults()
+    As = O.static_slice(net)
+    errs = []
+    for T in (2000, 20000):
+        Ad = O.interaction_slice(net, T) / net.dt
+        errs.append(np.abs(Ad - As).max() / np.abs(As).max())
+    assert errs[1] < errs[0] / 50 and errs[1] < 1e-5
+    assert np.all(As[:8, :8] == 0) and np.abs(As[:8, 8:]).min() > 0
+
+
+def test_interaction_static_tail_restores_the_dropped_history_at_late_times():
+    """P14b: slip rate only at step 0.  With truncated pair windows the plain sum is zero once the window has
+    passed; with the static tail it approaches the untruncated sum (A^m V^0 -> dt A^static V^0) as m grows."""
+    net = _two_small_faults()
+    steps = 700
+    V = np.zeros((steps, net.N))
+    V[0] = np.linspace(1.0, 2.0, net.N)
+    hp = dict(eta_tmin=0.01, eta_tmax=0.01, eta_w=1.5, q_w=0, max_steps=steps)
+    full = O.stress_history(net, V, dict(hp, flags=2))[3]
+    trunc = O.stress_history(net, V, dict(hp, flags=0))[3]
+    tail = O.stress_history(net, V, dict(hp, flags=4))[3]
+    last = O.pair_windows(net, 0.01, 0.01, steps)[2]
+    m0 = int(last.max()) + 1
+    assert m0 < 150 and np.all(trunc[m0:] == 0)
+    e = [np.linalg.norm(tail[m] - full[m]) / np.linalg.norm(full[m]) for m in (300, 690)]
+    assert e[0] < 0.05 and e[1] < e[0] / 4 and e[1] < 1e-2
+    assert np.all(tail[:int(last.min()) + 1] == trunc[:int(last.min()) + 1])
+
+
+def test_self_static_tail_completes_the_weight_sum():
+    """P14c: slip rate only at step 0 (a slip step).  The untruncated spectral term tends to the static response
+    sum_T w_n^T D_n = (2/pi) Si(n pi) D_n; the truncated term plus the static tail reaches it (differences decay
+    like the weight mass still missing from the untruncated sum), while the plain truncated term stays off."""
+    L, N = 500.0, 16
+    net = O.network(np.array([[0.0, 0.0, 0.3, L, N]]), MU, CS)
+    steps = 900
+    V = np.zeros((steps, N))
+    V[0] = np.sin(np.pi * (np.arange(N) + 0.5) / N)
+    hp = dict(eta_tmin=0.01, eta_tmax=0.01, eta_w=0.5, q_w=0, max_steps=steps)
+    full = O.stress_history(net, V, dict(hp, flags=2))[2]
+    trunc = O.stress_history(net, V, dict(hp, flags=0))[2]
+    tail = O.stress_history(net, V, dict(hp, flags=4))[2]
+    W = O.mode_windows(N, L, net.dt, CS, 0.5, 0, steps)
+    assert W[1:].max() < 120
+    e_tail = [np.linalg.norm(tail[m] - full[m]) / np.linalg.norm(full[m]) for m in (300, 890)]
+    e_trunc = np.linalg.norm(trunc[890] - full[890]) / np.linalg.norm(full[890])
+    assert e_tail[1] < e_tail[0] / 2 and e_tail[1] < 2e-3 and e_trunc > 20 * e_tail[1]
