@@ -64,7 +64,12 @@ typedef int seas_status;
 /* operator flags */
 #define SEAS_FLAG_DENSE 1        /* admissibility never satisfied: every block dense (the plain space-time sum) */
 #define SEAS_FLAG_NO_TRUNC 2     /* no causal end truncation; full-length spectral windows (exact operator) */
-#define SEAS_FLAG_STATIC_TAIL 4  /* reserved: elastostatic response of truncated history (not implemented) */
+/* SEAS_FLAG_STATIC_TAIL (not in the paper, which truncates): add back, as an elastostatic response, the history each
+ * window drops.  Per spectral mode: (S_n - sum_{T<=W} w_n^T) D_n^{n-W-1}, S_n = (2/pi) Si(n pi) the weights' static
+ * limit; per ordered fault pair whose window ends at T_last: A^static delta^{n-T_last-1}, A^static the t -> infinity
+ * limit of the kernel over dt (Eq. primitives), delta the slip.  FP64 in every precision.  Costs a dense N x N FP64
+ * static operator and a slip ring per scenario; ignored with SEAS_FLAG_NO_TRUNC (nothing is dropped). */
+#define SEAS_FLAG_STATIC_TAIL 4
 
 /* storage precision and arithmetic of the interaction operator */
 #define SEAS_PREC_FP64 0   /* FP64 entries, FP64 arithmetic */

@@ -198,6 +198,10 @@ struct seas_op {
     std::vector<int32_t> pair_last;  // [F][F]
     std::vector<int64_t> bytes_upto; // stored interaction bytes with lag <= T
     int ring = 1;
+    // static tail (SEAS_FLAG_STATIC_TAIL)
+    bool tail = false;
+    DArr<double> d_smat;             // [N][N] -(mu / 2 c_s) A^static
+    DArr<int32_t> d_pair_last;
     seas_op_stats stats{};
 };
 
@@ -206,6 +210,7 @@ struct seas_scn {
     int B = 0;
     int64_t n = 0;                   // pushes so far
     DArr<double> vring, slip, slip_prev, fint, d_V, d_slip, d_tau, d_parts, partial;
+    DArr<double> sring;              // static tail: slip after each push, [op->ring + 1][N][B]
     DArr<unsigned char> xring;       // history in the operator's arithmetic (DF64: float2, BF16/FP16: float)
     DArr<double2> dring, fmodes;
     DArr<int> counter_err;           // [0]: interaction task counter, [1]: device error word
@@ -597,6 +602,8 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
     }
 }
 
+std::vector<double> static_mode_limits(int max_n);
+
 seas_status build_self(seas_op &op) {
     seas_net &net = *op.net;
     seas_ctx *c = net.ctx;
@@ -645,7 +652,7 @@ seas_status build_self(seas_op &op) {
             w_total += W + 1;
             g_total += W + 2;
         }
-        fd.ring = wmax + 1;
+        fd.ring = wmax + (op.tail ? 2 : 1);    // the static tail reads D one step past the longest window
         fd.dring_off = dring;        // batch-1 layout; scenarios derive their own table
         dring += (int64_t)(nf + 1) * fd.ring;
         op.faults_h.push_back(fd);
@@ -670,6 +677,67 @@ seas_status build_self(seas_op &op) {
                                     c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     op.stats.bytes_self = w_total * (int64_t)sizeof(double);
+    if (op.tail) {
+        // weight mass beyond each window: S_n - sum_{T <= W} w_n^T, S_n = (2/pi) Si(n pi)
+        std::vector<double> w((size_t)w_total);
+        CUDA_TRY(cudaMemcpy(w.data(), op.d_w.p, (size_t)w_total * sizeof(double), cudaMemcpyDeviceToHost));
+        int max_n = 0;
+        for (const ModeDev &m : op.modes_h) max_n = std::max(max_n, m.n);
+        const std::vector<double> S = static_mode_limits(max_n);
+        for (ModeDev &m : op.modes_h) {
+            double sum = 0.0;
+            for (int T = 0; T <= m.W; ++T) sum += w[(size_t)(m.w_off + T)];
+            m.tailc = S[(size_t)m.n] - sum;
+        }
+        SEAS_TRY(op.d_modes.upload(c, op.modes_h));
+    }
+    return SEAS_OK;
+}
+
+// Static limits S_n = sum_{T >= 0} w_n^T = (2/pi) Si(n pi), n = 0..max_n: Si(n pi) accumulated one half period at
+// a time, each by 20-point Gauss-Legendre (sin t / t is smooth on every [k pi, (k + 1) pi]).
+std::vector<double> static_mode_limits(int max_n) {
+    std::vector<double> gx, gw;
+    gauss_legendre(20, gx, gw);
+    std::vector<double> S((size_t)max_n + 1, 0.0);
+    long double si = 0.0L;
+    for (int k = 0; k < max_n; ++k) {
+        const long double a = (long double)kPi * k, h = 0.5L * (long double)kPi;
+        long double part = 0.0L;
+        for (size_t i = 0; i < gx.size(); ++i) {
+            const long double t = a + h * (1.0L + gx[i]);
+            part += gw[i] * sinl(t) / t;
+        }
+        si += h * part;
+        S[(size_t)k + 1] = (double)(2.0L / (long double)kPi * si);
+    }
+    return S;
+}
+
+// The elastostatic operator of the static tail: smat[i][j] = -(mu / 2 c_s) (n'_1 S_31 + n'_2 S_32) for receivers i
+// and sources j on different faults, S_3l the t -> inf limit of K_3l / dt (Eq. primitives differenced over the
+// source element as in Eq. kernel_interactions): S_31 = -(c_s/pi)(r2/rho_+^2 - r2/rho_-^2),
+// S_32 = (c_s/pi)(r1_+/rho_+^2 - r1_-/rho_-^2), r1_+- = r1 +- ds_j/2, in the source element's frame.
+seas_status build_static(seas_op &op) {
+    seas_net &net = *op.net;
+    seas_ctx *c = net.ctx;
+    const int64_t N = net.N;
+    std::vector<double> m((size_t)(N * N), 0.0);
+    const double cpi = net.med.cs / kPi, rad = -net.med.mu / (2.0 * net.med.cs);
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < N; ++j) {
+            if (net.fault_of[i] == net.fault_of[j]) continue;
+            const double dx = net.x[i] - net.x[j], dy = net.y[i] - net.y[j];
+            const double r1 = dx * net.e1x[j] + dy * net.e1y[j], r2 = dx * net.nx[j] + dy * net.ny[j];
+            const double n1 = net.nx[i] * net.e1x[j] + net.ny[i] * net.e1y[j];
+            const double n2 = net.nx[i] * net.nx[j] + net.ny[i] * net.ny[j];
+            const double h = 0.5 * net.ds[j], rp = r1 + h, rm = r1 - h;
+            const double pp = rp * rp + r2 * r2, pm = rm * rm + r2 * r2;
+            const double s31 = -cpi * (r2 / pp - r2 / pm), s32 = cpi * (rp / pp - rm / pm);
+            m[(size_t)(i * N + j)] = rad * (n1 * s31 + n2 * s32);
+        }
+    SEAS_TRY(op.d_smat.upload(c, m));
+    SEAS_TRY(op.d_pair_last.upload(c, op.pair_last));
     return SEAS_OK;
 }
 
@@ -936,7 +1004,7 @@ extern "C" seas_status seas_build_hmatrix(seas_net *net, const seas_hparams *hp,
     if (hp->max_steps < 1 || hp->max_steps > (1 << 22)) return fail(SEAS_EINVAL, "max_steps in [1, 2^22]");
     if (hp->precision < kPrecFP64 || hp->precision > kPrecDF64)
         return fail(SEAS_EINVAL, "precision %d not available", hp->precision);
-    if (hp->flags & ~(SEAS_FLAG_DENSE | SEAS_FLAG_NO_TRUNC))
+    if (hp->flags & ~(SEAS_FLAG_DENSE | SEAS_FLAG_NO_TRUNC | SEAS_FLAG_STATIC_TAIL))
         return fail(SEAS_EINVAL, "unsupported flags 0x%x", hp->flags);
     if (hp->max_block != 0 && hp->max_block < hp->leaf) return fail(SEAS_EINVAL, "max_block must be >= leaf");
     seas_ctx *c = net->ctx;
@@ -945,8 +1013,10 @@ extern "C" seas_status seas_build_hmatrix(seas_net *net, const seas_hparams *hp,
     auto op = std::make_unique<seas_op>();
     op->net = net;
     op->hp = *hp;
+    op->tail = (hp->flags & SEAS_FLAG_STATIC_TAIL) && !(hp->flags & SEAS_FLAG_NO_TRUNC);
     SEAS_TRY(build_self(*op));
     SEAS_TRY(build_interaction(*op));
+    if (op->tail) SEAS_TRY(build_static(*op));
     op->stats.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = op->stats;
     net->children++;
@@ -1071,6 +1141,11 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     a.blk_task_T = op.d_blk_task_T.p;
     a.blk_part = op.d_blk_part.p;
     a.n_sms = net.ctx->n_sms > 0 ? net.ctx->n_sms : 1;
+    a.tail = op.tail ? 1 : 0;
+    a.sring_depth = op.ring + 1;
+    a.sring = s.sring.p;
+    a.smat = op.d_smat.p;
+    a.pair_last = op.d_pair_last.p;
     return a;
 }
 
@@ -1113,6 +1188,10 @@ seas_status scenario_alloc(seas_op *op, int batch, std::unique_ptr<seas_scn> &s)
     SEAS_TRY(s->fmodes.alloc(c, (size_t)(op->n_modes_total * (int64_t)batch)));
     SEAS_TRY(s->h_in.alloc((size_t)(2 * BN) * sizeof(double)));
     SEAS_TRY(s->h_out.alloc((size_t)(4 * BN) * sizeof(double)));
+    if (op->tail) {
+        SEAS_TRY(s->sring.alloc(c, (size_t)((op->ring + 1) * BN)));
+        SEAS_TRY(s->sring.zero(c->stream));
+    }
     for (DArr<double> *d : {&s->vring, &s->slip, &s->slip_prev, &s->fint}) SEAS_TRY(d->zero(c->stream));
     SEAS_TRY(s->dring.zero(c->stream));
     SEAS_TRY(s->fmodes.zero(c->stream));
@@ -1265,7 +1344,10 @@ extern "C" seas_status seas_stress_step(seas_scn *s, double *tau, double *sigma_
     double *dparts = parts ? (mem == SEAS_MEM_DEVICE ? parts : s->d_parts.p) : nullptr;
     SEAS_TRY(timed(*s, 2, [&] { return launch_modeconv(a, c->stream); }));
     SEAS_TRY(timed(*s, 3, [&] { return launch_interaction(a, c->stream); }));
-    SEAS_TRY(timed(*s, 4, [&] { return launch_reduce(a, c->stream); }));
+    SEAS_TRY(timed(*s, 4, [&] {
+        const cudaError_t e = launch_reduce(a, c->stream);
+        return e != cudaSuccess ? e : launch_static_tail(a, c->stream);
+    }));
     SEAS_TRY(timed(*s, 5, [&] { return launch_ifft_assemble(a, dtau, dparts, c->stream); }));
     if (s->timing) {
         int64_t b = 0;
@@ -1309,6 +1391,7 @@ extern "C" seas_status seas_stress_step_static(seas_scn *s, double *tau, double 
     CUDA_TRY(launch_modeconv(a, c->stream));
     CUDA_TRY(launch_interaction(a, c->stream));
     CUDA_TRY(launch_reduce(a, c->stream));
+    CUDA_TRY(launch_static_tail(a, c->stream));
     CUDA_TRY(launch_ifft_assemble(a, tau, parts, c->stream));
     return SEAS_OK;
 }
@@ -1380,6 +1463,7 @@ extern "C" seas_status seas_scenario_save(seas_scn *s, const char *path) {
     if (st == SEAS_OK) st = dump(fp, s->slip_prev.p, s->slip_prev.bytes());
     if (st == SEAS_OK) st = dump(fp, s->dring.p, s->dring.bytes());
     if (st == SEAS_OK) st = dump(fp, s->xring.p, s->xring.bytes());
+    if (st == SEAS_OK) st = dump(fp, s->sring.p, s->sring.bytes());
     if (fclose(fp) != 0 && st == SEAS_OK) st = fail(SEAS_EIO, "close failed");
     return st;
 }
@@ -1409,6 +1493,7 @@ extern "C" seas_status seas_scenario_load(seas_op *op, const char *path, seas_sc
     if (st == SEAS_OK) st = slurp(fp, s->slip_prev.p, s->slip_prev.bytes());
     if (st == SEAS_OK) st = slurp(fp, s->dring.p, s->dring.bytes());
     if (st == SEAS_OK) st = slurp(fp, s->xring.p, s->xring.bytes());
+    if (st == SEAS_OK) st = slurp(fp, s->sring.p, s->sring.bytes());
     fclose(fp);
     if (st != SEAS_OK) return st;
     s->n = h.n;

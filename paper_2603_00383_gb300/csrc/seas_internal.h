@@ -56,6 +56,7 @@ struct ModeDev {
     int32_t fault;
     int32_t n;
     int32_t pad;
+    double tailc;       // static tail: weight mass beyond the window, (2/pi) Si(n pi) - sum_{T<=W} w_n^T (0: none)
 };
 
 // One H-matrix block: receiver rows [r0, r0 + p), source columns [c0, c0 + q) (global element indices).
@@ -160,6 +161,12 @@ struct StepArgs {
     const int32_t *blk_task_ptr, *blk_task_T;
     const int64_t *blk_part;      // first partial of each block
     int n_sms;
+    // static tail (SEAS_FLAG_STATIC_TAIL): the elastostatic response of the history the windows drop
+    int tail;                     // 1: on (the mode tails live in ModeDev::tailc)
+    int sring_depth;              // slots of the slip ring
+    double *sring;                // [sring_depth][N][B]: slip after each push
+    const double *smat;           // [N][N]: -(mu / 2 c_s) A^static, receiver-major (same-fault entries unused)
+    const int32_t *pair_last;     // [F][F]: last lag of each ordered fault pair's window
 };
 
 // Allocation-free stepping (seas_stress_step_static): scratch in a static device array of this many doubles.
@@ -173,6 +180,7 @@ cudaError_t launch_fft_forward(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_reduce(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_static_tail(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_ifft_assemble(const StepArgs &a, double *tau, double *parts, cudaStream_t s);
 
 }  // namespace seas

@@ -126,6 +126,7 @@ __global__ void k_push(StepArgs a, const double *__restrict__ V, const double *_
         }
         if (!replace_last) a.slip_prev[e] = a.slip[e];
         a.slip[e] = s;
+        if (a.tail) a.sring[(a.step % a.sring_depth) * BN + i * a.B + b] = s;
     }
 }
 
@@ -191,6 +192,14 @@ __global__ void __launch_bounds__(kThreads) k_modeconv(StepArgs a) {
         im += __shfl_xor_sync(0xffffffffu, im, o);
     }
     if (lane == 0) {
+        if (a.tail && a.step > mo.W) {
+            // static tail: the spectrum at the window's far edge times the weight mass beyond the window
+            int s = slot0 - mo.W - 1;
+            if (s < 0) s += R;
+            const double2 d = ring[s];
+            re += mo.tailc * d.x;
+            im += mo.tailc * d.y;
+        }
         const double f = fd.kfac * mo.n;
         a.fmodes[(int64_t)b * a.n_modes_total + fd.mode_off + mo.n] = make_double2(f * re, f * im);
     }
@@ -1109,6 +1118,44 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
     }
 }
 
+// Static tail of the interaction (flag SEAS_FLAG_STATIC_TAIL, not in the paper): for receiver e on fault a and each
+// source fault b whose window ends at lag T_last(a, b) < step, f_int[e] += sum_{j in b} smat[e][j] delta_j^{step -
+// T_last - 1}: the dropped lags T > T_last carry A^T ~ dt A^static, and dt times their slip rates is that slip.  One
+// warp per receiver element, lanes over the source columns, a fixed shuffle tree: deterministic.
+__global__ void __launch_bounds__(kThreads) k_static_tail(StepArgs a) {
+    const int64_t e = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= a.N) return;
+    int fa = 0;
+    while (fa + 1 < a.F && a.faults[fa + 1].off <= e) ++fa;
+    const double *row = a.smat + e * (int64_t)a.N;
+    const int64_t BN = (int64_t)a.B * a.N;
+    double sum[kMaxBatch];
+#pragma unroll
+    for (int bb = 0; bb < kMaxBatch; ++bb) sum[bb] = 0.0;
+    for (int fb = 0; fb < a.F; ++fb) {
+        if (fb == fa) continue;
+        const int64_t src = a.step - a.pair_last[fa * a.F + fb] - 1;
+        if (src < 0) continue;
+        const double *sl = a.sring + (src % a.sring_depth) * BN;
+        const int j0 = a.faults[fb].off, j1 = j0 + a.faults[fb].nf;
+        for (int j = j0 + lane; j < j1; j += 32) {
+            const double m = row[j];
+#pragma unroll
+            for (int bb = 0; bb < kMaxBatch; ++bb)
+                if (bb < a.B) sum[bb] = fma(m, sl[(int64_t)j * a.B + bb], sum[bb]);
+        }
+    }
+#pragma unroll
+    for (int bb = 0; bb < kMaxBatch; ++bb) {
+        if (bb < a.B) {
+            double v = sum[bb];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) a.fint[(int64_t)bb * a.N + e] += v;
+        }
+    }
+}
+
 // f_int[b][e] = sum over the blocks that element e receives from, and over their causal tasks, of the tasks'
 // partial sums; one warp per element, lane c takes covering blocks c, c + 32, ... (its tasks in lag order), then
 // a fixed tree: the summation order never depends on timing.  Also resets the task counter for the next step.
@@ -1231,6 +1278,13 @@ cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s) {
 cudaError_t launch_reduce(const StepArgs &a, cudaStream_t s) {
     const int grid = (a.N + kThreads / 32 - 1) / (kThreads / 32);
     k_reduce<<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_static_tail(const StepArgs &a, cudaStream_t s) {
+    if (!a.tail) return cudaSuccess;
+    const int grid = (a.N + kThreads / 32 - 1) / (kThreads / 32);
+    k_static_tail<<<grid, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

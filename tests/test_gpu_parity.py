@@ -335,3 +335,49 @@ def test_six_fault_3072_precisions_sampled(prec):
     e = rel(p_gpu[2, rows], f_int)
     print(f"six_fault_3072 precision {prec}: rel int at step {w.steps - 1}: {e:.2e}")
     assert e <= (1e-5 if prec == seas.SEAS_PREC_DF64 else MP_BOUND[prec])
+
+
+# ---------------------------------------------------------------- static tail (SEAS_FLAG_STATIC_TAIL) ---------------
+
+TAIL_HP = dict(eta_tmin=0.01, eta_tmax=0.01, eta_w=0.5, q_w=0)
+
+
+def _tail_case(w, hp):
+    net = O.network(w.faults, w.mu, w.cs)
+    V = w.slip_rate(0, 0, w.steps)
+    ref = O.stress_history(net, V, dict(w.hparams, **hp, flags=seas.SEAS_FLAG_STATIC_TAIL))
+    plain = O.stress_history(net, V, dict(w.hparams, **hp, flags=0))
+    return V, ref, plain
+
+
+@pytest.mark.parametrize("case", ["two_fault_128", "tiny2"])
+def test_static_tail_matches_oracle(case):
+    """Truncated windows plus the static tail, every block dense: the CUDA path equals the oracle to 1e-10 on tau
+    and on each part, and the tail visibly changes the self and interaction parts once the windows have passed."""
+    w = synth.two_fault_128() if case == "two_fault_128" else synth.tiny(2, n_faults=3, steps=200)
+    hp = dict(TAIL_HP, max_steps=w.steps)
+    V, ref, plain = _tail_case(w, hp)
+    with seas.Session(w, flags=seas.SEAS_FLAG_DENSE | seas.SEAS_FLAG_STATIC_TAIL, **hp) as s:
+        tau, P = run_host(s, V)
+    errs = [rel(tau, ref[0])] + [rel(P[:, k], ref[k + 1]) for k in range(3)]
+    print(case, "static tail rel-L2 tau/rad/self/int:", errs)
+    assert max(errs) <= EXACT
+    assert rel(ref[2], plain[2]) > 1e-6 and rel(ref[3], plain[3]) > 1e-6
+
+
+def test_static_tail_checkpoint_resume_is_bitwise():
+    """The slip ring the interaction tail reads is part of the checkpoint."""
+    w = synth.tiny(2, n_faults=3, steps=200)
+    hp = dict(TAIL_HP, max_steps=w.steps, flags=seas.SEAS_FLAG_DENSE | seas.SEAS_FLAG_STATIC_TAIL)
+    V = w.slip_rate(0, 0, w.steps)
+    with seas.Session(w, **hp) as s:
+        full, _ = run_host(s, V, parts=False)
+    with seas.Session(w, **hp) as s:
+        run_host(s, V[:150], parts=False)
+        with tempfile.TemporaryDirectory() as d:
+            path = os.path.join(d, "scn.ckpt")
+            seas.seas_scenario_save(s.scn, path)
+            seas.seas_destroy_scn(s.scn)
+            s.scn = seas.seas_scenario_load(s.op, path)
+        rest, _ = run_host(s, V[150:], parts=False)
+    np.testing.assert_array_equal(rest, full[150:])
