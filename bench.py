@@ -212,12 +212,25 @@ class Clocks:
 
 
 def dist_setup(args):
+    """One process per GPU (torchrun's RANK / WORLD_SIZE / LOCAL_RANK / MASTER_*); NCCL on GPUs, gloo otherwise.
+    The process group only carries the barrier and the max-over-ranks time: scenarios share no data."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         return dist, int(os.environ["RANK"]), world, int(os.environ.get("LOCAL_RANK", "0"))
     return None, 0, 1, 0
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of the scenario a rank runs: independent histories per rank (weak scaling)."""
+    return synth.SEED + rank
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
 
 
 def barrier(dist):
@@ -303,7 +316,7 @@ def run_ours(args, w, K, W):
     from paper_2603_00383_gb300 import seas
     dist, rank, world, local = dist_setup(args)
     wr = synth.six_fault_3072(steps=K) if w.name == "six_fault_3072" else w
-    wr.seed = synth.SEED + rank                          # independent scenario per rank
+    wr.seed = rank_seed(rank)                            # independent scenario per rank
     # CPU oracle sample first (before any GPU work in this process)
     oracle = None
     if rank == 0 and args.cpu_sample > 0:
@@ -335,7 +348,7 @@ def run_ours(args, w, K, W):
         with open(args.dump_step_bytes, "w") as fh:
             json.dump({"precision": args.precision, "steps": K,
                        "bytes": [seas.seas_op_step_bytes(s.op, n) for n in range(K)]}, fh)
-    value = wr.N * K * world / (res["total_ms"] / 1e3)
+    value = job_rate(wr.N * K, world, res["total_ms"] / 1e3)
     err = err_of(tau)
     stats = res["stats"]
 
