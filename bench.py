@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS), help="headline storage precision")
     ap.add_argument("--no-variants", action="store_true", help="skip the other storage precisions")
     ap.add_argument("--no-batched", action="store_true", help="skip the 8-scenario ensemble runs")
+    ap.add_argument("--no-tail", action="store_true", help="skip the static-tail run")
     ap.add_argument("--dump-step-bytes", default=None, help="write the per-step algorithmic interaction bytes here")
     return ap.parse_args()
 
@@ -270,10 +271,11 @@ def timed_run(seas, torch, s, Vd, K, dist, device, out_tau=None):
     return total_ms, per, tau
 
 
-def run_precision(seas, torch, wr, prec, Vd, K, W, dist, device, stream, peak, batch=1):
+def run_precision(seas, torch, wr, prec, Vd, K, W, dist, device, stream, peak, batch=1, flags=None):
     """Builds the operator in one storage precision and times K steps of `batch` scenarios sharing it (Vd is
     [K][batch * N]); returns the measurements and tau."""
-    s = seas.Session(wr, batch=batch, device=device.index, stream=stream.cuda_stream, precision=prec)
+    extra = {} if flags is None else {"flags": flags}
+    s = seas.Session(wr, batch=batch, device=device.index, stream=stream.cuda_stream, precision=prec, **extra)
     warm = seas.seas_scenario_create(s.op, batch)
     tw = torch.zeros(batch * wr.N, dtype=torch.float64, device=device)
     for n in range(W):
@@ -390,6 +392,17 @@ def run_ours(args, w, K, W):
             del tau3
         del V8d
 
+    # the flagged static tail (elastostatic response of the history the windows drop) on the headline operator
+    tail = None
+    if not args.no_tail:
+        r4, tau4, s4 = run_precision(seas, torch, wr, head_code, Vd, K, W, dist, device, stream, peak,
+                                     flags=int(wr.hparams.get("flags", 0)) | seas.SEAS_FLAG_STATIC_TAIL)
+        tv = job_rate(wr.N * K, world, r4["total_ms"] / 1e3)
+        tail = {"value": tv, "unit": METRIC, "ms_per_step": r4["total_ms"] / K, "cost_vs_headline": value / tv - 1,
+                "tail_share_of_tau": (tau4 - tau).norm().item() / tau.norm().item()}
+        s4.close()
+        del tau4
+
     # plain FP64 GPU path: every block dense (leaf blocks, exact windows), no compression, FP64 arithmetic
     plain = None
     if not args.no_plain:
@@ -451,7 +464,7 @@ def run_ours(args, w, K, W):
                 "rel_l2_vs_oracle": err, "operator": {k: stats[k] for k in (
                     "n_blocks_far", "n_blocks_near", "compression_ratio", "bytes_interaction", "mean_rank",
                     "max_rank", "build_seconds", "n_tasks")},
-                "vs_plain_fp64_gpu": plain, "variants": variants, "batched": batched, "e2e": e2e,
+                "vs_plain_fp64_gpu": plain, "variants": variants, "batched": batched, "static_tail": tail, "e2e": e2e,
                 "roofline": roofline,
                 "cpu_baseline": cpu, "clocks": res["clocks"], "gpu_launches": int(sum(launches.values()))}
     s.close()
