@@ -204,9 +204,9 @@ seas_status seas_plan_hmatrix(const seas_fault *faults, int n_faults, const seas
 
 /* Kernel timing on the context stream (tracing).  set_timing(1) resets and starts recording a CUDA event pair
  * around every kernel the scenario launches; get_timing synchronises and returns, per kernel class (0 push,
- * 1 forward FFT, 2 mode convolution, 3 interaction, 4 interaction reduction, 5 inverse FFT + assembly), the
- * launch count and the summed device time, plus the algorithmic bytes the interaction kernel streamed (stored
- * operator slices with lag <= step, summed over the timed steps). */
+ * 1 forward FFT, 2 mode convolution, 3 interaction, 4 interaction reduction (with the static tail when that flag
+ * is set), 5 inverse FFT + assembly), the launch count and the summed device time, plus the algorithmic bytes the
+ * interaction kernel streamed (seas_op_step_bytes summed over the timed steps). */
 typedef struct {
     int64_t launches[6];
     double ms[6];
@@ -219,7 +219,8 @@ seas_status seas_scenario_get_timing(seas_scn *scn, seas_timing *out);
  * (p q near, k (p + q) far) times the storage element size; the 16-byte row padding is not counted. */
 seas_status seas_op_step_bytes(const seas_op *op, int64_t step, int64_t *bytes);
 
-/* Checkpoint/resume of a scenario: the step counter, slip-rate ring, slip and spectral ring. */
+/* Checkpoint/resume of a scenario: the step counter, slip-rate ring, slip and spectral ring (and the slip ring of
+ * the static tail when that flag is set). */
 seas_status seas_scenario_save(seas_scn *scn, const char *path);
 seas_status seas_scenario_load(seas_op *op, const char *path, seas_scn **scn);
 
