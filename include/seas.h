@@ -156,7 +156,9 @@ seas_status seas_op_pair_windows(const seas_op *op, int32_t *last_lag);
 /* Per fault f and mode n = 0..N_f: last lag W_f(n) of the spectral window (flattened fault after fault). */
 seas_status seas_op_mode_windows(const seas_op *op, int32_t *w);
 
-/* Allocates the history ring buffers of `batch` (1..8) independent scenarios sharing the operator. */
+/* Allocates the history ring buffers of `batch` (1..8) independent scenarios sharing the operator.  BF16 operators
+ * with batches of 5..8 run on tensor-core consumers that tile at most 128 receivers per block (SEAS_EINVAL
+ * otherwise; the default max_block of 64 always fits). */
 seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **scn);
 
 /* Pushes V^n ([batch][N] float64) and optionally delta^n (same layout; NULL: integrate).  mem: where V and slip

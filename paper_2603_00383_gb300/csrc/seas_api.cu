@@ -1205,6 +1205,13 @@ extern "C" seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **o
     *out = nullptr;
     if (batch < 1 || batch > kMaxBatch) return fail(SEAS_EINVAL, "batch must be in [1, %d]", kMaxBatch);
     const int xb = op->hp.precision == kPrecBF16 || op->hp.precision == kPrecFP16 ? 4 : 8;
+    if (op->hp.precision == kPrecBF16 && batch > 4) {
+        // the tensor-core consumers of BF16 batches of 5..8 tile at most 128 receivers of a block
+        int max_p = 0;
+        for (const BlockDev &b : op->blocks_h) max_p = std::max(max_p, b.p);
+        if (pad_row(max_p, kPrecBF16) > 128)
+            return fail(SEAS_EINVAL, "BF16 batches of 5..8 need blocks of at most 128 receivers (widest: %d)", max_p);
+    }
     if ((int64_t)(op->max_q + 8) * batch * xb + 16 + kItemBytes > kStageBytes)
         return fail(SEAS_EINVAL, "batch %d too large for blocks of %d columns (stage of %d bytes)", batch, op->max_q,
                     kStageBytes);

@@ -595,6 +595,223 @@ __device__ __forceinline__ void ld16(const X *p, X (&o)[N]) {
     for (int i = 0; i < (int)(N * sizeof(X) / 16); ++i) d[i] = q[i];
 }
 
+// [tensor-core consumers: begin]
+// ------------------------------------------------------------------------------------------------------------
+// Tensor-core consumers for BF16 storage with 8 scenarios: with B = 8 the interaction is a multi-right-hand-side
+// contraction, and each 16 receivers x 8 scenarios x 16 sources tile is one warp-level MMA (m16n8k16, BF16 inputs,
+// FP32 accumulation) instead of 2048 FFMAs and their shared-memory operand loads.  The FP32 history values (x, z)
+// are split into BF16 hi + lo parts (two MMAs), so they keep 16 mantissa bits; the BF16 operator is used as stored.
+// Per stage the MMA accumulators are FP32 and are added, Kahan-compensated, into the task's accumulator.
+// ------------------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+
+// d += A b: A 16 x 16 row-major BF16 (four registers), b 16 x 8 BF16 (two registers), d 16 x 8 FP32.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Two BF16 values in one register, the first in the low half (the lower index of an MMA fragment pair).
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// B fragments (rows k = 2 tg + {0, 1} and 2 tg + 8 + {0, 1} of a 16 x 8 tile, column g) of four FP32 values,
+// split into hi and lo BF16 parts.
+__device__ __forceinline__ void split_b(const float (&v)[4], uint32_t (&hi)[2], uint32_t (&lo)[2]) {
+    __nv_bfloat16 h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        h[e] = __float2bfloat16_rn(v[e]);
+        l[e] = __float2bfloat16_rn(v[e] - __bfloat162float(h[e]));
+    }
+    hi[0] = pack_bf16(h[0], h[1]);
+    hi[1] = pack_bf16(h[2], h[3]);
+    lo[0] = pack_bf16(l[0], l[1]);
+    lo[1] = pack_bf16(l[2], l[3]);
+}
+
+// Zero the halves of A-fragment registers whose inner index (k = k0 + 2 tg + {0, 1}, and + 8 for registers 2, 3)
+// is not below kvalid: operand bytes past an item are not guaranteed to be finite numbers.
+__device__ __forceinline__ void mask_a_k(uint32_t (&a)[4], int tg, int kvalid) {
+    const int k0 = 2 * tg;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int k = k0 + (r >= 2 ? 8 : 0);
+        const uint32_t keep = (k < kvalid ? 0x0000ffffu : 0u) | (k + 1 < kvalid ? 0xffff0000u : 0u);
+        a[r] &= keep;
+    }
+}
+
+// Consumer warps of k_interaction<BF16, 8> (same stage protocol as the CUDA-core consumers: phase A of stage g + 1
+// and phase B of stage g between two barriers).  Phase A: each (low-rank item, 16 rank rows) unit is one warp's
+// Z tile over the item's source columns.  Phase B: the task's receivers form mt 16-row tiles; warp w owns tile
+// w mod mtp in group w / mtp (mtp = mt rounded up to 1, 2, 4 or 8) and the stage's (item, 16-row chunk) units are
+// dealt round-robin to the groups; at the task's end the groups are added in a fixed order.  Blocks are at most 128
+// receivers wide here (scenario creation checks).
+template <int CW, int ZR>
+__device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, unsigned char *stage_mem, float *zs,
+                                            double *red, uint64_t *full, uint64_t *empty, int *sh_flag) {
+    constexpr int NC = CW * 32;
+    constexpr int B8 = 8;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int g = lane >> 2, tg = lane & 3, mi = lane >> 3, rr = lane & 7;
+
+    auto phase_a = [&](const StageInfo &sx, const unsigned char *bx, float *zout) {
+        if (sx.n_zrows <= 0) return;
+        const int q2 = pad_row(sx.q, kPrecBF16);
+        int u = 0;
+        for (int m = 0; m < sx.n; ++m) {
+            const StageItem &it = sx.it[m];
+            if (it.k <= 0) continue;
+            const int k = it.k, zb = it.z_end - k;
+            const __nv_bfloat16 *V = reinterpret_cast<const __nv_bfloat16 *>(bx + it.data_off);
+            const float *x = reinterpret_cast<const float *>(bx + it.x_off);
+            for (int r0 = 0; r0 < k; r0 += 16, ++u) {
+                if (u % CW != warp) continue;
+                float d[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int K0 = 0; K0 < q2; K0 += 16) {
+                    uint32_t af[4];
+                    ldsm_x4(af, V + (int64_t)(r0 + (mi & 1) * 8 + rr) * q2 + K0 + (mi >> 1) * 8);
+                    mask_a_k(af, tg, q2 - K0);
+                    float xv[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int j = K0 + 2 * tg + (e & 1) + (e >= 2 ? 8 : 0);
+                        xv[e] = j < q2 && g < a.B ? x[j * a.B + g] : 0.f;
+                    }
+                    uint32_t bh[2], bl[2];
+                    split_b(xv, bh, bl);
+                    mma_bf16(d, af, bh[0], bh[1]);
+                    mma_bf16(d, af, bl[0], bl[1]);
+                }
+                if (r0 + g < k) {
+                    zout[(zb + r0 + g) * B8 + 2 * tg] = d[0] * it.scale;
+                    zout[(zb + r0 + g) * B8 + 2 * tg + 1] = d[1] * it.scale;
+                }
+                if (r0 + g + 8 < k) {
+                    zout[(zb + r0 + g + 8) * B8 + 2 * tg] = d[2] * it.scale;
+                    zout[(zb + r0 + g + 8) * B8 + 2 * tg + 1] = d[3] * it.scale;
+                }
+            }
+        }
+    };
+
+    int cur = -1, mt = 1, mtp = 1, G = CW, grp = 0, tile = 0;
+    bool act = true;
+    float2 acc[4];
+    float dst[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        acc[v] = make_float2(0.f, 0.f);
+        dst[v] = 0.f;
+    }
+    if (t == 0) *sh_flag = mbar_wait(&full[0], 0, a.err) ? 0 : 1;
+    consumer_sync<NC>();
+    if (*sh_flag) return;
+    if (info[0].task >= 0) phase_a(info[0], stage_mem, zs);
+    for (int gi = 0;; ++gi) {
+        const int slot = gi % kStages;
+        if (t == 0 && info[slot].task >= 0)
+            *sh_flag = mbar_wait(&full[(gi + 1) % kStages], ((gi + 1) / kStages) & 1, a.err) ? 0 : 1;
+        consumer_sync<NC>();
+        if (*sh_flag) return;
+        if (t == 0 && gi > 0) mbar_arrive(&empty[(gi - 1) % kStages]);
+        const StageInfo &si = info[slot];
+        const int task = si.task;
+        if (task < 0) break;
+        {
+            const int ns = (gi + 1) % kStages;
+            if (info[ns].task >= 0) phase_a(info[ns], stage_mem + (size_t)ns * kStageBytes, zs + ((gi + 1) & 1) * ZR * B8);
+        }
+        const float *zcur = zs + (gi & 1) * ZR * B8;
+        const int p = si.p, p2 = pad_row(p, kPrecBF16), q2 = pad_row(si.q, kPrecBF16);
+        if (task != cur) {
+            cur = task;
+            mt = (p2 + 15) / 16;
+            mtp = mt <= 1 ? 1 : mt <= 2 ? 2 : mt <= 4 ? 4 : 8;
+            G = CW / mtp;
+            grp = warp / mtp;
+            tile = warp % mtp;
+            act = tile < mt;
+        }
+        const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
+        // phase B
+        {
+            int u = 0;
+            const int i0 = tile * 16;
+            for (int m = 0; m < si.n; ++m) {
+                const StageItem &it = si.it[m];
+                const bool dense = it.k < 0;
+                const int rows = dense ? it.i1 - it.i0 : it.k;
+                const __nv_bfloat16 *S = reinterpret_cast<const __nv_bfloat16 *>(base + it.data_off) +
+                                         (dense ? 0 : (int64_t)it.k * q2);
+                // history rows: x has the batch's own stride, z rows are BT = 8 wide
+                const float *src = dense ? reinterpret_cast<const float *>(base + it.x_off)
+                                         : zcur + (int64_t)(it.z_end - it.k) * B8;
+                const int sst = dense ? a.B : B8;
+                const float sc = dense ? it.scale : 1.f;
+                for (int k0 = 0; k0 < rows; k0 += 16, ++u) {
+                    if (u % G != grp || !act) continue;
+                    uint32_t af[4];
+                    ldsm_x4_t(af, S + (int64_t)(k0 + (mi >> 1) * 8 + rr) * p2 + i0 + (mi & 1) * 8);
+                    mask_a_k(af, tg, rows - k0);
+                    float bv[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int r = k0 + 2 * tg + (e & 1) + (e >= 2 ? 8 : 0);
+                        bv[e] = r < rows && g < a.B ? src[r * sst + g] * sc : 0.f;
+                    }
+                    uint32_t bh[2], bl[2];
+                    split_b(bv, bh, bl);
+                    mma_bf16(dst, af, bh[0], bh[1]);
+                    mma_bf16(dst, af, bl[0], bl[1]);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {                      // compensated accumulation, once per stage
+                PTHalf<__nv_bfloat16>::kahan(acc[v], dst[v]);
+                dst[v] = 0.f;
+            }
+        }
+        if (si.flush) {
+            // D fragment: v = 0, 1 -> receiver row g, scenario 2 tg + v; v = 2, 3 -> row g + 8.  Groups added in a
+            // fixed order by the thread that owns each (receiver, scenario).
+            const int64_t part_off = si.part_off;
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                red[(warp * 32 + lane) * 4 + v] = act ? (double)acc[v].x - (double)acc[v].y : 0.0;
+            consumer_sync<NC>();
+            for (int o = t; o < p2 * B8; o += NC) {
+                const int i = o >> 3, nn = o & 7, ti = i >> 4, ii = i & 15;
+                const int lo = (ii & 7) * 4 + (nn >> 1), reg = (ii >> 3) * 2 + (nn & 1);
+                if (i < p && nn < a.B) {
+                    double sum = 0.0;
+                    for (int gg = 0; gg < G; ++gg) sum += red[((gg * mtp + ti) * 32 + lo) * 4 + reg];
+                    a.partial[(int64_t)nn * a.n_partial + part_off + i] = sum;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[v] = make_float2(0.f, 0.f);
+            cur = -1;
+        }
+    }
+}
+
+// [tensor-core consumers: end]
 template <int PREC, int BT>
 __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs a) {
     constexpr int CW = InterShape<BT>::CW, NC = InterShape<BT>::NC, RV = InterShape<BT>::RV;
@@ -793,6 +1010,12 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
         }
     }
 
+    // [tensor-core consumers: begin]
+    if constexpr (PREC == kPrecBF16 && BT == 8) {
+        consume_mma<CW, kZRows>(a, info, stage_mem, reinterpret_cast<float *>(zs), red, full, empty, &sh_flag);
+        return;
+    }
+    // [tensor-core consumers: end]
     // ---------------------------------------------------------------------- consumer warps
     // Thread t works in group t / P and owns the VE-wide column vectors (t mod P) + s P, s < nvt, of the block's
     // rows (P a power of two, G = NC / P groups for NC consumer threads).  The stage's row updates (rows of A^T times x_j, rows of U^T

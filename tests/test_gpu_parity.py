@@ -401,3 +401,27 @@ def test_hmatrix_error_stays_at_aca_tolerance_for_every_eta_h(two_fault_oracle):
     print("eta_H sweep: rel-L2 int", errs, "far blocks", far)
     assert far[0] > 0 and far[-1] == 0 and errs[-1] <= EXACT
     assert max(errs) <= 3 * tol and max(errs[:-1]) > EXACT
+
+
+@pytest.mark.parametrize("batch", [8, 6])
+def test_bf16_ensemble_tensor_core_path_matches_oracle(two_fault_oracle, batch):
+    """BF16 batches of 5..8 run on the tensor-core consumers (16 x 8 x 16 MMA tiles, history split into BF16
+    hi + lo).  Members 0 and batch - 1 against the oracle: self and radiation exact, interaction within the BF16
+    bound; member 0 against the single-scenario CUDA-core BF16 path: the same storage rounding."""
+    w, V0, ref0 = two_fault_oracle
+    net = O.network(w.faults, w.mu, w.cs)
+    N, last = net.N, batch - 1
+    refl = O.stress_history(net, w.slip_rate(last, 0, w.steps), w.hparams)
+    Vb = np.stack([w.slip_rate(b, 0, w.steps) for b in range(batch)], axis=1).reshape(w.steps, -1)
+    with seas.Session(w, batch=batch, precision=seas.SEAS_PREC_BF16) as s:
+        tau, P = run_host(s, Vb)
+    with seas.Session(w, precision=seas.SEAS_PREC_BF16) as s1:
+        _, P1 = run_host(s1, np.ascontiguousarray(V0))
+    for b, ref in ((0, ref0), (last, refl)):
+        cols = slice(b * N, (b + 1) * N)
+        e = [rel(P[:, k, cols], ref[k + 1]) for k in range(3)]
+        print(f"BF16 batch {batch} member {b}: rel-L2 rad {e[0]:.2e} self {e[1]:.2e} int {e[2]:.2e}")
+        assert e[0] <= EXACT and e[1] <= EXACT and e[2] <= MP_BOUND[seas.SEAS_PREC_BF16]
+    e1 = rel(P[:, 2, :N], P1[:, 2])
+    print(f"BF16 batch {batch} member 0 vs single-scenario path: {e1:.2e}")
+    assert e1 <= 1e-2
