@@ -366,3 +366,76 @@ def test_self_static_tail_completes_the_weight_sum():
     e_tail = [np.linalg.norm(tail[m] - full[m]) / np.linalg.norm(full[m]) for m in (300, 890)]
     e_trunc = np.linalg.norm(trunc[890] - full[890]) / np.linalg.norm(full[890])
     assert e_tail[1] < e_tail[0] / 2 and e_tail[1] < 2e-3 and e_trunc > 20 * e_tail[1]
+
+
+# ---------------------------------------------------------------- earthquake-cycle step (oracle only) --------------
+
+from oracle import seas_integrator as SI  # noqa: E402
+
+FR = SI.Friction(a=0.01, b=0.015, dc=1e-3, f0=0.6, v0=1e-9, sigma_n=50e6)
+
+
+def test_state_law_limits_are_the_aging_and_slip_laws():
+    """P15a: Eq. state_evolution_law is the aging law 1 - V theta / D_c at eps = 1 and tends to the slip law
+    -(V theta / D_c) ln(V theta / D_c) as eps -> 0."""
+    rng = np.random.default_rng(3)
+    V = 10.0 ** rng.uniform(-12, 0, 50)
+    theta = 10.0 ** rng.uniform(-4, 8, 50)
+    om = V * theta / FR.dc
+    np.testing.assert_allclose(SI.state_rate(V, theta, FR), 1.0 - om, rtol=1e-12, atol=1e-12)
+    slip = SI.Friction(**{**FR.__dict__, "eps": 1e-7})
+    np.testing.assert_allclose(SI.state_rate(V, theta, slip), -om * np.log(om), rtol=1e-4, atol=1e-12)
+
+
+def test_newton_root_equals_an_independent_bisection():
+    """P15b: the Newton solve of tau - (mu / 2 c_s) V = sigma_n f(V, theta) (in ln V) agrees with a bisection in
+    ln V on the same balance to the 1e-8 tolerance, for stresses spanning creep to seismic slip."""
+    rad = 32e9 / (2 * 3464.0)
+    rng = np.random.default_rng(5)
+    theta = 10.0 ** rng.uniform(-3, 7, 40)
+    tau = FR.sigma_n * (FR.f0 + rng.uniform(-0.1, 0.1, 40))
+    V, it = SI.solve_v(tau, theta, FR, rad, 1e-9)
+    lo, hi = np.full(40, -60.0), np.full(40, 5.0)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        g = tau - rad * np.exp(mid) - FR.sigma_n * SI.friction(np.exp(mid), theta, FR)
+        lo = np.where(g > 0, mid, lo)
+        hi = np.where(g > 0, hi, mid)
+    np.testing.assert_allclose(V, np.exp(0.5 * (lo + hi)), rtol=1e-6)
+    assert it < 60 and V.min() < 1e-6 < V.max()
+
+
+def test_steady_initial_state_of_the_benchmark_stays_put():
+    """P15c: the benchmark's initial condition (V = V_*, theta = D_c / V_*, tau^o = f_* sigma_n + mu V_* / (2 c_s),
+    no slip before t = 0) is an equilibrium: over 40 steps V stays at V_* to 1e-6 (a sign error in the radiation
+    term or the friction law would move it at once)."""
+    net = O.network(np.array([[0.0, 0.0, 0.2, 200.0, 8], [30.0, -300.0, 0.9, 160.0, 8]]), MU, CS)
+    tau0 = FR.f0 * FR.sigma_n + MU / (2 * CS) * FR.v0
+    it = SI.Integrator(net, FR, np.full(net.N, tau0), FR.v0, FR.dc / FR.v0, max_steps=41)
+    for _ in range(40):
+        V = it.step()
+    assert np.abs(V / FR.v0 - 1).max() < 1e-6
+
+
+def test_predictor_corrector_converges_at_second_order_without_elasticity():
+    """P15d: with negligible elasticity (mu -> 0) a step reduces to the slider ODE dtheta/dt = G(V(theta), theta),
+    V(theta) from sigma_n f(V, theta) = tau^o; the oracle's predictor-corrector reaches scipy's solution with an
+    error that falls about four times when dt halves."""
+    fr = SI.Friction(a=0.01, b=0.015, dc=2e-9, f0=0.6, v0=1e-6, sigma_n=50e6)
+    tau0 = fr.f0 * fr.sigma_n
+    errs = []
+    for n_elem in (4, 8):
+        net = O.network(np.array([[0.0, 0.0, 0.0, 10.0, n_elem]]), 1e-3, CS)
+        steps = int(round(0.01 / net.dt))
+        th0 = 5 * fr.dc / fr.v0
+        v_init = math.exp((fr.a * math.log(fr.v0) - fr.b * math.log(th0 / fr.dc)) / (fr.a + fr.b))  # balanced
+        it = SI.Integrator(net, fr, np.full(net.N, tau0), v_init, th0, max_steps=steps + 1)
+        for _ in range(steps):
+            it.step()
+        def rhs(t, y):
+            th = y[0]
+            v = math.exp((fr.a * math.log(fr.v0) - fr.b * math.log(th / fr.dc)) / (fr.a + fr.b))
+            return [1.0 - v * th / fr.dc]
+        ref = integrate.solve_ivp(rhs, (0, steps * net.dt), [th0], rtol=1e-12, atol=1e-20).y[0, -1]
+        errs.append(abs(it.theta[0] - ref) / ref)
+    assert errs[1] < errs[0] / 3.5 and errs[1] < 1e-4
