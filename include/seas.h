@@ -172,16 +172,19 @@ seas_status seas_stress_step(seas_scn *scn, double *tau, double *sigma_n, double
 
 /* Allocation-free variant of seas_stress_step, for callers that must not allocate device memory while stepping:
  * a solver embedded in a host code whose own allocator has already reserved the GPU's memory, or a time loop that
- * cannot afford cudaMalloc/cudaFree, which may synchronize the whole device.  The paper has no counterpart; this is
- * a property of the library only.  tau ([batch][N]) and parts (nullable, [3][batch][N]) are DEVICE pointers that
- * the caller owns; the call computes what seas_stress_step computes (same kernels, same summation order) on the
- * context's stream, but is not counted by seas_scenario_set_timing.  Its scratch (the interaction's per-task
- * partial sums and the summed interaction term) is a file-scope static device array of 4,194,304 doubles (32 MiB),
- * held by every GPU that loads the library until the process exits; a scenario whose partial-sum rows times batch
- * plus batch * N exceed that gets SEAS_EINVAL and nothing runs.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, which allocates nothing), so make that first call before any stream
- * capture.  All calls share the array, which keeps the last call's contents (every entry a call reads it first
- * writes); calls that overlap on the GPU (other streams, threads or contexts of this process) race on it. */
+ * cannot afford cudaMalloc/cudaFree, which may synchronize the whole device.  seas_stress_step itself allocates
+ * nothing per step either (seas_scenario_create allocates the scenario's scratch once, and still does so for
+ * scenarios stepped only through this call); the difference is only where the per-call scratch lives.  The paper has
+ * no counterpart; this is a property of the library only.  tau ([batch][N]) and parts (nullable, [3][batch][N]) are
+ * DEVICE pointers that the caller owns; the call computes what seas_stress_step computes (same kernels, same
+ * summation order) on the context's stream, but is not counted by seas_scenario_set_timing.  Its scratch (the
+ * interaction's per-task partial sums and the summed interaction term) is a file-scope static device array of
+ * 4,194,304 doubles (32 MiB), held by every GPU that loads the library until the process exits; a scenario whose
+ * partial-sum rows times batch plus batch * N exceed that gets SEAS_EINVAL and nothing runs.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, which allocates nothing), so make that first
+ * call before any stream capture.  All calls share the array, which keeps the last call's contents (every entry a
+ * call reads it first writes); calls that overlap on the GPU (other streams, threads or contexts of this process)
+ * race on it. */
 seas_status seas_stress_step_static(seas_scn *scn, double *tau, double *parts);
 
 /* Number of pushes so far. */

@@ -403,7 +403,9 @@ def self_history(net: Network, f: int, delta: np.ndarray, tables: SelfTables) ->
 
 
 def self_rows(net: Network, f: int, delta: np.ndarray, m: int, tables: SelfTables, rows) -> np.ndarray:
-    """f_self^m at local ``rows`` of fault f, from delta[0..m][N_f]."""
+    """f_self^m at local ``rows`` of fault f, from delta[0..m][N_f] (windows as in ``tables``; no static tail)."""
+    if tables.c is not None:
+        raise NotImplementedError("self_rows evaluates the windowed sum only; use self_history with a static tail")
     n_f, L = tables.n_f, tables.L
     Wmax = int(tables.W.max())
     lo = max(0, m - Wmax)

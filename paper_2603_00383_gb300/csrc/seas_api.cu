@@ -1494,7 +1494,13 @@ extern "C" seas_status seas_scenario_load(seas_op *op, const char *path, seas_sc
     std::unique_ptr<seas_scn> s;
     seas_status st = scenario_alloc(op, h.B, s);
     if (st == SEAS_OK && h.dring_len != s->dring_len) st = fail(SEAS_EIO, "checkpoint spectral ring size mismatch");
-    if (st == SEAS_OK) CUDA_TRY(cudaStreamSynchronize(op->net->ctx->stream));
+    if (st == SEAS_OK) {
+        const cudaError_t e = cudaStreamSynchronize(op->net->ctx->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(SEAS_ECUDA, "cudaStreamSynchronize failed: %s", cudaGetErrorString(e));
+        }
+    }
     if (st == SEAS_OK) st = slurp(fp, s->vring.p, s->vring.bytes());
     if (st == SEAS_OK) st = slurp(fp, s->slip.p, s->slip.bytes());
     if (st == SEAS_OK) st = slurp(fp, s->slip_prev.p, s->slip_prev.bytes());

@@ -131,17 +131,24 @@ class Handle:
         self.__dict__.update(meta)
 
 
-def _buf(x, n: int, what: str):
-    """(pointer, mem) of a float64 buffer of n elements: NumPy -> host, CUDA tensor -> device."""
+def _buf(x, n: int, what: str, device: int = None):
+    """(pointer, mem) of a float64 buffer of n elements: NumPy -> host, CUDA tensor -> device.  ``device``: the
+    handle's GPU; a tensor on another GPU is rejected (the kernels would write through a foreign pointer)."""
     if x is None:
         return None, None
     if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
         if str(x.dtype) != "torch.float64" or not x.is_contiguous() or x.numel() != n:
             raise ValueError(f"{what}: need a contiguous float64 CUDA tensor of {n} elements")
+        if device is not None and x.device.index is not None and x.device.index != device:
+            raise ValueError(f"{what}: tensor on cuda:{x.device.index}, the scenario lives on cuda:{device}")
         return C.c_void_p(x.data_ptr()), SEAS_MEM_DEVICE
     if not isinstance(x, np.ndarray) or x.dtype != np.float64 or not x.flags.c_contiguous or x.size != n:
         raise ValueError(f"{what}: need a C-contiguous float64 array of {n} elements")
     return C.c_void_p(x.ctypes.data), SEAS_MEM_HOST
+
+
+def _device_of(scn: Handle) -> int:
+    return scn.op.net.ctx.device
 
 
 def seas_strerror(status: int) -> str:
@@ -270,8 +277,9 @@ def seas_scenario_create(op: Handle, batch: int = 1) -> Handle:
 
 def seas_push_slip_rate(scn: Handle, V, slip=None, replace_last: bool = False):
     n = scn.B * scn.N
-    pv, mem = _buf(V, n, "V")
-    ps, mem_s = _buf(slip, n, "slip")
+    dev = _device_of(scn)
+    pv, mem = _buf(V, n, "V", dev)
+    ps, mem_s = _buf(slip, n, "slip", dev)
     if slip is not None and mem_s != mem:
         raise ValueError("V and slip must live in the same memory")
     _check(lib().seas_push_slip_rate(scn.ptr, pv, ps, mem, 1 if replace_last else 0))
@@ -279,9 +287,10 @@ def seas_push_slip_rate(scn: Handle, V, slip=None, replace_last: bool = False):
 
 def seas_stress_step(scn: Handle, tau, sigma_n=None, parts=None):
     n = scn.B * scn.N
-    pt, mem = _buf(tau, n, "tau")
-    pn, mn = _buf(sigma_n, n, "sigma_n")
-    pp, mp = _buf(parts, 3 * n, "parts")
+    dev = _device_of(scn)
+    pt, mem = _buf(tau, n, "tau", dev)
+    pn, mn = _buf(sigma_n, n, "sigma_n", dev)
+    pp, mp = _buf(parts, 3 * n, "parts", dev)
     for m in (mn, mp):
         if m is not None and m != mem:
             raise ValueError("tau, sigma_n and parts must live in the same memory")
@@ -292,8 +301,9 @@ def seas_stress_step_static(scn: Handle, tau, parts=None):
     """seas_stress_step into device buffers (CUDA tensors) with its scratch in a static device array, for callers
     that must not allocate device memory while stepping; limits and sharing rules are in include/seas.h."""
     n = scn.B * scn.N
-    pt, mem = _buf(tau, n, "tau")
-    pp, mp = _buf(parts, 3 * n, "parts")
+    dev = _device_of(scn)
+    pt, mem = _buf(tau, n, "tau", dev)
+    pp, mp = _buf(parts, 3 * n, "parts", dev)
     if mem != SEAS_MEM_DEVICE or (mp is not None and mp != SEAS_MEM_DEVICE):
         raise ValueError("seas_stress_step_static takes device buffers")
     _check(lib().seas_stress_step_static(scn.ptr, pt, pp))

@@ -439,3 +439,125 @@ def test_predictor_corrector_converges_at_second_order_without_elasticity():
         ref = integrate.solve_ivp(rhs, (0, steps * net.dt), [th0], rtol=1e-12, atol=1e-20).y[0, -1]
         errs.append(abs(it.theta[0] - ref) / ref)
     assert errs[1] < errs[0] / 3.5 and errs[1] < 1e-4
+
+
+# ---------------------------------------------------------------- single-row evaluators and the interaction factor --
+
+def test_interaction_rows_equals_the_full_history_across_chunk_and_window_edges():
+    """interaction_rows (one step, chosen receivers, lags in chunks) is the row slice of interaction_history (every
+    step, every receiver, one lag stack): checked at steps on both sides of chunk boundaries and of the per-pair
+    window ends, with and without windows, for chunk sizes 64 and 128, on a three-fault network."""
+    w = synth.tiny(4, n_faults=3, steps=270)
+    net = O.network(w.faults, MU, CS)
+    V = w.slip_rate(0, 0, 270)
+    hi = np.array([[-1, 131, 200], [64, -1, 127], [129, 255, -1]])
+    full = O.interaction_history(net, V)
+    win = O.interaction_history(net, V, pair_hi=hi)
+    assert np.abs(full[200]).max() > 0 and np.abs(win[269] - full[269]).max() > 1e-3 * np.abs(full[269]).max()
+    rows = np.array([0, 3, net.offset[1], net.N - 1, net.offset[2] + 1])
+    for n in (0, 1, 63, 64, 65, 127, 128, 129, 130, 131, 132, 199, 200, 201, 255, 256, 269):
+        for chunk in (64, 128):
+            np.testing.assert_allclose(O.interaction_rows(net, V, n, rows, chunk=chunk), full[n, rows],
+                                       rtol=1e-12, atol=1e-12 * np.abs(full[n]).max())
+            np.testing.assert_allclose(O.interaction_rows(net, V, n, rows, pair_hi=hi, chunk=chunk), win[n, rows],
+                                       rtol=1e-12, atol=1e-12 * np.abs(full[n]).max())
+
+
+def test_self_rows_equals_the_full_history_around_the_window_edge():
+    """self_rows (one step, chosen receivers, the slip history from the longest window back) is the row slice of
+    self_history (every step): mode-dependent windows (q_w = 3) so that modes have different last lags; steps on
+    both sides of the longest window."""
+    L, nf = 300.0, 12
+    net = O.network(np.array([[10.0, -5.0, 0.4, L, nf]]), MU, CS)
+    steps = 140
+    W = O.mode_windows(nf, L, net.dt, CS, 1.0, 3, steps)
+    assert W[1] > W[nf] and W[1] < steps - 20
+    V = synth.Workload("one", np.array([[10.0, -5.0, 0.4, L, nf]]), steps=steps).slip_rate(0, 0, steps)
+    delta = O.slip_from_rate(V, net.dt)
+    tab = O.SelfTables(nf, L, net.dt, CS, W)
+    full = O.self_history(net, 0, delta, tab)
+    Wm = int(W.max())
+    rows = np.array([0, 5, nf - 1])
+    for m in (0, 1, Wm - 1, Wm, Wm + 1, Wm + 2, steps - 1):
+        np.testing.assert_allclose(O.self_rows(net, 0, delta[: m + 1], m, tab, rows), full[m, rows],
+                                   rtol=1e-11, atol=1e-11 * np.abs(full).max())
+
+
+def _dislocation_traction(x, nrm, P, b):
+    """Traction on planes of normal nrm at points x from a screw dislocation of Burgers vector b at P (the textbook
+    anti-plane field sigma_31 = -(mu b / 2 pi) y / r^2, sigma_32 = (mu b / 2 pi) x / r^2, relative coordinates)."""
+    d = x - P
+    r2 = (d * d).sum(-1)
+    s31 = -(MU * b / (2 * np.pi)) * d[..., 1] / r2
+    s32 = (MU * b / (2 * np.pi)) * d[..., 0] / r2
+    return s31 * nrm[..., 0] + s32 * nrm[..., 1]
+
+
+def test_interaction_tends_to_the_stress_of_a_slipped_segment():
+    """Factor, sign and projection of interaction_history / interaction_rows, pinned to elastostatics: a step of
+    slip delta_f on each of three differently oriented faults (slip rate delta_f / dt in step 0, nothing after)
+    makes f_int tend, as c_s t grows, to the static stress of uniformly slipped segments, i.e. pairs of screw
+    dislocations (+delta at the start c - L/2 e'_1 of the fault, -delta at its end), a closed form independent of
+    Eq. primitives.  The convention is fixed by the radiation-damping sign of Eq. superimposition2: slip lowers the
+    stress on the slipping segment and raises it beyond its tips.  A wrong -mu / (2 c_s) factor, sign, normal frame
+    or transposed operand fails; the error decays like (r / c_s t)^2."""
+    faults = np.array([[0.0, 0.0, 0.25, 120.0, 6], [150.0, -90.0, 1.2, 100.0, 5], [-40.0, 160.0, -0.7, 90.0, 9]])
+    net = O.network(faults, MU, CS)
+    delta = np.array([0.7, -0.4, 1.3])
+    ref = np.zeros(net.N)
+    for f, (cx, cy, phi, L, _) in enumerate(faults):
+        e1 = np.array([math.cos(phi), math.sin(phi)])
+        c = np.array([cx, cy])
+        o = net.fault_of != f
+        ref[o] += _dislocation_traction(net.x[o], net.nrm[o], c - 0.5 * L * e1, delta[f])
+        ref[o] += _dislocation_traction(net.x[o], net.nrm[o], c + 0.5 * L * e1, -delta[f])
+    errs = []
+    for n in (5000, 20000):
+        V = np.zeros((n + 1, net.N))
+        for f in range(3):
+            V[0, net.offset[f]:net.offset[f + 1]] = delta[f] / net.dt
+        got = O.interaction_rows(net, V, n, np.arange(net.N))
+        errs.append(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    assert errs[1] < 3e-6 and errs[1] < errs[0] / 8
+    # the same through the all-steps evaluator on a shorter run
+    V = np.zeros((1500, net.N))
+    V[0, : net.offset[1]] = delta[0] / net.dt
+    hist = O.interaction_history(net, V)[-1]
+    one = np.zeros(net.N)
+    o = net.fault_of != 0
+    e1 = np.array([math.cos(0.25), math.sin(0.25)])
+    one[o] = (_dislocation_traction(net.x[o], net.nrm[o], -60.0 * e1, delta[0])
+              + _dislocation_traction(net.x[o], net.nrm[o], 60.0 * e1, -delta[0]))
+    assert np.linalg.norm(hist - one) / np.linalg.norm(one) < 2e-3
+
+
+def test_collinear_halves_self_plus_interaction_converge_to_the_whole_fault():
+    """Cutting one straight fault into two collinear halves: the spectral self term of the whole fault (Sec. 2.3.1)
+    and the spectral self terms of the halves plus their space-time cross interaction (Sec. 2.3.2,
+    interaction_history) are two discretisations of one operator and agree at O(ds) as the mesh is refined (slip
+    vanishing at the cut and at the ends, so no tip singularity sits between them).  Dropping the cross term,
+    flipping its sign or halving its factor leaves an O(1) error that does not shrink."""
+    L, phi = 1000.0, 0.3
+    e1 = np.array([math.cos(phi), math.sin(phi)])
+    errs, wrong = [], []
+    for N in (16, 32):
+        whole = O.network(np.array([[0.0, 0.0, phi, L, N]]), MU, CS)
+        ca, cb = -0.25 * L * e1, 0.25 * L * e1
+        split = O.network(np.array([[ca[0], ca[1], phi, L / 2, N // 2], [cb[0], cb[1], phi, L / 2, N // 2]]),
+                          MU, CS)
+        assert np.allclose(whole.x, split.x) and whole.dt == split.dt
+        steps = int(round(3 * L / (CS * whole.dt)))
+        t = np.arange(steps) * whole.dt
+        xi = (np.arange(N) + 0.5) / N
+        V = np.outer(np.sin(np.pi * CS * t / L) ** 2 * (t < L / CS), np.sin(2 * np.pi * xi) ** 2)
+        d = O.slip_from_rate(V, whole.dt)
+        fw = O.self_history(whole, 0, d, O.SelfTables(N, L, whole.dt, CS, np.full(N + 1, steps - 1)))
+        h = N // 2
+        th = O.SelfTables(h, L / 2, whole.dt, CS, np.full(h + 1, steps - 1))
+        fs = np.concatenate([O.self_history(split, 0, d[:, :h], th), O.self_history(split, 1, d[:, h:], th)], 1)
+        fi = O.interaction_history(split, V)
+        nw = np.linalg.norm(fw)
+        errs.append(np.linalg.norm(fs + fi - fw) / nw)
+        wrong.append(min(np.linalg.norm(fs + c * fi - fw) / nw for c in (0.0, -1.0, 0.5, 2.0)))
+    assert errs[0] < 0.02 and errs[1] < 0.6 * errs[0]
+    assert min(wrong) > 10 * errs[0]
