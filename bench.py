@@ -2,10 +2,12 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload six_fault_3072]
 
-A step is one push of the slip rate plus one seas_stress_step (all hot-path stages: push, forward FFT, mode
-convolution, H-matrix interaction, inverse FFT + assembly) on the six-fault, 3072-element network with the
-selective H-matrix (leaf 32, eta_H 2, ACA 1e-6) and causal / spectral windows; the timed K steps are the first K
-steps of a fresh scenario (K = 2000 is the whole workload).  Prints one JSON line.
+Workload: the six-fault, 3072-element network run for its full 2000 steps, with the selective H-matrix (leaf 32,
+eta_H 2, ACA 1e-6) and the causal / spectral windows.  A step is one push of the slip rate plus one seas_stress_step
+(all hot-path stages: push, forward FFT, mode convolution, H-matrix interaction and its reduction, inverse FFT +
+assembly).  The operator is always built for the 2000-step workload; each scenario is advanced untimed to step
+2000 - K (the last W of those steps are the warm-up) and the K deepest steps, [2000 - K, 2000), are timed, so the
+timed steps carry the full history depth whatever K is.  Prints one JSON line.
 """
 import argparse
 import json
@@ -15,7 +17,7 @@ import sys
 import tempfile
 import time
 
-if "--impl" in sys.argv and "reference" in sys.argv:      # the oracle arm runs single-threaded on the host
+if "--impl" in sys.argv and "reference" in sys.argv:      # the oracle arm runs single-threaded per process
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ.setdefault(var, "1")
 
@@ -27,12 +29,15 @@ sys.path.insert(0, ROOT)
 from paper_2603_00383_gb300 import synth  # noqa: E402
 
 METRIC = "element-steps/s"
+# name -> (seas precision code, dtype label of the arithmetic)
+PRECISIONS = {"fp64": (0, "f64"), "df64": (3, "df64 (fp32 pairs)"), "bf16": (1, "bf16 storage, f32 compensated"),
+              "fp16s": (2, "fp16 storage with per-slice scale, f32 compensated")}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--steps", type=int, default=200, help="timed steps K: the K deepest steps of the workload")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="six_fault_3072")
@@ -43,16 +48,13 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the other storage precisions")
     ap.add_argument("--no-batched", action="store_true", help="skip the 8-scenario ensemble runs")
     ap.add_argument("--no-tail", action="store_true", help="skip the static-tail run")
+    ap.add_argument("--no-oracle-rows", action="store_true", help="skip the oracle interaction rows (errors)")
     ap.add_argument("--dump-step-bytes", default=None, help="write the per-step algorithmic interaction bytes here")
     return ap.parse_args()
 
 
-# name -> (seas precision code, dtype label of the arithmetic)
-# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops at the 2070 MHz maximum SM clock
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
-FP64_PEAK_KIND = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"
-PRECISIONS = {"fp64": (0, "f64"), "df64": (3, "df64 (fp32 pairs)"), "bf16": (1, "bf16 storage, f32 compensated"),
-              "fp16s": (2, "fp16 storage with per-slice scale, f32 compensated")}
+def log(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
 def load_peaks():
@@ -64,29 +66,41 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def window(w, K):
+    """The timed window [start, steps): the K deepest steps of the workload."""
+    K = max(1, min(int(K), w.steps))
+    return w.steps - K, K
+
+
 # ------------------------------------------------------------------------------------------------ oracle sample --
 
-def oracle_sample(w, K, count, seed=11):
+def oracle_sample(w, start, K, count, seed=11):
     """(element, step) pairs of the CPU-baseline / reference sample: elements of fault 0 (whose spectral tables the
-    oracle builds once, untimed), steps spread over the run so the mean history depth is that of the workload."""
+    oracle builds once, untimed), steps spread over the timed window."""
     n0 = int(w.faults[0, 4])
     k = np.arange(count)
     elems = (k * 97 + seed) % n0
-    steps = (k * 7919 + 13 * seed) % K
+    steps = start + (k * 7919 + 13 * seed) % K
     return elems, steps
+
+
+def oracle_rows(w):
+    """Receivers of the interaction-error check: two per fault (first and middle element)."""
+    off = np.concatenate([[0], np.cumsum(w.faults[:, 4].astype(int))])
+    return np.array([r for f in range(w.n_faults) for r in (off[f], (off[f] + off[f + 1]) // 2)])
 
 
 class OracleStepper:
     """Evaluates tau at single (element, step) pairs with the CPU oracle (interaction row + spectral self term of
     fault 0 + radiation damping), with the workload's windows."""
 
-    def __init__(self, w, K, tables=None):
+    def __init__(self, w, tables=None):
         from oracle import seas_oracle as O
         self.O = O
         self.w = w
         self.net = O.network(w.faults, w.mu, w.cs)
         hp = w.hparams
-        self.V = w.slip_rate(0, 0, K)
+        self.V = w.slip_rate(0, 0, w.steps)
         self.delta = O.slip_from_rate(self.V, self.net.dt)
         no_trunc = bool(hp.get("flags", 0) & 2)
         _, _, self.last = O.pair_windows(self.net, hp["eta_tmin"], hp["eta_tmax"], hp["max_steps"], no_trunc)
@@ -104,58 +118,63 @@ class OracleStepper:
         fs = O.self_rows(self.net, 0, self.delta[: n + 1, : self.n0], int(n), self.tab0, [int(i)])[0]
         return -(self.w.mu / (2 * self.w.cs)) * self.V[n, i] + fs + fi
 
+    def interaction(self, rows, n):
+        return self.O.interaction_rows(self.net, self.V, int(n), rows, pair_hi=self.last)
+
 
 _WORKER = None
 
 
-def _worker_init(name, K, tables):
+def _worker_init(name, tables):
     global _WORKER
-    _WORKER = OracleStepper(synth.WORKLOADS[name](), K, tables)
+    _WORKER = OracleStepper(synth.WORKLOADS[name](), tables)
 
 
 def _worker_tau(pair):
     return _WORKER.tau(pair[0], pair[1])
 
 
-def run_reference(args, w, K, W):
-    """The oracle arm: each step evaluates one (element, step) sample of the workload on the host; the samples are
-    spread over the host cores by a spawn process pool (tables built once, shipped to the workers)."""
+def config_of(w, start, K):
+    hp = w.hparams
+    return {"workload": w.name, "faults": w.n_faults, "elements": w.N, "steps": w.steps,
+            "timed_window": [start, start + K], "batch": 1,
+            "leaf": hp["leaf"], "eta_h": hp["eta_h"], "aca_tol": hp["aca_tol"], "eta_tmax": hp["eta_tmax"],
+            "eta_w": hp["eta_w"], "q_w": "n_max" if hp["q_w"] <= 0 else hp["q_w"],
+            "parallelism": "replicas (independent scenarios per GPU)",
+            "l2": "operator larger than L2 (no flush between steps)"}
+
+
+def run_reference(args, w, start, K, W):
+    """The oracle arm: each step evaluates one (element, step) sample of the timed window on the host; the samples
+    are spread over the host cores by a spawn process pool (tables built once, shipped to the workers)."""
     import multiprocessing as mp
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     cores = max(1, (os.cpu_count() or 1))
     t0 = time.perf_counter()
-    st = OracleStepper(w, K)
+    st = OracleStepper(w)
     setup = time.perf_counter() - t0
-    elems, steps = oracle_sample(w, K, K + W)
+    elems, steps = oracle_sample(w, start, K, K + W)
     pairs = list(zip(elems.tolist(), steps.tolist()))
     ctx = mp.get_context("spawn")
-    with ctx.Pool(cores, initializer=_worker_init, initargs=(w.name, K, st.tab0)) as pool:
+    with ctx.Pool(cores, initializer=_worker_init, initargs=(w.name, st.tab0)) as pool:
         pool.map(_worker_tau, pairs[:max(W, cores)], chunksize=1)          # warm-up: every worker initialised
         t0 = time.perf_counter()
         pool.map(_worker_tau, pairs[W:], chunksize=4)
         T = time.perf_counter() - t0
     value = K / T
-    sample = (f"{K} oracle element-steps (one receiver of fault 0 at a step drawn uniformly from the {K}-step run, "
-              f"all lags of every source, NumPy FP64) over a {cores}-process spawn pool; spectral tables of fault 0 "
-              f"built once untimed ({setup:.1f} s)")
+    sample = (f"{K} oracle element-steps (one receiver of fault 0 at a step drawn from the timed window "
+              f"[{start}, {start + K}) of the {w.steps}-step run, all lags of every source within the windows, "
+              f"NumPy FP64) over a {cores}-process spawn pool; spectral tables of fault 0 built once untimed "
+              f"({setup:.1f} s)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
             "steps": K, "warmup": W, "ms_per_step": 1e3 * T / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(w, K),
+            "config": config_of(w, start, K),
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return line
-
-
-def config_of(w, K):
-    hp = w.hparams
-    return {"workload": w.name, "faults": w.n_faults, "elements": w.N, "steps": K, "batch": 1,
-            "leaf": hp["leaf"], "eta_h": hp["eta_h"], "aca_tol": hp["aca_tol"], "eta_tmax": hp["eta_tmax"],
-            "eta_w": hp["eta_w"], "q_w": "n_max" if hp["q_w"] <= 0 else hp["q_w"],
-            "parallelism": "replicas (independent scenarios per GPU)",
-            "l2": "operator larger than L2 (no flush between steps)"}
 
 
 # ---------------------------------------------------------------------------------------------------- GPU arm ------
@@ -248,195 +267,273 @@ def max_over_ranks(dist, x, device):
     return float(t.item())
 
 
-def timed_run(seas, torch, s, Vd, K, dist, device, out_tau=None):
-    """K steps with device-resident inputs; per-step CUDA events on the library's stream."""
-    N = Vd.shape[1]
-    tau = out_tau if out_tau is not None else torch.zeros((K, N), dtype=torch.float64, device=device)
+def advance(seas, torch, scn, Vd, n0, n1, device):
+    """Untimed steps n0 .. n1 - 1 (device-resident inputs)."""
+    t = torch.zeros(Vd.shape[1], dtype=torch.float64, device=device)
+    for n in range(n0, n1):
+        seas.seas_push_slip_rate(scn, Vd[n])
+        seas.seas_stress_step(scn, t)
+    torch.cuda.synchronize(device)
+
+
+def timed_run(seas, torch, scn, Vd, start, K, dist, device):
+    """Steps start .. start + K - 1 with device-resident inputs; per-step CUDA events on the library's stream
+    (created before the timed region); the parts of the last step are kept."""
+    BN = Vd.shape[1]
+    tau = torch.zeros((K, BN), dtype=torch.float64, device=device)
+    parts = torch.zeros(3 * BN, dtype=torch.float64, device=device)
     stream = torch.cuda.current_stream(device)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    begin, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(dist)
     torch.cuda.synchronize(device)
-    start.record(stream)
-    for n in range(K):
-        ev[n][0].record(stream)
-        seas.seas_push_slip_rate(s.scn, Vd[n])
-        seas.seas_stress_step(s.scn, tau[n])
-        ev[n][1].record(stream)
-    stop.record(stream)
+    begin.record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        seas.seas_push_slip_rate(scn, Vd[start + k])
+        seas.seas_stress_step(scn, tau[k], parts=parts if k == K - 1 else None)
+        ev[k][1].record(stream)
+    end.record(stream)
     torch.cuda.synchronize(device)
     barrier(dist)
-    total_ms = start.elapsed_time(stop)
+    total_ms = begin.elapsed_time(end)
     per = np.array([a.elapsed_time(b) for a, b in ev])
-    return total_ms, per, tau
+    return total_ms, per, tau, parts.reshape(3, BN)
 
 
-def run_precision(seas, torch, wr, prec, Vd, K, W, dist, device, stream, peak, batch=1, flags=None):
-    """Builds the operator in one storage precision and times K steps of `batch` scenarios sharing it (Vd is
-    [K][batch * N]); returns the measurements and tau."""
-    extra = {} if flags is None else {"flags": flags}
-    s = seas.Session(wr, batch=batch, device=device.index, stream=stream.cuda_stream, precision=prec, **extra)
-    warm = seas.seas_scenario_create(s.op, batch)
-    tw = torch.zeros(batch * wr.N, dtype=torch.float64, device=device)
-    for n in range(W):
-        seas.seas_push_slip_rate(warm, Vd[n % K])
-        seas.seas_stress_step(warm, tw)
-    torch.cuda.synchronize(device)
-    seas.seas_destroy_scn(warm)
-    seas.seas_scenario_set_timing(s.scn, True)
-    with Clocks(device.index) as clk:
-        total_ms, per, tau = timed_run(seas, torch, s, Vd, K, dist, device)
-    seas.seas_scenario_check(s.scn)                      # raises if a bounded device wait ran out
-    timing = seas.seas_scenario_get_timing(s.scn)
-    total_ms = max_over_ranks(dist, total_ms, device)
+def roofline_of(timing, batch, peak, fp64_peak, prec):
+    """Roofline of the interaction kernel from the library's per-kernel events over a timed window."""
     ms = timing["ms"]
-    launches = timing["launches"]
-    n_launch = max(1, launches["interaction"])
+    n_launch = max(1, timing["launches"]["interaction"])
     inter_ms = ms["interaction"]
     secs = inter_ms / 1e3
-    achieved = timing["interaction_bytes"] / secs / 1e9 if inter_ms > 0 else 0.0
+    gbs = timing["interaction_bytes"] / secs / 1e9 if inter_ms > 0 else 0.0
     common = {"kernel": "k_interaction", "algorithmic_bytes_per_launch": timing["interaction_bytes"] / n_launch,
-              "mean_launch_ms": inter_ms / n_launch, "dominant_by_time": max(ms, key=ms.get), "kernel_ms": ms}
+              "mean_launch_ms": inter_ms / n_launch, "dominant_by_time": max(ms, key=ms.get),
+              "kernel_ms": ms, "launches": timing["launches"]}
     if prec == 0:
-        # FP64: one FMA per 8 algorithmic bytes per scenario; the FP64 pipe (2 FMA/clk/SM) is below the HBM rate
-        tflops = 2.0 * timing["interaction_bytes"] / 8 * s.scn.B / secs / 1e12 if inter_ms > 0 else 0.0
-        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tflops / FP64_PEAK_TFLOPS, "peak_kind": FP64_PEAK_KIND,
-                "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak[0]}
+        # FP64: one FMA per 8 algorithmic bytes per scenario; the FP64 pipe is below the HBM rate
+        tflops = 2.0 * timing["interaction_bytes"] / 8 * batch / secs / 1e12 if inter_ms > 0 else 0.0
+        roof = {"bound": "alu", "achieved": tflops, "peak": fp64_peak[0], "unit": "TFLOP/s",
+                "frac": tflops / fp64_peak[0], "peak_kind": fp64_peak[1],
+                "hbm_achieved_gbs": gbs, "hbm_frac": gbs / peak[0]}
     else:
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak[0], "unit": "GB/s", "frac": achieved / peak[0],
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peak[0], "unit": "GB/s", "frac": gbs / peak[0],
                 "peak_kind": peak[1]}
     roof.update(common)
-    res = {"total_ms": total_ms, "per": per, "stats": s.stats, "timing": timing, "clocks": clk.summary(),
-           "roofline": roof}
-    s_keep = s
-    return res, tau, s_keep
+    return roof
 
 
-def run_ours(args, w, K, W):
+def rel(a, b):
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def run_ours(args, w, start, K, W):
     import torch
     from paper_2603_00383_gb300 import seas
     dist, rank, world, local = dist_setup(args)
-    wr = synth.six_fault_3072(steps=K) if w.name == "six_fault_3072" else w
-    wr.seed = rank_seed(rank)                            # independent scenario per rank
-    # CPU oracle sample first (before any GPU work in this process)
-    oracle = None
-    if rank == 0 and args.cpu_sample > 0:
-        st = OracleStepper(wr, K)
-        elems, steps = oracle_sample(wr, K, args.cpu_sample)
+    w.seed = rank_seed(rank)                                # independent scenario per rank
+    # CPU oracle first (before any GPU work in this process): the CPU baseline and the interaction rows that every
+    # storage precision is checked against
+    oracle, ref_int = None, None
+    rows = oracle_rows(w)
+    if rank == 0 and (args.cpu_sample > 0 or not args.no_oracle_rows):
         t0 = time.perf_counter()
-        ref = np.array([st.tau(i, n) for i, n in zip(elems, steps)])
-        T = time.perf_counter() - t0
-        oracle = (elems, steps, ref, T)
+        st = OracleStepper(w)
+        log(f"oracle tables {time.perf_counter() - t0:.1f} s")
+        if args.cpu_sample > 0:
+            elems, steps = oracle_sample(w, start, K, args.cpu_sample)
+            t0 = time.perf_counter()
+            ref = np.array([st.tau(i, n) for i, n in zip(elems, steps)])
+            T = time.perf_counter() - t0
+            oracle = (elems, steps, ref, T)
+            log(f"cpu baseline {args.cpu_sample} element-steps in {T:.1f} s")
+        if not args.no_oracle_rows:
+            t0 = time.perf_counter()
+            ref_int = st.interaction(rows, w.steps - 1)
+            log(f"oracle interaction rows {time.perf_counter() - t0:.1f} s")
         del st
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     stream = torch.cuda.current_stream(device)
-    V = wr.slip_rate(0, 0, K)
+    V = w.slip_rate(0, 0, w.steps)
     Vd = torch.from_numpy(V).to(device)
     peak = load_peaks()
+    fma = seas.seas_measure_fp64_peak(local)
+    fp64_peak = (2.0 * fma / 1e12, "measured: FP64 FMA probe of the library (seas_measure_fp64_peak), "
+                                   f"{fma / 1e9:.1f} G FMA/s")
+    log(f"fp64 probe {fp64_peak[0]:.3f} TFLOP/s")
 
-    def err_of(tau):
+    def tau_err(tau_win, elems_steps=None):
         if oracle is None:
             return None
         elems, steps, ref, _ = oracle
-        got = tau.cpu().numpy()[steps, elems]
-        return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        got = tau_win.cpu().numpy()[steps - start, elems]
+        return rel(got, ref)
 
+    def int_err(parts_last, b=0):
+        if ref_int is None:
+            return None
+        return rel(parts_last[2, b * w.N + rows].cpu().numpy(), ref_int)
+
+    def session(prec, batch=1, flags=None):
+        extra = {} if flags is None else {"flags": flags}
+        t0 = time.perf_counter()
+        s = seas.Session(w, batch=batch, device=local, stream=stream.cuda_stream, precision=prec, **extra)
+        log(f"build prec {prec} batch {batch} flags {flags}: {time.perf_counter() - t0:.1f} s, "
+            f"{s.stats['bytes_interaction'] / 1e9:.2f} GB")
+        return s
+
+    def measure(s, Vx, batch, prec, clocks=False):
+        """Advance to the window, then time it with per-kernel events (created beforehand)."""
+        t0 = time.perf_counter()
+        advance(seas, torch, s.scn, Vx, 0, start, device)
+        log(f"advance {start} steps: {time.perf_counter() - t0:.1f} s")
+        seas.seas_scenario_set_timing(s.scn, True)
+        if clocks:
+            with Clocks(local) as clk:
+                total_ms, per, tau, parts = timed_run(seas, torch, s.scn, Vx, start, K, dist, device)
+            clk_summary = clk.summary()
+        else:
+            total_ms, per, tau, parts = timed_run(seas, torch, s.scn, Vx, start, K, dist, device)
+            clk_summary = None
+        seas.seas_scenario_check(s.scn)                  # raises if a bounded device wait ran out
+        timing = seas.seas_scenario_get_timing(s.scn)
+        seas.seas_scenario_set_timing(s.scn, False)
+        total_ms = max_over_ranks(dist, total_ms, device)
+        return {"total_ms": total_ms, "per": per, "tau": tau, "parts": parts, "timing": timing,
+                "roofline": roofline_of(timing, batch, peak, fp64_peak, prec), "clocks": clk_summary}
+
+    # ---- headline: scenario A (no kernel timing) for value and latency; B, a copy of A's state at the window's
+    # start, for the per-kernel events of the roofline; C, another copy, end to end through host buffers
     head_code, head_dtype = PRECISIONS[args.precision]
-    res, tau, s = run_precision(seas, torch, wr, head_code, Vd, K, W, dist, device, stream, peak)
+    s = session(head_code)
+    t0 = time.perf_counter()
+    advance(seas, torch, s.scn, Vd, 0, start, device)
+    log(f"advance {start} steps: {time.perf_counter() - t0:.1f} s")
+    ckpt_dir = tempfile.mkdtemp(prefix="seas_bench_")
+    ckpt = os.path.join(ckpt_dir, "window_start.ckpt")
+    seas.seas_scenario_save(s.scn, ckpt)
+    with Clocks(local) as clk:
+        total_ms, per, tau, parts = timed_run(seas, torch, s.scn, Vd, start, K, dist, device)
+    clocks = clk.summary()
+    seas.seas_scenario_check(s.scn)
+    total_ms = max_over_ranks(dist, total_ms, device)
+    value = job_rate(w.N * K, world, total_ms / 1e3)
+    err_tau = tau_err(tau)
+    err_int = int_err(parts)
+    log(f"headline {value / 1e6:.3f} M element-steps/s, p50 {np.percentile(per, 50):.3f} ms")
+
+    sB = seas.seas_scenario_load(s.op, ckpt)
+    seas.seas_scenario_set_timing(sB, True)
+    _, perB, tauB, _ = timed_run(seas, torch, sB, Vd, start, K, dist, device)
+    seas.seas_scenario_check(sB)
+    timing = seas.seas_scenario_get_timing(sB)
+    seas.seas_destroy_scn(sB)
+    roofline = roofline_of(timing, 1, peak, fp64_peak, head_code)
+    roofline["timed_with"] = ("per-kernel CUDA events on the library's stream over the same step window, in a "
+                              "copy of the scenario taken at the window's start (the headline run records none)")
+    if not torch.equal(tauB, tau):
+        log("warning: kernel-timing pass differs from the headline run")
     if args.dump_step_bytes and rank == 0:
-        # algorithmic interaction bytes of every step, to match profiled launches to steps
         with open(args.dump_step_bytes, "w") as fh:
-            json.dump({"precision": args.precision, "steps": K,
-                       "bytes": [seas.seas_op_step_bytes(s.op, n) for n in range(K)]}, fh)
-    value = job_rate(wr.N * K, world, res["total_ms"] / 1e3)
-    err = err_of(tau)
-    stats = res["stats"]
+            json.dump({"precision": args.precision, "steps": w.steps,
+                       "bytes": [seas.seas_op_step_bytes(s.op, n) for n in range(w.steps)]}, fh)
+    window_bytes = float(np.mean([seas.seas_op_step_bytes(s.op, n) for n in range(start, start + K)]))
+
+    e2e = None
+    if not args.no_e2e:
+        sC = seas.seas_scenario_load(s.op, ckpt)
+        Vh = torch.from_numpy(V).pin_memory().numpy()
+        th = torch.zeros(w.N, dtype=torch.float64).pin_memory().numpy()
+        barrier(dist)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        for k in range(K):
+            seas.seas_push_slip_rate(sC, Vh[start + k])
+            seas.seas_stress_step(sC, th)
+        torch.cuda.synchronize(device)
+        barrier(dist)
+        e2e_s = max_over_ranks(dist, time.perf_counter() - t0, device)
+        seas.seas_destroy_scn(sC)
+        e2e = {"value": w.N * K * world / e2e_s, "unit": METRIC, "h2d_bytes_per_step": w.N * 8,
+               "d2h_bytes_per_step": w.N * 8, "last_step_equal": bool(np.array_equal(th, tau[-1].cpu().numpy()))}
+    os.unlink(ckpt)
+    os.rmdir(ckpt_dir)
 
     variants = {}
     if not args.no_variants:
         for name, (code, dtype) in PRECISIONS.items():
             if name == args.precision:
                 continue
-            r2, tau2, s2 = run_precision(seas, torch, wr, code, Vd, K, W, dist, device, stream, peak)
-            variants[name] = {"value": wr.N * K * world / (r2["total_ms"] / 1e3), "unit": METRIC, "dtype": dtype,
-                              "ms_per_step": r2["total_ms"] / K, "p50_ms": float(np.percentile(r2["per"], 50)),
-                              "p99_ms": float(np.percentile(r2["per"], 99)), "rel_l2_vs_oracle": err_of(tau2),
-                              "rel_l2_vs_headline": (tau2 - tau).norm().item() / tau.norm().item(),
-                              "bytes_interaction": r2["stats"]["bytes_interaction"],
+            s2 = session(code)
+            r2 = measure(s2, Vd, 1, code)
+            variants[name] = {"value": job_rate(w.N * K, world, r2["total_ms"] / 1e3), "unit": METRIC,
+                              "dtype": dtype, "ms_per_step": r2["total_ms"] / K,
+                              "p50_ms": float(np.percentile(r2["per"], 50)),
+                              "p99_ms": float(np.percentile(r2["per"], 99)),
+                              "rel_l2_interaction_vs_oracle": int_err(r2["parts"]),
+                              "rel_l2_tau_vs_oracle": tau_err(r2["tau"]),
+                              "rel_l2_interaction_vs_headline": rel(r2["parts"][2].cpu().numpy(),
+                                                                    parts[2].cpu().numpy()),
+                              "rel_l2_tau_vs_headline": rel(r2["tau"].cpu().numpy(), tau.cpu().numpy()),
+                              "bytes_interaction": s2.stats["bytes_interaction"],
                               "roofline": {k: r2["roofline"][k] for k in (
                                   "bound", "achieved", "peak", "unit", "frac", "mean_launch_ms")}}
             s2.close()
+            del r2
 
     # batched ensemble: 8 scenarios (independent seeded histories, scenario 0 = the headline's) share one operator;
     # one persistent interaction kernel per step serves all 8 with each operator byte read once
     batched = {}
     if not args.no_batched:
         B = 8
-        V8 = np.stack([wr.slip_rate(b, 0, K) for b in range(B)], axis=1).reshape(K, B * wr.N)
+        V8 = np.stack([w.slip_rate(b, 0, w.steps) for b in range(B)], axis=1).reshape(w.steps, B * w.N)
         V8d = torch.from_numpy(V8).to(device)
         del V8
         for name in ("bf16", "fp64"):
             code, dtype = PRECISIONS[name]
-            r3, tau3, s3 = run_precision(seas, torch, wr, code, V8d, K, W, dist, device, stream, peak, batch=B)
-            t0 = tau3[:, : wr.N]
-            batched[name] = {"value": B * wr.N * K * world / (r3["total_ms"] / 1e3), "unit": METRIC, "batch": B,
-                             "dtype": dtype, "ms_per_step": r3["total_ms"] / K,
+            s3 = session(code, batch=B)
+            r3 = measure(s3, V8d, B, code)
+            t0 = r3["tau"][:, : w.N]
+            batched[name] = {"value": job_rate(B * w.N * K, world, r3["total_ms"] / 1e3), "unit": METRIC,
+                             "batch": B, "dtype": dtype, "ms_per_step": r3["total_ms"] / K,
                              "p50_ms": float(np.percentile(r3["per"], 50)),
                              "p99_ms": float(np.percentile(r3["per"], 99)),
-                             "rel_l2_member0_vs_headline": (t0 - tau).norm().item() / tau.norm().item(),
+                             "rel_l2_member0_interaction_vs_oracle": int_err(r3["parts"], 0),
+                             "rel_l2_member0_tau_vs_headline": rel(t0.cpu().numpy(), tau.cpu().numpy()),
                              "roofline": {k: r3["roofline"][k] for k in (
                                  "bound", "achieved", "peak", "unit", "frac", "mean_launch_ms")}}
             s3.close()
-            del tau3
+            del r3
         del V8d
 
     # the flagged static tail (elastostatic response of the history the windows drop) on the headline operator
     tail = None
     if not args.no_tail:
-        r4, tau4, s4 = run_precision(seas, torch, wr, head_code, Vd, K, W, dist, device, stream, peak,
-                                     flags=int(wr.hparams.get("flags", 0)) | seas.SEAS_FLAG_STATIC_TAIL)
-        tv = job_rate(wr.N * K, world, r4["total_ms"] / 1e3)
+        s4 = session(head_code, flags=int(w.hparams.get("flags", 0)) | seas.SEAS_FLAG_STATIC_TAIL)
+        r4 = measure(s4, Vd, 1, head_code)
+        tv = job_rate(w.N * K, world, r4["total_ms"] / 1e3)
         tail = {"value": tv, "unit": METRIC, "ms_per_step": r4["total_ms"] / K, "cost_vs_headline": value / tv - 1,
-                "tail_share_of_tau": (tau4 - tau).norm().item() / tau.norm().item()}
+                "tail_share_of_tau": rel(r4["tau"].cpu().numpy(), tau.cpu().numpy())}
         s4.close()
-        del tau4
+        del r4
 
     # plain FP64 GPU path: every block dense (leaf blocks, exact windows), no compression, FP64 arithmetic
     plain = None
     if not args.no_plain:
-        p = seas.Session(wr, device=local, stream=stream.cuda_stream, flags=seas.SEAS_FLAG_DENSE)
-        pm, pper, ptau = timed_run(seas, torch, p, Vd, K, dist, device)
-        seas.seas_scenario_check(p.scn)
-        pm = max_over_ranks(dist, pm, device)
-        pv = wr.N * K * world / (pm / 1e3)
-        plain = {"value": pv, "unit": METRIC, "ms_per_step": pm / K, "p50_ms": float(np.percentile(pper, 50)),
-                 "p99_ms": float(np.percentile(pper, 99)), "speedup": value / pv,
-                 "bytes_interaction": p.stats["bytes_interaction"], "rel_l2_vs_oracle": err_of(ptau),
-                 "rel_l2_tau_vs_headline": (ptau - tau).norm().item() / ptau.norm().item()}
+        p = session(0, flags=seas.SEAS_FLAG_DENSE)
+        rp = measure(p, Vd, 1, 0)
+        pv = job_rate(w.N * K, world, rp["total_ms"] / 1e3)
+        plain = {"value": pv, "unit": METRIC, "ms_per_step": rp["total_ms"] / K,
+                 "p50_ms": float(np.percentile(rp["per"], 50)), "p99_ms": float(np.percentile(rp["per"], 99)),
+                 "speedup": value / pv, "bytes_interaction": p.stats["bytes_interaction"],
+                 "rel_l2_interaction_vs_oracle": int_err(rp["parts"]), "rel_l2_tau_vs_oracle": tau_err(rp["tau"]),
+                 "rel_l2_tau_vs_headline": rel(tau.cpu().numpy(), rp["tau"].cpu().numpy())}
         p.close()
+        del rp
 
-    # end to end through the C ABI with host buffers (copies inside the timed region)
-    e2e = None
-    if not args.no_e2e:
-        s2 = seas.seas_scenario_create(s.op, 1)
-        Vh = torch.from_numpy(V).pin_memory().numpy()
-        th = torch.zeros(wr.N, dtype=torch.float64).pin_memory().numpy()
-        barrier(dist)
-        torch.cuda.synchronize(device)
-        t0 = time.perf_counter()
-        for n in range(K):
-            seas.seas_push_slip_rate(s2, Vh[n])
-            seas.seas_stress_step(s2, th)
-        torch.cuda.synchronize(device)
-        barrier(dist)
-        e2e_s = max_over_ranks(dist, time.perf_counter() - t0, device)
-        seas.seas_destroy_scn(s2)
-        e2e = {"value": wr.N * K * world / e2e_s, "unit": METRIC, "h2d_bytes_per_step": wr.N * 8,
-               "d2h_bytes_per_step": wr.N * 8}
-
-    roofline = res["roofline"]
     roofline["traffic"] = None
     tf = os.path.join(ROOT, "profiles", "interaction_traffic.json")
     if os.path.exists(tf):
@@ -444,29 +541,33 @@ def run_ours(args, w, K, W):
             tr = json.load(fh)
         ratio = tr.get("dram_over_algorithmic", {}).get(args.precision)
         if tr.get("kernel_version") == seas_kernel_version() and ratio is not None:
-            # DRAM bytes of the captured launch over its algorithmic bytes, scaled to this run's mean launch
+            # DRAM bytes of the captured launch over its algorithmic bytes, scaled to this window's mean launch
             roofline["traffic"] = ratio * roofline["algorithmic_bytes_per_launch"]
-            roofline["traffic_source"] = tr.get("source")
 
     line = None
     if rank == 0:
         cpu = None
         if oracle is not None:
             cpu = {"value": args.cpu_sample / oracle[3], "unit": METRIC, "cores": 1, "kind": "oracle",
-                   "sample": f"{args.cpu_sample} element-steps (receivers of fault 0 at steps spread over the run, "
-                             f"all lags of all sources, NumPy FP64), {oracle[3]:.1f} s"}
-        launches = res["timing"]["launches"]
+                   "sample": f"{args.cpu_sample} element-steps (receivers of fault 0 at steps spread over the timed "
+                             f"window [{start}, {start + K}), all lags of all sources within the windows, NumPy "
+                             f"FP64, one thread), {oracle[3]:.1f} s"}
+        launches = timing["launches"]
+        stats = s.stats
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": W,
-                "ms_per_step": res["total_ms"] / K, "p50_ms": float(np.percentile(res["per"], 50)),
-                "p99_ms": float(np.percentile(res["per"], 99)), "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": total_ms / K, "p50_ms": float(np.percentile(per, 50)),
+                "p99_ms": float(np.percentile(per, 99)), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": head_dtype, "data": "synthetic",
-                "config": dict(config_of(wr, K), precision=args.precision),
-                "rel_l2_vs_oracle": err, "operator": {k: stats[k] for k in (
+                "config": dict(config_of(w, start, K), precision=args.precision,
+                               window_algorithmic_bytes_per_step=window_bytes),
+                "rel_l2_tau_vs_oracle": err_tau, "rel_l2_interaction_vs_oracle": err_int,
+                "oracle_rows": {"interaction": [int(r) for r in rows], "step": w.steps - 1},
+                "operator": {k: stats[k] for k in (
                     "n_blocks_far", "n_blocks_near", "compression_ratio", "bytes_interaction", "mean_rank",
                     "max_rank", "build_seconds", "n_tasks")},
                 "vs_plain_fp64_gpu": plain, "variants": variants, "batched": batched, "static_tail": tail, "e2e": e2e,
-                "roofline": roofline,
-                "cpu_baseline": cpu, "clocks": res["clocks"], "gpu_launches": int(sum(launches.values()))}
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": int(sum(launches.values()))}
     s.close()
     if dist is not None:
         dist.destroy_process_group()
@@ -494,14 +595,14 @@ def seas_kernel_version():
 def main():
     args = parse()
     w = synth.WORKLOADS[args.workload]()
-    K = args.steps if args.steps is not None else w.steps
+    start, K = window(w, args.steps)
     W = max(3, args.warmup)
     if args.impl == "reference":
-        line = run_reference(args, w, K, W)
+        line = run_reference(args, w, start, K, W)
     else:
         from paper_2603_00383_gb300 import build
         build.build()
-        line = run_ours(args, w, K, W)
+        line = run_ours(args, w, start, K, W)
     if line is not None:
         print(json.dumps(line))
 

@@ -187,6 +187,18 @@ seas_status seas_stress_step(seas_scn *scn, double *tau, double *sigma_n, double
  * race on it. */
 seas_status seas_stress_step_static(seas_scn *scn, double *tau, double *parts);
 
+/* Watchdog of the scenario's device waits (the interaction kernel's producer/consumer hand-offs).  Every wait is
+ * bounded by `seconds` of wall time (default 2 s; accepted range [1e-6, 60]); a wait that runs out sets the
+ * scenario's device error word, which is sticky: seas_scenario_check and host-output seas_stress_step then return
+ * SEAS_ETIMEOUT, and later interaction launches of the scenario return at once.  The context stays usable (other
+ * scenarios are unaffected).  No counterpart in the paper. */
+seas_status seas_scenario_set_wait_limit(seas_scn *scn, double seconds);
+/* Launches one thread that waits, with the scenario's bound, on a device barrier nothing arrives on, so the wait
+ * runs out and takes the same path as a stalled pipeline (error word set, SEAS_ETIMEOUT reported by the next
+ * seas_scenario_check).  For testing the watchdog on a live context: no copy is in flight and no other thread is
+ * involved.  No counterpart in the paper. */
+seas_status seas_scenario_probe_wait(seas_scn *scn);
+
 /* Number of pushes so far. */
 seas_status seas_scenario_step(const seas_scn *scn, int64_t *n);
 
@@ -211,7 +223,8 @@ seas_status seas_plan_hmatrix(const seas_fault *faults, int n_faults, const seas
  * around every kernel the scenario launches; get_timing synchronises and returns, per kernel class (0 push,
  * 1 forward FFT, 2 mode convolution, 3 interaction, 4 interaction reduction (with the static tail when that flag
  * is set), 5 inverse FFT + assembly), the launch count and the summed device time, plus the algorithmic bytes the
- * interaction kernel streamed (seas_op_step_bytes summed over the timed steps). */
+ * interaction kernel streamed (seas_op_step_bytes summed over the timed steps).  The first set_timing(1) of a
+ * scenario creates its events (8192 pairs), so that timed steps pay only for the event records. */
 typedef struct {
     int64_t launches[6];
     double ms[6];
@@ -223,6 +236,11 @@ seas_status seas_scenario_get_timing(seas_scn *scn, seas_timing *out);
 /* Algorithmic interaction-operator bytes of step `step`: the values of every stored slice with lag <= step
  * (p q near, k (p + q) far) times the storage element size; the 16-byte row padding is not counted. */
 seas_status seas_op_step_bytes(const seas_op *op, int64_t step, int64_t *bytes);
+
+/* Device probe (no counterpart in the paper; used for roofline reporting): the FP64 fused multiply-add rate of GPU
+ * `device` in FMA/s, measured by a kernel of independent FMA chains on every SM (best of three ~30 ms launches).
+ * Allocates and frees a few bytes; SEAS_EINVAL for a bad device, SEAS_ECUDA on a CUDA error. */
+seas_status seas_measure_fp64_peak(int device, double *fma_per_second);
 
 /* Checkpoint/resume of a scenario: the step counter, slip-rate ring, slip and spectral ring (and the slip ring of
  * the static tail when that flag is set). */

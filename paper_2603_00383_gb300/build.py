@@ -2,7 +2,7 @@
 
     python -m paper_2603_00383_gb300.build [--force]
 
-Three translation units are compiled in parallel and linked into paper_2603_00383_gb300/libseas.so; the build is
+The translation units are compiled in parallel and linked into paper_2603_00383_gb300/libseas.so; the build is
 skipped when the library is newer than every source and header.
 """
 from __future__ import annotations
@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libseas.so")
-SOURCES = ["seas_api.cu", "seas_build.cu", "seas_step.cu"]
+SOURCES = ["seas_api.cu", "seas_build.cu", "seas_step.cu", "seas_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -214,6 +214,7 @@ struct seas_scn {
     DArr<unsigned char> xring;       // history in the operator's arithmetic (DF64: float2, BF16/FP16: float)
     DArr<double2> dring, fmodes;
     DArr<int> counter_err;           // [0]: interaction task counter, [1]: device error word
+    uint64_t wait_ns = 2000000000ull;   // bound of one device wait (seas_scenario_set_wait_limit)
     int64_t ring_stride = 0;
     DArr<FaultDev> faults;           // fault table with spectral-ring offsets for this batch size
     int64_t dring_len = 0;
@@ -1135,6 +1136,7 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     a.n_partial = op.n_partial;
     a.counter = s.counter_err.p;
     a.err = s.counter_err.p + 1;
+    a.wait_ns = s.wait_ns;
     a.cover_ptr = op.d_cover_ptr.p;
     a.cover_blk = op.d_cover_blk.p;
     a.blk_task_ptr = op.d_blk_task_ptr.p;
@@ -1258,11 +1260,6 @@ seas_status timed(seas_scn &s, int cls, F &&launch) {
         CUDA_TRY(launch());
         return SEAS_OK;
     }
-    if (s.ev.empty()) {
-        s.ev.resize(2 * kEventPairs);
-        s.ev_class.resize(kEventPairs);
-        for (cudaEvent_t &e : s.ev) CUDA_TRY(cudaEventCreate(&e));
-    }
     if (s.ev_used == kEventPairs) SEAS_TRY(timing_resolve(s));
     CUDA_TRY(cudaEventRecord(s.ev[2 * s.ev_used], st));
     CUDA_TRY(launch());
@@ -1280,6 +1277,12 @@ extern "C" seas_status seas_scenario_set_timing(seas_scn *s, int enable) {
     s->ev_used = 0;
     s->acc = seas_timing{};
     s->timing = enable != 0;
+    if (s->timing && s->ev.empty()) {
+        // events are created here, not by the first timed launch, so that timing adds no creation cost to a step
+        s->ev.resize(2 * kEventPairs);
+        s->ev_class.resize(kEventPairs);
+        for (cudaEvent_t &e : s->ev) CUDA_TRY(cudaEventCreate(&e));
+    }
     return SEAS_OK;
 }
 
@@ -1400,6 +1403,23 @@ extern "C" seas_status seas_stress_step_static(seas_scn *s, double *tau, double 
     CUDA_TRY(launch_reduce(a, c->stream));
     CUDA_TRY(launch_static_tail(a, c->stream));
     CUDA_TRY(launch_ifft_assemble(a, tau, parts, c->stream));
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_scenario_set_wait_limit(seas_scn *s, double seconds) {
+    if (!s) return fail(SEAS_EINVAL, "NULL scenario");
+    if (!(std::isfinite(seconds) && seconds >= 1e-6 && seconds <= 60.0))
+        return fail(SEAS_EINVAL, "wait limit %g s outside [1e-6, 60]", seconds);
+    s->wait_ns = (uint64_t)(seconds * 1e9);
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_scenario_probe_wait(seas_scn *s) {
+    if (!s) return fail(SEAS_EINVAL, "NULL scenario");
+    seas_ctx *c = s->op->net->ctx;
+    CUDA_TRY(cudaSetDevice(c->device));
+    const StepArgs a = step_args(*s, s->n > 0 ? s->n - 1 : 0);
+    CUDA_TRY(launch_wait_probe(a, c->stream));
     return SEAS_OK;
 }
 

@@ -156,6 +156,7 @@ struct StepArgs {
     int64_t n_partial;
     int *counter;                 // dynamic task counter (reset by the reduction)
     int *err;                     // device error word (bounded waits that ran out)
+    uint64_t wait_ns;             // bound of one device wait (wall clock), per scenario
     // reduction: per element the blocks it receives from; per block its tasks' first lags
     const int32_t *cover_ptr, *cover_blk;
     const int32_t *blk_task_ptr, *blk_task_T;
@@ -182,5 +183,6 @@ cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_reduce(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_static_tail(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_ifft_assemble(const StepArgs &a, double *tau, double *parts, cudaStream_t s);
+cudaError_t launch_wait_probe(const StepArgs &a, cudaStream_t s);
 
 }  // namespace seas

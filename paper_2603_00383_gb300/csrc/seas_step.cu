@@ -271,7 +271,6 @@ template <int BT> struct InterShape {
     static constexpr int NT = NC + 32;
     static constexpr int RV = CW == 8 ? 8 : 4;
 };
-constexpr uint64_t kWaitNs = 2000000000ull;   // bound of one mbarrier wait
 constexpr int kMaxStageRanks = 192;     // rank-1 terms of all low-rank items of one stage (z buffer), B <= 4
 constexpr int kMaxStageRanks8 = 96;     // the same for batches of 5..8 (the z buffers are double-buffered)
 
@@ -352,14 +351,15 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Bounded wait (about 2 s of wall time, and at most 2^30 polls); false, with the error word set, if the phase
-// never completes.  Called by one thread per role, which then shares the outcome, so an abort is uniform.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+// Bounded wait (limit_ns of wall time, 2 s unless the scenario sets another, and at most 2^30 polls); false, with
+// the error word set, if the phase never completes.  Called by one thread per role, which then shares the outcome,
+// so an abort is uniform.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 0; i < (1u << 30); ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63) == 0 && global_ns() - t0 > kWaitNs) break;
+        if ((i & 63) == 0 && global_ns() - t0 > limit_ns) break;
     }
     atomicExch(err, 1);
     return false;
@@ -719,14 +719,14 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
         acc[v] = make_float2(0.f, 0.f);
         dst[v] = 0.f;
     }
-    if (t == 0) *sh_flag = mbar_wait(&full[0], 0, a.err) ? 0 : 1;
+    if (t == 0) *sh_flag = mbar_wait(&full[0], 0, a.err, a.wait_ns) ? 0 : 1;
     consumer_sync<NC>();
     if (*sh_flag) return;
     if (info[0].task >= 0) phase_a(info[0], stage_mem, zs);
     for (int gi = 0;; ++gi) {
         const int slot = gi % kStages;
         if (t == 0 && info[slot].task >= 0)
-            *sh_flag = mbar_wait(&full[(gi + 1) % kStages], ((gi + 1) / kStages) & 1, a.err) ? 0 : 1;
+            *sh_flag = mbar_wait(&full[(gi + 1) % kStages], ((gi + 1) / kStages) & 1, a.err, a.wait_ns) ? 0 : 1;
         consumer_sync<NC>();
         if (*sh_flag) return;
         if (t == 0 && gi > 0) mbar_arrive(&empty[(gi - 1) % kStages]);
@@ -869,7 +869,7 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
             const int slot = g % kStages;
             if (g >= kStages) {
                 int ok = 1;
-                if (lane == 0) ok = mbar_wait(&empty[slot], ((g / kStages) - 1) & 1, a.err);
+                if (lane == 0) ok = mbar_wait(&empty[slot], ((g / kStages) - 1) & 1, a.err, a.wait_ns);
                 if (!__shfl_sync(0xffffffffu, ok, 0)) return;
             }
             if (it >= ie) {                        // next task
@@ -1104,14 +1104,14 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
     // (z into buffer (g + 1) & 1) and phase B of stage g (z from buffer g & 1), so one barrier per stage
     // separates every producer of z from its readers and the pipe never drains between the phases.  Stage g - 1
     // is handed back to the producer at the barrier that opens interval g.
-    if (t == 0) sh_flag = mbar_wait(&full[0], 0, a.err) ? 0 : 1;
+    if (t == 0) sh_flag = mbar_wait(&full[0], 0, a.err, a.wait_ns) ? 0 : 1;
     consumer_sync<NC>();
     if (sh_flag) return;
     if (info[0].task >= 0) phase_a(info[0], stage_mem, zs);
     for (int g = 0;; ++g) {
         const int slot = g % kStages;
         if (t == 0 && info[slot].task >= 0)
-            sh_flag = mbar_wait(&full[(g + 1) % kStages], ((g + 1) / kStages) & 1, a.err) ? 0 : 1;
+            sh_flag = mbar_wait(&full[(g + 1) % kStages], ((g + 1) / kStages) & 1, a.err, a.wait_ns) ? 0 : 1;
         consumer_sync<NC>();
         if (sh_flag) return;
         if (t == 0 && g > 0) mbar_arrive(&empty[(g - 1) % kStages]);
@@ -1418,6 +1418,18 @@ __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
     }
 }
 
+// Watchdog check: one thread waits, with the scenario's bound, on an mbarrier that no thread arrives on.  The wait
+// runs out and sets the scenario's error word exactly as a stalled interaction pipeline would, without any copy in
+// flight or any other thread involved, so the timeout path can be exercised on a live context.
+__global__ void k_wait_probe(StepArgs a) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(&bar, 0, a.err, a.wait_ns);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+}
+
 template <int PREC, int BT>
 cudaError_t launch_interaction_bt(const StepArgs &a, cudaStream_t s) {
     const size_t smem = InterLayout<BT>::total;
@@ -1496,6 +1508,11 @@ cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s) {
         case kPrecFP16: return launch_interaction_prec<kPrecFP16>(a, s);
         default: return launch_interaction_prec<kPrecFP64>(a, s);
     }
+}
+
+cudaError_t launch_wait_probe(const StepArgs &a, cudaStream_t s) {
+    k_wait_probe<<<1, 32, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const StepArgs &a, cudaStream_t s) {

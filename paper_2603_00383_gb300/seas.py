@@ -26,7 +26,8 @@ EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_
             "seas_stress_step", "seas_scenario_step", "seas_sync", "seas_strerror", "seas_last_error",
             "seas_scenario_save", "seas_scenario_load", "seas_destroy_scn", "seas_destroy_op", "seas_destroy_net",
             "seas_destroy_ctx", "seas_plan_hmatrix", "seas_scenario_set_timing", "seas_scenario_get_timing",
-            "seas_op_step_bytes", "seas_scenario_check", "seas_stress_step_static"]
+            "seas_op_step_bytes", "seas_scenario_check", "seas_stress_step_static",
+            "seas_measure_fp64_peak", "seas_scenario_set_wait_limit", "seas_scenario_probe_wait"]
 
 
 class SeasError(RuntimeError):
@@ -99,6 +100,9 @@ _SIGS = {
     "seas_op_step_bytes": ([_VP, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
     "seas_scenario_check": ([_VP], C.c_int),
     "seas_stress_step_static": ([_VP, _VP, _VP], C.c_int),
+    "seas_measure_fp64_peak": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
+    "seas_scenario_set_wait_limit": ([_VP, C.c_double], C.c_int),
+    "seas_scenario_probe_wait": ([_VP], C.c_int),
 }
 
 
@@ -331,6 +335,21 @@ def seas_op_step_bytes(op: Handle, step: int) -> int:
     b = C.c_int64()
     _check(lib().seas_op_step_bytes(op.ptr, step, C.byref(b)))
     return b.value
+
+
+def seas_measure_fp64_peak(device: int = 0) -> float:
+    """FP64 FMA/s of the GPU, measured by the library's probe kernel."""
+    r = C.c_double()
+    _check(lib().seas_measure_fp64_peak(device, C.byref(r)))
+    return r.value
+
+
+def seas_scenario_set_wait_limit(scn: Handle, seconds: float):
+    _check(lib().seas_scenario_set_wait_limit(scn.ptr, float(seconds)))
+
+
+def seas_scenario_probe_wait(scn: Handle):
+    _check(lib().seas_scenario_probe_wait(scn.ptr))
 
 
 def seas_scenario_check(scn: Handle):

@@ -16,7 +16,7 @@ def declared_symbols():
     with open(os.path.join(ROOT, "include", "seas.h")) as fh:
         text = fh.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(seas_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(seas_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_library_exports_every_declared_symbol():

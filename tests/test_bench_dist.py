@@ -28,7 +28,7 @@ def _rank_main(rank, world, port, q):
         dist, r, w, local = bench.dist_setup(None)
         bench.barrier(dist)
         slowest = bench.max_over_ranks(dist, 1.5 + r, "cpu")        # rank r "took" 1.5 + r seconds
-        ref = bench.run_reference(None, synth.two_fault_128(), 4, 3) if r != 0 else "skipped"
+        ref = bench.run_reference(None, synth.two_fault_128(), 396, 4, 3) if r != 0 else "skipped"
         q.put((r, w, local, slowest, bench.rank_seed(r), ref))
         dist.destroy_process_group()
     except Exception as e:                                        # report instead of hanging the parent
@@ -54,3 +54,18 @@ def test_two_gloo_ranks_share_only_the_barrier_and_the_max_time():
     assert out[0][4] != out[1][4]                                # independent scenarios
     assert out[1][5] is None                                     # the oracle arm does no work off rank 0
     assert bench.job_rate(3072 * 2000, 2, 2.5) == pytest.approx(2 * 3072 * 2000 / 2.5)
+
+
+def test_timed_window_is_the_deepest_steps_whatever_k_is():
+    """The bench always runs the workload for its full length and times its K deepest steps."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2603_00383_gb300 import synth
+    w = synth.six_fault_3072()
+    assert bench.window(w, 20) == (1980, 20)
+    assert bench.window(w, 5000) == (0, 2000)
+    elems, steps = bench.oracle_sample(w, 1980, 20, 48)
+    assert steps.min() >= 1980 and steps.max() < 2000 and elems.max() < 256
+    rows = bench.oracle_rows(w)
+    off = [0, 256, 640, 1152, 1664, 2304, 3072]
+    assert all(any(off[f] <= r < off[f + 1] for r in rows) for f in range(6))

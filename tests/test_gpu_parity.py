@@ -94,50 +94,73 @@ def test_two_fault_128_hmatrix_error_within_aca_tolerance(two_fault_oracle):
     assert e_int <= 1e-5
 
 
-def test_six_fault_3072_full_size_sampled_rows():
-    """The paper-scale network at full size (3072 elements, 2000 steps, H-matrix leaf 32 / eta 2 / ACA 1e-6, causal
-    and spectral windows), run as the bench runs it (device-resident inputs), checked on sampled rows and steps
-    against the oracle evaluated one row at a time with the same windows."""
-    torch = pytest.importorskip("torch")
-    w = synth.six_fault_3072()
-    net = O.network(w.faults, w.mu, w.cs)
-    V = w.slip_rate(0, 0, w.steps)
-    hp = w.hparams
-    check_steps = [401, 1999]
-    rng = np.random.default_rng(7)
-    rows = np.sort(rng.choice(net.N, 6, replace=False))
-    rows0 = np.arange(0, 256, 51)                    # rows of fault 0 for the self term
+SIX_STEPS = (401, 1597, 1598, 1999)
+
+
+def six_fault_golden():
+    """Stored oracle values of the six-fault workload (tests/golden/make_six_fault_3072.py): {(part, step): (rows,
+    values)} for part "int" (64 receivers over all faults) and "self" (8 receivers of every fault)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "six_fault_3072_oracle.txt")
     out = {}
-    with seas.Session(w) as s:
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            part, n, r, v = line.split()
+            out.setdefault((part, int(n)), []).append((int(r), float(v)))
+    return {k: (np.array([r for r, _ in v]), np.array([x for _, x in v])) for k, v in out.items()}
+
+
+def run_six_fault(torch, w, steps, **hp):
+    """Runs the six-fault workload as the bench runs it (device-resident inputs, one scenario); returns the pair
+    windows, the operator stats and, for each step in ``steps``, tau and the parts [3][N]."""
+    V = w.slip_rate(0, 0, w.steps)
+    out = {}
+    with seas.Session(w, **hp) as s:
         Vd = torch.from_numpy(V).cuda()
-        tau = torch.zeros(net.N, dtype=torch.float64, device="cuda")
-        parts = torch.zeros(3 * net.N, dtype=torch.float64, device="cuda")
+        tau = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+        parts = torch.zeros(3 * w.N, dtype=torch.float64, device="cuda")
         wins = seas.seas_op_pair_windows(s.op)
         for n in range(w.steps):
             seas.seas_push_slip_rate(s.scn, Vd[n])
-            seas.seas_stress_step(s.scn, tau, parts=parts)
-            if n in check_steps:
+            seas.seas_stress_step(s.scn, tau, parts=parts if n in steps else None)
+            if n in steps:
                 seas.seas_scenario_check(s.scn)
-                out[n] = (tau.cpu().numpy().copy(), parts.cpu().numpy().reshape(3, net.N).copy())
+                out[n] = (tau.cpu().numpy().copy(), parts.cpu().numpy().reshape(3, w.N).copy())
         stats = s.stats
+    return V, wins, stats, out
+
+
+def test_six_fault_3072_full_size_sampled_rows():
+    """The paper-scale network at full size (3072 elements on faults of 256..768 elements, 2000 steps, H-matrix
+    leaf 32 / eta 2 / ACA 1e-6, causal and spectral windows), run as the bench runs it, against stored oracle values
+    with the same windows: the self part on 8 receivers of every fault (radix-2, 3 and 5 transforms), the
+    interaction on 64 receivers spread over all faults, at steps 401, 1597, 1598 (just past the shortest pair
+    window) and 1999; the radiation part exactly."""
+    torch = pytest.importorskip("torch")
+    w = synth.six_fault_3072()
+    net = O.network(w.faults, w.mu, w.cs)
+    hp = w.hparams
+    gold = six_fault_golden()
+    V, wins, stats, out = run_six_fault(torch, w, SIX_STEPS)
     _, _, last = O.pair_windows(net, hp["eta_tmin"], hp["eta_tmax"], hp["max_steps"])
     np.testing.assert_array_equal(wins, last)
-    W0 = O.mode_windows(256, net.length[0], net.dt, net.cs, hp["eta_w"], hp["q_w"], hp["max_steps"])
-    tab0 = O.SelfTables(256, net.length[0], net.dt, net.cs, W0)
-    delta = O.slip_from_rate(V, net.dt)
-    for n in check_steps:
+    assert last[last >= 0].min() == 1597
+    for n in SIX_STEPS:
         t_gpu, p_gpu = out[n]
-        f_int = O.interaction_rows(net, V, n, rows, pair_hi=last)
-        f_int_untrunc = O.interaction_rows(net, V, n, rows)
-        f_self = O.self_rows(net, 0, delta[: n + 1, :256], n, tab0, rows0)
-        e_int = rel(p_gpu[2, rows], f_int)
-        e_trunc = rel(f_int, f_int_untrunc)
-        e_self = rel(p_gpu[1, rows0], f_self)
-        print(f"six_fault_3072 step {n}: compression {stats['compression_ratio']:.1f}%, rel int {e_int:.2e} "
-              f"(truncation vs untruncated {e_trunc:.2e}), rel self {e_self:.2e}")
-        assert e_self <= EXACT
+        ri, fi = gold[("int", n)]
+        rs, fs = gold[("self", n)]
+        assert len(ri) >= 64 and len(rs) >= 48
+        assert set(net.fault_of[ri]) == set(range(6)) and set(net.fault_of[rs]) == set(range(6))
+        e_int = rel(p_gpu[2, ri], fi)
+        e_self = rel(p_gpu[1, rs], fs)
+        e_self_f = [rel(p_gpu[1, rs[net.fault_of[rs] == f]], fs[net.fault_of[rs] == f]) for f in range(6)]
+        print(f"six_fault_3072 step {n}: compression {stats['compression_ratio']:.1f}%, rel int {e_int:.2e}, "
+              f"rel self {e_self:.2e} (per fault max {max(e_self_f):.2e})")
+        assert max(e_self_f) <= EXACT
         assert e_int <= 1e-5
         np.testing.assert_array_equal(p_gpu[0], -(w.mu / (2 * w.cs)) * V[n])
+        np.testing.assert_allclose(p_gpu.sum(0), t_gpu, rtol=1e-14, atol=1e-14 * np.abs(t_gpu).max())
 
 
 def test_batch_members_are_independent():
@@ -278,7 +301,10 @@ def test_linearity_at_full_size():
 
 # ---------------------------------------------------------------- storage precisions --------------------------------
 
-MP_BOUND = {seas.SEAS_PREC_BF16: 2e-2, seas.SEAS_PREC_FP16S: 2e-3}
+# Interaction rel-L2 bounds of the reduced storage precisions: about three times the measured error on the two-fault
+# network (BF16 1.3e-3, FP16 with per-slice scale 1.6e-4), which the storage rounding (2^-9, 2^-12 per entry) over
+# sums of 1e4..1e5 terms explains.
+MP_BOUND = {seas.SEAS_PREC_BF16: 5e-3, seas.SEAS_PREC_FP16S: 5e-4}
 
 
 @pytest.mark.parametrize("seed", [1, 3])
@@ -311,30 +337,23 @@ def test_two_fault_128_storage_precisions(two_fault_oracle, prec):
     assert e[2] <= (EXACT if prec == seas.SEAS_PREC_DF64 else MP_BOUND[prec])
 
 
-@pytest.mark.parametrize("prec", [seas.SEAS_PREC_DF64, seas.SEAS_PREC_BF16])
+@pytest.mark.parametrize("prec", [seas.SEAS_PREC_DF64, seas.SEAS_PREC_BF16, seas.SEAS_PREC_FP16S])
 def test_six_fault_3072_precisions_sampled(prec):
-    """Full-size network (H-matrix, windows) in DF64 and BF16, device-resident inputs, sampled rows at the last
-    step against the oracle with the same windows."""
+    """Full-size network (H-matrix, windows) in DF64, BF16 and FP16 with per-slice scale, device-resident inputs:
+    the interaction on the 64 stored oracle receivers at steps 1598 and 1999, the self part (FP64 in every mode)
+    on the stored receivers of every fault."""
     torch = pytest.importorskip("torch")
     w = synth.six_fault_3072()
-    net = O.network(w.faults, w.mu, w.cs)
-    V = w.slip_rate(0, 0, w.steps)
-    hp = w.hparams
-    rows = np.sort(np.random.default_rng(7).choice(net.N, 6, replace=False))
-    with seas.Session(w, precision=prec) as s:
-        Vd = torch.from_numpy(V).cuda()
-        parts = torch.zeros(3 * net.N, dtype=torch.float64, device="cuda")
-        tau = torch.zeros(net.N, dtype=torch.float64, device="cuda")
-        for n in range(w.steps):
-            seas.seas_push_slip_rate(s.scn, Vd[n])
-            seas.seas_stress_step(s.scn, tau, parts=parts)
-        seas.seas_scenario_check(s.scn)
-        p_gpu = parts.cpu().numpy().reshape(3, net.N)
-    _, _, last = O.pair_windows(net, hp["eta_tmin"], hp["eta_tmax"], hp["max_steps"])
-    f_int = O.interaction_rows(net, V, w.steps - 1, rows, pair_hi=last)
-    e = rel(p_gpu[2, rows], f_int)
-    print(f"six_fault_3072 precision {prec}: rel int at step {w.steps - 1}: {e:.2e}")
-    assert e <= (1e-5 if prec == seas.SEAS_PREC_DF64 else MP_BOUND[prec])
+    gold = six_fault_golden()
+    _, _, _, out = run_six_fault(torch, w, (1598, 1999), precision=prec)
+    for n in (1598, 1999):
+        p_gpu = out[n][1]
+        ri, fi = gold[("int", n)]
+        rs, fs = gold[("self", n)]
+        e = rel(p_gpu[2, ri], fi)
+        print(f"six_fault_3072 precision {prec}: rel int at step {n}: {e:.2e}, self {rel(p_gpu[1, rs], fs):.2e}")
+        assert e <= (1e-5 if prec == seas.SEAS_PREC_DF64 else MP_BOUND[prec])
+        assert rel(p_gpu[1, rs], fs) <= EXACT
 
 
 # ---------------------------------------------------------------- static tail (SEAS_FLAG_STATIC_TAIL) ---------------
@@ -424,4 +443,75 @@ def test_bf16_ensemble_tensor_core_path_matches_oracle(two_fault_oracle, batch):
         assert e[0] <= EXACT and e[1] <= EXACT and e[2] <= MP_BOUND[seas.SEAS_PREC_BF16]
     e1 = rel(P[:, 2, :N], P1[:, 2])
     print(f"BF16 batch {batch} member 0 vs single-scenario path: {e1:.2e}")
-    assert e1 <= 1e-2
+    assert e1 <= 1e-5
+
+
+def test_fp64_ensemble_of_8_matches_oracle(two_fault_oracle):
+    """Eight FP64 scenarios sharing the exact two-fault operator: members 0 and 7 against the oracle at the FP64
+    bar on tau and on each part."""
+    w, V0, ref0 = two_fault_oracle
+    net = O.network(w.faults, w.mu, w.cs)
+    N = net.N
+    ref7 = O.stress_history(net, w.slip_rate(7, 0, w.steps), w.hparams)
+    Vb = np.stack([w.slip_rate(b, 0, w.steps) for b in range(8)], axis=1).reshape(w.steps, -1)
+    with seas.Session(w, batch=8) as s:
+        tau, P = run_host(s, Vb)
+    for b, ref in ((0, ref0), (7, ref7)):
+        cols = slice(b * N, (b + 1) * N)
+        errs = [rel(tau[:, cols], ref[0])] + [rel(P[:, k, cols], ref[k + 1]) for k in range(3)]
+        print(f"FP64 batch 8 member {b}: rel-L2 tau/rad/self/int {errs}")
+        assert max(errs) <= EXACT
+
+
+def test_watchdog_timeout_is_reported_sticky_and_local():
+    """A device wait that runs out (a barrier nothing arrives on, with a 100 us bound) sets the scenario's error
+    word: seas_scenario_check and the next host-output step report SEAS_ETIMEOUT without waiting again, while another
+    scenario on the same operator and context keeps stepping correctly."""
+    import time
+    w = synth.tiny(1, steps=30)
+    V = w.slip_rate(0, 0, w.steps)
+    with seas.Session(w, **DENSE_EXACT) as s:
+        ref, _ = run_host(s, V[:5], parts=False)
+    with seas.Session(w, **DENSE_EXACT) as s:
+        for bad in (0.0, -1.0, 1e3, float("nan")):
+            with pytest.raises(seas.SeasError) as e:
+                seas.seas_scenario_set_wait_limit(s.scn, bad)
+            assert e.value.status == seas.SEAS_EINVAL
+        run_host(s, V[:3], parts=False)
+        seas.seas_scenario_set_wait_limit(s.scn, 1e-4)
+        t0 = time.perf_counter()
+        seas.seas_scenario_probe_wait(s.scn)
+        with pytest.raises(seas.SeasError) as e:
+            seas.seas_scenario_check(s.scn)
+        assert e.value.status == seas.SEAS_ETIMEOUT
+        seas.seas_push_slip_rate(s.scn, np.ascontiguousarray(V[3]))
+        with pytest.raises(seas.SeasError) as e:
+            seas.seas_stress_step(s.scn, np.zeros(w.N))
+        assert e.value.status == seas.SEAS_ETIMEOUT
+        assert time.perf_counter() - t0 < 1.0
+        other = seas.seas_scenario_create(s.op, 1)
+        t = np.zeros(w.N)
+        for n in range(5):
+            seas.seas_push_slip_rate(other, np.ascontiguousarray(V[n]))
+            seas.seas_stress_step(other, t)
+        np.testing.assert_array_equal(t, ref[4])
+        seas.seas_destroy_scn(other)
+
+
+def test_spectral_self_term_over_a_20000_lag_history():
+    """The spectral weights are differences of cumulative time integrals of the kernel (w^T = G(T+1) - G(T)): over a
+    20,000-step untruncated history, where the late weights are ~1e-9 of G, the self part still meets the FP64 bar
+    against the oracle, which integrates each interval on its own."""
+    steps = 20000
+    w = synth.Workload("one_long", np.array([[0.0, 0.0, 0.4, 160.0, 16]]), steps=steps,
+                       hparams=dict(max_steps=steps, leaf=4, flags=seas.SEAS_FLAG_NO_TRUNC))
+    net = O.network(w.faults, w.mu, w.cs)
+    V = w.slip_rate(0, 0, steps)
+    tab = O.SelfTables(16, 160.0, net.dt, net.cs, np.full(17, steps - 1))
+    ref = O.self_history(net, 0, O.slip_from_rate(V, net.dt), tab)
+    with seas.Session(w) as s:
+        _, P = run_host(s, V)
+    e_all = rel(P[:, 1], ref)
+    e_late = rel(P[-2000:, 1], ref[-2000:])
+    print(f"20000-lag self term: rel-L2 {e_all:.2e} (last 2000 steps {e_late:.2e})")
+    assert e_all <= EXACT and e_late <= EXACT
