@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-tail", action="store_true", help="skip the static-tail run")
     ap.add_argument("--no-oracle-rows", action="store_true", help="skip the oracle interaction rows (errors)")
     ap.add_argument("--dump-step-bytes", default=None, help="write the per-step algorithmic interaction bytes here")
+    ap.add_argument("--served-seconds", type=float, default=15.0, help="wall time of the served run (0: skip)")
     return ap.parse_args()
 
 
@@ -534,6 +535,8 @@ def run_ours(args, w, start, K, W):
         p.close()
         del rp
 
+    served = run_served(args, dist, local) if args.served_seconds > 0 and rank == 0 else None
+
     roofline["traffic"] = None
     tf = os.path.join(ROOT, "profiles", "interaction_traffic.json")
     if os.path.exists(tf):
@@ -566,12 +569,61 @@ def run_ours(args, w, start, K, W):
                     "n_blocks_far", "n_blocks_near", "compression_ratio", "bytes_interaction", "mean_rank",
                     "max_rank", "build_seconds", "n_tasks")},
                 "vs_plain_fp64_gpu": plain, "variants": variants, "batched": batched, "static_tail": tail, "e2e": e2e,
+                "served": served,
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": int(sum(launches.values()))}
     s.close()
     if dist is not None:
         dist.destroy_process_group()
     return line
+
+
+SERVED = dict(pool=8, rate=20.0, steps_lo=1000, steps_hi=20000, lag_cap=500, batch=8, budget=24 << 30,
+              precision="bf16")
+
+
+def run_served(args, dist, local):
+    """Served workload: Poisson arrivals (20 per second) of scenario requests on a pool of 8 seeded networks of
+    256..8000 elements (log-uniform), 1000..20000 steps each (log-uniform), BF16 operators with windows capped at
+    500 lags, slot groups of 8 members, an HBM budget of 24 GiB.  The operators are built before the window (warm
+    start); the server then runs the arrival trace for --served-seconds of wall time.  Throughput counts the steps
+    completed in that window; latency is each request-step's group tick (CUDA events on the group's stream)."""
+    import torch
+    from paper_2603_00383_gb300 import seas, serve
+    cfg = dict(SERVED)
+    code, dtype = PRECISIONS[cfg["precision"]]
+    geoms = [synth.served_network(g, max_steps=cfg["lag_cap"], precision=code) for g in range(cfg["pool"])]
+    trace = serve.poisson_trace(cfg["pool"], cfg["rate"], args.served_seconds, cfg["steps_lo"], cfg["steps_hi"])
+    srv = serve.Server(geoms, budget=cfg["budget"], batch=cfg["batch"], device=local, precision=code)
+    t0 = time.perf_counter()
+    srv.prebuild(range(cfg["pool"]))
+    torch.cuda.synchronize(local)
+    log(f"served: warm start {time.perf_counter() - t0:.1f} s, "
+        f"builds {[round(x, 1) for x in srv.backend.build_seconds.values()]} s")
+    with Clocks(local) as clk:
+        wall = srv.run(trace, until=args.served_seconds)
+    torch.cuda.synchronize(local)
+    reqs = list(srv.sched.requests.values())
+    lat = np.array(srv.latency_ms) if srv.latency_ms else np.zeros(1)
+    waits = [r.admitted - r.arrival for r in reqs if r.admitted is not None]
+    out = {"value": srv.element_steps / wall, "unit": METRIC, "dtype": dtype, "wall_s": wall,
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "request_steps": len(srv.latency_ms), "group_ticks": srv.ticks,
+           "requests": {"arrived": len(trace), "admitted": sum(r.admitted is not None for r in reqs),
+                        "completed": sum(r.state == "done" for r in reqs),
+                        "rejected": sum(r.state == "rejected" for r in reqs)},
+           "queue_wait_p50_s": float(np.percentile(waits, 50)) if waits else None,
+           "queue_wait_p99_s": float(np.percentile(waits, 99)) if waits else None,
+           "pool_elements": [w.N for w in geoms], "hbm_held_gb": srv.sched.used / 1e9,
+           "config": {k: v for k, v in cfg.items() if k != "budget"} | {"budget_gib": cfg["budget"] >> 30},
+           "clocks": clk.summary()}
+    log(f"served: {out['value'] / 1e6:.2f} M element-steps/s, p50 {out['p50_ms']:.3f} ms, p99 {out['p99_ms']:.3f} ms,"
+        f" {out['requests']}")
+    for g in list(srv.backend.op):
+        for gid in [gid for gid, G in srv.backend.groups.items() if G["geom"] == g]:
+            srv.backend.drop(gid)
+        srv.backend.evict(g)
+    return out
 
 
 def seas_kernel_version():

@@ -70,6 +70,10 @@ typedef int seas_status;
  * limit of the kernel over dt (Eq. primitives), delta the slip.  FP64 in every precision.  Costs a dense N x N FP64
  * static operator and a slip ring per scenario; ignored with SEAS_FLAG_NO_TRUNC (nothing is dropped). */
 #define SEAS_FLAG_STATIC_TAIL 4
+/* SEAS_FLAG_LAG_CAP: max_steps caps every window (lags 0 .. max_steps - 1 are kept, older history is dropped like a
+ * window end) but does not limit the number of pushes, so scenarios may run any number of steps (used by long-running
+ * served requests).  Without it, a push past max_steps returns SEAS_ESTATE. */
+#define SEAS_FLAG_LAG_CAP 8
 
 /* storage precision and arithmetic of the interaction operator */
 #define SEAS_PREC_FP64 0   /* FP64 entries, FP64 arithmetic */
@@ -139,6 +143,9 @@ typedef struct {
  * ready in this stream's order. */
 seas_status seas_create(seas_ctx **ctx, int device, size_t hbm_budget, void *cuda_stream);
 
+/* Device bytes the context's handles hold now (operators, scenarios, networks) and its budget (0: none). */
+seas_status seas_ctx_get_memory(const seas_ctx *ctx, size_t *used, size_t *budget);
+
 /* Builds the discretised network (Sec. 2.3.1 "Discretization", Sec. 3.1 frames).  Rejects non-finite or
  * non-positive sizes, N_f whose 2,3,5-free part is not 1, N_f > 7168, and receiver centroids lying on another
  * fault (within 1e-6 ds of one of its elements, where the kernel is singular). */
@@ -199,8 +206,23 @@ seas_status seas_scenario_set_wait_limit(seas_scn *scn, double seconds);
  * involved.  No counterpart in the paper. */
 seas_status seas_scenario_probe_wait(seas_scn *scn);
 
-/* Number of pushes so far. */
+/* Number of pushes so far (ticks of the batch; equal to every member's step count unless members were admitted
+ * later). */
 seas_status seas_scenario_step(const seas_scn *scn, int64_t *n);
+
+/* Continuous batching (no counterpart in the paper, which runs one scenario): the members of a batch need not start
+ * together.  seas_scenario_admit(scn, m) makes member m a fresh scenario whose first push is the batch's next push:
+ * its slip-rate, slip and spectral histories are set to zero on the device (asynchronously on the context stream,
+ * no allocation), so its tau from then on equals that of a scenario of its own (to rounding: the summation order
+ * depends on the batch width).  Every member shares the batch's ring slots (tick mod depth); a member admitted at
+ * tick s reads zeros for lags beyond its own step n - s.  seas_scenario_retire(scn, m) stops counting member m:
+ * its outputs are then meaningless and its pushes are ignored by the max_steps check; the interaction kernel skips
+ * lags beyond the oldest active member's step.  A member's own step count must stay below max_steps (SEAS_ESTATE
+ * from push otherwise); the batch's tick may grow past it.  seas_scenario_member_step returns member m's pushes
+ * since admission (-1 when retired).  All members start active at seas_scenario_create. */
+seas_status seas_scenario_admit(seas_scn *scn, int member);
+seas_status seas_scenario_retire(seas_scn *scn, int member);
+seas_status seas_scenario_member_step(const seas_scn *scn, int member, int64_t *n);
 
 seas_status seas_sync(seas_ctx *ctx);
 /* Synchronises the scenario's stream and reports SEAS_ETIMEOUT if a bounded device wait of its kernels ran out
@@ -242,8 +264,8 @@ seas_status seas_op_step_bytes(const seas_op *op, int64_t step, int64_t *bytes);
  * Allocates and frees a few bytes; SEAS_EINVAL for a bad device, SEAS_ECUDA on a CUDA error. */
 seas_status seas_measure_fp64_peak(int device, double *fma_per_second);
 
-/* Checkpoint/resume of a scenario: the step counter, slip-rate ring, slip and spectral ring (and the slip ring of
- * the static tail when that flag is set). */
+/* Checkpoint/resume of a scenario: the step counter, the members' start ticks and states, slip-rate ring, slip and
+ * spectral ring (and the slip ring of the static tail when that flag is set). */
 seas_status seas_scenario_save(seas_scn *scn, const char *path);
 seas_status seas_scenario_load(seas_op *op, const char *path, seas_scn **scn);
 

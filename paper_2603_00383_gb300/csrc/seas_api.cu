@@ -208,7 +208,9 @@ struct seas_op {
 struct seas_scn {
     seas_op *op = nullptr;
     int B = 0;
-    int64_t n = 0;                   // pushes so far
+    int64_t n = 0;                   // pushes so far (ticks)
+    std::vector<int64_t> start;      // per member: tick of its first push (0 unless admitted later)
+    std::vector<char> active;        // per member: 1 while admitted
     DArr<double> vring, slip, slip_prev, fint, d_V, d_slip, d_tau, d_parts, partial;
     DArr<double> sring;              // static tail: slip after each push, [op->ring + 1][N][B]
     DArr<unsigned char> xring;       // history in the operator's arithmetic (DF64: float2, BF16/FP16: float)
@@ -252,6 +254,13 @@ extern "C" seas_status seas_create(seas_ctx **out, int device, size_t hbm_budget
         c->own_stream = true;
     }
     *out = c.release();
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_ctx_get_memory(const seas_ctx *c, size_t *used, size_t *budget) {
+    if (!c) return fail(SEAS_EINVAL, "ctx is NULL");
+    if (used) *used = c->used;
+    if (budget) *budget = c->budget;
     return SEAS_OK;
 }
 
@@ -1005,7 +1014,7 @@ extern "C" seas_status seas_build_hmatrix(seas_net *net, const seas_hparams *hp,
     if (hp->max_steps < 1 || hp->max_steps > (1 << 22)) return fail(SEAS_EINVAL, "max_steps in [1, 2^22]");
     if (hp->precision < kPrecFP64 || hp->precision > kPrecDF64)
         return fail(SEAS_EINVAL, "precision %d not available", hp->precision);
-    if (hp->flags & ~(SEAS_FLAG_DENSE | SEAS_FLAG_NO_TRUNC | SEAS_FLAG_STATIC_TAIL))
+    if (hp->flags & ~(SEAS_FLAG_DENSE | SEAS_FLAG_NO_TRUNC | SEAS_FLAG_STATIC_TAIL | SEAS_FLAG_LAG_CAP))
         return fail(SEAS_EINVAL, "unsupported flags 0x%x", hp->flags);
     if (hp->max_block != 0 && hp->max_block < hp->leaf) return fail(SEAS_EINVAL, "max_block must be >= leaf");
     seas_ctx *c = net->ctx;
@@ -1109,6 +1118,10 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     a.n_modes_total = op.n_modes_total;
     a.max_nf = op.max_nf;
     a.step = step;
+    int64_t lag_max = -1;            // the oldest active member's step
+    for (int b = 0; b < s.B; ++b)
+        if (s.active[b]) lag_max = std::max<int64_t>(lag_max, step - s.start[b]);
+    a.lag_max = lag_max;
     a.ring = op.ring;
     a.ring_stride = s.ring_stride;
     a.dt = net.dt;
@@ -1130,8 +1143,10 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     a.items = op.d_items.p;
     a.tasks = op.d_tasks.p;
     a.n_tasks_active =
-        (int)(std::upper_bound(op.task_T.begin(), op.task_T.end(), (int32_t)std::min<int64_t>(step, INT32_MAX)) -
-              op.task_T.begin());
+        lag_max < 0 ? 0
+                    : (int)(std::upper_bound(op.task_T.begin(), op.task_T.end(),
+                                             (int32_t)std::min<int64_t>(lag_max, INT32_MAX)) -
+                            op.task_T.begin());
     a.partial = s.partial.p;
     a.n_partial = op.n_partial;
     a.counter = s.counter_err.p;
@@ -1157,6 +1172,8 @@ seas_status scenario_alloc(seas_op *op, int batch, std::unique_ptr<seas_scn> &s)
     s = std::make_unique<seas_scn>();
     s->op = op;
     s->B = batch;
+    s->start.assign(batch, 0);
+    s->active.assign(batch, 1);
     const int64_t BN = N * batch;
     // spectral rings: per fault [batch][N_f + 1][R_f], faults one after the other
     std::vector<FaultDev> ft = op->faults_h;
@@ -1311,8 +1328,11 @@ extern "C" seas_status seas_push_slip_rate(seas_scn *s, const double *V, const d
     seas_op &op = *s->op;
     seas_ctx *c = op.net->ctx;
     if (replace_last && s->n == 0) return fail(SEAS_ESTATE, "replace_last before the first push");
-    if (!replace_last && s->n >= op.hp.max_steps)
-        return fail(SEAS_ESTATE, "push %lld beyond max_steps %d", (long long)s->n, op.hp.max_steps);
+    if (!replace_last && !(op.hp.flags & SEAS_FLAG_LAG_CAP))
+        for (int b = 0; b < s->B; ++b)
+            if (s->active[b] && s->n - s->start[b] >= op.hp.max_steps)
+                return fail(SEAS_ESTATE, "push %lld of member %d beyond max_steps %d",
+                            (long long)(s->n - s->start[b]), b, op.hp.max_steps);
     CUDA_TRY(cudaSetDevice(c->device));
     const int64_t BN = (int64_t)s->B * op.net->N;
     const double *dV = V, *dS = slip;
@@ -1406,6 +1426,32 @@ extern "C" seas_status seas_stress_step_static(seas_scn *s, double *tau, double 
     return SEAS_OK;
 }
 
+extern "C" seas_status seas_scenario_admit(seas_scn *s, int member) {
+    if (!s) return fail(SEAS_EINVAL, "NULL scenario");
+    if (member < 0 || member >= s->B) return fail(SEAS_EINVAL, "member %d outside [0, %d)", member, s->B);
+    seas_ctx *c = s->op->net->ctx;
+    CUDA_TRY(cudaSetDevice(c->device));
+    const StepArgs a = step_args(*s, s->n);
+    CUDA_TRY(launch_reset_member(a, member, c->stream));
+    s->start[member] = s->n;
+    s->active[member] = 1;
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_scenario_retire(seas_scn *s, int member) {
+    if (!s) return fail(SEAS_EINVAL, "NULL scenario");
+    if (member < 0 || member >= s->B) return fail(SEAS_EINVAL, "member %d outside [0, %d)", member, s->B);
+    s->active[member] = 0;
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_scenario_member_step(const seas_scn *s, int member, int64_t *n) {
+    if (!s || !n) return fail(SEAS_EINVAL, "NULL argument");
+    if (member < 0 || member >= s->B) return fail(SEAS_EINVAL, "member %d outside [0, %d)", member, s->B);
+    *n = s->active[member] ? s->n - s->start[member] : -1;
+    return SEAS_OK;
+}
+
 extern "C" seas_status seas_scenario_set_wait_limit(seas_scn *s, double seconds) {
     if (!s) return fail(SEAS_EINVAL, "NULL scenario");
     if (!(std::isfinite(seconds) && seconds >= 1e-6 && seconds <= 60.0))
@@ -1475,7 +1521,7 @@ extern "C" seas_status seas_scenario_save(seas_scn *s, const char *path) {
     if (!fp) return fail(SEAS_EIO, "cannot open %s for writing", path);
     CkptHeader h{};
     std::memcpy(h.magic, "SEASCKP1", 8);
-    h.version = 2;
+    h.version = 3;
     h.B = s->B;
     h.N = op.net->N;
     h.F = op.net->F;
@@ -1485,6 +1531,9 @@ extern "C" seas_status seas_scenario_save(seas_scn *s, const char *path) {
     h.n_modes_total = op.n_modes_total;
     seas_status st = SEAS_OK;
     if (fwrite(&h, sizeof h, 1, fp) != 1) st = fail(SEAS_EIO, "short write");
+    if (st == SEAS_OK && (fwrite(s->start.data(), sizeof(int64_t), s->B, fp) != (size_t)s->B ||
+                          fwrite(s->active.data(), 1, s->B, fp) != (size_t)s->B))
+        st = fail(SEAS_EIO, "short write");
     if (st == SEAS_OK) st = dump(fp, s->vring.p, s->vring.bytes());
     if (st == SEAS_OK) st = dump(fp, s->slip.p, s->slip.bytes());
     if (st == SEAS_OK) st = dump(fp, s->slip_prev.p, s->slip_prev.bytes());
@@ -1502,14 +1551,24 @@ extern "C" seas_status seas_scenario_load(seas_op *op, const char *path, seas_sc
     FILE *fp = fopen(path, "rb");
     if (!fp) return fail(SEAS_EIO, "cannot open %s", path);
     CkptHeader h{};
-    if (fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "SEASCKP1", 8) != 0 || h.version != 2) {
+    if (fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "SEASCKP1", 8) != 0 || h.version != 3) {
         fclose(fp);
         return fail(SEAS_EIO, "%s is not a scenario checkpoint", path);
     }
     if (h.N != op->net->N || h.F != op->net->F || h.ring != op->ring || h.n_modes_total != op->n_modes_total ||
-        h.B < 1 || h.n < 0 || h.n > op->hp.max_steps) {
+        h.B < 1 || h.n < 0) {
         fclose(fp);
         return fail(SEAS_EIO, "checkpoint does not match this operator");
+    }
+    if (h.B > kMaxBatch) {
+        fclose(fp);
+        return fail(SEAS_EIO, "checkpoint batch %d exceeds %d", h.B, kMaxBatch);
+    }
+    std::vector<int64_t> start(h.B);
+    std::vector<char> active(h.B);
+    if (fread(start.data(), sizeof(int64_t), h.B, fp) != (size_t)h.B || fread(active.data(), 1, h.B, fp) != (size_t)h.B) {
+        fclose(fp);
+        return fail(SEAS_EIO, "%s: truncated member table", path);
     }
     std::unique_ptr<seas_scn> s;
     seas_status st = scenario_alloc(op, h.B, s);
@@ -1530,6 +1589,8 @@ extern "C" seas_status seas_scenario_load(seas_op *op, const char *path, seas_sc
     fclose(fp);
     if (st != SEAS_OK) return st;
     s->n = h.n;
+    s->start = start;
+    s->active = active;
     op->children++;
     *out = s.release();
     return SEAS_OK;

@@ -130,7 +130,9 @@ cudaError_t launch_spectral_tables(const ModeDev *modes, int n_modes, const int6
 struct StepArgs {
     int N, F, B, n_modes_total;   // elements, faults, batch, sum over faults of (N_f + 1)
     int max_nf;                   // largest N_f (shared memory of the FFT kernels)
-    int64_t step;                 // index of the step being evaluated
+    int64_t step;                 // tick of the step being evaluated (ring slots are tick mod depth)
+    int64_t lag_max;              // largest lag with nonzero history: the oldest active member's step (<= step);
+                                  // members admitted later have zero history before their first tick
     int ring;                     // slip-rate ring depth R
     int64_t ring_stride;          // doubles per ring slot: layout [slot][element][scenario], padded to even + 2
     double dt, rad;               // rad = -mu / (2 c_s)
@@ -184,5 +186,6 @@ cudaError_t launch_reduce(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_static_tail(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_ifft_assemble(const StepArgs &a, double *tau, double *parts, cudaStream_t s);
 cudaError_t launch_wait_probe(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_reset_member(const StepArgs &a, int member, cudaStream_t s);
 
 }  // namespace seas

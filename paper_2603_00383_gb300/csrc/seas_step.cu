@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) k_modeconv(StepArgs a) {
     const ModeDev mo = a.modes[md];
     const FaultDev fd = a.faults[mo.fault];
     const int R = fd.ring;
-    const int64_t Tmax = mo.W < a.step ? mo.W : a.step;
+    const int64_t Tmax = mo.W < a.lag_max ? mo.W : a.lag_max;
     const double2 *ring = a.dring + fd.dring_off + ((int64_t)b * (fd.nf + 1) + mo.n) * R;
     const double *w = a.w + mo.w_off;
     const int slot0 = (int)(a.step % R);
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_modeconv(StepArgs a) {
         im += __shfl_xor_sync(0xffffffffu, im, o);
     }
     if (lane == 0) {
-        if (a.tail && a.step > mo.W) {
+        if (a.tail && a.lag_max > mo.W) {
             // static tail: the spectrum at the window's far edge times the weight mass beyond the window
             int s = slot0 - mo.W - 1;
             if (s < 0) s += R;
@@ -891,7 +891,7 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
                 have = false;
             }
             if (!have && it + lane < ie) item = a.items[it + lane];
-            const bool valid = it + lane < ie && item.T <= a.step;
+            const bool valid = it + lane < ie && item.T <= a.lag_max;
             const int p2 = pad_row(bd.p, PREC), q2 = pad_row(bd.q, PREC);
             int data_bytes = 0, x_bytes = 0, nrow = 0, nz = 0;
             int64_t xs_start = 0;
@@ -1358,8 +1358,9 @@ __global__ void __launch_bounds__(kThreads) k_static_tail(StepArgs a) {
     for (int bb = 0; bb < kMaxBatch; ++bb) sum[bb] = 0.0;
     for (int fb = 0; fb < a.F; ++fb) {
         if (fb == fa) continue;
-        const int64_t src = a.step - a.pair_last[fa * a.F + fb] - 1;
-        if (src < 0) continue;
+        const int64_t back = (int64_t)a.pair_last[fa * a.F + fb] + 1;
+        if (a.lag_max < back) continue;                 // no member's window has passed yet
+        const int64_t src = a.step - back;
         const double *sl = a.sring + (src % a.sring_depth) * BN;
         const int j0 = a.faults[fb].off, j1 = j0 + a.faults[fb].nf;
         for (int j = j0 + lane; j < j1; j += 32) {
@@ -1398,7 +1399,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
         int lo = t0, hi = t1;                               // causal tasks: T_start <= step
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (a.blk_task_T[mid] <= a.step) lo = mid + 1; else hi = mid;
+            if (a.blk_task_T[mid] <= a.lag_max) lo = mid + 1; else hi = mid;
         }
         const int64_t base = a.blk_part[blk] + (e - bd.r0);
         for (int k = 0; k < lo - t0; ++k) {
@@ -1415,6 +1416,35 @@ __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) a.fint[(int64_t)bb * a.N + e] = v;
         }
+    }
+}
+
+// Admission of member `mb` of a batch (continuous batching): its whole history -- every slot of the slip-rate ring
+// (and of its reduced-precision mirror and the slip ring of the static tail), its slip, and its spectral rings --
+// is set to zero, so that the member starts as a scenario with no slip before the next push.
+__global__ void __launch_bounds__(kThreads) k_reset_member(StepArgs a, int mb) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    const int64_t BN = (int64_t)a.B * a.N;
+    for (int64_t e = tid; e < (int64_t)a.ring * a.N; e += nt) {
+        const int64_t slot = e / a.N, i = e - slot * a.N, o = slot * a.ring_stride + i * a.B + mb;
+        a.vring[o] = 0.0;
+        if (a.prec == kPrecDF64) reinterpret_cast<float2 *>(a.xring)[o] = make_float2(0.f, 0.f);
+        else if (a.prec != kPrecFP64) reinterpret_cast<float *>(a.xring)[o] = 0.f;
+    }
+    if (a.tail)
+        for (int64_t e = tid; e < (int64_t)a.sring_depth * a.N; e += nt) {
+            const int64_t slot = e / a.N, i = e - slot * a.N;
+            a.sring[slot * BN + i * a.B + mb] = 0.0;
+        }
+    for (int64_t i = tid; i < a.N; i += nt) {
+        a.slip[(int64_t)mb * a.N + i] = 0.0;
+        a.slip_prev[(int64_t)mb * a.N + i] = 0.0;
+    }
+    for (int f = 0; f < a.F; ++f) {
+        const FaultDev fd = a.faults[f];
+        const int64_t len = (int64_t)(fd.nf + 1) * fd.ring;
+        double2 *d = a.dring + fd.dring_off + (int64_t)mb * len;
+        for (int64_t e = tid; e < len; e += nt) d[e] = make_double2(0.0, 0.0);
     }
 }
 
@@ -1508,6 +1538,11 @@ cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s) {
         case kPrecFP16: return launch_interaction_prec<kPrecFP16>(a, s);
         default: return launch_interaction_prec<kPrecFP64>(a, s);
     }
+}
+
+cudaError_t launch_reset_member(const StepArgs &a, int member, cudaStream_t s) {
+    k_reset_member<<<152 * 4, kThreads, 0, s>>>(a, member);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_wait_probe(const StepArgs &a, cudaStream_t s) {

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libseas.so")
 SEAS_OK = 0
 SEAS_EINVAL, SEAS_ENOMEM, SEAS_ECUDA, SEAS_ESTATE, SEAS_EBUSY, SEAS_ETIMEOUT, SEAS_EIO = -1, -2, -3, -4, -5, -6, -7
 SEAS_MEM_HOST, SEAS_MEM_DEVICE = 0, 1
-SEAS_FLAG_DENSE, SEAS_FLAG_NO_TRUNC, SEAS_FLAG_STATIC_TAIL = 1, 2, 4
+SEAS_FLAG_DENSE, SEAS_FLAG_NO_TRUNC, SEAS_FLAG_STATIC_TAIL, SEAS_FLAG_LAG_CAP = 1, 2, 4, 8
 SEAS_PREC_FP64, SEAS_PREC_BF16, SEAS_PREC_FP16S, SEAS_PREC_DF64 = 0, 1, 2, 3
 
 EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_get_elements", "seas_build_hmatrix",
@@ -27,7 +27,8 @@ EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_
             "seas_scenario_save", "seas_scenario_load", "seas_destroy_scn", "seas_destroy_op", "seas_destroy_net",
             "seas_destroy_ctx", "seas_plan_hmatrix", "seas_scenario_set_timing", "seas_scenario_get_timing",
             "seas_op_step_bytes", "seas_scenario_check", "seas_stress_step_static",
-            "seas_measure_fp64_peak", "seas_scenario_set_wait_limit", "seas_scenario_probe_wait"]
+            "seas_measure_fp64_peak", "seas_scenario_set_wait_limit", "seas_scenario_probe_wait",
+            "seas_scenario_admit", "seas_scenario_retire", "seas_scenario_member_step", "seas_ctx_get_memory"]
 
 
 class SeasError(RuntimeError):
@@ -103,6 +104,10 @@ _SIGS = {
     "seas_measure_fp64_peak": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
     "seas_scenario_set_wait_limit": ([_VP, C.c_double], C.c_int),
     "seas_scenario_probe_wait": ([_VP], C.c_int),
+    "seas_scenario_admit": ([_VP, C.c_int], C.c_int),
+    "seas_scenario_retire": ([_VP, C.c_int], C.c_int),
+    "seas_scenario_member_step": ([_VP, C.c_int, C.POINTER(C.c_int64)], C.c_int),
+    "seas_ctx_get_memory": ([_VP, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)], C.c_int),
 }
 
 
@@ -220,6 +225,13 @@ def seas_plan_hmatrix(faults, mu: float, cs: float, cp: float, beta: float, hp: 
     return dict(blocks=blocks, pair_last=last, mode_windows=windows, dt=dt.value)
 
 
+def seas_ctx_get_memory(ctx: Handle):
+    """(bytes held by the context's handles, budget)."""
+    u, b = C.c_size_t(), C.c_size_t()
+    _check(lib().seas_ctx_get_memory(ctx.ptr, C.byref(u), C.byref(b)))
+    return u.value, b.value
+
+
 def seas_build_network(ctx: Handle, faults, mu: float, cs: float, cp: float = 6000.0, beta: float = 0.5) -> Handle:
     """faults: [F, 5] array (cx, cy, strike_rad, length, n_elem)."""
     faults, arr = _faults(faults)
@@ -316,6 +328,20 @@ def seas_stress_step_static(scn: Handle, tau, parts=None):
 def seas_scenario_step(scn: Handle) -> int:
     n = C.c_int64()
     _check(lib().seas_scenario_step(scn.ptr, C.byref(n)))
+    return n.value
+
+
+def seas_scenario_admit(scn: Handle, member: int):
+    _check(lib().seas_scenario_admit(scn.ptr, int(member)))
+
+
+def seas_scenario_retire(scn: Handle, member: int):
+    _check(lib().seas_scenario_retire(scn.ptr, int(member)))
+
+
+def seas_scenario_member_step(scn: Handle, member: int) -> int:
+    n = C.c_int64()
+    _check(lib().seas_scenario_member_step(scn.ptr, int(member), C.byref(n)))
     return n.value
 
 

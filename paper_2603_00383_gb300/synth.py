@@ -34,6 +34,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 FLAG_DENSE = 1          # every block stored dense (admissibility never satisfied)
 FLAG_NO_TRUNC = 2       # no causal end truncation of pair windows, full spectral windows
 FLAG_STATIC_TAIL = 4    # add the elastostatic response of truncated history (default off)
+FLAG_LAG_CAP = 8        # max_steps caps the windows but not the number of steps
 
 PREC_FP64 = 0
 PREC_BF16 = 1
@@ -241,3 +242,61 @@ def ensemble_network(geom_id: int, seed: int = SEED) -> Workload:
 
 
 WORKLOADS = {"two_fault_128": two_fault_128, "six_fault_3072": six_fault_3072, "paper_two_fault": paper_two_fault}
+
+
+def served_network(geom_id: int, seed: int = SEED, n_lo: int = 256, n_hi: int = 8000, max_steps: int = 1000,
+                   precision: int = PREC_FP64) -> Workload:
+    """Network of the served workload: N log-uniform in [n_lo, n_hi], F in [2, 12] (at most N / 64 faults), 20 m
+    elements, box 40 km * sqrt(N / 3000), operator lags capped at ``max_steps`` (the served requests run longer:
+    windows end at the cap)."""
+    u = uniform01(seed ^ 0x5E4E, np.arange(4 * geom_id, 4 * geom_id + 4, dtype=np.uint64))
+    N = int(round(math.exp(math.log(n_lo) + u[1] * (math.log(n_hi) - math.log(n_lo)))))
+    F = max(2, min(2 + int(11 * u[0]), N // 64))
+    sizes = _smooth_sizes(N, F, seed + 31 * geom_id)
+    box = 40000.0 * math.sqrt(sum(sizes) / 3000.0)
+    faults = place_faults(sizes, 20.0, box, 500.0, seed + 7907 * geom_id)
+    return Workload(f"served{geom_id}", faults, steps=max_steps, seed=seed + 200000 * geom_id,
+                    hparams=_hp(leaf=32, eta_h=2.0, aca_tol=1e-6, max_steps=max_steps, precision=precision,
+                                flags=FLAG_LAG_CAP))
+
+
+class SlipRateStream:
+    """Slip rates of one served request, generated on the GPU in chunks of ``chunk`` steps with the statistics of
+    Workload.slip_rate (log10 V ~ U[-9, -6] per element and step, plus the rupture pulse on fault 0).  The uniform
+    numbers come from torch's counter-based Philox generator, seeded per (request seed, chunk), so the values of a
+    step depend only on the request's seed and the step, not on what else runs.  Holds no method arithmetic."""
+
+    def __init__(self, workload: Workload, seed: int, device, chunk: int = 256):
+        import torch
+        self.torch = torch
+        self.w = workload
+        self.seed = int(seed)
+        self.device = device
+        self.chunk = int(chunk)
+        n0 = int(workload.faults[0, 4])
+        ds0 = float(workload.faults[0, 3]) / n0
+        self.n0 = n0
+        self.xi = torch.from_numpy(np.abs((np.arange(n0) + 0.5 - 0.5 * n0) * ds0)).to(device)
+        self.ds0 = ds0
+        self.front = 0.8 * workload.cs * workload.input_dt()
+        self._k = -1
+        self._buf = None
+
+    def _fill(self, k: int):
+        torch = self.torch
+        g = torch.Generator(device=self.device)
+        g.manual_seed((self.seed * 1000003 + k) & 0x7FFFFFFFFFFFFFFF)
+        u = torch.rand((self.chunk, self.w.N), generator=g, device=self.device, dtype=torch.float64)
+        V = torch.pow(10.0, -9.0 + 3.0 * u)
+        if self.w.pulse:
+            m = torch.arange(k * self.chunk, (k + 1) * self.chunk, device=self.device, dtype=torch.float64)
+            arg = (self.xi[None, :] - self.front * m[:, None]) / (5.0 * self.ds0)
+            V[:, : self.n0] += torch.exp(-0.5 * arg * arg)
+        self._k, self._buf = k, V
+
+    def row(self, m: int):
+        """V^m, a [N] float64 tensor on the device (a view valid until the next chunk is generated)."""
+        k = m // self.chunk
+        if k != self._k:
+            self._fill(k)
+        return self._buf[m - k * self.chunk]
