@@ -264,8 +264,8 @@ seas_status seas_op_step_bytes(const seas_op *op, int64_t step, int64_t *bytes);
  * Allocates and frees a few bytes; SEAS_EINVAL for a bad device, SEAS_ECUDA on a CUDA error. */
 seas_status seas_measure_fp64_peak(int device, double *fma_per_second);
 
-/* Checkpoint/resume of a scenario: the step counter, the members' start ticks and states, slip-rate ring, slip and
- * spectral ring (and the slip ring of the static tail when that flag is set). */
+/* Checkpoint/resume of a scenario: the step counter, the members' start ticks and states, the interaction's lag
+ * horizon, slip-rate ring, slip and spectral ring (and the slip ring of the static tail when that flag is set). */
 seas_status seas_scenario_save(seas_scn *scn, const char *path);
 seas_status seas_scenario_load(seas_op *op, const char *path, seas_scn **scn);
 

@@ -191,6 +191,15 @@ struct seas_op {
     DArr<ItemDev> d_items;
     DArr<TaskDev> d_tasks;
     std::vector<int32_t> task_T;     // T_start of each task (ascending)
+    // pass 1 (source side of the far blocks)
+    DArr<unsigned char> d_varena;    // V^T rows, source cluster-major
+    DArr<RunDev> d_runs;
+    DArr<TaskDev> d_ztasks;
+    DArr<SrcDev> d_srcs;
+    DArr<int32_t> d_zmap;
+    DArr<float> d_zscale;
+    std::vector<int32_t> ztask_T;    // T_start of each pass-1 task (ascending)
+    int64_t z_rows = 0;              // rows of the z buffer (rows of the receiver-side arena)
     int64_t n_partial = 0;           // partial-sum slots (rows) over all tasks
     int max_q = 0;                   // widest block (source columns)
     DArr<int32_t> d_cover_ptr, d_cover_blk, d_blk_task_ptr, d_blk_task_T;
@@ -211,11 +220,13 @@ struct seas_scn {
     int64_t n = 0;                   // pushes so far (ticks)
     std::vector<int64_t> start;      // per member: tick of its first push (0 unless admitted later)
     std::vector<char> active;        // per member: 1 while admitted
+    int64_t horizon = -1;            // largest lag the interaction has switched on (non-decreasing)
+    DArr<unsigned char> zbuf;        // pass-1 output: [z rows][batch] in the dot type of the precision
     DArr<double> vring, slip, slip_prev, fint, d_V, d_slip, d_tau, d_parts, partial;
     DArr<double> sring;              // static tail: slip after each push, [op->ring + 1][N][B]
     DArr<unsigned char> xring;       // history in the operator's arithmetic (DF64: float2, BF16/FP16: float)
     DArr<double2> dring, fmodes;
-    DArr<int> counter_err;           // [0]: interaction task counter, [1]: device error word
+    DArr<int> counter_err;           // [0], [2]: task counters of the two interaction passes, [1]: device error word
     uint64_t wait_ns = 2000000000ull;   // bound of one device wait (seas_scenario_set_wait_limit)
     int64_t ring_stride = 0;
     DArr<FaultDev> faults;           // fault table with spectral-ring offsets for this batch size
@@ -275,6 +286,7 @@ extern "C" seas_status seas_sync(seas_ctx *c) {
 // shared memory than its layout needs (an internal error; the kernel returned before touching shared memory).
 static seas_status device_error_status(int err) {
     if (err == 1) return fail(SEAS_ETIMEOUT, "a bounded device wait ran out in the interaction kernel");
+    if (err == 3) return fail(SEAS_ECUDA, "interaction unit larger than a pipeline stage (internal error)");
     if (err) return fail(SEAS_ECUDA, "interaction kernel launched with too little shared memory (error word %d)", err);
     return SEAS_OK;
 }
@@ -792,14 +804,13 @@ seas_status build_interaction(seas_op &op) {
         max_block_entries = std::max<int64_t>(max_block_entries, (int64_t)b.p * b.q);
         op.max_q = std::max(op.max_q, b.q);
     }
-    // rank-1 terms per low-rank item and rows per dense item of each block (items <= kItemBytes)
+    // rows per dense item of each block (items of at most kItemBytes and kItemRows rows)
     const int prec = hp.precision;
     const int eb = elem_bytes(prec);
-    std::vector<int32_t> group(nb), drows(nb);
+    std::vector<int32_t> drows(nb);
     for (int b = 0; b < nb; ++b) {
-        const int p2 = pad_row(op.blocks_h[b].p, prec), q2 = pad_row(op.blocks_h[b].q, prec);
-        group[b] = (int32_t)std::min<int64_t>(kMaxItemRank, std::max<int64_t>(1, kItemBytes / (eb * (p2 + q2))));
-        drows[b] = (int32_t)std::max<int64_t>(1, kItemBytes / (eb * p2));
+        const int p2 = pad_row(op.blocks_h[b].p, prec);
+        drows[b] = (int32_t)std::min<int64_t>(kItemRows, std::max<int64_t>(1, kItemBytes / (eb * p2)));
     }
     const int64_t cap = std::max(kChunkEntries, max_block_entries);
     bool any_far = false;
@@ -812,14 +823,17 @@ seas_status build_interaction(seas_op &op) {
             SEAS_TRY(factors.alloc(c, (size_t)cap));
         }
     }
-    // Slices in block-major, lag-minor order, so that each block's slices are adjacent in the arena.
+    // Slices in block-major, lag-minor order, so that each block's slices are adjacent in the receiver-side arena.
+    // Far slices' V^T rows go to a block-major staging buffer first and are gathered into the source-major
+    // arena of pass 1 once every rank is known.
     struct Stored {
         int32_t block, T, k;
-        const unsigned char *data;
+        const unsigned char *u, *v;
         float scale;
         int chunk;
     };
     std::vector<Stored> stored;
+    std::vector<std::unique_ptr<DArr<unsigned char>>> vstage;
     int64_t bytes_dense = 0, bytes_stored = 0, rank_sum = 0;
     int cb = 0;
     int32_t cT = nb ? lo[0] : 0;
@@ -842,13 +856,13 @@ seas_status build_interaction(seas_op &op) {
         while (cb < nb) {
             const int64_t pq = (int64_t)op.blocks_h[cb].p * op.blocks_h[cb].q;
             if (entries + pq > cap) break;
-            sl.push_back(SliceGen{cb, cT, op.block_far[cb], group[cb], entries});
+            sl.push_back(SliceGen{cb, cT, op.block_far[cb], 0, entries});
             prefix.push_back(entries);
             entries += pq;
             advance();
         }
         DArr<SliceGen> d_sl;
-        DArr<int64_t> d_pref, d_off;
+        DArr<int64_t> d_pref, d_off, d_voff;
         DArr<SliceOut> d_out;
         SEAS_TRY(d_sl.upload(c, sl));
         SEAS_TRY(d_pref.upload(c, prefix));
@@ -861,43 +875,51 @@ seas_status build_interaction(seas_op &op) {
         CUDA_TRY(cudaMemcpyAsync(so.data(), d_out.p, so.size() * sizeof(SliceOut), cudaMemcpyDeviceToHost,
                                  c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
-        std::vector<int64_t> dst(sl.size());
-        int64_t total = 0;
+        std::vector<int64_t> dst(sl.size()), vdst(sl.size());
+        int64_t total = 0, vtotal = 0;
         for (size_t k = 0; k < sl.size(); ++k) {
             const BlockDev &b = op.blocks_h[sl[k].block];
             dst[k] = total;
+            vdst[k] = vtotal;
             if (so[k].k == 0) {
                 op.stats.n_slices_zero++;
                 continue;
             }
             const int p2 = pad_row(b.p, prec), q2 = pad_row(b.q, prec);
             bytes_dense += (int64_t)b.p * b.q * 8;
-            const int64_t n = so[k].k < 0 ? (int64_t)b.q * p2 : (int64_t)so[k].k * (p2 + q2);
-            if (so[k].k < 0) op.stats.n_slices_dense++;
-            else {
+            if (so[k].k < 0) {
+                op.stats.n_slices_dense++;
+                total += (int64_t)b.q * p2;
+            } else {
                 op.stats.n_slices_lowrank++;
                 rank_sum += so[k].k;
                 op.stats.max_rank = std::max(op.stats.max_rank, so[k].k);
+                total += (int64_t)so[k].k * p2;
+                vtotal += (int64_t)so[k].k * q2;
             }
-            total += n;
         }
         if (total > 0) {
             auto buf = std::make_unique<DArr<unsigned char>>();
+            auto vbuf = std::make_unique<DArr<unsigned char>>();
             SEAS_TRY(buf->alloc(c, (size_t)(total * eb)));
+            SEAS_TRY(vbuf->alloc(c, (size_t)std::max<int64_t>(16, vtotal * eb)));
             SEAS_TRY(d_off.upload(c, dst));
+            SEAS_TRY(d_voff.upload(c, vdst));
             DArr<float> d_scale;
             SEAS_TRY(d_scale.alloc(c, sl.size()));
             CUDA_TRY(launch_pack(op.d_blocks.p, d_sl.p, d_out.p, (int)sl.size(), scratch.p, factors.p, d_off.p,
-                                 buf->p, d_scale.p, prec, c->stream));
+                                 buf->p, d_voff.p, vbuf->p, d_scale.p, prec, c->stream));
             std::vector<float> scl(sl.size());
             CUDA_TRY(cudaMemcpyAsync(scl.data(), d_scale.p, scl.size() * sizeof(float), cudaMemcpyDeviceToHost,
                                      c->stream));
             CUDA_TRY(cudaStreamSynchronize(c->stream));
             for (size_t k = 0; k < sl.size(); ++k)
                 if (so[k].k != 0)
-                    stored.push_back(Stored{sl[k].block, sl[k].T, so[k].k, buf->p + dst[k] * eb, scl[k], chunk_id});
-            bytes_stored += total * eb;
+                    stored.push_back(Stored{sl[k].block, sl[k].T, so[k].k, buf->p + dst[k] * eb,
+                                            vbuf->p + vdst[k] * eb, scl[k], chunk_id});
+            bytes_stored += (total + vtotal) * eb;
             op.arena.push_back(std::move(buf));
+            vstage.push_back(std::move(vbuf));
         }
         ++chunk_id;
     }
@@ -905,19 +927,128 @@ seas_status build_interaction(seas_op &op) {
     resid.release();
     factors.release();
 
-    // Work items (<= kItemBytes, adjacent in memory) and tasks (runs of items of one block within one arena
-    // chunk, <= kTaskBytes); each task owns p partial-sum rows, the k-th task of block b at
-    // blk_part[b] + k * p.
+    // z rows: one per row of the receiver-side arena, in its order (dense slices' rows unused)
+    std::vector<int64_t> zrow0(stored.size());
+    int64_t zrows = 0;
+    for (size_t i = 0; i < stored.size(); ++i) {
+        zrow0[i] = zrows;
+        zrows += stored[i].k < 0 ? op.blocks_h[stored[i].block].q : stored[i].k;
+    }
+    if (zrows >= ((int64_t)1 << 31)) return fail(SEAS_EINVAL, "operator too large (%lld z rows)", (long long)zrows);
+    op.z_rows = zrows;
+
+    // ---- pass 1: far slices grouped by source cluster, then lag, then block (stable), V^T rows gathered into one
+    // source-major arena; runs of one (source cluster, lag) split so that a run and its history slice fit a stage
+    std::vector<int32_t> src_of(nb, -1);
+    std::vector<SrcDev> srcs;
+    {
+        std::vector<std::pair<std::pair<int, int>, int>> keys;
+        for (int b = 0; b < nb; ++b)
+            if (op.block_far[b]) keys.push_back({{op.blocks_h[b].c0, op.blocks_h[b].q}, b});
+        std::sort(keys.begin(), keys.end());
+        for (size_t k = 0; k < keys.size(); ++k) {
+            if (k == 0 || keys[k].first != keys[k - 1].first)
+                srcs.push_back(SrcDev{keys[k].first.first, keys[k].first.second});
+            src_of[keys[k].second] = (int32_t)srcs.size() - 1;
+        }
+    }
+    std::vector<size_t> far_ix;
+    for (size_t i = 0; i < stored.size(); ++i)
+        if (stored[i].k > 0) far_ix.push_back(i);
+    std::stable_sort(far_ix.begin(), far_ix.end(), [&](size_t x, size_t y) {
+        const int sx = src_of[stored[x].block], sy = src_of[stored[y].block];
+        return sx != sy ? sx < sy : stored[x].T < stored[y].T;
+    });
+    int64_t vbytes = 0;
+    for (size_t i : far_ix) vbytes += (int64_t)stored[i].k * pad_row(op.blocks_h[stored[i].block].q, prec) * eb;
+    SEAS_TRY(op.d_varena.alloc(c, (size_t)std::max<int64_t>(16, vbytes)));
+    std::vector<RunDev> runs;
+    std::vector<int32_t> zmap;
+    std::vector<float> zscale;
+    std::vector<TaskDev> ztasks;
+    {
+        std::vector<const void *> gsrc;
+        std::vector<void *> gdst;
+        std::vector<int32_t> gbytes;
+        int64_t off = 0;
+        const int64_t x_cap = (int64_t)kMaxBatch * 8;          // history bytes per source column, worst case
+        TaskDev zt{-1, 0, 0, 0, 0};
+        int64_t zt_bytes = 0;
+        for (size_t n = 0; n < far_ix.size(); ++n) {
+            const Stored &x = stored[far_ix[n]];
+            const int sidx = src_of[x.block];
+            const int q2 = pad_row(srcs[sidx].q, prec);
+            const int64_t row_bytes = (int64_t)q2 * eb;
+            const int64_t max_rows =
+                std::max<int64_t>(1, (kStageBytes - 16 - (int64_t)q2 * x_cap) / row_bytes);
+            unsigned char *d = op.d_varena.p + off;
+            gsrc.push_back(x.v);
+            gdst.push_back(d);
+            gbytes.push_back((int32_t)(x.k * row_bytes));
+            for (int l = 0; l < x.k; ++l) {
+                zmap.push_back((int32_t)(zrow0[far_ix[n]] + l));
+                zscale.push_back(x.scale);
+            }
+            for (int l = 0; l < x.k;) {
+                const bool extend = !runs.empty() && zt.block == sidx && runs.back().T == x.T &&
+                                    runs.back().rows < max_rows;
+                if (!extend) {
+                    // a new run; a new task when the source cluster changes or the task is full
+                    if (zt.block != sidx || zt_bytes >= kTaskBytes) {
+                        if (zt.block >= 0) {
+                            zt.item_end = (int32_t)runs.size();
+                            ztasks.push_back(zt);
+                        }
+                        zt = TaskDev{sidx, (int32_t)runs.size(), 0, x.T, 0};
+                        zt_bytes = 0;
+                    }
+                    runs.push_back(RunDev{x.T, 0, d + (int64_t)l * row_bytes, (int64_t)zmap.size() - x.k + l});
+                }
+                const int take = (int)std::min<int64_t>(x.k - l, max_rows - runs.back().rows);
+                runs.back().rows += take;
+                zt_bytes += take * row_bytes;
+                l += take;
+            }
+            off += x.k * row_bytes;
+        }
+        if (zt.block >= 0) {
+            zt.item_end = (int32_t)runs.size();
+            ztasks.push_back(zt);
+        }
+        DArr<const void *> d_gs;
+        DArr<void *> d_gd;
+        DArr<int32_t> d_gb;
+        SEAS_TRY(d_gs.upload(c, gsrc));
+        SEAS_TRY(d_gd.upload(c, gdst));
+        SEAS_TRY(d_gb.upload(c, gbytes));
+        CUDA_TRY(launch_gather(d_gs.p, d_gd.p, d_gb.p, (int)gsrc.size(), c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    vstage.clear();
+    std::stable_sort(ztasks.begin(), ztasks.end(),
+                     [](const TaskDev &x, const TaskDev &y) { return x.T_start < y.T_start; });
+    for (auto &t : ztasks) op.ztask_T.push_back(t.T_start);
+    SEAS_TRY(op.d_runs.upload(c, runs));
+    SEAS_TRY(op.d_ztasks.upload(c, ztasks));
+    SEAS_TRY(op.d_srcs.upload(c, srcs));
+    SEAS_TRY(op.d_zmap.upload(c, zmap));
+    if (prec == kPrecFP16) SEAS_TRY(op.d_zscale.upload(c, zscale));
+
+    // ---- pass 2: work items (<= kItemBytes and kItemRows rows, adjacent in memory) and tasks (runs of items of one
+    // block within one arena chunk, <= kTaskBytes); consecutive far slices of a block merge into one item; each
+    // task owns p partial-sum rows, the k-th task of block b at blk_part[b] + k * p.
     std::vector<ItemDev> items;
     std::vector<TaskDev> tasks;
     size_t s = 0;
     while (s < stored.size()) {
         const int blk = stored[s].block;
         const BlockDev &b = op.blocks_h[blk];
-        const int p2 = pad_row(b.p, prec), q2 = pad_row(b.q, prec);
+        const int p2 = pad_row(b.p, prec);
+        const int64_t row_bytes = (int64_t)p2 * eb;
         TaskDev task{blk, (int32_t)items.size(), 0, stored[s].T, 0};
         int64_t task_bytes = 0;
         int chunk = stored[s].chunk;
+        bool open_far = false;                 // the last item is a far item that may take more rows
         for (; s < stored.size() && stored[s].block == blk; ++s) {
             const Stored &x = stored[s];
             if (task_bytes >= kTaskBytes || x.chunk != chunk) {
@@ -926,19 +1057,35 @@ seas_status build_interaction(seas_op &op) {
                 task = TaskDev{blk, (int32_t)items.size(), 0, x.T, 0};
                 task_bytes = 0;
                 chunk = x.chunk;
+                open_far = false;
             }
             if (x.k < 0) {
                 for (int j = 0; j < b.q; j += drows[blk]) {
                     const int j1 = std::min(b.q, j + drows[blk]);
-                    items.push_back(ItemDev{x.T, -1, j, j1, x.data + (int64_t)j * p2 * eb, x.scale, 0});
+                    items.push_back(ItemDev{x.T, -1, j, j1, x.u + (int64_t)j * row_bytes, x.scale, 0, -1});
                 }
-                task_bytes += (int64_t)b.q * p2 * eb;
+                task_bytes += (int64_t)b.q * row_bytes;
+                open_far = false;
             } else {
-                for (int l = 0; l < x.k; l += group[blk]) {
-                    const int l1 = std::min(x.k, l + group[blk]);
-                    items.push_back(ItemDev{x.T, l1 - l, l, l1, x.data + (int64_t)l * (p2 + q2) * eb, x.scale, 0});
+                for (int l = 0; l < x.k;) {
+                    if (open_far) {
+                        ItemDev &it = items.back();
+                        const int room = (int)std::min<int64_t>(kItemRows - it.k, kItemBytes / row_bytes - it.k);
+                        if (room > 0) {
+                            const int take = std::min(room, x.k - l);
+                            it.k += take;
+                            it.i1 = it.k;
+                            l += take;
+                            continue;
+                        }
+                    }
+                    const int take = (int)std::min<int64_t>(
+                        x.k - l, std::max<int64_t>(1, std::min<int64_t>(kItemRows, kItemBytes / row_bytes)));
+                    items.push_back(ItemDev{x.T, take, 0, take, x.u + (int64_t)l * row_bytes, 1.0f, 0, zrow0[s] + l});
+                    open_far = true;
+                    l += take;
                 }
-                task_bytes += (int64_t)x.k * (p2 + q2) * eb;
+                task_bytes += (int64_t)x.k * row_bytes;
             }
         }
         task.item_end = (int32_t)items.size();
@@ -1121,6 +1268,9 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     int64_t lag_max = -1;            // the oldest active member's step
     for (int b = 0; b < s.B; ++b)
         if (s.active[b]) lag_max = std::max<int64_t>(lag_max, step - s.start[b]);
+    // the interaction's horizon never shrinks (its z rows beyond the horizon must stay as they were: zero)
+    if (lag_max > s.horizon && step == s.n - 1) s.horizon = lag_max;
+    lag_max = std::max(lag_max, std::min<int64_t>(s.horizon, step));
     a.lag_max = lag_max;
     a.ring = op.ring;
     a.ring_stride = s.ring_stride;
@@ -1147,6 +1297,18 @@ StepArgs step_args(seas_scn &s, int64_t step) {
                     : (int)(std::upper_bound(op.task_T.begin(), op.task_T.end(),
                                              (int32_t)std::min<int64_t>(lag_max, INT32_MAX)) -
                             op.task_T.begin());
+    a.runs = op.d_runs.p;
+    a.ztasks = op.d_ztasks.p;
+    a.srcs = op.d_srcs.p;
+    a.zmap = op.d_zmap.p;
+    a.zscale = op.d_zscale.p;
+    a.n_ztasks_active =
+        lag_max < 0 ? 0
+                    : (int)(std::upper_bound(op.ztask_T.begin(), op.ztask_T.end(),
+                                             (int32_t)std::min<int64_t>(lag_max, INT32_MAX)) -
+                            op.ztask_T.begin());
+    a.zbuf = s.zbuf.p;
+    a.pass = 2;
     a.partial = s.partial.p;
     a.n_partial = op.n_partial;
     a.counter = s.counter_err.p;
@@ -1194,7 +1356,12 @@ seas_status scenario_alloc(seas_op *op, int batch, std::unique_ptr<seas_scn> &s)
         SEAS_TRY(s->xring.zero(c->stream));
     }
     SEAS_TRY(s->partial.alloc(c, (size_t)(op->n_partial * batch)));
-    SEAS_TRY(s->counter_err.alloc(c, 2));
+    {
+        const int zb = op->hp.precision == kPrecBF16 || op->hp.precision == kPrecFP16 ? 4 : 8;
+        SEAS_TRY(s->zbuf.alloc(c, (size_t)std::max<int64_t>(16, op->z_rows * batch * zb)));
+        SEAS_TRY(s->zbuf.zero(c->stream));
+    }
+    SEAS_TRY(s->counter_err.alloc(c, 4));
     SEAS_TRY(s->counter_err.zero(c->stream));
     SEAS_TRY(s->slip.alloc(c, (size_t)BN));
     SEAS_TRY(s->slip_prev.alloc(c, (size_t)BN));
@@ -1231,9 +1398,17 @@ extern "C" seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **o
         if (pad_row(max_p, kPrecBF16) > 128)
             return fail(SEAS_EINVAL, "BF16 batches of 5..8 need blocks of at most 128 receivers (widest: %d)", max_p);
     }
-    if ((int64_t)(op->max_q + 8) * batch * xb + 16 + kItemBytes > kStageBytes)
-        return fail(SEAS_EINVAL, "batch %d too large for blocks of %d columns (stage of %d bytes)", batch, op->max_q,
-                    kStageBytes);
+    {
+        // one row of a pass-1 run plus its history slice must fit a pipeline stage (pass-2 items always do)
+        const int eb = elem_bytes(op->hp.precision);
+        for (size_t b = 0; b < op->blocks_h.size(); ++b) {
+            if (!op->block_far[b]) continue;
+            const int64_t q2 = pad_row(op->blocks_h[b].q, op->hp.precision);
+            if (q2 * eb + (q2 * batch * xb + 15) / 16 * 16 + 16 > kStageBytes)
+                return fail(SEAS_EINVAL, "batch %d too large for blocks of %d columns (stage of %d bytes)", batch,
+                            op->blocks_h[b].q, kStageBytes);
+        }
+    }
     CUDA_TRY(cudaSetDevice(op->net->ctx->device));
     std::unique_ptr<seas_scn> s;
     SEAS_TRY(scenario_alloc(op, batch, s));
@@ -1532,7 +1707,8 @@ extern "C" seas_status seas_scenario_save(seas_scn *s, const char *path) {
     seas_status st = SEAS_OK;
     if (fwrite(&h, sizeof h, 1, fp) != 1) st = fail(SEAS_EIO, "short write");
     if (st == SEAS_OK && (fwrite(s->start.data(), sizeof(int64_t), s->B, fp) != (size_t)s->B ||
-                          fwrite(s->active.data(), 1, s->B, fp) != (size_t)s->B))
+                          fwrite(s->active.data(), 1, s->B, fp) != (size_t)s->B ||
+                          fwrite(&s->horizon, sizeof(int64_t), 1, fp) != 1))
         st = fail(SEAS_EIO, "short write");
     if (st == SEAS_OK) st = dump(fp, s->vring.p, s->vring.bytes());
     if (st == SEAS_OK) st = dump(fp, s->slip.p, s->slip.bytes());
@@ -1566,7 +1742,9 @@ extern "C" seas_status seas_scenario_load(seas_op *op, const char *path, seas_sc
     }
     std::vector<int64_t> start(h.B);
     std::vector<char> active(h.B);
-    if (fread(start.data(), sizeof(int64_t), h.B, fp) != (size_t)h.B || fread(active.data(), 1, h.B, fp) != (size_t)h.B) {
+    int64_t horizon = -1;
+    if (fread(start.data(), sizeof(int64_t), h.B, fp) != (size_t)h.B || fread(active.data(), 1, h.B, fp) != (size_t)h.B ||
+        fread(&horizon, sizeof(int64_t), 1, fp) != 1) {
         fclose(fp);
         return fail(SEAS_EIO, "%s: truncated member table", path);
     }
@@ -1591,6 +1769,7 @@ extern "C" seas_status seas_scenario_load(seas_op *op, const char *path, seas_sc
     s->n = h.n;
     s->start = start;
     s->active = active;
+    s->horizon = horizon;
     op->children++;
     *out = s.release();
     return SEAS_OK;

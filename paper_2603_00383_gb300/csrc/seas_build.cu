@@ -244,17 +244,18 @@ __device__ double block_absmax(const double *v, int64_t n, int64_t stride_rows, 
 // Scale putting the largest value near 2^14, inside float16's range with room to spare.
 __device__ __forceinline__ double fp16_scale(double amax) { return amax > 0.0 ? amax / 16384.0 : 1.0; }
 
-// Copies each stored slice into the operator arena in the storage precision, rows padded to 16 bytes
+// Copies each stored slice into the operator arenas in the storage precision, rows padded to 16 bytes
 // (p2 = pad_row(p), q2 = pad_row(q) elements):
-//   dense   -> A^T, q rows of p2;
-//   lowrank -> groups of `group` rank-1 terms l0..l1-1, each group [V^T rows (q2 each)][U^T rows (p2 each)].
+//   dense   -> receiver-side arena at dst: A^T, q rows of p2;
+//   lowrank -> receiver-side arena at dst: U^T, k rows of p2; source-side arena at vdst: V^T, k rows of q2.
 // FP16 stores values divided by a per-slice scale (dense: one; low rank: one for U and one for V); the scale of
 // the product (1 for the other precisions) goes to scales[slice].
 template <int PREC>
 __global__ void k_pack(const BlockDev *__restrict__ blocks, const SliceGen *__restrict__ slices,
                        const SliceOut *__restrict__ out, const double *__restrict__ scratch,
                        const double *__restrict__ factors, const int64_t *__restrict__ dst_off,
-                       typename Store<PREC>::T *__restrict__ dst, float *__restrict__ scales) {
+                       typename Store<PREC>::T *__restrict__ dst, const int64_t *__restrict__ vdst_off,
+                       typename Store<PREC>::T *__restrict__ vdst, float *__restrict__ scales) {
     using T = typename Store<PREC>::T;
     __shared__ double sh[32];
     const SliceGen s = slices[blockIdx.x];
@@ -294,23 +295,27 @@ __global__ void k_pack(const BlockDev *__restrict__ blocks, const SliceGen *__re
     } else if (threadIdx.x == 0) {
         scales[blockIdx.x] = 1.0f;
     }
-    const int64_t n = (int64_t)o.k * (p2 + q2);
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-        const int g = (int)(e / ((int64_t)s.group * (p2 + q2)));     // group index
-        const int l0 = g * s.group;
-        const int nl = min(s.group, o.k - l0);
-        const int64_t r = e - (int64_t)l0 * (p2 + q2);               // offset inside the group
-        double v;
-        if (r < (int64_t)nl * q2) {
-            const int l = l0 + (int)(r / q2), j = (int)(r % q2);
-            v = j < q ? Vt[(int64_t)l * q + j] * inv_v : 0.0;
-        } else {
-            const int64_t r2 = r - (int64_t)nl * q2;
-            const int l = l0 + (int)(r2 / p2), i = (int)(r2 % p2);
-            v = i < p ? Ut[(int64_t)l * p + i] * inv_u : 0.0;
-        }
-        d[e] = Store<PREC>::cv(v);
+    T *vd = vdst + vdst_off[blockIdx.x];
+    const int64_t nu = (int64_t)o.k * p2, nv = (int64_t)o.k * q2;
+    for (int64_t e = threadIdx.x; e < nu; e += blockDim.x) {
+        const int l = (int)(e / p2), i = (int)(e - (int64_t)l * p2);
+        d[e] = Store<PREC>::cv(i < p ? Ut[(int64_t)l * p + i] * inv_u : 0.0);
     }
+    for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) {
+        const int l = (int)(e / q2), j = (int)(e - (int64_t)l * q2);
+        vd[e] = Store<PREC>::cv(j < q ? Vt[(int64_t)l * q + j] * inv_v : 0.0);
+    }
+}
+
+// One warp per run: 16-byte copies.
+__global__ void __launch_bounds__(kThreads) k_gather(const void *const *__restrict__ src, void *const *__restrict__ dst,
+                                                     const int32_t *__restrict__ bytes, int n) {
+    const int w = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const uint4 *s = static_cast<const uint4 *>(src[w]);
+    uint4 *d = static_cast<uint4 *>(dst[w]);
+    const int n16 = bytes[w] >> 4;
+    for (int c = lane; c < n16; c += 32) d[c] = s[c];
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -400,26 +405,37 @@ cudaError_t launch_compress(const BlockDev *blocks, const SliceGen *slices, int 
 
 cudaError_t launch_pack(const BlockDev *blocks, const SliceGen *slices, const SliceOut *out, int n_slices,
                         const double *scratch, const double *factors, const int64_t *dst_off, void *dst,
-                        float *scales, int prec, cudaStream_t s) {
+                        const int64_t *vdst_off, void *vdst, float *scales, int prec, cudaStream_t s) {
     if (n_slices <= 0) return cudaSuccess;
     switch (prec) {
         case kPrecFP64:
             k_pack<kPrecFP64><<<n_slices, kThreads, 0, s>>>(blocks, slices, out, scratch, factors, dst_off,
-                                                            static_cast<double *>(dst), scales);
+                                                            static_cast<double *>(dst), vdst_off,
+                                                            static_cast<double *>(vdst), scales);
             break;
         case kPrecDF64:
             k_pack<kPrecDF64><<<n_slices, kThreads, 0, s>>>(blocks, slices, out, scratch, factors, dst_off,
-                                                            static_cast<float2 *>(dst), scales);
+                                                            static_cast<float2 *>(dst), vdst_off,
+                                                            static_cast<float2 *>(vdst), scales);
             break;
         case kPrecBF16:
             k_pack<kPrecBF16><<<n_slices, kThreads, 0, s>>>(blocks, slices, out, scratch, factors, dst_off,
-                                                            static_cast<__nv_bfloat16 *>(dst), scales);
+                                                            static_cast<__nv_bfloat16 *>(dst), vdst_off,
+                                                            static_cast<__nv_bfloat16 *>(vdst), scales);
             break;
         default:
             k_pack<kPrecFP16><<<n_slices, kThreads, 0, s>>>(blocks, slices, out, scratch, factors, dst_off,
-                                                            static_cast<__half *>(dst), scales);
+                                                            static_cast<__half *>(dst), vdst_off,
+                                                            static_cast<__half *>(vdst), scales);
             break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const void *const *src, void *const *dst, const int32_t *bytes, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int per = kThreads / 32;
+    k_gather<<<(n + per - 1) / per, kThreads, 0, s>>>(src, dst, bytes, n);
     return cudaGetLastError();
 }
 

@@ -12,12 +12,12 @@ constexpr int kMaxFFT = 7168;       // largest N_f: two N_f-point complex buffer
 constexpr int kMaxStages = 16;      // radix stages of one FFT plan
 constexpr int kMaxBlockSide = 1024; // rows / columns of one H-matrix block (4 accumulator rows per thread)
 constexpr int kRowsPerThread = kMaxBlockSide / kThreads;
-constexpr int kMaxItemRank = 128;   // rank-1 terms of one low-rank work item (shared-memory z buffer)
+constexpr int kItemRows = 256;      // rows of one pass-2 item (bounds its staged history / z rows)
 constexpr int kMaxBatch = 8;        // scenarios per scenario handle (one pass of the interaction kernel)
-constexpr int kItemBytes = 24 * 1024;   // largest work item (operator bytes)
+constexpr int kItemBytes = 24 * 1024;   // largest pass-2 item (operator bytes)
 constexpr int kStageBytes = 64 * 1024;  // one shared-memory stage of the interaction pipeline
 constexpr int kStages = 3;              // stages in flight per CTA
-constexpr int kStageItems = 31;         // work items per stage
+constexpr int kStageItems = 31;         // units per stage (one producer lane each)
 constexpr int64_t kTaskBytes = 1 << 20; // operator bytes per task (one deterministic partial sum)
 
 __host__ __device__ inline int pad2(int n) { return n + (n & 1); }
@@ -64,22 +64,42 @@ struct BlockDev {
     int32_t r0, p, c0, q;
 };
 
-// One unit of interaction work: the inner range [i0, i1) of one (block, lag) slice, stored contiguously at `a`
-// (rows padded to 16 bytes: p2 = pad_row(p), q2 = pad_row(q) elements of the storage precision):
-//   dense   (k < 0): rows i0..i1-1 of A^T, each p2 elements:  y += sum_j A^T[j][:] x_{c0+j}
-//   lowrank (k > 0): k = i1 - i0 rows of V^T (each q2 elements) followed by k rows of U^T (each p2 elements):
-//                    y += sum_l U^T[l][:] (V^T[l][:] . x)
-// Consecutive items of a task are adjacent in memory.
+// The interaction runs in two passes per step (two launches of the persistent kernel):
+//   pass 1 (source side): for every far slice (b, T), z = V_{b,T}^T x^{step - T}, with x the slip-rate history of the
+//     block's source columns.  Work is grouped by source cluster: a run holds the V^T rows (q2 elements each) of all
+//     far slices with the same source columns at one lag, so one staged history slice serves all of them; each
+//     row's z goes to the z buffer row given by zmap.
+//   pass 2 (receiver side): for every block, y += sum over its slices of U_{b,T} z (far) or A_{b,T}^T x (dense),
+//     accumulated per task over consecutive lags and written to the task's partial rows.
+// The z buffer of a scenario has one row per row of the pass-2 arena ([row][batch]); rows of dense slices are
+// unused.  Work that needs no history beyond the scenario's start multiplies zeros, so whole tasks are switched on
+// by their first lag only.
+
+// Pass-2 unit: rows of one block stored contiguously at `a` (rows of p2 = pad_row(p) elements of the storage
+// precision).  Consecutive items of a task are adjacent in memory.
+//   dense (k < 0): rows i0..i1-1 of A^T of one lag T:  y += sum_j A^T[j][:] x_{c0+j}^{step-T}
+//   far   (k > 0): k rows of U^T of consecutive lags from T on, whose z rows are zrow .. zrow + k - 1
 struct ItemDev {
     int32_t T;
     int32_t k;
     int32_t i0, i1;
     const void *a;
-    float scale;        // stored values times scale = operator values (1 except FP16)
+    float scale;        // dense: stored values times scale = operator values (1 except FP16); far: 1 (pass 1 scales z)
     int32_t pad;
+    int64_t zrow;
 };
 
-// A run of items of one block (sorted by lag, adjacent in memory) whose partial sums land in one slot:
+// Pass-1 unit: `rows` V^T rows (q2 elements each) at `v`, the far slices of one source cluster at lag T; row r's z
+// goes to z row zmap[map + r] (times zscale[map + r] for FP16).  Consecutive runs of a task are adjacent in memory.
+struct RunDev {
+    int32_t T;
+    int32_t rows;
+    const void *v;
+    int64_t map;
+};
+
+// A run of units whose rows share one partial slot (pass 2: items of one block; pass 1: runs of one source
+// cluster at consecutive lags, `block` then names the source cluster).  Pass 2 partial sums:
 // partial[b * n_partial + part_off + row].
 struct TaskDev {
     int32_t block;
@@ -89,12 +109,17 @@ struct TaskDev {
     int64_t part_off;
 };
 
+// Source cluster of pass 1: columns [c0, c0 + q).
+struct SrcDev {
+    int32_t c0, q;
+};
+
 // One (block, lag) slice produced during the build.
 struct SliceGen {
     int32_t block;
     int32_t T;
     int32_t far;        // 1: admissible (compress), 0: near (store dense)
-    int32_t group;      // rank-1 terms per stored low-rank item (packing layout)
+    int32_t pad;
     int64_t scratch;    // first double of its p*q entries (layout A^T: q rows of p) in the scratch buffers
 };
 
@@ -121,7 +146,9 @@ cudaError_t launch_compress(const BlockDev *blocks, const SliceGen *slices, int 
                             double *resid, double *factors, SliceOut *out, double tol, cudaStream_t s);
 cudaError_t launch_pack(const BlockDev *blocks, const SliceGen *slices, const SliceOut *out, int n_slices,
                         const double *scratch, const double *factors, const int64_t *dst_off, void *dst,
-                        float *scales, int prec, cudaStream_t s);
+                        const int64_t *vdst_off, void *vdst, float *scales, int prec, cudaStream_t s);
+// dst[i] = src[i] for n runs of bytes[i] bytes (16-byte multiples, 16-byte aligned)
+cudaError_t launch_gather(const void *const *src, void *const *dst, const int32_t *bytes, int n, cudaStream_t s);
 cudaError_t launch_spectral_tables(const ModeDev *modes, int n_modes, const int64_t *g_prefix, int64_t n_g,
                                    const double *mode_L, double cs_dt, const double *gl_x, const double *gl_w,
                                    int gl_n, double *G, double *w, cudaStream_t s);
@@ -153,10 +180,18 @@ struct StepArgs {
     const BlockDev *blocks;
     const ItemDev *items;
     const TaskDev *tasks;
-    int n_tasks_active;           // tasks with T_start <= step (a prefix of the T_start-sorted list)
+    int n_tasks_active;           // pass-2 tasks with T_start <= lag_max (a prefix of the T_start-sorted list)
+    const RunDev *runs;           // pass 1
+    const TaskDev *ztasks;
+    const SrcDev *srcs;
+    const int32_t *zmap;
+    const float *zscale;          // FP16 only
+    int n_ztasks_active;
+    void *zbuf;                   // [z rows][B] in the arithmetic's dot type (double, float2 or float)
+    int pass;                     // 1 or 2: which pass a launch of the interaction kernel runs
     double *partial;              // [B][n_partial]
     int64_t n_partial;
-    int *counter;                 // dynamic task counter (reset by the reduction)
+    int *counter;                 // [0]: pass-2 task counter, [2]: pass-1 task counter (reset by the reduction)
     int *err;                     // device error word (bounded waits that ran out)
     uint64_t wait_ns;             // bound of one device wait (wall clock), per scenario
     // reduction: per element the blocks it receives from; per block its tasks' first lags

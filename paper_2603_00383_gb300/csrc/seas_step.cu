@@ -271,38 +271,36 @@ template <int BT> struct InterShape {
     static constexpr int NT = NC + 32;
     static constexpr int RV = CW == 8 ? 8 : 4;
 };
-constexpr int kMaxStageRanks = 192;     // rank-1 terms of all low-rank items of one stage (z buffer), B <= 4
-constexpr int kMaxStageRanks8 = 96;     // the same for batches of 5..8 (the z buffers are double-buffered)
-
+// One unit in a stage: pass 2 -- an item (k < 0: dense rows i0..i1-1 of A^T, k > 0: far rows of U^T); pass 1 -- a
+// run (k = its V^T rows).  Rows of all units of a stage are numbered consecutively (row_end: running count).
 struct StageItem {
     int32_t k, i0, i1;
-    int32_t data_off, x_off;     // byte offsets in the stage (x_off already includes the 16-byte round-down)
-    int32_t row_end;             // running count of row updates (phase B) through this item
-    int32_t z_end;               // running count of rank rows (phase A) through this item
+    int32_t data_off, x_off;     // byte offsets in the stage of the unit's operator rows and of its history / z rows
+    int32_t row_end;
     float scale;
+    int32_t pad;
+    int64_t map;                 // pass 1: first zmap entry of the run
 };
 
 struct StageInfo {
     int32_t task;                // -1: no more work
-    int32_t n;                   // items in the stage
-    int32_t flush;               // last stage of the task
-    int32_t p, q, r0, c0;
-    int32_t n_rows, n_zrows;     // row updates and rank rows of the stage
+    int32_t n;                   // units in the stage
+    int32_t flush;               // last stage of the task (pass 2)
+    int32_t p, q, r0, c0;        // pass 2: the block; pass 1: q and c0 of the source cluster (p = 0, r0 = 0)
+    int32_t n_rows;              // rows of the stage's units
     int64_t part_off;
     StageItem it[kStageItems];
 };
 
 // Dynamic shared memory of the interaction kernel for batch width BT, in bytes from the start: the stages, their
-// descriptors, the double-buffered z rows, the flush buffer and the full/empty mbarriers.  The kernel and its
-// launcher both use this, and the kernel checks the end against the size it was launched with.
+// descriptors, the flush buffer and the full/empty mbarriers.  The kernel and its launcher both use this, and the
+// kernel checks the end against the size it was launched with.
 template <int BT> struct InterLayout {
-    static constexpr int kZRows = BT > 4 ? kMaxStageRanks8 : kMaxStageRanks;
     static constexpr size_t info = (size_t)kStages * kStageBytes;
-    static constexpr size_t zs = info + kStages * sizeof(StageInfo);
-    static constexpr size_t red = zs + (size_t)2 * kZRows * BT * 8;
+    static constexpr size_t red = info + kStages * sizeof(StageInfo);
     static constexpr size_t bars = red + (size_t)InterShape<BT>::NC * InterShape<BT>::RV * sizeof(double);
     static constexpr size_t total = bars + 2 * kStages * sizeof(uint64_t);
-    static_assert(sizeof(StageInfo) % 8 == 0 && zs % 8 == 0 && red % 8 == 0 && bars % 8 == 0, "8-byte alignment");
+    static_assert(sizeof(StageInfo) % 8 == 0 && red % 8 == 0 && bars % 8 == 0, "8-byte alignment");
     static_assert(total <= 227 * 1024, "shared memory per CTA");
 };
 
@@ -656,60 +654,22 @@ __device__ __forceinline__ void mask_a_k(uint32_t (&a)[4], int tg, int kvalid) {
     }
 }
 
-// Consumer warps of k_interaction<BF16, 8> (same stage protocol as the CUDA-core consumers: phase A of stage g + 1
-// and phase B of stage g between two barriers).  Phase A: each (low-rank item, 16 rank rows) unit is one warp's
-// Z tile over the item's source columns.  Phase B: the task's receivers form mt 16-row tiles; warp w owns tile
-// w mod mtp in group w / mtp (mtp = mt rounded up to 1, 2, 4 or 8) and the stage's (item, 16-row chunk) units are
-// dealt round-robin to the groups; at the task's end the groups are added in a fixed order.  Blocks are at most 128
-// receivers wide here (scenario creation checks).
-template <int CW, int ZR>
-__device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, unsigned char *stage_mem, float *zs,
-                                            double *red, uint64_t *full, uint64_t *empty, int *sh_flag) {
+// Consumer warps of k_interaction<BF16, 8, PASS>: one consumer barrier per stage (it also hands the previous stage
+// back to the producer).
+//   Pass 1: each (run, 16 rows) piece is one warp's Z tile over the run's source columns; its rows go to the z rows
+//   that zmap gives.
+//   Pass 2: the task's receivers form mt 16-row tiles; warp w owns tile w mod mtp in group w / mtp (mtp = mt
+//   rounded up to 1, 2, 4 or 8) and the stage's (unit, 16-row chunk) pieces are dealt round-robin to the groups; at
+//   the task's end the groups are added in a fixed order.  Blocks are at most 128 receivers wide here (scenario
+//   creation checks).
+template <int CW, int PASS>
+__device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, unsigned char *stage_mem, double *red,
+                                            uint64_t *full, uint64_t *empty, int *sh_flag) {
     constexpr int NC = CW * 32;
     constexpr int B8 = 8;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int g = lane >> 2, tg = lane & 3, mi = lane >> 3, rr = lane & 7;
-
-    auto phase_a = [&](const StageInfo &sx, const unsigned char *bx, float *zout) {
-        if (sx.n_zrows <= 0) return;
-        const int q2 = pad_row(sx.q, kPrecBF16);
-        int u = 0;
-        for (int m = 0; m < sx.n; ++m) {
-            const StageItem &it = sx.it[m];
-            if (it.k <= 0) continue;
-            const int k = it.k, zb = it.z_end - k;
-            const __nv_bfloat16 *V = reinterpret_cast<const __nv_bfloat16 *>(bx + it.data_off);
-            const float *x = reinterpret_cast<const float *>(bx + it.x_off);
-            for (int r0 = 0; r0 < k; r0 += 16, ++u) {
-                if (u % CW != warp) continue;
-                float d[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int K0 = 0; K0 < q2; K0 += 16) {
-                    uint32_t af[4];
-                    ldsm_x4(af, V + (int64_t)(r0 + (mi & 1) * 8 + rr) * q2 + K0 + (mi >> 1) * 8);
-                    mask_a_k(af, tg, q2 - K0);
-                    float xv[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int j = K0 + 2 * tg + (e & 1) + (e >= 2 ? 8 : 0);
-                        xv[e] = j < q2 && g < a.B ? x[j * a.B + g] : 0.f;
-                    }
-                    uint32_t bh[2], bl[2];
-                    split_b(xv, bh, bl);
-                    mma_bf16(d, af, bh[0], bh[1]);
-                    mma_bf16(d, af, bl[0], bl[1]);
-                }
-                if (r0 + g < k) {
-                    zout[(zb + r0 + g) * B8 + 2 * tg] = d[0] * it.scale;
-                    zout[(zb + r0 + g) * B8 + 2 * tg + 1] = d[1] * it.scale;
-                }
-                if (r0 + g + 8 < k) {
-                    zout[(zb + r0 + g + 8) * B8 + 2 * tg] = d[2] * it.scale;
-                    zout[(zb + r0 + g + 8) * B8 + 2 * tg + 1] = d[3] * it.scale;
-                }
-            }
-        }
-    };
-
+    float *zg = static_cast<float *>(a.zbuf);
     int cur = -1, mt = 1, mtp = 1, G = CW, grp = 0, tile = 0;
     bool act = true;
     float2 acc[4];
@@ -719,61 +679,81 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
         acc[v] = make_float2(0.f, 0.f);
         dst[v] = 0.f;
     }
-    if (t == 0) *sh_flag = mbar_wait(&full[0], 0, a.err, a.wait_ns) ? 0 : 1;
-    consumer_sync<NC>();
-    if (*sh_flag) return;
-    if (info[0].task >= 0) phase_a(info[0], stage_mem, zs);
     for (int gi = 0;; ++gi) {
         const int slot = gi % kStages;
-        if (t == 0 && info[slot].task >= 0)
-            *sh_flag = mbar_wait(&full[(gi + 1) % kStages], ((gi + 1) / kStages) & 1, a.err, a.wait_ns) ? 0 : 1;
+        if (t == 0) *sh_flag = mbar_wait(&full[slot], (gi / kStages) & 1, a.err, a.wait_ns) ? 0 : 1;
         consumer_sync<NC>();
         if (*sh_flag) return;
         if (t == 0 && gi > 0) mbar_arrive(&empty[(gi - 1) % kStages]);
         const StageInfo &si = info[slot];
-        const int task = si.task;
-        if (task < 0) break;
-        {
-            const int ns = (gi + 1) % kStages;
-            if (info[ns].task >= 0) phase_a(info[ns], stage_mem + (size_t)ns * kStageBytes, zs + ((gi + 1) & 1) * ZR * B8);
-        }
-        const float *zcur = zs + (gi & 1) * ZR * B8;
-        const int p = si.p, p2 = pad_row(p, kPrecBF16), q2 = pad_row(si.q, kPrecBF16);
-        if (task != cur) {
-            cur = task;
-            mt = (p2 + 15) / 16;
-            mtp = mt <= 1 ? 1 : mt <= 2 ? 2 : mt <= 4 ? 4 : 8;
-            G = CW / mtp;
-            grp = warp / mtp;
-            tile = warp % mtp;
-            act = tile < mt;
-        }
+        if (si.task < 0) break;
         const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
-        // phase B
-        {
+        if constexpr (PASS == 1) {
+            const int q2 = pad_row(si.q, kPrecBF16);
+            int u = 0;
+            for (int m = 0; m < si.n; ++m) {
+                const StageItem &it = si.it[m];
+                const int rows = it.k;
+                const __nv_bfloat16 *V = reinterpret_cast<const __nv_bfloat16 *>(base + it.data_off);
+                const float *x = reinterpret_cast<const float *>(base + it.x_off);
+                for (int r0 = 0; r0 < rows; r0 += 16, ++u) {
+                    if (u % CW != warp) continue;
+                    float d[4] = {0.f, 0.f, 0.f, 0.f};
+                    const int arow = min(r0 + (mi & 1) * 8 + rr, rows - 1);     // rows past the run: not read
+                    for (int K0 = 0; K0 < q2; K0 += 16) {
+                        uint32_t af[4];
+                        ldsm_x4(af, V + (int64_t)arow * q2 + K0 + (mi >> 1) * 8);
+                        mask_a_k(af, tg, q2 - K0);
+                        float xv[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int j = K0 + 2 * tg + (e & 1) + (e >= 2 ? 8 : 0);
+                            xv[e] = j < q2 && g < a.B ? x[j * a.B + g] : 0.f;
+                        }
+                        uint32_t bh[2], bl[2];
+                        split_b(xv, bh, bl);
+                        mma_bf16(d, af, bh[0], bh[1]);
+                        mma_bf16(d, af, bl[0], bl[1]);
+                    }
+                    // D fragment: v = 0, 1 -> row g, scenario 2 tg + v; v = 2, 3 -> row g + 8
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int row = r0 + g + (v >= 2 ? 8 : 0), col = 2 * tg + (v & 1);
+                        if (row < rows && col < a.B) zg[(int64_t)a.zmap[it.map + row] * a.B + col] = d[v];
+                    }
+                }
+            }
+        } else {
+            const int p = si.p, p2 = pad_row(p, kPrecBF16);
+            if (si.task != cur) {
+                cur = si.task;
+                mt = (p2 + 15) / 16;
+                mtp = mt <= 1 ? 1 : mt <= 2 ? 2 : mt <= 4 ? 4 : 8;
+                G = CW / mtp;
+                grp = warp / mtp;
+                tile = warp % mtp;
+                act = tile < mt;
+            }
             int u = 0;
             const int i0 = tile * 16;
             for (int m = 0; m < si.n; ++m) {
                 const StageItem &it = si.it[m];
-                const bool dense = it.k < 0;
-                const int rows = dense ? it.i1 - it.i0 : it.k;
-                const __nv_bfloat16 *S = reinterpret_cast<const __nv_bfloat16 *>(base + it.data_off) +
-                                         (dense ? 0 : (int64_t)it.k * q2);
-                // history rows: x has the batch's own stride, z rows are BT = 8 wide
-                const float *src = dense ? reinterpret_cast<const float *>(base + it.x_off)
-                                         : zcur + (int64_t)(it.z_end - it.k) * B8;
-                const int sst = dense ? a.B : B8;
-                const float sc = dense ? it.scale : 1.f;
+                const int rows = it.k < 0 ? it.i1 - it.i0 : it.k;
+                const __nv_bfloat16 *S = reinterpret_cast<const __nv_bfloat16 *>(base + it.data_off);
+                // B operand rows: history values (dense) or z values (far), both [rows][B]
+                const float *src = reinterpret_cast<const float *>(base + it.x_off);
+                const float sc = it.k < 0 ? it.scale : 1.f;
                 for (int k0 = 0; k0 < rows; k0 += 16, ++u) {
                     if (u % G != grp || !act) continue;
                     uint32_t af[4];
-                    ldsm_x4_t(af, S + (int64_t)(k0 + (mi >> 1) * 8 + rr) * p2 + i0 + (mi & 1) * 8);
+                    const int arow = min(k0 + (mi >> 1) * 8 + rr, rows - 1);    // rows past the unit: not read
+                    ldsm_x4_t(af, S + (int64_t)arow * p2 + i0 + (mi & 1) * 8);
                     mask_a_k(af, tg, rows - k0);
                     float bv[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int r = k0 + 2 * tg + (e & 1) + (e >= 2 ? 8 : 0);
-                        bv[e] = r < rows && g < a.B ? src[r * sst + g] * sc : 0.f;
+                        bv[e] = r < rows && g < a.B ? src[r * a.B + g] * sc : 0.f;
                     }
                     uint32_t bh[2], bl[2];
                     split_b(bv, bh, bl);
@@ -786,33 +766,33 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
                 PTHalf<__nv_bfloat16>::kahan(acc[v], dst[v]);
                 dst[v] = 0.f;
             }
-        }
-        if (si.flush) {
-            // D fragment: v = 0, 1 -> receiver row g, scenario 2 tg + v; v = 2, 3 -> row g + 8.  Groups added in a
-            // fixed order by the thread that owns each (receiver, scenario).
-            const int64_t part_off = si.part_off;
+            if (si.flush) {
+                // D fragment: v = 0, 1 -> receiver row g, scenario 2 tg + v; v = 2, 3 -> row g + 8.  Groups added in
+                // a fixed order by the thread that owns each (receiver, scenario).
+                const int64_t part_off = si.part_off;
 #pragma unroll
-            for (int v = 0; v < 4; ++v)
-                red[(warp * 32 + lane) * 4 + v] = act ? (double)acc[v].x - (double)acc[v].y : 0.0;
-            consumer_sync<NC>();
-            for (int o = t; o < p2 * B8; o += NC) {
-                const int i = o >> 3, nn = o & 7, ti = i >> 4, ii = i & 15;
-                const int lo = (ii & 7) * 4 + (nn >> 1), reg = (ii >> 3) * 2 + (nn & 1);
-                if (i < p && nn < a.B) {
-                    double sum = 0.0;
-                    for (int gg = 0; gg < G; ++gg) sum += red[((gg * mtp + ti) * 32 + lo) * 4 + reg];
-                    a.partial[(int64_t)nn * a.n_partial + part_off + i] = sum;
+                for (int v = 0; v < 4; ++v)
+                    red[(warp * 32 + lane) * 4 + v] = act ? (double)acc[v].x - (double)acc[v].y : 0.0;
+                consumer_sync<NC>();
+                for (int o = t; o < p2 * B8; o += NC) {
+                    const int i = o >> 3, nn = o & 7, ti = i >> 4, ii = i & 15;
+                    const int lo = (ii & 7) * 4 + (nn >> 1), reg = (ii >> 3) * 2 + (nn & 1);
+                    if (i < p && nn < a.B) {
+                        double sum = 0.0;
+                        for (int gg = 0; gg < G; ++gg) sum += red[((gg * mtp + ti) * 32 + lo) * 4 + reg];
+                        a.partial[(int64_t)nn * a.n_partial + part_off + i] = sum;
+                    }
                 }
-            }
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[v] = make_float2(0.f, 0.f);
-            cur = -1;
+                for (int v = 0; v < 4; ++v) acc[v] = make_float2(0.f, 0.f);
+                cur = -1;
+            }
         }
     }
 }
 
 // [tensor-core consumers: end]
-template <int PREC, int BT>
+template <int PREC, int BT, int PASS>
 __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs a) {
     constexpr int CW = InterShape<BT>::CW, NC = InterShape<BT>::NC, RV = InterShape<BT>::RV;
     using T = PT<PREC>;
@@ -820,20 +800,20 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
     using X = typename T::X;
     using Z = typename T::Z;
     using Acc = typename T::Acc;
+    static_assert(sizeof(X) == sizeof(Z), "history and z values are staged alike");
     constexpr int SB = (int)sizeof(S);
     constexpr int XB = (int)sizeof(X);
     constexpr int XA = 16 / XB;                     // history elements per 16 bytes
     extern __shared__ __align__(128) unsigned char smem_raw[];
     using LY = InterLayout<BT>;
-    constexpr int kZRows = LY::kZRows;
     unsigned char *stage_mem = smem_raw;                                            // kStages x kStageBytes
     StageInfo *info = reinterpret_cast<StageInfo *>(smem_raw + LY::info);
-    Z *zs = reinterpret_cast<Z *>(smem_raw + LY::zs);                              // [2][kZRows][BT]
     double *red = reinterpret_cast<double *>(smem_raw + LY::red);                  // [NC][RV]
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + LY::bars);
     uint64_t *empty = full + kStages;
     __shared__ int sh_flag;
     const X *xring = PREC == kPrecFP64 ? reinterpret_cast<const X *>(a.vring) : reinterpret_cast<const X *>(a.xring);
+    const Z *zbuf = reinterpret_cast<const Z *>(a.zbuf);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -856,14 +836,33 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
 
     if (warp == CW) {
         // ------------------------------------------------------------------ producer warp
-        // Operator bytes of a stage: one bulk copy (lane 0).  History slices x: 16-byte cp.async over the 32
-        // lanes, each lane arriving on the stage barrier when its copies have landed.
-        // Lane l holds the descriptor of item it + l; after a stage of n items the descriptors shift down by n
-        // and the tail is fetched at once, so its latency overlaps the wait for the next free stage.
+        // A task's units are adjacent in memory: their operator rows go in one bulk copy per stage (lane 0).  The
+        // history (pass 1 runs, pass 2 dense items) or z rows (pass 2 far items) of each unit are copied by the
+        // whole warp with 16-byte cp.async when aligned; each lane arrives on the stage barrier when its copies
+        // have landed.  Lane l holds the descriptor of unit it + l; after a stage of n units the descriptors shift
+        // down by n and the tail is fetched at once.
+        const int n_active = PASS == 1 ? a.n_ztasks_active : a.n_tasks_active;
+        const TaskDev *tasks = PASS == 1 ? a.ztasks : a.tasks;
         int task = -1, it = 0, ie = 0;
         TaskDev td{};
-        BlockDev bd{};
-        ItemDev item{};
+        int p = 0, q = 0, r0 = 0, c0 = 0;
+        struct Unit {
+            int32_t T, k, i0, i1;
+            const void *a;
+            float scale;
+            int64_t map;       // pass 1: zmap offset; pass 2: first z row (far)
+        } u{};
+        auto load = [&](int idx) {
+            Unit r{};
+            if (PASS == 1) {
+                const RunDev rd = a.runs[idx];
+                r = Unit{rd.T, rd.rows, 0, rd.rows, rd.v, 1.f, rd.map};
+            } else {
+                const ItemDev id = a.items[idx];
+                r = Unit{id.T, id.k, id.i0, id.i1, id.a, id.scale, id.zrow};
+            }
+            return r;
+        };
         bool have = false;                          // descriptors of `it` are loaded
         for (int g = 0;; ++g) {
             const int slot = g % kStages;
@@ -874,9 +873,9 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
             }
             if (it >= ie) {                        // next task
                 int t = 0;
-                if (lane == 0) t = atomicAdd(a.counter, 1);
+                if (lane == 0) t = atomicAdd(PASS == 1 ? a.counter + 2 : a.counter, 1);
                 t = __shfl_sync(0xffffffffu, t, 0);
-                if (t >= a.n_tasks_active) {
+                if (t >= n_active) {
                     if (lane == 0) info[slot].task = -1;
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&full[slot]);
@@ -884,125 +883,133 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
                     return;
                 }
                 task = t;
-                td = a.tasks[t];
-                bd = a.blocks[td.block];
+                td = tasks[t];
+                if (PASS == 1) {
+                    const SrcDev sd = a.srcs[td.block];
+                    p = 0; r0 = 0; q = sd.q; c0 = sd.c0;
+                } else {
+                    const BlockDev bd = a.blocks[td.block];
+                    p = bd.p; r0 = bd.r0; q = bd.q; c0 = bd.c0;
+                }
                 it = td.item_begin;
                 ie = td.item_end;
                 have = false;
             }
-            if (!have && it + lane < ie) item = a.items[it + lane];
-            const bool valid = it + lane < ie && item.T <= a.lag_max;
-            const int p2 = pad_row(bd.p, PREC), q2 = pad_row(bd.q, PREC);
-            int data_bytes = 0, x_bytes = 0, nrow = 0, nz = 0;
-            int64_t xs_start = 0;
-            int x_count = 0;
+            if (!have && it + lane < ie) u = load(it + lane);
+            const bool valid = it + lane < ie;
+            const int w2 = PASS == 1 ? pad_row(q, PREC) : pad_row(p, PREC);     // operator row length
+            int data_bytes = 0, x_bytes = 0, nrow = 0;
             if (valid) {
-                const int rows = item.i1 - item.i0;
-                data_bytes = SB * rows * (item.k < 0 ? p2 : p2 + q2);
-                const int e0 = bd.c0 + (item.k < 0 ? item.i0 : 0);
-                xs_start = (int64_t)e0 * a.B;
-                x_count = (item.k < 0 ? rows : bd.q) * a.B;           // history values copied
-                const int x_span = (item.k < 0 ? rows : q2) * a.B;    // values the consumers read (zero tail)
-                x_bytes = (XB * x_span + 15) / 16 * 16;
-                nrow = rows;
-                nz = item.k > 0 ? rows : 0;
+                nrow = u.k < 0 ? u.i1 - u.i0 : u.k;
+                data_bytes = SB * nrow * w2;
+                const int span = (PASS == 1 ? pad_row(q, PREC) : nrow) * a.B;
+                x_bytes = (XB * span + 15) / 16 * 16;
             }
-            // items in the stage: the longest prefix of valid lanes (at most kStageItems) whose bytes and rank
-            // rows fit
-            const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-            const int nvalid = __ffs(~vmask) - 1 < 0 ? 32 : __ffs(~vmask) - 1;      // leading run of valid lanes
-            int incl = data_bytes + x_bytes, zincl = nz;
+            // units in the stage: the longest prefix of valid lanes (at most kStageItems) whose bytes fit
+            int incl = data_bytes + x_bytes;
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                const int r = __shfl_up_sync(0xffffffffu, zincl, o);
-                if (lane >= o) {
-                    incl += v;
-                    zincl += r;
-                }
+                if (lane >= o) incl += v;
             }
-            const unsigned fit = __ballot_sync(0xffffffffu, lane < nvalid && lane < kStageItems &&
-                                                                incl <= kStageBytes && zincl <= kZRows);
+            const unsigned fit = __ballot_sync(0xffffffffu, valid && lane < kStageItems && incl <= kStageBytes);
             const int n = __ffs(~fit) - 1 < 0 ? 32 : __ffs(~fit) - 1;
+            if (n == 0) {                          // a unit larger than a stage (the build rules this out): stop
+                if (lane == 0) {
+                    atomicExch(a.err, 3);
+                    info[slot].task = -1;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[slot]);
+                cp_async_arrive(&full[slot]);
+                return;
+            }
             const bool in = lane < n;
             int dincl = in ? data_bytes : 0, xincl = in ? x_bytes : 0, rincl = in ? nrow : 0;
-            zincl = in ? nz : 0;
             for (int o = 1; o < 32; o <<= 1) {
                 const int d = __shfl_up_sync(0xffffffffu, dincl, o);
                 const int x = __shfl_up_sync(0xffffffffu, xincl, o);
                 const int r = __shfl_up_sync(0xffffffffu, rincl, o);
-                const int z = __shfl_up_sync(0xffffffffu, zincl, o);
                 if (lane >= o) {
                     dincl += d;
                     xincl += x;
                     rincl += r;
-                    zincl += z;
                 }
             }
             const int total_data = __shfl_sync(0xffffffffu, dincl, 31);
-            const int total_x = __shfl_sync(0xffffffffu, xincl, 31);
             const int total_rows = __shfl_sync(0xffffffffu, rincl, 31);
-            const int total_z = __shfl_sync(0xffffffffu, zincl, 31);
-            // the task is finished when the next item is missing or not yet causal (or, defensively, when no
-            // item fits: the cursor must always advance)
-            const bool next_valid =
-                n > 0 && n < 32 && __shfl_sync(0xffffffffu, (int)valid, n < 32 ? n : 31) != 0;
             StageInfo *si = &info[slot];
             if (lane == 0) {
                 si->task = task;
                 si->n = n;
-                si->flush = next_valid ? 0 : 1;
-                si->p = bd.p;
-                si->q = bd.q;
-                si->r0 = bd.r0;
-                si->c0 = bd.c0;
+                si->flush = it + n >= ie ? 1 : 0;
+                si->p = p;
+                si->q = q;
+                si->r0 = r0;
+                si->c0 = c0;
                 si->n_rows = total_rows;
-                si->n_zrows = total_z;
                 si->part_off = td.part_off;
             }
             const int data_off = dincl - (in ? data_bytes : 0);
             const int x_off = total_data + xincl - (in ? x_bytes : 0);
-            if (in) si->it[lane] = StageItem{item.k, item.i0, item.i1, data_off, x_off, rincl, zincl, item.scale};
+            if (in) si->it[lane] = StageItem{u.k, u.i0, u.i1, data_off, x_off, rincl, u.scale, 0, u.map};
             unsigned char *dst = stage_mem + (size_t)slot * kStageBytes;
-            // each lane stages its own item's history slice.  First the part of its x area past the copied
-            // values is zeroed (padding columns of V^T multiply it): plain shared stores, published by lane 0's
-            // arrive below.
-            X *xd = reinterpret_cast<X *>(dst + x_off);
+            // source, count and span (count plus the zero tail that padding columns multiply) of each unit's
+            // history / z values
+            const X *xsrc = nullptr;
+            int xcnt = 0, xspan = 0;
             if (in) {
-                const int span = x_bytes / XB;
-                for (int c = x_count; c < span; ++c) xd[c] = X{};
+                if (PASS == 2 && u.k > 0) {
+                    xsrc = reinterpret_cast<const X *>(zbuf + u.map * a.B);
+                    xcnt = xspan = nrow * a.B;
+                } else {
+                    // lags past the step (whole tasks are switched on) read a slot not yet written: zeros
+                    const int64_t back = (a.step - u.T) % a.ring;
+                    const int slot_v = (int)(back < 0 ? back + a.ring : back);
+                    const int e0 = c0 + (PASS == 1 ? 0 : u.i0);
+                    xsrc = xring + (int64_t)slot_v * a.ring_stride + (int64_t)e0 * a.B;
+                    xcnt = (PASS == 1 ? q : nrow) * a.B;
+                    xspan = (PASS == 1 ? pad_row(q, PREC) : nrow) * a.B;
+                }
+            }
+            // zero tails first (plain shared stores, published by lane 0's arrive below)
+            for (int m = 0; m < n; ++m) {
+                const int cnt = __shfl_sync(0xffffffffu, xcnt, m), span = __shfl_sync(0xffffffffu, xspan, m);
+                X *xd = reinterpret_cast<X *>(dst + __shfl_sync(0xffffffffu, x_off, m));
+                for (int c = cnt + lane; c < span; c += 32) xd[c] = X{};
             }
             __syncwarp();
             if (lane == 0) mbar_arrive_tx(&full[slot], (uint32_t)total_data);
             __syncwarp();
-            // lane 0 holds item `it`, the first of the n adjacent items: their operator bytes in one bulk copy
-            if (lane == 0 && total_data > 0) bulk_g2s(dst, item.a, (uint32_t)total_data, &full[slot]);
-            // history values from the item's ring row, landing on a 16-byte boundary of the stage: 16-byte copies
-            // when the source is 16-byte aligned too, element copies otherwise
-            if (in) {
-                const int slot_v = (int)((a.step - item.T) % a.ring);
-                const X *src = xring + (int64_t)slot_v * a.ring_stride + xs_start;
-                int c = 0;
+            // lane 0 holds unit `it`, the first of the n adjacent units: their operator bytes in one bulk copy
+            if (lane == 0 && total_data > 0) bulk_g2s(dst, u.a, (uint32_t)total_data, &full[slot]);
+            for (int m = 0; m < n; ++m) {
+                const int cnt = __shfl_sync(0xffffffffu, xcnt, m);
+                const X *src = reinterpret_cast<const X *>(
+                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(xsrc), m));
+                X *xd = reinterpret_cast<X *>(dst + __shfl_sync(0xffffffffu, x_off, m));
                 if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-                    for (; c + XA <= x_count; c += XA) cp_async16(xd + c, src + c);
+                    const int n16 = cnt / XA;
+                    for (int c = lane; c < n16; c += 32) cp_async16(xd + c * XA, src + c * XA);
+                    for (int c = n16 * XA + lane; c < cnt; c += 32) cp_async_elem<XB>(xd + c, src + c);
+                } else {
+                    for (int c = lane; c < cnt; c += 32) cp_async_elem<XB>(xd + c, src + c);
                 }
-                for (; c < x_count; ++c) cp_async_elem<XB>(xd + c, src + c);
             }
             cp_async_arrive(&full[slot]);
             it += n;
-            if (!next_valid) it = ie;              // remaining items are not causal yet: task done
-            // shift the descriptors of items it .. it + 31 down and fetch the tail now
+            // shift the descriptors of units it .. it + 31 down and fetch the tail now
             if (it < ie) {
-                ItemDev nxt;
-                nxt.T = __shfl_sync(0xffffffffu, item.T, (lane + n) & 31);
-                nxt.k = __shfl_sync(0xffffffffu, item.k, (lane + n) & 31);
-                nxt.i0 = __shfl_sync(0xffffffffu, item.i0, (lane + n) & 31);
-                nxt.i1 = __shfl_sync(0xffffffffu, item.i1, (lane + n) & 31);
-                nxt.scale = __shfl_sync(0xffffffffu, item.scale, (lane + n) & 31);
-                nxt.a = reinterpret_cast<const void *>(
-                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(item.a), (lane + n) & 31));
-                nxt.pad = 0;
-                if (lane + n < 32) item = nxt;
-                else if (it + lane < ie) item = a.items[it + lane];
+                Unit nx;
+                nx.T = __shfl_sync(0xffffffffu, u.T, (lane + n) & 31);
+                nx.k = __shfl_sync(0xffffffffu, u.k, (lane + n) & 31);
+                nx.i0 = __shfl_sync(0xffffffffu, u.i0, (lane + n) & 31);
+                nx.i1 = __shfl_sync(0xffffffffu, u.i1, (lane + n) & 31);
+                nx.scale = __shfl_sync(0xffffffffu, u.scale, (lane + n) & 31);
+                nx.a = reinterpret_cast<const void *>(
+                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(u.a), (lane + n) & 31));
+                nx.map = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)u.map, (lane + n) & 31);
+                if (lane + n < 32) u = nx;
+                else if (it + lane < ie) u = load(it + lane);
                 have = true;
             } else {
                 have = false;
@@ -1012,331 +1019,323 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
 
     // [tensor-core consumers: begin]
     if constexpr (PREC == kPrecBF16 && BT == 8) {
-        consume_mma<CW, kZRows>(a, info, stage_mem, reinterpret_cast<float *>(zs), red, full, empty, &sh_flag);
+        consume_mma<CW, PASS>(a, info, stage_mem, red, full, empty, &sh_flag);
         return;
     }
     // [tensor-core consumers: end]
     // ---------------------------------------------------------------------- consumer warps
-    // Thread t works in group t / P and owns the VE-wide column vectors (t mod P) + s P, s < nvt, of the block's
-    // rows (P a power of two, G = NC / P groups for NC consumer threads).  The stage's row updates (rows of A^T times x_j, rows of U^T
-    // times z_l) form one flat list dealt round-robin to the groups; the rank rows of phase A a flat list dealt
-    // to lane groups.  A monotone cursor maps a flat index to its item.  BF16/FP16: plain FP32 partial sums
-    // inside a stage, added into the Kahan-compensated accumulator once per stage.
-    constexpr int VE = VecWidth<PREC, BT>::value;
-    // vectors per thread and row: aim at 8 multiply-adds per row (fewer index operations per product); at
-    // least enough vectors for the widest block when all NC consumers share a row
-    constexpr int NVT_T = 8 / (VE * BT) > 1 ? 8 / (VE * BT) : 1;
-    constexpr int NVT_MIN = (kMaxBlockSide + VE * NC - 1) / (VE * NC);
-    constexpr int NVT = NVT_T > NVT_MIN ? NVT_T : NVT_MIN;
-    constexpr bool MP = PREC == kPrecBF16 || PREC == kPrecFP16;
-    using E = typename VecLoad<PREC, VE>::E;
-    using PAcc = typename std::conditional<MP, float, Acc>::type;                     // per-stage partial
     const int t = threadIdx.x;
-    int cur = -1, P = 1, G = 1, vec = 0, grp = 0, nvt = 1;
-    Acc acc[NVT][VE][BT];
-    PAcc part[NVT][VE][BT];
-
-    // phase A of one stage: z = V^T x for every rank row.  L lanes share a rank row, each summing at least four
-    // vectors before the shuffle tree (the tree's adds run on the same pipe as the products), which keeps every
-    // consumer warp busy; DF64 takes one lane per row, its shuffle adds costing a dozen FP32 operations each.
-    // The lanes of row slot rw start their sweep rw * L vectors further on, so the rows a warp reads fall in
-    // different shared-memory banks.  With a full batch (B == BT) the VE * BT history values of a vector are
-    // contiguous and are read with 16-byte loads.
-    auto phase_a = [&](const StageInfo &sx, const unsigned char *bx, Z *zout) {
-        const int nz = sx.n_zrows;
-        if (nz <= 0) return;
-        const int qv = pad_row(sx.q, PREC) / VE;
-        const int q2 = qv * VE;
-        const int q4 = PREC == kPrecDF64 ? 0 : qv >> 2;
-        const int L = q4 >= 32 ? 32 : q4 >= 16 ? 16 : q4 >= 8 ? 8 : q4 >= 4 ? 4 : q4 >= 2 ? 2 : 1;
-        const int subs = 32 / L, SA = CW * subs;
-        const int sl = lane % L, rw = lane / L, slotA = warp * subs + rw;
-        const int rot = (rw * L) % qv;
-        const bool xvec = a.B == BT;
-        const int trips = (nz + SA - 1) / SA;                  // uniform over the warp
-        int k = 0, zstart = 0;
-        for (int r = 0; r < trips; ++r) {
-            const int f = slotA + r * SA;
-            const bool act = f < nz;
-            Z z[BT];
+    constexpr int VE = VecWidth<PREC, BT>::value;
+    using E = typename VecLoad<PREC, VE>::E;
+    if constexpr (PASS == 1) {
+        // z = V^T x for every row of the stage's runs.  L lanes share a row, each summing at least four vectors
+        // before the shuffle tree (the tree's adds run on the same pipe as the products); DF64 takes one lane per
+        // row, its shuffle adds costing a dozen FP32 operations each.  The lanes of row slot rw start their sweep
+        // rw * L vectors further on, so the rows a warp reads fall in different shared-memory banks.  With a full
+        // batch (B == BT) the VE * BT history values of a vector are contiguous and are read with 16-byte loads.
+        Z *zout = reinterpret_cast<Z *>(a.zbuf);
+        for (int g = 0;; ++g) {
+            const int slot = g % kStages;
+            if (t == 0) sh_flag = mbar_wait(&full[slot], (g / kStages) & 1, a.err, a.wait_ns) ? 0 : 1;
+            consumer_sync<NC>();
+            if (sh_flag) return;
+            if (t == 0 && g > 0) mbar_arrive(&empty[(g - 1) % kStages]);
+            const StageInfo &sx = info[slot];
+            if (sx.task < 0) break;
+            const unsigned char *bx = stage_mem + (size_t)slot * kStageBytes;
+            const int nz = sx.n_rows;
+            const int qv = pad_row(sx.q, PREC) / VE;
+            const int q2 = qv * VE;
+            const int q4 = PREC == kPrecDF64 ? 0 : qv >> 2;
+            const int L = q4 >= 32 ? 32 : q4 >= 16 ? 16 : q4 >= 8 ? 8 : q4 >= 4 ? 4 : q4 >= 2 ? 2 : 1;
+            const int subs = 32 / L, SA = CW * subs;
+            const int sl = lane % L, rw = lane / L, slotA = warp * subs + rw;
+            const int rot = (rw * L) % qv;
+            const bool xvec = a.B == BT;
+            const int trips = (nz + SA - 1) / SA;                  // uniform over the warp
+            int k = 0, zstart = 0;
+            for (int r = 0; r < trips; ++r) {
+                const int f = slotA + r * SA;
+                const bool act = f < nz;
+                Z z[BT];
 #pragma unroll
-            for (int bb = 0; bb < BT; ++bb) z[bb] = T::zz();
-            float sc = 1.f;
-            if (act) {
-                while (f >= sx.it[k].z_end) {
-                    zstart = sx.it[k].z_end;
-                    ++k;
-                }
-                const StageItem &itm = sx.it[k];
-                const S *vr = reinterpret_cast<const S *>(bx + itm.data_off) + (int64_t)(f - zstart) * q2;
-                const X *x = reinterpret_cast<const X *>(bx + itm.x_off);
-                sc = itm.scale;
-                for (int i = sl; i < qv; i += L) {
-                    int u = i + rot;
-                    if (u >= qv) u -= qv;
-                    E v[VE];
-                    VecLoad<PREC, VE>::ld(vr + u * VE, v);
-                    if (xvec) {
-                        X xv[VE * BT];
-                        ld16(x + u * VE * BT, xv);
-#pragma unroll
-                        for (int e = 0; e < VE; ++e)
-#pragma unroll
-                            for (int bb = 0; bb < BT; ++bb) edot(z[bb], v[e], xv[e * BT + bb]);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < VE; ++e)
-#pragma unroll
-                            for (int bb = 0; bb < BT; ++bb)
-                                edot(z[bb], v[e], x[(u * VE + e) * a.B + (bb < a.B ? bb : 0)]);
+                for (int bb = 0; bb < BT; ++bb) z[bb] = T::zz();
+                int64_t zrow = 0;
+                float sc = 1.f;
+                if (act) {
+                    while (f >= sx.it[k].row_end) {
+                        zstart = sx.it[k].row_end;
+                        ++k;
                     }
-                }
-            }
-#pragma unroll
-            for (int bb = 0; bb < BT; ++bb) {
-                for (int o = L / 2; o > 0; o >>= 1) z[bb] = T::shfl_add(z[bb], o, L);
-                if (act && sl == 0) zout[f * BT + bb] = T::zscale(z[bb], sc);
-            }
-        }
-    };
-
-    // Software pipeline over stages: between two consumer barriers, interval g runs phase A of stage g + 1
-    // (z into buffer (g + 1) & 1) and phase B of stage g (z from buffer g & 1), so one barrier per stage
-    // separates every producer of z from its readers and the pipe never drains between the phases.  Stage g - 1
-    // is handed back to the producer at the barrier that opens interval g.
-    if (t == 0) sh_flag = mbar_wait(&full[0], 0, a.err, a.wait_ns) ? 0 : 1;
-    consumer_sync<NC>();
-    if (sh_flag) return;
-    if (info[0].task >= 0) phase_a(info[0], stage_mem, zs);
-    for (int g = 0;; ++g) {
-        const int slot = g % kStages;
-        if (t == 0 && info[slot].task >= 0)
-            sh_flag = mbar_wait(&full[(g + 1) % kStages], ((g + 1) / kStages) & 1, a.err, a.wait_ns) ? 0 : 1;
-        consumer_sync<NC>();
-        if (sh_flag) return;
-        if (t == 0 && g > 0) mbar_arrive(&empty[(g - 1) % kStages]);
-        const StageInfo &si = info[slot];
-        const int task = si.task;
-        if (task < 0) break;
-        {
-            const int ns = (g + 1) % kStages;
-            if (info[ns].task >= 0)
-                phase_a(info[ns], stage_mem + (size_t)ns * kStageBytes, zs + ((g + 1) & 1) * kZRows * BT);
-        }
-        const Z *zcur = zs + (g & 1) * kZRows * BT;
-        const int p = si.p, p2 = pad_row(p, PREC), q2 = pad_row(si.q, PREC);
-        if (task != cur) {
-            cur = task;
-            // P: threads per row, a power of two, so that groups tile the warps (P <= 32) or whole warps tile
-            // a group (P > 32)
-            const int pv = p2 / VE;
-            const int pn = (pv + NVT_T - 1) / NVT_T;
-            P = 1;
-            while (P < pn && P < NC) P <<= 1;
-            G = NC / P;
-            vec = t % P;
-            grp = t / P;
-            nvt = (pv + P - 1) / P;
-#pragma unroll
-            for (int s = 0; s < NVT; ++s)
-#pragma unroll
-                for (int e = 0; e < VE; ++e)
-#pragma unroll
-                    for (int bb = 0; bb < BT; ++bb) {
-                        acc[s][e][bb] = T::zero();
-                        part[s][e][bb] = PAcc{};
-                    }
-        }
-        const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
-        // phase B: row updates
-        if (grp < G) {
-            const int nr = si.n_rows;
-            int k = 0, rstart = 0, zbase = 0;
-            for (int f = grp; f < nr; f += G) {
-                while (f >= si.it[k].row_end) {
-                    rstart = si.it[k].row_end;
-                    zbase = si.it[k].z_end;
-                    ++k;
-                }
-                const StageItem &itm = si.it[k];
-                const int r = f - rstart;
-                const S *rowp;
-                E cv[BT];
-                if (itm.k < 0) {
-                    rowp = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)r * p2;
-                    const X *x = reinterpret_cast<const X *>(base + itm.x_off);
-#pragma unroll
-                    for (int bb = 0; bb < BT; ++bb) {
-                        const X xv = T::xscale(x[r * a.B + (bb < a.B ? bb : 0)], itm.scale);
-                        cv[bb] = *reinterpret_cast<const E *>(&xv);
-                    }
-                } else {
-                    const int rows = itm.i1 - itm.i0;
-                    rowp = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)rows * q2 + (int64_t)r * p2;
-#pragma unroll
-                    for (int bb = 0; bb < BT; ++bb) {
-                        const Z zv = zcur[(zbase + r) * BT + bb];
-                        cv[bb] = *reinterpret_cast<const E *>(&zv);
-                    }
-                }
-#pragma unroll
-                for (int s = 0; s < NVT; ++s) {
-                    if (s < nvt) {
-                        const int u = vec + s * P;
-                        if (u * VE < p2) {
-                            E v[VE];
-                            VecLoad<PREC, VE>::ld(rowp + u * VE, v);
+                    const StageItem &itm = sx.it[k];
+                    const S *vr = reinterpret_cast<const S *>(bx + itm.data_off) + (int64_t)(f - zstart) * q2;
+                    const X *x = reinterpret_cast<const X *>(bx + itm.x_off);
+                    zrow = a.zmap[itm.map + (f - zstart)];
+                    if (PREC == kPrecFP16) sc = a.zscale[itm.map + (f - zstart)];
+                    for (int i = sl; i < qv; i += L) {
+                        int uu = i + rot;
+                        if (uu >= qv) uu -= qv;
+                        E v[VE];
+                        VecLoad<PREC, VE>::ld(vr + uu * VE, v);
+                        if (xvec) {
+                            X xv[VE * BT];
+                            ld16(x + uu * VE * BT, xv);
 #pragma unroll
                             for (int e = 0; e < VE; ++e)
 #pragma unroll
-                                for (int bb = 0; bb < BT; ++bb) {
-                                    if constexpr (MP) emac(part[s][e][bb], v[e], cv[bb]);
-                                    else emac(acc[s][e][bb], v[e], cv[bb]);
-                                }
+                                for (int bb = 0; bb < BT; ++bb) edot(z[bb], v[e], xv[e * BT + bb]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < VE; ++e)
+#pragma unroll
+                                for (int bb = 0; bb < BT; ++bb)
+                                    edot(z[bb], v[e], x[(uu * VE + e) * a.B + (bb < a.B ? bb : 0)]);
                         }
                     }
                 }
+#pragma unroll
+                for (int bb = 0; bb < BT; ++bb) {
+                    for (int o = L / 2; o > 0; o >>= 1) z[bb] = T::shfl_add(z[bb], o, L);
+                    if (act && sl == 0 && bb < a.B) zout[zrow * a.B + bb] = T::zscale(z[bb], sc);
+                }
             }
-            if constexpr (MP) {                                // compensated accumulation, once per stage
+        }
+        return;
+    } else {
+        // Thread t works in group t / P and owns the VE-wide column vectors (t mod P) + s P, s < nvt, of the block's
+        // rows (P a power of two, G = NC / P groups for NC consumer threads).  The stage's rows (rows of A^T times a
+        // history value, rows of U^T times a z value) form one flat list dealt round-robin to the groups; a
+        // monotone cursor maps a flat index to its unit.  BF16/FP16: plain FP32 partial sums inside a stage, added
+        // into the Kahan-compensated accumulator once per stage.
+        // vectors per thread and row: aim at 8 multiply-adds per row (fewer index operations per product); at
+        // least enough vectors for the widest block when all NC consumers share a row
+        constexpr int NVT_T = 8 / (VE * BT) > 1 ? 8 / (VE * BT) : 1;
+        constexpr int NVT_MIN = (kMaxBlockSide + VE * NC - 1) / (VE * NC);
+        constexpr int NVT = NVT_T > NVT_MIN ? NVT_T : NVT_MIN;
+        constexpr bool MP = PREC == kPrecBF16 || PREC == kPrecFP16;
+        using PAcc = typename std::conditional<MP, float, Acc>::type;                 // per-stage partial
+        int cur = -1, P = 1, G = 1, vec = 0, grp = 0, nvt = 1;
+        Acc acc[NVT][VE][BT];
+        PAcc part[NVT][VE][BT];
+        for (int g = 0;; ++g) {
+            const int slot = g % kStages;
+            if (t == 0) sh_flag = mbar_wait(&full[slot], (g / kStages) & 1, a.err, a.wait_ns) ? 0 : 1;
+            consumer_sync<NC>();
+            if (sh_flag) return;
+            if (t == 0 && g > 0) mbar_arrive(&empty[(g - 1) % kStages]);
+            const StageInfo &si = info[slot];
+            const int task = si.task;
+            if (task < 0) break;
+            const int p = si.p, p2 = pad_row(p, PREC);
+            if (task != cur) {
+                cur = task;
+                // P: threads per row, a power of two, so that groups tile the warps (P <= 32) or whole warps
+                // tile a group (P > 32)
+                const int pv = p2 / VE;
+                const int pn = (pv + NVT_T - 1) / NVT_T;
+                P = 1;
+                while (P < pn && P < NC) P <<= 1;
+                G = NC / P;
+                vec = t % P;
+                grp = t / P;
+                nvt = (pv + P - 1) / P;
 #pragma unroll
                 for (int s = 0; s < NVT; ++s)
 #pragma unroll
                     for (int e = 0; e < VE; ++e)
 #pragma unroll
                         for (int bb = 0; bb < BT; ++bb) {
-                            PTHalf<__half>::kahan(acc[s][e][bb], part[s][e][bb]);
+                            acc[s][e][bb] = T::zero();
                             part[s][e][bb] = PAcc{};
                         }
             }
-        }
-        if (si.flush) {
-            const int64_t part_off = si.part_off;
-            // column c = (vec + s P) VE + e; value v of a thread: vector s = v / (VE BT), element e = (v / BT) mod
-            // VE, scenario bb = v mod BT.  The G groups are reduced in a fixed order, RV values per round through
-            // shared memory; rounds past the task's vectors are skipped (uniform).  The barrier that opens the
-            // next interval protects red from the next writes.
-            constexpr int NV = NVT * VE * BT;
-            const int nv = nvt * VE * BT;
-            if (G == 1) {
-#pragma unroll
-                for (int s = 0; s < NVT; ++s)
-#pragma unroll
-                    for (int e = 0; e < VE; ++e) {
-                        const int c = (vec + s * P) * VE + e;
-                        if (s < nvt && c < p)
-#pragma unroll
-                            for (int bb = 0; bb < BT; ++bb)
-                                if (bb < a.B)
-                                    a.partial[(int64_t)bb * a.n_partial + part_off + c] = T::to_d(acc[s][e][bb]);
+            const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
+            if (grp < G) {
+                const int nr = si.n_rows;
+                int k = 0, rstart = 0;
+                for (int f = grp; f < nr; f += G) {
+                    while (f >= si.it[k].row_end) {
+                        rstart = si.it[k].row_end;
+                        ++k;
                     }
-            } else if (NV <= 8 && P <= 16) {
-                // Reduce-scatter over the 32 / P groups of a warp: at the level with lane distance o a lane keeps
-                // the half of its values selected by lane bit o and adds its partner's copy of that half, so the
-                // values per lane halve at each level (plain adds once a single value is left).  Lane l then holds
-                // values base(l) .. base(l) + cnt - 1 of column vector l mod P, summed over the warp's groups.
-                // The CW warp sums of each (vector, value) are added by one of P NV threads.
-                double vals[NV];
+                    const StageItem &itm = si.it[k];
+                    const int r = f - rstart;
+                    const S *rowp = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)r * p2;
+                    E cv[BT];
+                    if (itm.k < 0) {
+                        const X *x = reinterpret_cast<const X *>(base + itm.x_off);
 #pragma unroll
-                for (int v = 0; v < NV; ++v) vals[v] = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
-                int base = 0, cnt = NV;
-                bool writer = true;
+                        for (int bb = 0; bb < BT; ++bb) {
+                            const X xv = T::xscale(x[r * a.B + (bb < a.B ? bb : 0)], itm.scale);
+                            cv[bb] = *reinterpret_cast<const E *>(&xv);
+                        }
+                    } else {
+                        const Z *zr = reinterpret_cast<const Z *>(base + itm.x_off);
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    const int o = 16 >> k;
-                    if (o < P) break;
-                    const bool upper = (lane & o) != 0;
-                    if ((NV >> k) >= 2) {
-                        const int half = (NV >> k) / 2;
+                        for (int bb = 0; bb < BT; ++bb) {
+                            const Z zv = zr[r * a.B + (bb < a.B ? bb : 0)];
+                            cv[bb] = *reinterpret_cast<const E *>(&zv);
+                        }
+                    }
 #pragma unroll
-                        for (int j = 0; j < NV / 2; ++j) {
-                            if (j < half) {
-                                const double send = upper ? vals[j] : vals[j + half];
-                                const double keep = upper ? vals[j + half] : vals[j];
-                                vals[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    for (int s = 0; s < NVT; ++s) {
+                        if (s < nvt) {
+                            const int uu = vec + s * P;
+                            if (uu * VE < p2) {
+                                E v[VE];
+                                VecLoad<PREC, VE>::ld(rowp + uu * VE, v);
+#pragma unroll
+                                for (int e = 0; e < VE; ++e)
+#pragma unroll
+                                    for (int bb = 0; bb < BT; ++bb) {
+                                        if constexpr (MP) emac(part[s][e][bb], v[e], cv[bb]);
+                                        else emac(acc[s][e][bb], v[e], cv[bb]);
+                                    }
                             }
                         }
-                        if (upper) base += half;
-                        cnt = half;
-                    } else {
-                        vals[0] += __shfl_xor_sync(0xffffffffu, vals[0], o);
-                        if (upper) writer = false;             // the partner holds the same sum
                     }
                 }
-                const int vv = lane % P;
-                if (writer) {
+                if constexpr (MP) {                                // compensated accumulation, once per stage
 #pragma unroll
-                    for (int j = 0; j < NV; ++j)
-                        if (j < cnt) red[(warp * P + vv) * NV + base + j] = vals[j];
+                    for (int s = 0; s < NVT; ++s)
+#pragma unroll
+                        for (int e = 0; e < VE; ++e)
+#pragma unroll
+                            for (int bb = 0; bb < BT; ++bb) {
+                                PTHalf<__half>::kahan(acc[s][e][bb], part[s][e][bb]);
+                                part[s][e][bb] = PAcc{};
+                            }
                 }
-                consumer_sync<NC>();
-                if (t < P * NV) {
-                    const int vt = t % P, v = t / P;
-                    const int sv = v / (VE * BT), e = (v / BT) % VE, bb = v % BT;
-                    const int c = (vt + sv * P) * VE + e;
-                    if (v < nv && c < p && bb < a.B) {
-                        double sum = 0.0;
+            }
+            if (si.flush) {
+                const int64_t part_off = si.part_off;
+                // column c = (vec + s P) VE + e; value v of a thread: vector s = v / (VE BT), element e = (v / BT) mod
+                // VE, scenario bb = v mod BT.  The G groups are reduced in a fixed order, RV values per round through
+                // shared memory; rounds past the task's vectors are skipped (uniform).  The barrier that opens the
+                // next interval protects red from the next writes.
+                constexpr int NV = NVT * VE * BT;
+                const int nv = nvt * VE * BT;
+                if (G == 1) {
 #pragma unroll
-                        for (int w = 0; w < CW; ++w) sum += red[(w * P + vt) * NV + v];
-                        a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
-                    }
-                }
-            } else if (P <= 32) {
-                // the 32 / P groups of a warp by a shuffle tree, then the CW warp sums of each (column, value) by
-                // one of RV P threads
+                    for (int s = 0; s < NVT; ++s)
 #pragma unroll
-                for (int r0 = 0; r0 < NV; r0 += RV) {
-                    if (r0 >= nv) break;
-                    if (r0 > 0) consumer_sync<NC>();
+                        for (int e = 0; e < VE; ++e) {
+                            const int c = (vec + s * P) * VE + e;
+                            if (s < nvt && c < p)
 #pragma unroll
-                    for (int m = 0; m < RV; ++m) {
-                        const int v = r0 + m;
-                        if (v < NV) {
-                            double x = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
-                            for (int o = 16; o >= P; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                            if (lane < P) red[(warp * 32 + lane) * RV + m] = x;
+                                for (int bb = 0; bb < BT; ++bb)
+                                    if (bb < a.B)
+                                        a.partial[(int64_t)bb * a.n_partial + part_off + c] = T::to_d(acc[s][e][bb]);
+                        }
+                } else if (NV <= 8 && P <= 16) {
+                    // Reduce-scatter over the 32 / P groups of a warp: at the level with lane distance o a lane keeps
+                    // the half of its values selected by lane bit o and adds its partner's copy of that half, so the
+                    // values per lane halve at each level (plain adds once a single value is left).  Lane l then holds
+                    // values base(l) .. base(l) + cnt - 1 of column vector l mod P, summed over the warp's groups.
+                    // The CW warp sums of each (vector, value) are added by one of P NV threads.
+                    double vals[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) vals[v] = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
+                    int base = 0, cnt = NV;
+                    bool writer = true;
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        const int o = 16 >> k;
+                        if (o < P) break;
+                        const bool upper = (lane & o) != 0;
+                        if ((NV >> k) >= 2) {
+                            const int half = (NV >> k) / 2;
+#pragma unroll
+                            for (int j = 0; j < NV / 2; ++j) {
+                                if (j < half) {
+                                    const double send = upper ? vals[j] : vals[j + half];
+                                    const double keep = upper ? vals[j + half] : vals[j];
+                                    vals[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                                }
+                            }
+                            if (upper) base += half;
+                            cnt = half;
+                        } else {
+                            vals[0] += __shfl_xor_sync(0xffffffffu, vals[0], o);
+                            if (upper) writer = false;             // the partner holds the same sum
                         }
                     }
+                    const int vv = lane % P;
+                    if (writer) {
+#pragma unroll
+                        for (int j = 0; j < NV; ++j)
+                            if (j < cnt) red[(warp * P + vv) * NV + base + j] = vals[j];
+                    }
                     consumer_sync<NC>();
-                    if (t < RV * P) {
-                        const int m = t / P, vv = t % P, v = r0 + m;
+                    if (t < P * NV) {
+                        const int vt = t % P, v = t / P;
                         const int sv = v / (VE * BT), e = (v / BT) % VE, bb = v % BT;
-                        const int c = (vv + sv * P) * VE + e;
+                        const int c = (vt + sv * P) * VE + e;
                         if (v < nv && c < p && bb < a.B) {
                             double sum = 0.0;
 #pragma unroll
-                            for (int w = 0; w < CW; ++w) sum += red[(w * 32 + vv) * RV + m];
+                            for (int w = 0; w < CW; ++w) sum += red[(w * P + vt) * NV + v];
                             a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
                         }
                     }
-                }
-            } else {
-                // 2 to 8 groups of whole warps: group 0 adds the others' values
+                } else if (P <= 32) {
+                    // the 32 / P groups of a warp by a shuffle tree, then the CW warp sums of each (column, value) by
+                    // one of RV P threads
 #pragma unroll
-                for (int r0 = 0; r0 < NV; r0 += RV) {
-                    if (r0 >= nv) break;
-                    if (r0 > 0) consumer_sync<NC>();
-#pragma unroll
-                    for (int m = 0; m < RV; ++m) {
-                        const int v = r0 + m;
-                        if (v < NV) red[t * RV + m] = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
-                    }
-                    consumer_sync<NC>();
-                    if (grp == 0) {
+                    for (int r0 = 0; r0 < NV; r0 += RV) {
+                        if (r0 >= nv) break;
+                        if (r0 > 0) consumer_sync<NC>();
 #pragma unroll
                         for (int m = 0; m < RV; ++m) {
                             const int v = r0 + m;
+                            if (v < NV) {
+                                double x = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
+                                for (int o = 16; o >= P; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                                if (lane < P) red[(warp * 32 + lane) * RV + m] = x;
+                            }
+                        }
+                        consumer_sync<NC>();
+                        if (t < RV * P) {
+                            const int m = t / P, vv = t % P, v = r0 + m;
                             const int sv = v / (VE * BT), e = (v / BT) % VE, bb = v % BT;
-                            const int c = (vec + sv * P) * VE + e;
+                            const int c = (vv + sv * P) * VE + e;
                             if (v < nv && c < p && bb < a.B) {
                                 double sum = 0.0;
-                                for (int gg = 0; gg < G; ++gg) sum += red[(gg * P + vec) * RV + m];
+#pragma unroll
+                                for (int w = 0; w < CW; ++w) sum += red[(w * 32 + vv) * RV + m];
                                 a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
                             }
                         }
                     }
+                } else {
+                    // 2 to 8 groups of whole warps: group 0 adds the others' values
+#pragma unroll
+                    for (int r0 = 0; r0 < NV; r0 += RV) {
+                        if (r0 >= nv) break;
+                        if (r0 > 0) consumer_sync<NC>();
+#pragma unroll
+                        for (int m = 0; m < RV; ++m) {
+                            const int v = r0 + m;
+                            if (v < NV) red[t * RV + m] = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
+                        }
+                        consumer_sync<NC>();
+                        if (grp == 0) {
+#pragma unroll
+                            for (int m = 0; m < RV; ++m) {
+                                const int v = r0 + m;
+                                const int sv = v / (VE * BT), e = (v / BT) % VE, bb = v % BT;
+                                const int c = (vec + sv * P) * VE + e;
+                                if (v < nv && c < p && bb < a.B) {
+                                    double sum = 0.0;
+                                    for (int gg = 0; gg < G; ++gg) sum += red[(gg * P + vec) * RV + m];
+                                    a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
+                                }
+                            }
+                        }
+                    }
                 }
+                cur = -1;
             }
-            cur = -1;
         }
     }
 }
@@ -1386,7 +1385,10 @@ __global__ void __launch_bounds__(kThreads) k_static_tail(StepArgs a) {
 __global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
     const int64_t e = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.counter = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.counter[0] = 0;                                   // pass-2 task counter
+        a.counter[2] = 0;                                   // pass-1 task counter
+    }
     if (e >= a.N) return;
     double sum[kMaxBatch];
 #pragma unroll
@@ -1460,15 +1462,25 @@ __global__ void k_wait_probe(StepArgs a) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
 }
 
-template <int PREC, int BT>
-cudaError_t launch_interaction_bt(const StepArgs &a, cudaStream_t s) {
+template <int PREC, int BT, int PASS>
+cudaError_t launch_interaction_pass(const StepArgs &a, cudaStream_t s) {
+    const int n = PASS == 1 ? a.n_ztasks_active : a.n_tasks_active;
+    if (n <= 0) return cudaSuccess;
     const size_t smem = InterLayout<BT>::total;
-    cudaError_t e = cudaFuncSetAttribute(k_interaction<PREC, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_interaction<PREC, BT, PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = a.n_tasks_active < a.n_sms ? a.n_tasks_active : a.n_sms;
-    k_interaction<PREC, BT><<<grid, InterShape<BT>::NT, smem, s>>>(a);
+    const int grid = n < a.n_sms ? n : a.n_sms;
+    k_interaction<PREC, BT, PASS><<<grid, InterShape<BT>::NT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// Pass 1 (z = V^T x of the far slices, source side), then pass 2 (the receivers' sums), in stream order.
+template <int PREC, int BT>
+cudaError_t launch_interaction_bt(const StepArgs &a, cudaStream_t s) {
+    const cudaError_t e = launch_interaction_pass<PREC, BT, 1>(a, s);
+    if (e != cudaSuccess) return e;
+    return launch_interaction_pass<PREC, BT, 2>(a, s);
 }
 
 template <int PREC>
@@ -1531,7 +1543,7 @@ cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s) {
-    if (a.n_tasks_active <= 0) return cudaSuccess;
+    if (a.n_tasks_active <= 0 && a.n_ztasks_active <= 0) return cudaSuccess;
     switch (a.prec) {
         case kPrecDF64: return launch_interaction_prec<kPrecDF64>(a, s);
         case kPrecBF16: return launch_interaction_prec<kPrecBF16>(a, s);
