@@ -173,6 +173,15 @@ seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **scn);
  * SEAS_ESTATE after max_steps pushes.  Host inputs are checked for finiteness (SEAS_EINVAL). */
 seas_status seas_push_slip_rate(seas_scn *scn, const double *V, const double *slip, int mem, int replace_last);
 
+/* A slip rate held over gamma >= 1 consecutive lattice steps (t_n, t_{n+gamma}] (the time step gamma dt_min of
+ * Sec. 2.4, step 1): V ([batch][N]) goes into gamma ring slots and the slip of lattice step n + j is
+ * delta^n + j dt V (j = 1..gamma), or, with slip given, the straight line from delta^n to slip at j = gamma; the
+ * spectral history gets every lattice step.  seas_stress_step then returns tau at t_{n+gamma}.  replace_last != 0
+ * overwrites the previous push, which must have held the same gamma (SEAS_EINVAL otherwise).  gamma = 1 is
+ * seas_push_slip_rate; a push counts gamma steps against max_steps. */
+seas_status seas_push_slip_rate_steps(seas_scn *scn, const double *V, const double *slip, int mem, int gamma,
+                                      int replace_last);
+
 /* tau at the last pushed step into tau ([batch][N]); sigma_n (nullable) receives zeros; parts (nullable,
  * [3][batch][N]) receives radiation damping, f_self and f_int separately. */
 seas_status seas_stress_step(seas_scn *scn, double *tau, double *sigma_n, double *parts, int mem);
@@ -258,6 +267,45 @@ seas_status seas_scenario_get_timing(seas_scn *scn, seas_timing *out);
 /* Algorithmic interaction-operator bytes of step `step`: the values of every stored slice with lag <= step
  * (p q near, k (p + q) far) times the storage element size; the 16-byte row padding is not counted. */
 seas_status seas_op_step_bytes(const seas_op *op, int64_t step, int64_t *bytes);
+
+/* ---- earthquake-cycle stepping on top of the functional (Sec. 2.2, Sec. 2.4) ----
+ * Rate-and-state friction of one element: f = f_* + a ln(V / V_*) + b ln(V theta / D_c) (Eq. R&S_friction) under the
+ * background normal stress sigma_n (Pa, compressive positive); the state follows Eq. state_evolution_law with the
+ * integrator's eps in (0, 1] (1: the aging law). */
+typedef struct {
+    double a, b, dc, f0, v0, sigma_n;
+} seas_friction;
+
+typedef struct seas_integ seas_integ;
+
+/* Creates an integrator on a scenario that has no pushes yet.  fr: n_fr = 1 (every element) or N entries (element
+ * j of every batch member); tau0: background shear stress [batch][N] (Pa); V0, theta0: initial slip rate and state
+ * [batch][N]; mem: where tau0, V0 and theta0 live.  The initial rate starts the first predictor but is no slip-rate
+ * history (no slip before t = 0).  SEAS_EINVAL if a lag-0 interaction slice exists (faults closer than c_s dt: the
+ * per-element Newton solves would couple) or a parameter is out of range; SEAS_ESTATE if the scenario has pushes.
+ * The integrator owns its device state (charged to the context's budget); destroy it before the scenario. */
+seas_status seas_integrator_create(seas_scn *scn, const seas_friction *fr, int n_fr, double eps, const double *tau0,
+                                   const double *V0, const double *theta0, int mem, seas_integ **out);
+/* Advances `steps` time steps of dt (the operator's lattice step) on the device, asynchronously on the context
+ * stream.  One step (Sec. 2.4): predictor delta* = delta + dt V, theta* = theta + dt thetadot; push of a zero slip
+ * rate with slip delta* and a stress step give the elastic stress without its instantaneous part; Newton in ln V per
+ * element on tau_known + tau0 - (mu / 2 c_s) V = sigma_n f(V, theta*) to |residual| <= 1e-8 (|tau| + sigma_n);
+ * thetadot*; the corrector repeats this with V -> (V + V*)/2, thetadot -> (thetadot + thetadot*)/2 (replacing the
+ * pushed slip); the step's slot is then replaced by V**.  Three pushes and two stress steps per step, all FP64. */
+seas_status seas_integrator_step(seas_integ *it, int steps);
+/* One time step of gamma lattice steps (dt = gamma dt_min, Sec. 2.4 step 1): the predictor and corrector hold their
+ * rate over the step's lattice steps (seas_push_slip_rate_steps) and the slip grows linearly along them; the lattice
+ * history then receives V** on each of them.  gamma = 1 is one seas_integrator_step. */
+seas_status seas_integrator_step_gamma(seas_integ *it, int gamma);
+/* `steps` adaptive time steps: gamma = ceil(dt_ev / dt_min) with dt_ev = min over elements of xi D_c / V (Sec. 2.4,
+ * step 1), clamped to [1, gamma_max]; xi is the caller's (the paper takes it from a stiffness criterion of the
+ * literature).  Synchronises once per step to read dt_ev.  *lattice_steps (nullable) receives the lattice steps
+ * advanced. */
+seas_status seas_integrator_step_adaptive(seas_integ *it, double xi, int gamma_max, int steps, int64_t *lattice_steps);
+/* Synchronises and copies V, theta and slip ([batch][N] each, nullable) into host or device buffers; SEAS_ESTATE if
+ * a Newton solve did not converge in 100 iterations since the integrator was created. */
+seas_status seas_integrator_state(seas_integ *it, double *V, double *theta, double *slip, int mem);
+seas_status seas_destroy_integrator(seas_integ *it);
 
 /* Device probe (no counterpart in the paper; used for roofline reporting): the FP64 fused multiply-add rate of GPU
  * `device` in FMA/s, measured by a kernel of independent FMA chains on every SM (best of three ~30 ms launches).

@@ -140,3 +140,57 @@ class Integrator:
         self.thetadot = state_rate(v2, th2, fr)
         self.iterations.append((it1, it2))
         return v2
+
+    # ------------------------------------------------------------------------------------------------------------
+    # Variable time step on the dt_min lattice (Sec. 2.4, step 1): a step of gamma lattice steps holds one slip rate
+    # over the whole interval.
+    # ------------------------------------------------------------------------------------------------------------
+
+    def _known_stress_lattice(self, slips_new, v_push):
+        """Elastic stress at the end of a step of gamma = len(slips_new) lattice steps, without the radiation-damping
+        term: spectral self term of the lattice slip history ending in slips_new; interaction over lags T >= 1 of the
+        lattice slip-rate history, in which the interval's own lattice steps (lags 1 .. gamma - 1) carry v_push, the
+        rate the predictor (or corrector) holds over the interval."""
+        net = self.net
+        gamma = len(slips_new)
+        n = len(self.V) + gamma - 1                       # lattice index of the new step
+        hist = np.stack(self.delta[1:] + list(slips_new))
+        tau = np.zeros(net.N)
+        for f in range(net.F):
+            o0, o1 = net.offset[f], net.offset[f + 1]
+            tau[o0:o1] = O.self_history(net, f, hist[:, o0:o1], self.tables[f])[-1]
+        Vh = self.V + [v_push] * (gamma - 1)              # lattice rates 0 .. n - 1 (0: the initial rate)
+        for T in range(1, n):
+            tau += -self.rad * (self.A[T] @ Vh[n - T])
+        return tau
+
+    def step_gamma(self, gamma: int):
+        """One predictor-corrector step of gamma lattice steps (dt = gamma dt_min): the step's slip rate is held over
+        its lattice steps (predictor: V^{n-1}; corrector: (V^{n-1} + V*)/2), the slip grows linearly along them, and
+        the lattice history receives gamma copies of V** and the slips delta + j dt (V + V*)/2.  gamma = 1 is step().
+        Returns V**."""
+        net, fr, dt = self.net, self.fr, self.net.dt
+        if len(self.V) + gamma > self.max_steps:
+            raise RuntimeError("max_steps reached")
+        v_old, d_old, th_old, thd_old = self.V[-1], self.delta[-1], self.theta, self.thetadot
+        dtg = gamma * dt
+        slips1 = [d_old + (j * dt) * v_old for j in range(1, gamma + 1)]
+        th1 = th_old + dtg * thd_old
+        v1, it1 = solve_v(self._known_stress_lattice(slips1, v_old) + self.tau0, th1, fr, self.rad, v_old)
+        thd1 = state_rate(v1, th1, fr)
+        vavg = 0.5 * (v_old + v1)
+        slips2 = [d_old + (j * dt) * vavg for j in range(1, gamma + 1)]
+        th2 = th_old + dtg * 0.5 * (thd_old + thd1)
+        v2, it2 = solve_v(self._known_stress_lattice(slips2, vavg) + self.tau0, th2, fr, self.rad, v1)
+        self.V += [v2] * gamma
+        self.delta += slips2
+        self.theta = th2
+        self.thetadot = state_rate(v2, th2, fr)
+        self.iterations.append((it1, it2))
+        return v2
+
+    def adaptive_gamma(self, xi: float, gamma_max: int) -> int:
+        """gamma = ceil(dt_ev / dt_min), dt_ev = min_i xi D_c / V_i (Sec. 2.4, step 1), at least 1 and at most
+        gamma_max.  xi is taken as a given constant (the paper refers its stiffness-dependent value elsewhere)."""
+        dt_ev = float(np.min(xi * self.fr.dc / self.V[-1]))
+        return int(min(gamma_max, max(1, math.ceil(dt_ev / self.net.dt))))

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libseas.so")
-SOURCES = ["seas_api.cu", "seas_build.cu", "seas_step.cu", "seas_probe.cu"]
+SOURCES = ["seas_api.cu", "seas_build.cu", "seas_step.cu", "seas_probe.cu", "seas_integ.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -221,6 +221,7 @@ struct seas_scn {
     std::vector<int64_t> start;      // per member: tick of its first push (0 unless admitted later)
     std::vector<char> active;        // per member: 1 while admitted
     int64_t horizon = -1;            // largest lag the interaction has switched on (non-decreasing)
+    int last_gamma = 1;              // lattice steps of the last push (seas_push_slip_rate_steps)
     DArr<unsigned char> zbuf;        // pass-1 output: [z rows][batch] in the dot type of the precision
     DArr<double> vring, slip, slip_prev, fint, d_V, d_slip, d_tau, d_parts, partial;
     DArr<double> sring;              // static tail: slip after each push, [op->ring + 1][N][B]
@@ -1498,16 +1499,24 @@ extern "C" seas_status seas_op_step_bytes(const seas_op *op, int64_t step, int64
 
 extern "C" seas_status seas_push_slip_rate(seas_scn *s, const double *V, const double *slip, int mem,
                                            int replace_last) {
+    return seas_push_slip_rate_steps(s, V, slip, mem, 1, replace_last);
+}
+
+extern "C" seas_status seas_push_slip_rate_steps(seas_scn *s, const double *V, const double *slip, int mem, int gamma,
+                                                 int replace_last) {
     if (!s || !V) return fail(SEAS_EINVAL, "NULL argument");
     if (mem != SEAS_MEM_HOST && mem != SEAS_MEM_DEVICE) return fail(SEAS_EINVAL, "mem must be HOST or DEVICE");
+    if (gamma < 1) return fail(SEAS_EINVAL, "gamma must be >= 1");
     seas_op &op = *s->op;
     seas_ctx *c = op.net->ctx;
     if (replace_last && s->n == 0) return fail(SEAS_ESTATE, "replace_last before the first push");
+    if (replace_last && gamma != s->last_gamma)
+        return fail(SEAS_EINVAL, "replace_last with gamma %d: the last push held %d steps", gamma, s->last_gamma);
     if (!replace_last && !(op.hp.flags & SEAS_FLAG_LAG_CAP))
         for (int b = 0; b < s->B; ++b)
-            if (s->active[b] && s->n - s->start[b] >= op.hp.max_steps)
+            if (s->active[b] && s->n - s->start[b] + gamma > op.hp.max_steps)
                 return fail(SEAS_ESTATE, "push %lld of member %d beyond max_steps %d",
-                            (long long)(s->n - s->start[b]), b, op.hp.max_steps);
+                            (long long)(s->n - s->start[b] + gamma - 1), b, op.hp.max_steps);
     CUDA_TRY(cudaSetDevice(c->device));
     const int64_t BN = (int64_t)s->B * op.net->N;
     const double *dV = V, *dS = slip;
@@ -1528,11 +1537,14 @@ extern "C" seas_status seas_push_slip_rate(seas_scn *s, const double *V, const d
             dS = s->d_slip.p;
         }
     }
-    const int64_t step = replace_last ? s->n - 1 : s->n;
-    StepArgs a = step_args(*s, step);
-    SEAS_TRY(timed(*s, 0, [&] { return launch_push(a, dV, dS, replace_last, c->stream); }));
-    SEAS_TRY(timed(*s, 1, [&] { return launch_fft_forward(a, c->stream); }));
-    if (!replace_last) s->n++;
+    const int64_t tick0 = replace_last ? s->n - gamma : s->n;
+    for (int j = 1; j <= gamma; ++j) {
+        StepArgs a = step_args(*s, tick0 + j - 1);
+        SEAS_TRY(timed(*s, 0, [&] { return launch_push(a, dV, dS, replace_last, j, gamma, c->stream); }));
+        SEAS_TRY(timed(*s, 1, [&] { return launch_fft_forward(a, c->stream); }));
+    }
+    if (!replace_last) s->n += gamma;
+    s->last_gamma = gamma;
     return SEAS_OK;
 }
 
@@ -1626,6 +1638,28 @@ extern "C" seas_status seas_scenario_member_step(const seas_scn *s, int member, 
     *n = s->active[member] ? s->n - s->start[member] : -1;
     return SEAS_OK;
 }
+
+namespace seas {
+
+int scenario_view(const seas_scn *s, ScnView *v) {
+    if (!s || !v) return fail(SEAS_EINVAL, "NULL argument");
+    const seas_op &op = *s->op;
+    v->stream = op.net->ctx->stream;
+    v->device = op.net->ctx->device;
+    v->B = s->B;
+    v->N = op.net->N;
+    v->dt = op.net->dt;
+    v->rad = op.net->med.mu / (2.0 * op.net->med.cs);
+    v->n = s->n;
+    v->first_lag = op.task_T.empty() ? INT32_MAX : op.task_T.front();
+    return SEAS_OK;
+}
+
+int scn_alloc(seas_scn *s, size_t bytes, void **p) { return dev_alloc(s->op->net->ctx, bytes, p); }
+
+void scn_free(seas_scn *s, void *p, size_t bytes) { dev_free(s->op->net->ctx, p, bytes); }
+
+}  // namespace seas
 
 extern "C" seas_status seas_scenario_set_wait_limit(seas_scn *s, double seconds) {
     if (!s) return fail(SEAS_EINVAL, "NULL scenario");

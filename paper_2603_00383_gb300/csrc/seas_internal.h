@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "seas.h"
+
 namespace seas {
 
 constexpr int kThreads = 256;       // threads per CTA of every kernel
@@ -212,8 +214,21 @@ constexpr int64_t kStaticScratchDoubles = int64_t(1) << 22;
 constexpr int kMaxDevices = 64;
 cudaError_t static_scratch(double **ptr);   // device address of the array on the current device
 
-cudaError_t launch_push(const StepArgs &a, const double *V, const double *slip_in, int replace_last,
-                        cudaStream_t s);
+// View of a scenario for the earthquake-cycle integrator (seas_integ.cu), and device allocations charged to the
+// scenario's context budget.
+struct ScnView {
+    cudaStream_t stream;
+    int device, B, N;
+    double dt, rad;          // rad = mu / (2 c_s)
+    int64_t n;               // pushes so far
+    int32_t first_lag;       // smallest lag of any stored interaction slice (INT32_MAX: none)
+};
+int scenario_view(const seas_scn *s, ScnView *v);
+int scn_alloc(seas_scn *s, size_t bytes, void **p);
+void scn_free(seas_scn *s, void *p, size_t bytes);
+
+cudaError_t launch_push(const StepArgs &a, const double *V, const double *slip_in, int replace_last, int j,
+                        int gamma, cudaStream_t s);
 cudaError_t launch_fft_forward(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s);

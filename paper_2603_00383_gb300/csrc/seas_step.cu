@@ -101,8 +101,11 @@ __device__ double2 *fft_stockham(double2 *src, double2 *dst, int N, const int *r
     return src;
 }
 
+// Push j (1..gamma) of a slip rate held over gamma lattice steps: V into the ring slot of the tick, and the slip
+// delta^{n+j} = delta^n + j dt V (or the caller's slip delta^{n+gamma} on the straight line from delta^n); delta^n is
+// kept in slip_prev for the corrector's replacement.  gamma = 1: one ordinary push.
 __global__ void k_push(StepArgs a, const double *__restrict__ V, const double *__restrict__ slip_in,
-                       int replace_last) {
+                       int replace_last, int j, int gamma) {
     const int64_t BN = (int64_t)a.B * a.N;
     const int slot = (int)(a.step % a.ring);
     double *vr = a.vring + (int64_t)slot * a.ring_stride;
@@ -117,14 +120,14 @@ __global__ void k_push(StepArgs a, const double *__restrict__ V, const double *_
         } else if (a.prec != kPrecFP64) {
             reinterpret_cast<float *>(a.xring)[(int64_t)slot * a.ring_stride + i * a.B + b] = (float)v;
         }
+        const double base = replace_last || j > 1 ? a.slip_prev[e] : a.slip[e];
         double s;
         if (slip_in) {
-            s = slip_in[e];
+            s = gamma == 1 ? slip_in[e] : base + (slip_in[e] - base) * ((double)j / (double)gamma);
         } else {
-            const double base = replace_last ? a.slip_prev[e] : a.slip[e];
-            s = __dadd_rn(base, __dmul_rn(v, a.dt));   // delta^n = delta^{n-1} + dt V^n
+            s = __dadd_rn(base, __dmul_rn(v, (double)j * a.dt));   // delta^n = delta^{n-1} + dt V^n
         }
-        if (!replace_last) a.slip_prev[e] = a.slip[e];
+        if (!replace_last && j == 1) a.slip_prev[e] = a.slip[e];
         a.slip[e] = s;
         if (a.tail) a.sring[(a.step % a.sring_depth) * BN + i * a.B + b] = s;
     }
@@ -1513,12 +1516,12 @@ cudaError_t static_scratch(double **ptr) {
     return cudaSuccess;
 }
 
-cudaError_t launch_push(const StepArgs &a, const double *V, const double *slip_in, int replace_last,
-                        cudaStream_t s) {
+cudaError_t launch_push(const StepArgs &a, const double *V, const double *slip_in, int replace_last, int j,
+                        int gamma, cudaStream_t s) {
     const int64_t BN = (int64_t)a.B * a.N;
     int grid = (int)((BN + kThreads - 1) / kThreads);
     if (grid > 152 * 8) grid = 152 * 8;
-    k_push<<<grid, kThreads, 0, s>>>(a, V, slip_in, replace_last);
+    k_push<<<grid, kThreads, 0, s>>>(a, V, slip_in, replace_last, j, gamma);
     return cudaGetLastError();
 }
 

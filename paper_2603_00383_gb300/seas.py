@@ -28,7 +28,9 @@ EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_
             "seas_destroy_ctx", "seas_plan_hmatrix", "seas_scenario_set_timing", "seas_scenario_get_timing",
             "seas_op_step_bytes", "seas_scenario_check", "seas_stress_step_static",
             "seas_measure_fp64_peak", "seas_scenario_set_wait_limit", "seas_scenario_probe_wait",
-            "seas_scenario_admit", "seas_scenario_retire", "seas_scenario_member_step", "seas_ctx_get_memory"]
+            "seas_scenario_admit", "seas_scenario_retire", "seas_scenario_member_step", "seas_ctx_get_memory",
+            "seas_integrator_create", "seas_integrator_step", "seas_integrator_state", "seas_destroy_integrator",
+            "seas_push_slip_rate_steps", "seas_integrator_step_gamma", "seas_integrator_step_adaptive"]
 
 
 class SeasError(RuntimeError):
@@ -62,6 +64,11 @@ class seas_op_stats(C.Structure):
                 ("bytes_dense_causal", C.c_int64), ("compression_ratio", C.c_double), ("bytes_self", C.c_int64),
                 ("max_rank", C.c_int32), ("ring_depth", C.c_int32), ("mean_rank", C.c_double),
                 ("build_seconds", C.c_double), ("n_tasks", C.c_int64)]
+
+
+class seas_friction(C.Structure):
+    _fields_ = [("a", C.c_double), ("b", C.c_double), ("dc", C.c_double), ("f0", C.c_double), ("v0", C.c_double),
+                ("sigma_n", C.c_double)]
 
 
 class seas_timing(C.Structure):
@@ -108,6 +115,14 @@ _SIGS = {
     "seas_scenario_retire": ([_VP, C.c_int], C.c_int),
     "seas_scenario_member_step": ([_VP, C.c_int, C.POINTER(C.c_int64)], C.c_int),
     "seas_ctx_get_memory": ([_VP, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)], C.c_int),
+    "seas_integrator_create": ([_VP, C.POINTER(seas_friction), C.c_int, C.c_double, _VP, _VP, _VP, C.c_int, _PP],
+                               C.c_int),
+    "seas_integrator_step": ([_VP, C.c_int], C.c_int),
+    "seas_integrator_state": ([_VP, _VP, _VP, _VP, C.c_int], C.c_int),
+    "seas_destroy_integrator": ([_VP], C.c_int),
+    "seas_push_slip_rate_steps": ([_VP, _VP, _VP, C.c_int, C.c_int, C.c_int], C.c_int),
+    "seas_integrator_step_gamma": ([_VP, C.c_int], C.c_int),
+    "seas_integrator_step_adaptive": ([_VP, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int64)], C.c_int),
 }
 
 
@@ -301,6 +316,17 @@ def seas_push_slip_rate(scn: Handle, V, slip=None, replace_last: bool = False):
     _check(lib().seas_push_slip_rate(scn.ptr, pv, ps, mem, 1 if replace_last else 0))
 
 
+def seas_push_slip_rate_steps(scn: Handle, V, gamma: int, slip=None, replace_last: bool = False):
+    """V held over `gamma` lattice steps (slip integrated, or the straight line to `slip` at the last of them)."""
+    n = scn.B * scn.N
+    dev = _device_of(scn)
+    pv, mem = _buf(V, n, "V", dev)
+    ps, mem_s = _buf(slip, n, "slip", dev)
+    if slip is not None and mem_s != mem:
+        raise ValueError("V and slip must live in the same memory")
+    _check(lib().seas_push_slip_rate_steps(scn.ptr, pv, ps, mem, int(gamma), 1 if replace_last else 0))
+
+
 def seas_stress_step(scn: Handle, tau, sigma_n=None, parts=None):
     n = scn.B * scn.N
     dev = _device_of(scn)
@@ -343,6 +369,49 @@ def seas_scenario_member_step(scn: Handle, member: int) -> int:
     n = C.c_int64()
     _check(lib().seas_scenario_member_step(scn.ptr, int(member), C.byref(n)))
     return n.value
+
+
+def seas_integrator_create(scn: Handle, friction, eps: float, tau0, V0, theta0) -> Handle:
+    """friction: one (a, b, dc, f0, v0, sigma_n) tuple for every element, or a list of N of them."""
+    fr = [friction] if isinstance(friction[0], (int, float)) else list(friction)
+    arr = (seas_friction * len(fr))(*[seas_friction(*map(float, f)) for f in fr])
+    n = scn.B * scn.N
+    dev = _device_of(scn)
+    pt, mem = _buf(tau0, n, "tau0", dev)
+    pv, m1 = _buf(V0, n, "V0", dev)
+    pth, m2 = _buf(theta0, n, "theta0", dev)
+    if m1 != mem or m2 != mem:
+        raise ValueError("tau0, V0 and theta0 must live in the same memory")
+    h = C.c_void_p()
+    _check(lib().seas_integrator_create(scn.ptr, arr, len(fr), float(eps), pt, pv, pth, mem, C.byref(h)))
+    return Handle(h, "integ", scn=scn, N=scn.N, B=scn.B)
+
+
+def seas_integrator_step(it: Handle, steps: int = 1):
+    _check(lib().seas_integrator_step(it.ptr, int(steps)))
+
+
+def seas_integrator_step_gamma(it: Handle, gamma: int):
+    _check(lib().seas_integrator_step_gamma(it.ptr, int(gamma)))
+
+
+def seas_integrator_step_adaptive(it: Handle, xi: float, gamma_max: int, steps: int = 1) -> int:
+    """Returns the lattice steps advanced."""
+    n = C.c_int64()
+    _check(lib().seas_integrator_step_adaptive(it.ptr, float(xi), int(gamma_max), int(steps), C.byref(n)))
+    return n.value
+
+
+def seas_integrator_state(it: Handle):
+    """(V, theta, slip) as host arrays [B * N]."""
+    n = it.B * it.N
+    V, th, d = np.zeros(n), np.zeros(n), np.zeros(n)
+    _check(lib().seas_integrator_state(it.ptr, V.ctypes.data, th.ctypes.data, d.ctypes.data, SEAS_MEM_HOST))
+    return V, th, d
+
+
+def seas_destroy_integrator(it: Handle):
+    _destroy(lib().seas_destroy_integrator, it)
 
 
 def seas_scenario_set_timing(scn: Handle, enable: bool = True):

@@ -561,3 +561,67 @@ def test_collinear_halves_self_plus_interaction_converge_to_the_whole_fault():
         wrong.append(min(np.linalg.norm(fs + c * fi - fw) / nw for c in (0.0, -1.0, 0.5, 2.0)))
     assert errs[0] < 0.02 and errs[1] < 0.6 * errs[0]
     assert min(wrong) > 10 * errs[0]
+
+
+def test_gamma_step_of_one_is_the_fixed_step():
+    """P15e: a step of one lattice step is the fixed-dt step, to the last bit."""
+    net = O.network(np.array([[0.0, 0.0, 0.2, 200.0, 8], [30.0, -300.0, 0.9, 160.0, 8]]), MU, CS)
+    tau0 = np.full(net.N, FR.f0 * FR.sigma_n + MU / (2 * CS) * FR.v0)
+    tau0[:8] += 1.5e6 * np.exp(-((np.arange(8) + 0.5) / 8 - 0.4) ** 2 / 0.04)
+    a = SI.Integrator(net, FR, tau0, FR.v0, FR.dc / FR.v0, max_steps=12)
+    b = SI.Integrator(net, FR, tau0, FR.v0, FR.dc / FR.v0, max_steps=12)
+    for _ in range(10):
+        np.testing.assert_array_equal(a.step(), b.step_gamma(1))
+    np.testing.assert_array_equal(a.theta, b.theta)
+
+
+def test_gamma_steps_hold_the_rate_on_the_lattice():
+    """P15f: the known stress of a step of gamma lattice steps is the stress functional (stress_history) of the
+    lattice history in which the interval holds the pushed rate and the slip grows linearly, minus its radiation
+    damping: the integrator's lattice bookkeeping against the functional's own definition."""
+    net = O.network(np.array([[0.0, 0.0, 0.2, 200.0, 8], [30.0, -300.0, 0.9, 160.0, 8]]), MU, CS)
+    tau0 = np.full(net.N, FR.f0 * FR.sigma_n + MU / (2 * CS) * FR.v0)
+    it = SI.Integrator(net, FR, tau0, 1.3 * FR.v0, FR.dc / FR.v0, max_steps=40)
+    for g in (1, 3, 2):
+        it.step_gamma(g)
+    v_push = 2.0 * it.V[-1]
+    gamma = 4
+    slips = [it.delta[-1] + (j * net.dt) * v_push for j in range(1, gamma + 1)]
+    known = it._known_stress_lattice(slips, v_push)
+    V_lat = np.stack(it.V[1:] + [v_push] * gamma)
+    hp = dict(flags=2, max_steps=40)
+    tau, rad, fself, fint = O.stress_history(net, V_lat, hp, slip=np.stack(it.delta[1:] + slips))
+    np.testing.assert_allclose(known, (tau - rad)[-1], rtol=1e-12, atol=1e-6)
+
+
+def test_gamma_steps_converge_at_second_order_without_elasticity():
+    """P15g: with negligible elasticity the gamma-step scheme is the predictor-corrector of the slider ODE with
+    step gamma dt; its error at a fixed time falls about four times when gamma halves."""
+    fr = SI.Friction(a=0.01, b=0.015, dc=2e-9, f0=0.6, v0=1e-6, sigma_n=50e6)
+    tau0 = fr.f0 * fr.sigma_n
+    net = O.network(np.array([[0.0, 0.0, 0.0, 10.0, 4]]), 1e-3, CS)
+    th0 = 5 * fr.dc / fr.v0
+    v_init = math.exp((fr.a * math.log(fr.v0) - fr.b * math.log(th0 / fr.dc)) / (fr.a + fr.b))
+    lattice = 32
+    errs = []
+    for gamma in (4, 2):
+        it = SI.Integrator(net, fr, np.full(net.N, tau0), v_init, th0, max_steps=lattice + 1)
+        for _ in range(lattice // gamma):
+            it.step_gamma(gamma)
+
+        def rhs(t, y):
+            v = math.exp((fr.a * math.log(fr.v0) - fr.b * math.log(y[0] / fr.dc)) / (fr.a + fr.b))
+            return [1.0 - v * y[0] / fr.dc]
+        ref = integrate.solve_ivp(rhs, (0, lattice * net.dt), [th0], rtol=1e-12, atol=1e-20).y[0, -1]
+        errs.append(abs(it.theta[0] - ref) / ref)
+    assert errs[1] < errs[0] / 3.5
+
+
+def test_adaptive_gamma_follows_the_rate():
+    net = O.network(np.array([[0.0, 0.0, 0.2, 200.0, 8]]), MU, CS)
+    it = SI.Integrator(net, FR, np.full(net.N, FR.f0 * FR.sigma_n), FR.v0, FR.dc / FR.v0, max_steps=4)
+    g = it.adaptive_gamma(0.5, 10 ** 9)
+    assert g == math.ceil(0.5 * FR.dc / FR.v0 / net.dt)
+    assert it.adaptive_gamma(0.5, 100) == 100
+    it.V[-1] = np.full(net.N, 1.0)
+    assert it.adaptive_gamma(0.5, 100) == 1
