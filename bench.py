@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-oracle-rows", action="store_true", help="skip the oracle interaction rows (errors)")
     ap.add_argument("--dump-step-bytes", default=None, help="write the per-step algorithmic interaction bytes here")
     ap.add_argument("--served-seconds", type=float, default=15.0, help="wall time of the served run (0: skip)")
+    ap.add_argument("--max-steps", type=int, default=None,
+                    help="build the workload for this many steps instead (smaller operators for profiling captures)")
+    ap.add_argument("--batched-only", action="store_true", help="only the 8-scenario ensemble runs (profiling)")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 8 geometries x 8 scenarios run")
     return ap.parse_args()
 
 
@@ -306,11 +310,13 @@ def roofline_of(timing, batch, peak, fp64_peak, prec):
     """Roofline of the interaction kernel from the library's per-kernel events over a timed window."""
     ms = timing["ms"]
     n_launch = max(1, timing["launches"]["interaction"])
-    inter_ms = ms["interaction"]
+    inter_ms = ms["interaction"] + ms["interaction_source"]          # the two passes of one interaction step
     secs = inter_ms / 1e3
     gbs = timing["interaction_bytes"] / secs / 1e9 if inter_ms > 0 else 0.0
-    common = {"kernel": "k_interaction", "algorithmic_bytes_per_launch": timing["interaction_bytes"] / n_launch,
+    common = {"kernel": "k_interaction (source pass + receiver pass of one step)",
+              "algorithmic_bytes_per_launch": timing["interaction_bytes"] / n_launch,
               "mean_launch_ms": inter_ms / n_launch, "dominant_by_time": max(ms, key=ms.get),
+              "pass_ms": {"source": ms["interaction_source"] / n_launch, "receiver": ms["interaction"] / n_launch},
               "kernel_ms": ms, "launches": timing["launches"]}
     if prec == 0:
         # FP64: one FMA per 8 algorithmic bytes per scenario; the FP64 pipe is below the HBM rate
@@ -406,6 +412,8 @@ def run_ours(args, w, start, K, W):
         return {"total_ms": total_ms, "per": per, "tau": tau, "parts": parts, "timing": timing,
                 "roofline": roofline_of(timing, batch, peak, fp64_peak, prec), "clocks": clk_summary}
 
+    if args.batched_only:
+        return run_batched_only(args, w, start, K, seas, torch, session, measure, device, rows, int_err, world)
     # ---- headline: scenario A (no kernel timing) for value and latency; B, a copy of A's state at the window's
     # start, for the per-kernel events of the roofline; C, another copy, end to end through host buffers
     head_code, head_dtype = PRECISIONS[args.precision]
@@ -481,7 +489,7 @@ def run_ours(args, w, start, K, W):
                               "rel_l2_tau_vs_headline": rel(r2["tau"].cpu().numpy(), tau.cpu().numpy()),
                               "bytes_interaction": s2.stats["bytes_interaction"],
                               "roofline": {k: r2["roofline"][k] for k in (
-                                  "bound", "achieved", "peak", "unit", "frac", "mean_launch_ms")}}
+                                  "bound", "achieved", "peak", "unit", "frac", "mean_launch_ms", "pass_ms")}}
             s2.close()
             del r2
 
@@ -505,7 +513,7 @@ def run_ours(args, w, start, K, W):
                              "rel_l2_member0_interaction_vs_oracle": int_err(r3["parts"], 0),
                              "rel_l2_member0_tau_vs_headline": rel(t0.cpu().numpy(), tau.cpu().numpy()),
                              "roofline": {k: r3["roofline"][k] for k in (
-                                 "bound", "achieved", "peak", "unit", "frac", "mean_launch_ms")}}
+                                 "bound", "achieved", "peak", "unit", "frac", "mean_launch_ms", "pass_ms")}}
             s3.close()
             del r3
         del V8d
@@ -536,6 +544,7 @@ def run_ours(args, w, start, K, W):
         del rp
 
     served = run_served(args, dist, local) if args.served_seconds > 0 and rank == 0 else None
+    ensemble = run_ensemble88(args, dist, local, K, peak, world) if not args.no_ensemble else None
 
     roofline["traffic"] = None
     tf = os.path.join(ROOT, "profiles", "interaction_traffic.json")
@@ -569,13 +578,71 @@ def run_ours(args, w, start, K, W):
                     "n_blocks_far", "n_blocks_near", "compression_ratio", "bytes_interaction", "mean_rank",
                     "max_rank", "build_seconds", "n_tasks")},
                 "vs_plain_fp64_gpu": plain, "variants": variants, "batched": batched, "static_tail": tail, "e2e": e2e,
-                "served": served,
+                "served": served, "ensemble_8x8": ensemble,
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": int(sum(launches.values()))}
     s.close()
     if dist is not None:
         dist.destroy_process_group()
     return line
+
+
+def run_batched_only(args, w, start, K, seas, torch, session, measure, device, rows, int_err, world):
+    """The 8-scenario ensemble legs alone (profiling captures of the batched kernels)."""
+    B = 8
+    V8 = np.stack([w.slip_rate(b, 0, w.steps) for b in range(B)], axis=1).reshape(w.steps, B * w.N)
+    V8d = torch.from_numpy(V8).to(device)
+    out = {}
+    for name in ("bf16", "fp64"):
+        code, dtype = PRECISIONS[name]
+        s3 = session(code, batch=B)
+        r3 = measure(s3, V8d, B, code)
+        out[name] = {"value": job_rate(B * w.N * K, world, r3["total_ms"] / 1e3), "ms_per_step": r3["total_ms"] / K,
+                     "roofline": {k: r3["roofline"][k] for k in ("bound", "achieved", "frac", "mean_launch_ms",
+                                                                   "pass_ms")}}
+        s3.close()
+    return {"batched_only": out, "config": config_of(w, start, K)}
+
+
+def run_ensemble88(args, dist, local, K, peak, world):
+    """Batched ensemble: 64 scenarios over 8 seeded geometries (2..12 faults, 500..6000 elements, 1000..5000 steps),
+    8 scenarios with independent slip-rate histories per geometry sharing its BF16 operator in one scenario batch
+    (tensor-core consumers).  Each geometry is advanced untimed to its K deepest steps, which are timed; the value
+    is the element-steps of all 64 scenarios over the summed timed time of the 8 batches (run one after another)."""
+    import torch
+    from paper_2603_00383_gb300 import seas
+    code, dtype = PRECISIONS["bf16"]
+    device = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(device)
+    total_ms, units, inter_ms, inter_bytes, per = 0.0, 0, 0.0, 0, []
+    t_all = time.perf_counter()
+    for g in range(8):
+        w = synth.ensemble_network(g)
+        start, k = window(w, K)
+        B = 8
+        s = seas.Session(w, batch=B, device=local, stream=stream.cuda_stream, precision=code)
+        Vd = torch.from_numpy(np.stack([w.slip_rate(b, 0, w.steps) for b in range(B)], axis=1).reshape(
+            w.steps, B * w.N)).to(device)
+        advance(seas, torch, s.scn, Vd, 0, start, device)
+        seas.seas_scenario_set_timing(s.scn, True)
+        ms, pstep, _, _ = timed_run(seas, torch, s.scn, Vd, start, k, dist, device)
+        seas.seas_scenario_check(s.scn)
+        tm = seas.seas_scenario_get_timing(s.scn)
+        total_ms += ms
+        units += B * w.N * k
+        inter_ms += tm["ms"]["interaction"] + tm["ms"]["interaction_source"]
+        inter_bytes += tm["interaction_bytes"]
+        per.append({"geometry": g, "faults": w.n_faults, "elements": w.N, "steps": w.steps,
+                    "ms_per_step": ms / k, "p50_ms": float(np.percentile(pstep, 50)),
+                    "bytes_interaction": s.stats["bytes_interaction"]})
+        s.close()
+        del Vd
+    log(f"ensemble 8x8: {time.perf_counter() - t_all:.1f} s, {units / (total_ms / 1e3) / 1e6:.2f} M element-steps/s")
+    gbs = inter_bytes / (inter_ms / 1e3) / 1e9 if inter_ms > 0 else 0.0
+    total_ms = max_over_ranks(dist, total_ms, device)
+    return {"value": job_rate(units, world, total_ms / 1e3), "unit": METRIC, "dtype": dtype, "scenarios": 64,
+            "timed_steps_per_geometry": K, "geometries": per,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak[0], "unit": "GB/s", "frac": gbs / peak[0]}}
 
 
 SERVED = dict(pool=8, rate=20.0, steps_lo=1000, steps_hi=20000, lag_cap=500, batch=8, budget=24 << 30,
@@ -646,7 +713,8 @@ def seas_kernel_version():
 
 def main():
     args = parse()
-    w = synth.WORKLOADS[args.workload]()
+    w = synth.WORKLOADS[args.workload]() if args.max_steps is None else synth.WORKLOADS[args.workload](
+        steps=args.max_steps)
     start, K = window(w, args.steps)
     W = max(3, args.warmup)
     if args.impl == "reference":

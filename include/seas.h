@@ -147,8 +147,9 @@ seas_status seas_create(seas_ctx **ctx, int device, size_t hbm_budget, void *cud
 seas_status seas_ctx_get_memory(const seas_ctx *ctx, size_t *used, size_t *budget);
 
 /* Builds the discretised network (Sec. 2.3.1 "Discretization", Sec. 3.1 frames).  Rejects non-finite or
- * non-positive sizes, N_f whose 2,3,5-free part is not 1, N_f > 7168, and receiver centroids lying on another
- * fault (within 1e-6 ds of one of its elements, where the kernel is singular). */
+ * non-positive sizes, N_f with a prime factor above 23 (the FFT's radices), N_f > 7168, and receiver centroids lying
+ * on another fault (within 1e-6 ds of one of its elements, where the kernel is singular: faults that cross must do
+ * so at an element boundary, as the X-shaped network of Sec. 3.2 does). */
 seas_status seas_build_network(seas_ctx *ctx, const seas_fault *faults, int n_faults, const seas_medium *medium,
                                seas_net **net);
 seas_status seas_net_get_info(const seas_net *net, seas_net_info *info);
@@ -215,6 +216,18 @@ seas_status seas_scenario_set_wait_limit(seas_scn *scn, double seconds);
  * involved.  No counterpart in the paper. */
 seas_status seas_scenario_probe_wait(seas_scn *scn);
 
+/* CUDA-graph stepping.  seas_scenario_graph_create captures one step of the scenario -- a push of the slip rate in
+ * the caller's device buffer V ([batch][N], slip integrated) and a stress step into the device buffers tau
+ * ([batch][N]) and parts (nullable, [3][batch][N]) -- as one graph of all its kernels (interaction passes on every
+ * SM).  seas_scenario_graph_step then advances the scenario by one step: it uploads the step's index, lag horizon
+ * and task counts (asynchronously, from a pinned ring) and launches the graph, so a step costs two API calls
+ * instead of one launch per kernel.  V and tau are read and written at the addresses given at capture; the caller
+ * refills V between steps in stream order.  Results equal those of seas_push_slip_rate + seas_stress_step bit for
+ * bit; ordinary pushes and steps may be interleaved with graph steps.  Not available while kernel timing is on
+ * (SEAS_ESTATE); the graph lives until the scenario is destroyed.  No counterpart in the paper. */
+seas_status seas_scenario_graph_create(seas_scn *scn, const double *V, double *tau, double *parts);
+seas_status seas_scenario_graph_step(seas_scn *scn);
+
 /* Number of pushes so far (ticks of the batch; equal to every member's step count unless members were admitted
  * later). */
 seas_status seas_scenario_step(const seas_scn *scn, int64_t *n);
@@ -252,13 +265,14 @@ seas_status seas_plan_hmatrix(const seas_fault *faults, int n_faults, const seas
 
 /* Kernel timing on the context stream (tracing).  set_timing(1) resets and starts recording a CUDA event pair
  * around every kernel the scenario launches; get_timing synchronises and returns, per kernel class (0 push,
- * 1 forward FFT, 2 mode convolution, 3 interaction, 4 interaction reduction (with the static tail when that flag
- * is set), 5 inverse FFT + assembly), the launch count and the summed device time, plus the algorithmic bytes the
- * interaction kernel streamed (seas_op_step_bytes summed over the timed steps).  The first set_timing(1) of a
+ * 1 forward FFT, 2 mode convolution, 3 interaction receiver side (pass 2: U z and A x sums), 4 interaction reduction
+ * (with the static tail when that flag is set), 5 inverse FFT + assembly, 6 interaction source side (pass 1:
+ * z = V^T x)), the launch count and the summed device time, plus the algorithmic bytes the two interaction passes
+ * streamed (seas_op_step_bytes summed over the timed steps).  The first set_timing(1) of a
  * scenario creates its events (8192 pairs), so that timed steps pay only for the event records. */
 typedef struct {
-    int64_t launches[6];
-    double ms[6];
+    int64_t launches[7];
+    double ms[7];
     int64_t interaction_bytes;
     int64_t steps;
 } seas_timing;

@@ -140,9 +140,10 @@ struct HostBuf {
     }
 };
 
-bool is_235_smooth(int n) {
+// Fault sizes the FFT handles: products of the radices 2, 3, 5, 7, 11, 13, 17, 19 and 23.
+bool is_fft_size(int n) {
     if (n < 1) return false;
-    for (int f : {2, 3, 5})
+    for (int f : {2, 3, 5, 7, 11, 13, 17, 19, 23})
         while (n % f == 0) n /= f;
     return n == 1;
 }
@@ -222,6 +223,14 @@ struct seas_scn {
     std::vector<char> active;        // per member: 1 while admitted
     int64_t horizon = -1;            // largest lag the interaction has switched on (non-decreasing)
     int last_gamma = 1;              // lattice steps of the last push (seas_push_slip_rate_steps)
+    // captured step (seas_scenario_graph_create): the graph, its per-step values on the device, and a pinned ring
+    // of host copies the asynchronous uploads read from
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    DArr<DynDev> d_dyn;
+    HostBuf h_dyn;
+    int64_t dyn_used = 0;
+    cudaEvent_t dyn_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     DArr<unsigned char> zbuf;        // pass-1 output: [z rows][batch] in the dot type of the precision
     DArr<double> vring, slip, slip_prev, fint, d_V, d_slip, d_tau, d_parts, partial;
     DArr<double> sring;              // static tail: slip after each push, [op->ring + 1][N][B]
@@ -241,6 +250,10 @@ struct seas_scn {
     seas_timing acc{};
     ~seas_scn() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (cudaEvent_t e : dyn_ev)
+            if (e) cudaEventDestroy(e);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
     }
 };
 
@@ -358,8 +371,8 @@ seas_status make_geometry(const seas_fault *faults, int n_faults, const seas_med
             return fail(SEAS_EINVAL, "fault %d: non-finite or non-positive geometry", f);
         if (F.n_elem < 1 || F.n_elem > kMaxFFT)
             return fail(SEAS_EINVAL, "fault %d: n_elem %d outside [1, %d]", f, F.n_elem, kMaxFFT);
-        if (!is_235_smooth(F.n_elem))
-            return fail(SEAS_EINVAL, "fault %d: n_elem %d has a prime factor > 5 (FFT radices are 2, 3, 5)", f,
+        if (!is_fft_size(F.n_elem))
+            return fail(SEAS_EINVAL, "fault %d: n_elem %d has a prime factor > 23 (FFT radices are the primes <= 23)", f,
                         F.n_elem);
         N += F.n_elem;
     }
@@ -593,7 +606,7 @@ int32_t mode_window(const seas_net &net, int f, int n, const seas_hparams &hp, b
 
 std::vector<int> radix_plan(int n) {
     std::vector<int> r;
-    for (int R : {4, 2, 3, 5})
+    for (int R : {4, 2, 3, 5, 7, 11, 13, 17, 19, 23})
         while (n % R == 0 && !(R == 2 && n % 4 == 0)) {
             r.push_back(R);
             n /= R;
@@ -980,8 +993,9 @@ seas_status build_interaction(seas_op &op) {
             const int sidx = src_of[x.block];
             const int q2 = pad_row(srcs[sidx].q, prec);
             const int64_t row_bytes = (int64_t)q2 * eb;
+            // a run's rows, their z-row map (4 bytes a row) and its history slice fit one stage
             const int64_t max_rows =
-                std::max<int64_t>(1, (kStageBytes - 16 - (int64_t)q2 * x_cap) / row_bytes);
+                std::max<int64_t>(1, (kStageBytes - 32 - (int64_t)q2 * x_cap) / (row_bytes + 4));
             unsigned char *d = op.d_varena.p + off;
             gsrc.push_back(x.v);
             gdst.push_back(d);
@@ -1405,7 +1419,7 @@ extern "C" seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **o
         for (size_t b = 0; b < op->blocks_h.size(); ++b) {
             if (!op->block_far[b]) continue;
             const int64_t q2 = pad_row(op->blocks_h[b].q, op->hp.precision);
-            if (q2 * eb + (q2 * batch * xb + 15) / 16 * 16 + 16 > kStageBytes)
+            if (q2 * eb + (q2 * batch * xb + 15) / 16 * 16 + 32 > kStageBytes)
                 return fail(SEAS_EINVAL, "batch %d too large for blocks of %d columns (stage of %d bytes)", batch,
                             op->blocks_h[b].q, kStageBytes);
         }
@@ -1560,7 +1574,8 @@ extern "C" seas_status seas_stress_step(seas_scn *s, double *tau, double *sigma_
     double *dtau = mem == SEAS_MEM_DEVICE ? tau : s->d_tau.p;
     double *dparts = parts ? (mem == SEAS_MEM_DEVICE ? parts : s->d_parts.p) : nullptr;
     SEAS_TRY(timed(*s, 2, [&] { return launch_modeconv(a, c->stream); }));
-    SEAS_TRY(timed(*s, 3, [&] { return launch_interaction(a, c->stream); }));
+    SEAS_TRY(timed(*s, 6, [&] { return launch_interaction(a, 1, c->stream); }));
+    SEAS_TRY(timed(*s, 3, [&] { return launch_interaction(a, 2, c->stream); }));
     SEAS_TRY(timed(*s, 4, [&] {
         const cudaError_t e = launch_reduce(a, c->stream);
         return e != cudaSuccess ? e : launch_static_tail(a, c->stream);
@@ -1606,7 +1621,8 @@ extern "C" seas_status seas_stress_step_static(seas_scn *s, double *tau, double 
     a.partial = scratch;
     a.fint = scratch + op.n_partial * s->B;
     CUDA_TRY(launch_modeconv(a, c->stream));
-    CUDA_TRY(launch_interaction(a, c->stream));
+    CUDA_TRY(launch_interaction(a, 1, c->stream));
+    CUDA_TRY(launch_interaction(a, 2, c->stream));
     CUDA_TRY(launch_reduce(a, c->stream));
     CUDA_TRY(launch_static_tail(a, c->stream));
     CUDA_TRY(launch_ifft_assemble(a, tau, parts, c->stream));
@@ -1675,6 +1691,90 @@ extern "C" seas_status seas_scenario_probe_wait(seas_scn *s) {
     CUDA_TRY(cudaSetDevice(c->device));
     const StepArgs a = step_args(*s, s->n > 0 ? s->n - 1 : 0);
     CUDA_TRY(launch_wait_probe(a, c->stream));
+    return SEAS_OK;
+}
+
+namespace {
+constexpr int64_t kDynRing = 1024;     // pinned host copies of per-step values in flight
+}
+
+extern "C" seas_status seas_scenario_graph_create(seas_scn *s, const double *V, double *tau, double *parts) {
+    if (!s || !V || !tau) return fail(SEAS_EINVAL, "NULL argument");
+    if (s->gexec) return fail(SEAS_ESTATE, "the scenario already has a captured step");
+    if (s->timing) return fail(SEAS_ESTATE, "kernel timing is on: a captured step records no timing events");
+    seas_op &op = *s->op;
+    seas_ctx *c = op.net->ctx;
+    CUDA_TRY(cudaSetDevice(c->device));
+    SEAS_TRY(s->d_dyn.alloc(c, 1));
+    SEAS_TRY(s->h_dyn.alloc(sizeof(DynDev) * kDynRing));
+    for (cudaEvent_t &e : s->dyn_ev)
+        if (!e) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    StepArgs a = step_args(*s, s->n);
+    a.dyn = s->d_dyn.p;
+    // captured on a stream of its own (the context's stream may be the legacy default stream, which cannot be
+    // captured); the graph is launched on the context's stream
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    cudaStream_t st = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } guard{st};
+    CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    cudaError_t e = launch_push(a, V, nullptr, 0, 1, 1, st);
+    if (e == cudaSuccess) e = launch_fft_forward(a, st);
+    if (e == cudaSuccess) e = launch_modeconv(a, st);
+    if (e == cudaSuccess) e = launch_interaction(a, 1, st);
+    if (e == cudaSuccess) e = launch_interaction(a, 2, st);
+    if (e == cudaSuccess) e = launch_reduce(a, st);
+    if (e == cudaSuccess) e = launch_static_tail(a, st);
+    if (e == cudaSuccess) e = launch_ifft_assemble(a, tau, parts, st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(SEAS_ECUDA, "step capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t x = nullptr;
+    const cudaError_t e3 = cudaGraphInstantiate(&x, g, 0);
+    if (e3 != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(SEAS_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e3));
+    }
+    s->graph = g;
+    s->gexec = x;
+    s->dyn_used = 0;
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_scenario_graph_step(seas_scn *s) {
+    if (!s) return fail(SEAS_EINVAL, "NULL scenario");
+    if (!s->gexec) return fail(SEAS_ESTATE, "no captured step (seas_scenario_graph_create)");
+    seas_op &op = *s->op;
+    seas_ctx *c = op.net->ctx;
+    if (!(op.hp.flags & SEAS_FLAG_LAG_CAP))
+        for (int b = 0; b < s->B; ++b)
+            if (s->active[b] && s->n - s->start[b] >= op.hp.max_steps)
+                return fail(SEAS_ESTATE, "push %lld of member %d beyond max_steps %d",
+                            (long long)(s->n - s->start[b]), b, op.hp.max_steps);
+    CUDA_TRY(cudaSetDevice(c->device));
+    // a ring slot is written again only after the uploads issued kDynRing steps earlier have run
+    const int64_t i = s->dyn_used;
+    if (i % (kDynRing / 4) == 0) {
+        cudaEvent_t &ev = s->dyn_ev[(i / (kDynRing / 4)) % 4];
+        if (i >= kDynRing) CUDA_TRY(cudaEventSynchronize(ev));
+        CUDA_TRY(cudaEventRecord(ev, c->stream));
+    }
+    s->n++;
+    s->last_gamma = 1;
+    const StepArgs a = step_args(*s, s->n - 1);
+    DynDev *h = static_cast<DynDev *>(s->h_dyn.p) + (i % kDynRing);
+    *h = DynDev{a.step, a.lag_max, a.n_tasks_active, a.n_ztasks_active};
+    CUDA_TRY(cudaMemcpyAsync(s->d_dyn.p, h, sizeof(DynDev), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaGraphLaunch(s->gexec, c->stream));
+    s->dyn_used++;
     return SEAS_OK;
 }
 

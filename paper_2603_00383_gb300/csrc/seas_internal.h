@@ -17,7 +17,7 @@ constexpr int kRowsPerThread = kMaxBlockSide / kThreads;
 constexpr int kItemRows = 256;      // rows of one pass-2 item (bounds its staged history / z rows)
 constexpr int kMaxBatch = 8;        // scenarios per scenario handle (one pass of the interaction kernel)
 constexpr int kItemBytes = 24 * 1024;   // largest pass-2 item (operator bytes)
-constexpr int kStageBytes = 64 * 1024;  // one shared-memory stage of the interaction pipeline
+constexpr int kStageBytes = 68 * 1024;  // one shared-memory stage of the interaction pipeline
 constexpr int kStages = 3;              // stages in flight per CTA
 constexpr int kStageItems = 31;         // units per stage (one producer lane each)
 constexpr int64_t kTaskBytes = 1 << 20; // operator bytes per task (one deterministic partial sum)
@@ -156,6 +156,12 @@ cudaError_t launch_spectral_tables(const ModeDev *modes, int n_modes, const int6
                                    int gl_n, double *G, double *w, cudaStream_t s);
 
 // ---- step kernels (seas_step.cu) ----
+// Per-step values a replayed CUDA graph reads from device memory instead of its baked kernel parameters.
+struct DynDev {
+    int64_t step, lag_max;
+    int32_t n_tasks_active, n_ztasks_active;
+};
+
 struct StepArgs {
     int N, F, B, n_modes_total;   // elements, faults, batch, sum over faults of (N_f + 1)
     int max_nf;                   // largest N_f (shared memory of the FFT kernels)
@@ -191,6 +197,7 @@ struct StepArgs {
     int n_ztasks_active;
     void *zbuf;                   // [z rows][B] in the arithmetic's dot type (double, float2 or float)
     int pass;                     // 1 or 2: which pass a launch of the interaction kernel runs
+    const DynDev *dyn;            // non-null in a captured step: step, lag_max and task counts come from here
     double *partial;              // [B][n_partial]
     int64_t n_partial;
     int *counter;                 // [0]: pass-2 task counter, [2]: pass-1 task counter (reset by the reduction)
@@ -231,7 +238,7 @@ cudaError_t launch_push(const StepArgs &a, const double *V, const double *slip_i
                         int gamma, cudaStream_t s);
 cudaError_t launch_fft_forward(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s);
-cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_interaction(const StepArgs &a, int pass, cudaStream_t s);   // pass 1, then pass 2
 cudaError_t launch_reduce(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_static_tail(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_ifft_assemble(const StepArgs &a, double *tau, double *parts, cudaStream_t s);

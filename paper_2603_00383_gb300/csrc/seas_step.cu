@@ -18,6 +18,17 @@ static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
 
 namespace {
 
+// In a replayed graph the step-dependent fields come from device memory.
+__device__ __forceinline__ void apply_dyn(StepArgs &a) {
+    if (a.dyn) {
+        const DynDev d = *a.dyn;
+        a.step = d.step;
+        a.lag_max = d.lag_max;
+        a.n_tasks_active = d.n_tasks_active;
+        a.n_ztasks_active = d.n_ztasks_active;
+    }
+}
+
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -26,8 +37,9 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
 // ------------------------------------------------------------------------------------------------------------
-// Self-sorting (Stockham) mixed-radix FFT of N points held in shared memory, radices 2, 3, 4, 5.  Stage with
-// radix R after sub-transforms of size Ns: butterfly j takes src[j + r N/R] (r < R), twiddles it by
+// Self-sorting (Stockham) mixed-radix FFT of N points held in shared memory, radices 2, 3, 4, 5, 7, 11, 13, 17, 19,
+// 23 (the odd primes as plain R-point DFTs).  Stage with radix R after sub-transforms of size Ns: butterfly j takes
+// src[j + r N/R] (r < R), twiddles it by
 // W_{Ns R}^{r (j mod Ns)}, takes an R-point DFT and writes dst[(j / Ns) Ns R + (j mod Ns) + t Ns].
 // tw[k] = e^{-2 pi i k / N}; the inverse (unnormalised) uses conjugate twiddles.  Returns the buffer holding the
 // result.  All threads of the CTA must call it.
@@ -90,7 +102,13 @@ __device__ double2 *fft_stockham(double2 *src, double2 *dst, int N, const int *r
             case 2: fft_stage<2>(src, dst, N, Ns, tw, inverse); break;
             case 3: fft_stage<3>(src, dst, N, Ns, tw, inverse); break;
             case 4: fft_stage<4>(src, dst, N, Ns, tw, inverse); break;
-            default: fft_stage<5>(src, dst, N, Ns, tw, inverse); break;
+            case 5: fft_stage<5>(src, dst, N, Ns, tw, inverse); break;
+            case 7: fft_stage<7>(src, dst, N, Ns, tw, inverse); break;
+            case 11: fft_stage<11>(src, dst, N, Ns, tw, inverse); break;
+            case 13: fft_stage<13>(src, dst, N, Ns, tw, inverse); break;
+            case 17: fft_stage<17>(src, dst, N, Ns, tw, inverse); break;
+            case 19: fft_stage<19>(src, dst, N, Ns, tw, inverse); break;
+            default: fft_stage<23>(src, dst, N, Ns, tw, inverse); break;
         }
         __syncthreads();
         double2 *tmp = src;
@@ -104,8 +122,10 @@ __device__ double2 *fft_stockham(double2 *src, double2 *dst, int N, const int *r
 // Push j (1..gamma) of a slip rate held over gamma lattice steps: V into the ring slot of the tick, and the slip
 // delta^{n+j} = delta^n + j dt V (or the caller's slip delta^{n+gamma} on the straight line from delta^n); delta^n is
 // kept in slip_prev for the corrector's replacement.  gamma = 1: one ordinary push.
-__global__ void k_push(StepArgs a, const double *__restrict__ V, const double *__restrict__ slip_in,
+__global__ void k_push(StepArgs a_, const double *__restrict__ V, const double *__restrict__ slip_in,
                        int replace_last, int j, int gamma) {
+    StepArgs a = a_;
+    apply_dyn(a);
     const int64_t BN = (int64_t)a.B * a.N;
     const int slot = (int)(a.step % a.ring);
     double *vr = a.vring + (int64_t)slot * a.ring_stride;
@@ -137,7 +157,9 @@ __global__ void k_push(StepArgs a, const double *__restrict__ V, const double *_
 // delta_j e^{-2 pi i k j / M}, M = 2 N_f, k = 0..N_f, from one N_f-point complex FFT of z_j = x_{2j} + i x_{2j+1}
 // (x = delta padded with zeros): X_k = E_k + e^{-2 pi i k/M} O_k, E_k = (Z_k + conj Z_{N-k})/2,
 // O_k = (Z_k - conj Z_{N-k})/(2i).  One CTA per (fault, scenario); D^n goes to ring slot n mod R_f.
-__global__ void __launch_bounds__(kThreads) k_fft_forward(StepArgs a) {
+__global__ void __launch_bounds__(kThreads) k_fft_forward(StepArgs a_) {
+    StepArgs a = a_;
+    apply_dyn(a);
     extern __shared__ double2 smem[];
     const FaultDev &fd = a.faults[blockIdx.x];
     const int b = blockIdx.y;
@@ -169,7 +191,9 @@ __global__ void __launch_bounds__(kThreads) k_fft_forward(StepArgs a) {
 // Per-mode causal convolution (Eq. funcational_discretized_form):
 //   F_n = -(mu k_n / 2) sum_{T=0}^{min(W_f(n), step)} w_n^T D_n^{step - T},  k_n = pi n / L_f.
 // One warp per (mode, scenario); lanes stride the lags; the ring is mode-major so the lanes read contiguous slots.
-__global__ void __launch_bounds__(kThreads) k_modeconv(StepArgs a) {
+__global__ void __launch_bounds__(kThreads) k_modeconv(StepArgs a_) {
+    StepArgs a = a_;
+    apply_dyn(a);
     const int md = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int b = blockIdx.y;
@@ -211,8 +235,10 @@ __global__ void __launch_bounds__(kThreads) k_modeconv(StepArgs a) {
 // Inverse transform and assembly: f_self,j = sum_{n=-N_f+1}^{N_f} F_n e^{2 pi i n j / M} (F_{-n} = conj F_n,
 // F_0 = 0), kept for j < N_f, from one N_f-point inverse complex FFT; then
 // tau = -(mu / 2 c_s) V + f_self + f_int (Eq. superimposition2).
-__global__ void __launch_bounds__(kThreads) k_ifft_assemble(StepArgs a, double *__restrict__ tau,
+__global__ void __launch_bounds__(kThreads) k_ifft_assemble(StepArgs a_, double *__restrict__ tau,
                                                             double *__restrict__ parts) {
+    StepArgs a = a_;
+    apply_dyn(a);
     extern __shared__ double2 smem[];
     const FaultDev &fd = a.faults[blockIdx.x];
     const int b = blockIdx.y;
@@ -268,8 +294,10 @@ __global__ void __launch_bounds__(kThreads) k_ifft_assemble(StepArgs a, double *
 // Threads of the interaction kernel for a batch width BT: CW consumer warps (16 while the accumulators are small
 // enough for 120 registers, which hides more shared-memory and pipe latency) plus one producer warp; RV values per
 // flush round keep the reduction buffer at 16 KB.
-template <int BT> struct InterShape {
-    static constexpr int CW = BT <= 2 ? 16 : 8;
+template <int PREC, int BT, int PASS> struct InterShape {
+    // the tensor-core consumers (BF16, 8 scenarios) keep four accumulators per thread: 16 warps on the receiver
+    // side; on the source side, where a stage holds few pieces, 8 (fewer warps at each barrier)
+    static constexpr int CW = BT <= 2 || (PREC == kPrecBF16 && BT == 8 && PASS == 2) ? 16 : 8;
     static constexpr int NC = CW * 32;
     static constexpr int NT = NC + 32;
     static constexpr int RV = CW == 8 ? 8 : 4;
@@ -281,7 +309,7 @@ struct StageItem {
     int32_t data_off, x_off;     // byte offsets in the stage of the unit's operator rows and of its history / z rows
     int32_t row_end;
     float scale;
-    int32_t pad;
+    int32_t map_off;             // pass 1: byte offset in the stage of the run's z-row map (int32 per row)
     int64_t map;                 // pass 1: first zmap entry of the run
 };
 
@@ -298,10 +326,11 @@ struct StageInfo {
 // Dynamic shared memory of the interaction kernel for batch width BT, in bytes from the start: the stages, their
 // descriptors, the flush buffer and the full/empty mbarriers.  The kernel and its launcher both use this, and the
 // kernel checks the end against the size it was launched with.
-template <int BT> struct InterLayout {
+template <int PREC, int BT, int PASS> struct InterLayout {
     static constexpr size_t info = (size_t)kStages * kStageBytes;
     static constexpr size_t red = info + kStages * sizeof(StageInfo);
-    static constexpr size_t bars = red + (size_t)InterShape<BT>::NC * InterShape<BT>::RV * sizeof(double);
+    static constexpr size_t bars =
+        red + (size_t)InterShape<PREC, BT, PASS>::NC * InterShape<PREC, BT, PASS>::RV * sizeof(double);
     static constexpr size_t total = bars + 2 * kStages * sizeof(uint64_t);
     static_assert(sizeof(StageInfo) % 8 == 0 && red % 8 == 0 && bars % 8 == 0, "8-byte alignment");
     static_assert(total <= 227 * 1024, "shared memory per CTA");
@@ -657,10 +686,31 @@ __device__ __forceinline__ void mask_a_k(uint32_t (&a)[4], int tg, int kvalid) {
     }
 }
 
-// Consumer warps of k_interaction<BF16, 8, PASS>: one consumer barrier per stage (it also hands the previous stage
-// back to the producer).
+// Splits the FP32 operand rows [rows][8] of one unit, in place, into packed BF16 (hi, lo) pairs laid out as MMA B
+// fragments: word 16 rp + n holds the hi parts of rows 2 rp and 2 rp + 1 of scenario n, word 16 rp + 8 + n their lo
+// parts (a missing odd last row counts as zero).  Each thread reads exactly the two words it writes, so the
+// transform needs no barrier inside; the caller's barrier publishes it.
+__device__ __forceinline__ void split_rows_inplace(unsigned char *area, int rows, int t, int nthreads) {
+    float *f = reinterpret_cast<float *>(area);
+    uint32_t *w = reinterpret_cast<uint32_t *>(area);
+    const int pairs = (rows + 1) >> 1;
+    for (int o = t; o < pairs * 8; o += nthreads) {
+        const int rp = o >> 3, n = o & 7;
+        const float v0 = f[16 * rp + n];
+        const float v1 = 2 * rp + 1 < rows ? f[16 * rp + 8 + n] : 0.f;
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+        w[16 * rp + n] = pack_bf16(h0, h1);
+        w[16 * rp + 8 + n] = pack_bf16(l0, l1);
+    }
+}
+
+// Consumer warps of k_interaction<BF16, 8, PASS>.  Per stage: the barrier that opens it (and hands the previous
+// stage back to the producer), the split of the stage's FP32 operand rows into BF16 hi / lo fragments in place,
+// a second barrier, then the MMAs, which read their B fragments with one 32-bit shared load each.
 //   Pass 1: each (run, 16 rows) piece is one warp's Z tile over the run's source columns; its rows go to the z rows
-//   that zmap gives.
+//   that the staged z-row map gives.
 //   Pass 2: the task's receivers form mt 16-row tiles; warp w owns tile w mod mtp in group w / mtp (mtp = mt
 //   rounded up to 1, 2, 4 or 8) and the stage's (unit, 16-row chunk) pieces are dealt round-robin to the groups; at
 //   the task's end the groups are added in a fixed order.  Blocks are at most 128 receivers wide here (scenario
@@ -676,11 +726,12 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
     int cur = -1, mt = 1, mtp = 1, G = CW, grp = 0, tile = 0;
     bool act = true;
     float2 acc[4];
-    float dst[4];
+    float dst[4], dsl[4];                                  // products with the hi and the lo parts of the operand
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         acc[v] = make_float2(0.f, 0.f);
         dst[v] = 0.f;
+        dsl[v] = 0.f;
     }
     for (int gi = 0;; ++gi) {
         const int slot = gi % kStages;
@@ -690,7 +741,15 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
         if (t == 0 && gi > 0) mbar_arrive(&empty[(gi - 1) % kStages]);
         const StageInfo &si = info[slot];
         if (si.task < 0) break;
-        const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
+        unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
+        if constexpr (PASS == 2) {
+            // B operand rows of every unit (z or history rows), split into fragments once per stage
+            for (int m = 0; m < si.n; ++m) {
+                const StageItem &it = si.it[m];
+                split_rows_inplace(base + it.x_off, it.k < 0 ? it.i1 - it.i0 : it.k, t, NC);
+            }
+            consumer_sync<NC>();
+        }
         if constexpr (PASS == 1) {
             const int q2 = pad_row(si.q, kPrecBF16);
             int u = 0;
@@ -699,32 +758,43 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
                 const int rows = it.k;
                 const __nv_bfloat16 *V = reinterpret_cast<const __nv_bfloat16 *>(base + it.data_off);
                 const float *x = reinterpret_cast<const float *>(base + it.x_off);
-                for (int r0 = 0; r0 < rows; r0 += 16, ++u) {
-                    if (u % CW != warp) continue;
-                    float d[4] = {0.f, 0.f, 0.f, 0.f};
+                const int32_t *zm = reinterpret_cast<const int32_t *>(base + it.map_off);
+                const int pieces = (rows + 15) >> 4;
+                for (int pc = (warp - u % CW + CW) % CW; pc < pieces; pc += CW) {
+                    const int r0 = pc * 16;
+                    // four independent accumulator chains: (hi, lo) parts of x times (even, odd) K steps
+                    float d[4][4] = {};
                     const int arow = min(r0 + (mi & 1) * 8 + rr, rows - 1);     // rows past the run: not read
-                    for (int K0 = 0; K0 < q2; K0 += 16) {
+                    for (int K0 = 0, kk = 0; K0 < q2; K0 += 16, kk ^= 1) {
                         uint32_t af[4];
                         ldsm_x4(af, V + (int64_t)arow * q2 + K0 + (mi >> 1) * 8);
-                        mask_a_k(af, tg, q2 - K0);
+                        if (q2 - K0 < 16) mask_a_k(af, tg, q2 - K0);
+                        // history rows past the slice (a last piece of 8 columns) count as zero
                         float xv[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int j = K0 + 2 * tg + (e & 1) + (e >= 2 ? 8 : 0);
-                            xv[e] = j < q2 && g < a.B ? x[j * a.B + g] : 0.f;
+                            xv[e] = j < q2 ? x[j * 8 + g] : 0.f;
                         }
                         uint32_t bh[2], bl[2];
                         split_b(xv, bh, bl);
-                        mma_bf16(d, af, bh[0], bh[1]);
-                        mma_bf16(d, af, bl[0], bl[1]);
+                        if (kk == 0) {
+                            mma_bf16(d[0], af, bh[0], bh[1]);
+                            mma_bf16(d[1], af, bl[0], bl[1]);
+                        } else {
+                            mma_bf16(d[2], af, bh[0], bh[1]);
+                            mma_bf16(d[3], af, bl[0], bl[1]);
+                        }
                     }
                     // D fragment: v = 0, 1 -> row g, scenario 2 tg + v; v = 2, 3 -> row g + 8
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int row = r0 + g + (v >= 2 ? 8 : 0), col = 2 * tg + (v & 1);
-                        if (row < rows && col < a.B) zg[(int64_t)a.zmap[it.map + row] * a.B + col] = d[v];
+                        if (row < rows && col < a.B)
+                            zg[(int64_t)zm[row] * a.B + col] = (d[0][v] + d[1][v]) + (d[2][v] + d[3][v]);
                     }
                 }
+                u += pieces;
             }
         } else {
             const int p = si.p, p2 = pad_row(p, kPrecBF16);
@@ -743,31 +813,29 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
                 const StageItem &it = si.it[m];
                 const int rows = it.k < 0 ? it.i1 - it.i0 : it.k;
                 const __nv_bfloat16 *S = reinterpret_cast<const __nv_bfloat16 *>(base + it.data_off);
-                // B operand rows: history values (dense) or z values (far), both [rows][B]
-                const float *src = reinterpret_cast<const float *>(base + it.x_off);
-                const float sc = it.k < 0 ? it.scale : 1.f;
-                for (int k0 = 0; k0 < rows; k0 += 16, ++u) {
-                    if (u % G != grp || !act) continue;
-                    uint32_t af[4];
-                    const int arow = min(k0 + (mi >> 1) * 8 + rr, rows - 1);    // rows past the unit: not read
-                    ldsm_x4_t(af, S + (int64_t)arow * p2 + i0 + (mi & 1) * 8);
-                    mask_a_k(af, tg, rows - k0);
-                    float bv[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int r = k0 + 2 * tg + (e & 1) + (e >= 2 ? 8 : 0);
-                        bv[e] = r < rows && g < a.B ? src[r * a.B + g] * sc : 0.f;
+                // B operand rows (history values of dense items, z values of far items), split into fragments
+                const uint32_t *bw = reinterpret_cast<const uint32_t *>(base + it.x_off);
+                const int pieces = (rows + 15) >> 4;
+                if (act)
+                    for (int pc = (grp - u % G + G) % G; pc < pieces; pc += G) {
+                        const int k0 = pc * 16;
+                        uint32_t af[4];
+                        const int arow = min(k0 + (mi >> 1) * 8 + rr, rows - 1);   // rows past the unit: not read
+                        ldsm_x4_t(af, S + (int64_t)arow * p2 + i0 + (mi & 1) * 8);
+                        if (rows - k0 < 16) mask_a_k(af, tg, rows - k0);
+                        // row pairs past the unit's (rows + 1) / 2 are not read: zero
+                        const int rp = (k0 >> 1) + tg, pairs = (rows + 1) >> 1;
+                        const bool in0 = rp < pairs, in1 = rp + 4 < pairs;
+                        mma_bf16(dst, af, in0 ? bw[16 * rp + g] : 0u, in1 ? bw[16 * (rp + 4) + g] : 0u);
+                        mma_bf16(dsl, af, in0 ? bw[16 * rp + 8 + g] : 0u, in1 ? bw[16 * (rp + 4) + 8 + g] : 0u);
                     }
-                    uint32_t bh[2], bl[2];
-                    split_b(bv, bh, bl);
-                    mma_bf16(dst, af, bh[0], bh[1]);
-                    mma_bf16(dst, af, bl[0], bl[1]);
-                }
+                u += pieces;
             }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {                      // compensated accumulation, once per stage
-                PTHalf<__nv_bfloat16>::kahan(acc[v], dst[v]);
+                PTHalf<__nv_bfloat16>::kahan(acc[v], dst[v] + dsl[v]);
                 dst[v] = 0.f;
+                dsl[v] = 0.f;
             }
             if (si.flush) {
                 // D fragment: v = 0, 1 -> receiver row g, scenario 2 tg + v; v = 2, 3 -> row g + 8.  Groups added in
@@ -796,8 +864,11 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
 
 // [tensor-core consumers: end]
 template <int PREC, int BT, int PASS>
-__global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs a) {
-    constexpr int CW = InterShape<BT>::CW, NC = InterShape<BT>::NC, RV = InterShape<BT>::RV;
+__global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interaction(StepArgs a_) {
+    StepArgs a = a_;
+    apply_dyn(a);
+    constexpr int CW = InterShape<PREC, BT, PASS>::CW, NC = InterShape<PREC, BT, PASS>::NC;
+    constexpr int RV = InterShape<PREC, BT, PASS>::RV;
     using T = PT<PREC>;
     using S = typename T::S;
     using X = typename T::X;
@@ -808,7 +879,7 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
     constexpr int XB = (int)sizeof(X);
     constexpr int XA = 16 / XB;                     // history elements per 16 bytes
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    using LY = InterLayout<BT>;
+    using LY = InterLayout<PREC, BT, PASS>;
     unsigned char *stage_mem = smem_raw;                                            // kStages x kStageBytes
     StageInfo *info = reinterpret_cast<StageInfo *>(smem_raw + LY::info);
     double *red = reinterpret_cast<double *>(smem_raw + LY::red);                  // [NC][RV]
@@ -902,11 +973,19 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
             const bool valid = it + lane < ie;
             const int w2 = PASS == 1 ? pad_row(q, PREC) : pad_row(p, PREC);     // operator row length
             int data_bytes = 0, x_bytes = 0, nrow = 0;
+            int map_bytes = 0;
             if (valid) {
                 nrow = u.k < 0 ? u.i1 - u.i0 : u.k;
                 data_bytes = SB * nrow * w2;
-                const int span = (PASS == 1 ? pad_row(q, PREC) : nrow) * a.B;
+                // the tensor-core consumers split B rows in pairs: room for an even count of 8-wide rows
+                constexpr bool kPairB = PREC == kPrecBF16 && BT == 8;
+                const int brows = PASS == 1 ? pad_row(q, PREC) : nrow;
+                const int span = kPairB ? (brows + 1) / 2 * 2 * 8 : brows * a.B;
                 x_bytes = (XB * span + 15) / 16 * 16;
+                if (PASS == 1) {                   // the run's z-row map follows its history slice
+                    map_bytes = (4 * nrow + 15) / 16 * 16;
+                    x_bytes += map_bytes;
+                }
             }
             // units in the stage: the longest prefix of valid lanes (at most kStageItems) whose bytes fit
             int incl = data_bytes + x_bytes;
@@ -954,16 +1033,24 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
             }
             const int data_off = dincl - (in ? data_bytes : 0);
             const int x_off = total_data + xincl - (in ? x_bytes : 0);
-            if (in) si->it[lane] = StageItem{u.k, u.i0, u.i1, data_off, x_off, rincl, u.scale, 0, u.map};
+            if (in)
+                si->it[lane] = StageItem{u.k, u.i0, u.i1, data_off, x_off, rincl, u.scale, x_off + x_bytes - map_bytes,
+                                         u.map};
             unsigned char *dst = stage_mem + (size_t)slot * kStageBytes;
             // source, count and span (count plus the zero tail that padding columns multiply) of each unit's
             // history / z values
+            // The tensor-core consumers take their B rows 8 scenarios wide and in pairs: with a narrower batch the
+            // rows are spread to a stride of 8 (element copies) and every unused value is zero.
+            constexpr bool kPairRows = PREC == kPrecBF16 && BT == 8;
+            const bool spread = kPairRows && a.B != 8;
             const X *xsrc = nullptr;
             int xcnt = 0, xspan = 0;
             if (in) {
+                const int brows = PASS == 1 ? pad_row(q, PREC) : nrow;
+                xspan = kPairRows ? (brows + 1) / 2 * 2 * 8 : brows * a.B;
                 if (PASS == 2 && u.k > 0) {
                     xsrc = reinterpret_cast<const X *>(zbuf + u.map * a.B);
-                    xcnt = xspan = nrow * a.B;
+                    xcnt = nrow * a.B;
                 } else {
                     // lags past the step (whole tasks are switched on) read a slot not yet written: zeros
                     const int64_t back = (a.step - u.T) % a.ring;
@@ -971,14 +1058,13 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
                     const int e0 = c0 + (PASS == 1 ? 0 : u.i0);
                     xsrc = xring + (int64_t)slot_v * a.ring_stride + (int64_t)e0 * a.B;
                     xcnt = (PASS == 1 ? q : nrow) * a.B;
-                    xspan = (PASS == 1 ? pad_row(q, PREC) : nrow) * a.B;
                 }
             }
             // zero tails first (plain shared stores, published by lane 0's arrive below)
             for (int m = 0; m < n; ++m) {
                 const int cnt = __shfl_sync(0xffffffffu, xcnt, m), span = __shfl_sync(0xffffffffu, xspan, m);
                 X *xd = reinterpret_cast<X *>(dst + __shfl_sync(0xffffffffu, x_off, m));
-                for (int c = cnt + lane; c < span; c += 32) xd[c] = X{};
+                for (int c = (spread ? 0 : cnt) + lane; c < span; c += 32) xd[c] = X{};
             }
             __syncwarp();
             if (lane == 0) mbar_arrive_tx(&full[slot], (uint32_t)total_data);
@@ -990,12 +1076,24 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
                 const X *src = reinterpret_cast<const X *>(
                     __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(xsrc), m));
                 X *xd = reinterpret_cast<X *>(dst + __shfl_sync(0xffffffffu, x_off, m));
-                if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+                if (spread) {
+                    for (int c = lane; c < cnt; c += 32) cp_async_elem<XB>(xd + (c / a.B) * 8 + c % a.B, src + c);
+                } else if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
                     const int n16 = cnt / XA;
                     for (int c = lane; c < n16; c += 32) cp_async16(xd + c * XA, src + c * XA);
                     for (int c = n16 * XA + lane; c < cnt; c += 32) cp_async_elem<XB>(xd + c, src + c);
                 } else {
                     for (int c = lane; c < cnt; c += 32) cp_async_elem<XB>(xd + c, src + c);
+                }
+            }
+            if (PASS == 1) {
+                // z-row maps: 4-byte elements (their start in zmap need not be 16-byte aligned)
+                for (int m = 0; m < n; ++m) {
+                    const int rows = __shfl_sync(0xffffffffu, nrow, m);
+                    const int64_t mp = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)u.map, m);
+                    const int xo = __shfl_sync(0xffffffffu, x_off + x_bytes - map_bytes, m);
+                    int32_t *md = reinterpret_cast<int32_t *>(dst + xo);
+                    for (int c = lane; c < rows; c += 32) cp_async_elem<4>(md + c, a.zmap + mp + c);
                 }
             }
             cp_async_arrive(&full[slot]);
@@ -1073,7 +1171,7 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
                     const StageItem &itm = sx.it[k];
                     const S *vr = reinterpret_cast<const S *>(bx + itm.data_off) + (int64_t)(f - zstart) * q2;
                     const X *x = reinterpret_cast<const X *>(bx + itm.x_off);
-                    zrow = a.zmap[itm.map + (f - zstart)];
+                    zrow = reinterpret_cast<const int32_t *>(bx + itm.map_off)[f - zstart];
                     if (PREC == kPrecFP16) sc = a.zscale[itm.map + (f - zstart)];
                     for (int i = sl; i < qv; i += L) {
                         int uu = i + rot;
@@ -1347,7 +1445,9 @@ __global__ void __launch_bounds__(InterShape<BT>::NT, 1) k_interaction(StepArgs 
 // source fault b whose window ends at lag T_last(a, b) < step, f_int[e] += sum_{j in b} smat[e][j] delta_j^{step -
 // T_last - 1}: the dropped lags T > T_last carry A^T ~ dt A^static, and dt times their slip rates is that slip.  One
 // warp per receiver element, lanes over the source columns, a fixed shuffle tree: deterministic.
-__global__ void __launch_bounds__(kThreads) k_static_tail(StepArgs a) {
+__global__ void __launch_bounds__(kThreads) k_static_tail(StepArgs a_) {
+    StepArgs a = a_;
+    apply_dyn(a);
     const int64_t e = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (e >= a.N) return;
@@ -1385,7 +1485,9 @@ __global__ void __launch_bounds__(kThreads) k_static_tail(StepArgs a) {
 // f_int[b][e] = sum over the blocks that element e receives from, and over their causal tasks, of the tasks'
 // partial sums; one warp per element, lane c takes covering blocks c, c + 32, ... (its tasks in lag order), then
 // a fixed tree: the summation order never depends on timing.  Also resets the task counter for the next step.
-__global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a) {
+__global__ void __launch_bounds__(kThreads) k_reduce(StepArgs a_) {
+    StepArgs a = a_;
+    apply_dyn(a);
     const int64_t e = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1467,31 +1569,31 @@ __global__ void k_wait_probe(StepArgs a) {
 
 template <int PREC, int BT, int PASS>
 cudaError_t launch_interaction_pass(const StepArgs &a, cudaStream_t s) {
-    const int n = PASS == 1 ? a.n_ztasks_active : a.n_tasks_active;
+    // a captured step does not know its task counts at launch: every SM, CTAs without a task return
+    const int n = a.dyn ? a.n_sms : PASS == 1 ? a.n_ztasks_active : a.n_tasks_active;
     if (n <= 0) return cudaSuccess;
-    const size_t smem = InterLayout<BT>::total;
+    const size_t smem = InterLayout<PREC, BT, PASS>::total;
     cudaError_t e = cudaFuncSetAttribute(k_interaction<PREC, BT, PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = n < a.n_sms ? n : a.n_sms;
-    k_interaction<PREC, BT, PASS><<<grid, InterShape<BT>::NT, smem, s>>>(a);
+    k_interaction<PREC, BT, PASS><<<grid, InterShape<PREC, BT, PASS>::NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-// Pass 1 (z = V^T x of the far slices, source side), then pass 2 (the receivers' sums), in stream order.
+// pass 1: z = V^T x of the far slices (source side); pass 2: the receivers' sums.  Pass 2 reads what pass 1 wrote,
+// so the launcher issues them in this order on one stream.
 template <int PREC, int BT>
-cudaError_t launch_interaction_bt(const StepArgs &a, cudaStream_t s) {
-    const cudaError_t e = launch_interaction_pass<PREC, BT, 1>(a, s);
-    if (e != cudaSuccess) return e;
-    return launch_interaction_pass<PREC, BT, 2>(a, s);
+cudaError_t launch_interaction_bt(const StepArgs &a, int pass, cudaStream_t s) {
+    return pass == 1 ? launch_interaction_pass<PREC, BT, 1>(a, s) : launch_interaction_pass<PREC, BT, 2>(a, s);
 }
 
 template <int PREC>
-cudaError_t launch_interaction_prec(const StepArgs &a, cudaStream_t s) {
-    if (a.B > 4) return launch_interaction_bt<PREC, 8>(a, s);
-    if (a.B > 2) return launch_interaction_bt<PREC, 4>(a, s);
-    if (a.B > 1) return launch_interaction_bt<PREC, 2>(a, s);
-    return launch_interaction_bt<PREC, 1>(a, s);
+cudaError_t launch_interaction_prec(const StepArgs &a, int pass, cudaStream_t s) {
+    if (a.B > 4) return launch_interaction_bt<PREC, 8>(a, pass, s);
+    if (a.B > 2) return launch_interaction_bt<PREC, 4>(a, pass, s);
+    if (a.B > 1) return launch_interaction_bt<PREC, 2>(a, pass, s);
+    return launch_interaction_bt<PREC, 1>(a, pass, s);
 }
 
 }  // namespace
@@ -1545,13 +1647,13 @@ cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_interaction(const StepArgs &a, cudaStream_t s) {
-    if (a.n_tasks_active <= 0 && a.n_ztasks_active <= 0) return cudaSuccess;
+cudaError_t launch_interaction(const StepArgs &a, int pass, cudaStream_t s) {
+    if (!a.dyn && (pass == 1 ? a.n_ztasks_active : a.n_tasks_active) <= 0) return cudaSuccess;
     switch (a.prec) {
-        case kPrecDF64: return launch_interaction_prec<kPrecDF64>(a, s);
-        case kPrecBF16: return launch_interaction_prec<kPrecBF16>(a, s);
-        case kPrecFP16: return launch_interaction_prec<kPrecFP16>(a, s);
-        default: return launch_interaction_prec<kPrecFP64>(a, s);
+        case kPrecDF64: return launch_interaction_prec<kPrecDF64>(a, pass, s);
+        case kPrecBF16: return launch_interaction_prec<kPrecBF16>(a, pass, s);
+        case kPrecFP16: return launch_interaction_prec<kPrecFP16>(a, pass, s);
+        default: return launch_interaction_prec<kPrecFP64>(a, pass, s);
     }
 }
 

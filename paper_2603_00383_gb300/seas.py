@@ -30,7 +30,8 @@ EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_
             "seas_measure_fp64_peak", "seas_scenario_set_wait_limit", "seas_scenario_probe_wait",
             "seas_scenario_admit", "seas_scenario_retire", "seas_scenario_member_step", "seas_ctx_get_memory",
             "seas_integrator_create", "seas_integrator_step", "seas_integrator_state", "seas_destroy_integrator",
-            "seas_push_slip_rate_steps", "seas_integrator_step_gamma", "seas_integrator_step_adaptive"]
+            "seas_push_slip_rate_steps", "seas_integrator_step_gamma", "seas_integrator_step_adaptive",
+            "seas_scenario_graph_create", "seas_scenario_graph_step"]
 
 
 class SeasError(RuntimeError):
@@ -72,11 +73,11 @@ class seas_friction(C.Structure):
 
 
 class seas_timing(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 6), ("ms", C.c_double * 6), ("interaction_bytes", C.c_int64),
+    _fields_ = [("launches", C.c_int64 * 7), ("ms", C.c_double * 7), ("interaction_bytes", C.c_int64),
                 ("steps", C.c_int64)]
 
 
-KERNEL_CLASSES = ["push", "fft_forward", "modeconv", "interaction", "reduce", "ifft_assemble"]
+KERNEL_CLASSES = ["push", "fft_forward", "modeconv", "interaction", "reduce", "ifft_assemble", "interaction_source"]
 
 _lib = None
 _VP, _PP = C.c_void_p, C.POINTER(C.c_void_p)
@@ -123,6 +124,8 @@ _SIGS = {
     "seas_push_slip_rate_steps": ([_VP, _VP, _VP, C.c_int, C.c_int, C.c_int], C.c_int),
     "seas_integrator_step_gamma": ([_VP, C.c_int], C.c_int),
     "seas_integrator_step_adaptive": ([_VP, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int64)], C.c_int),
+    "seas_scenario_graph_create": ([_VP, _VP, _VP, _VP], C.c_int),
+    "seas_scenario_graph_step": ([_VP], C.c_int),
 }
 
 
@@ -349,6 +352,22 @@ def seas_stress_step_static(scn: Handle, tau, parts=None):
     if mem != SEAS_MEM_DEVICE or (mp is not None and mp != SEAS_MEM_DEVICE):
         raise ValueError("seas_stress_step_static takes device buffers")
     _check(lib().seas_stress_step_static(scn.ptr, pt, pp))
+
+
+def seas_scenario_graph_create(scn: Handle, V, tau, parts=None):
+    """Captures one step (push of the device buffer V, stress step into the device buffers tau / parts)."""
+    n = scn.B * scn.N
+    dev = _device_of(scn)
+    pv, m0 = _buf(V, n, "V", dev)
+    pt, m1 = _buf(tau, n, "tau", dev)
+    pp, m2 = _buf(parts, 3 * n, "parts", dev)
+    if m0 != SEAS_MEM_DEVICE or m1 != SEAS_MEM_DEVICE or (m2 is not None and m2 != SEAS_MEM_DEVICE):
+        raise ValueError("seas_scenario_graph_create takes device buffers")
+    _check(lib().seas_scenario_graph_create(scn.ptr, pv, pt, pp))
+
+
+def seas_scenario_graph_step(scn: Handle):
+    _check(lib().seas_scenario_graph_step(scn.ptr))
 
 
 def seas_scenario_step(scn: Handle) -> int:

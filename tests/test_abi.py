@@ -34,7 +34,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(seas.seas_hparams) == 64
     assert ctypes.sizeof(seas.seas_net_info) == 16
     assert ctypes.sizeof(seas.seas_op_stats) == 13 * 8
-    assert ctypes.sizeof(seas.seas_timing) == 6 * 8 + 6 * 8 + 16
+    assert ctypes.sizeof(seas.seas_timing) == 7 * 8 + 7 * 8 + 16
 
 
 def test_strerror_covers_every_status():

@@ -76,3 +76,79 @@ def test_integrator_rejects_touching_faults_and_bad_parameters():
                 seas.seas_integrator_create(s.scn, bad, 1.0, tau0, z * 1e-9, z)
         with pytest.raises(seas.SeasError):
             seas.seas_integrator_create(s.scn, fr, 0.0, tau0, z * 1e-9, z)
+
+
+def test_multi_step_push_equals_the_lattice_functional():
+    """A slip rate held over gamma lattice steps (seas_push_slip_rate_steps) is the functional of the lattice history
+    with that rate repeated gamma times (oracle stress_history on the expanded lattice), at every step's end; with
+    the caller's end slip, and through replace_last of a whole multi-step push."""
+    w = synth.tiny(2, n_faults=3, steps=200)
+    net = O.network(w.faults, w.mu, w.cs)
+    gammas = [1, 3, 2, 5, 1, 4, 7, 2, 6, 3, 1, 5]
+    rates = w.slip_rate(0, 0, len(gammas))
+    lattice = np.concatenate([np.repeat(rates[k][None], g, 0) for k, g in enumerate(gammas)])
+    ref = O.stress_history(net, lattice, dict(w.hparams, flags=seas.SEAS_FLAG_NO_TRUNC, max_steps=w.steps))
+    ends = np.cumsum(gammas) - 1
+    slip_lat = O.slip_from_rate(lattice, net.dt)
+    for mode in ("integrated", "caller_slip", "replaced"):
+        with seas.Session(w, flags=seas.SEAS_FLAG_DENSE | seas.SEAS_FLAG_NO_TRUNC) as s:
+            t = np.zeros(w.N)
+            P = np.zeros(3 * w.N)
+            out = []
+            for k, g in enumerate(gammas):
+                V = np.ascontiguousarray(rates[k])
+                if mode == "caller_slip":
+                    seas.seas_push_slip_rate_steps(s.scn, V, g, slip=np.ascontiguousarray(slip_lat[ends[k]]))
+                elif mode == "replaced":
+                    seas.seas_push_slip_rate_steps(s.scn, 3.0 * V + 1.0, g)
+                    seas.seas_push_slip_rate_steps(s.scn, V, g, replace_last=True)
+                else:
+                    seas.seas_push_slip_rate_steps(s.scn, V, g)
+                seas.seas_stress_step(s.scn, t, parts=P)
+                out.append(np.concatenate([t, P]))
+            if mode == "replaced":
+                with pytest.raises(seas.SeasError) as e:
+                    seas.seas_push_slip_rate_steps(s.scn, V, gammas[-1] + 1, replace_last=True)
+                assert e.value.status == seas.SEAS_EINVAL
+        out = np.array(out)
+        errs = [rel(out[:, :w.N], ref[0][ends])] + [rel(out[:, (k + 1) * w.N:(k + 2) * w.N], ref[k + 1][ends])
+                                                   for k in range(3)]
+        print(f"multi-step push ({mode}): rel-L2 tau/rad/self/int {errs}")
+        assert max(errs) <= 1e-10
+
+
+def test_gamma_and_adaptive_steps_match_the_oracle():
+    """Time steps of several lattice steps (Sec. 2.4 step 1) on the GPU against the oracle's gamma steps: a fixed
+    gamma sequence, then adaptive steps whose gamma the GPU picks from min xi D_c / V and the oracle recomputes."""
+    steps = 160
+    faults, net, tau0 = case(1.5e6)
+    fr = (FR.a, FR.b, FR.dc, FR.f0, FR.v0, FR.sigma_n)
+    w = synth.Workload("integ", faults, mu=MU, cs=CS, steps=steps,
+                       hparams=dict(max_steps=steps, leaf=4, flags=seas.SEAS_FLAG_DENSE | seas.SEAS_FLAG_NO_TRUNC))
+    gammas = [1, 2, 4, 3, 8, 5, 2, 6]
+    ref = SI.Integrator(net, FR, tau0, FR.v0, FR.dc / FR.v0, max_steps=steps)
+    ref_V = [ref.step_gamma(g) for g in gammas]
+    with seas.Session(w) as s:
+        it = seas.seas_integrator_create(s.scn, fr, 1.0, tau0, np.full(net.N, FR.v0), np.full(net.N, FR.dc / FR.v0))
+        got_V = []
+        for g in gammas:
+            seas.seas_integrator_step_gamma(it, g)
+            got_V.append(seas.seas_integrator_state(it)[0])
+        # adaptive: xi chosen so that gamma stays between 1 and 12 on this run
+        xi = 12 * net.dt * FR.v0 / FR.dc
+        adaptive_ref, adaptive_got = [], []
+        for _ in range(6):
+            g = ref.adaptive_gamma(xi, 12)
+            if len(ref.V) + g > steps:
+                break
+            adaptive_ref.append(g)
+            ref.step_gamma(g)
+            adaptive_got.append(seas.seas_integrator_step_adaptive(it, xi, 12, 1))
+        V, th, d = seas.seas_integrator_state(it)
+        seas.seas_destroy_integrator(it)
+    eV = rel(np.array(got_V), np.array(ref_V))
+    print(f"gamma steps {gammas}: rel-L2 V {eV:.2e}; adaptive gammas GPU {adaptive_got} oracle {adaptive_ref}; "
+          f"final rel-L2 V {rel(V, ref.V[-1]):.2e} theta {rel(th, ref.theta):.2e} slip {rel(d, ref.delta[-1]):.2e}")
+    assert eV < 1e-6
+    assert adaptive_got == adaptive_ref and max(adaptive_ref) > 1
+    assert rel(V, ref.V[-1]) < 1e-6 and rel(th, ref.theta) < 1e-6 and rel(d, ref.delta[-1]) < 1e-6

@@ -83,7 +83,7 @@ def test_block_first_lag_never_after_the_first_nonzero_lag():
 
 
 @pytest.mark.parametrize("bad", [
-    dict(n=7), dict(n=0), dict(length=-1.0), dict(cx=float("nan")), dict(n=7168 * 2)])
+    dict(n=29), dict(n=0), dict(length=-1.0), dict(cx=float("nan")), dict(n=7168 * 2)])
 def test_invalid_geometry_is_rejected(bad):
     f = dict(cx=0.0, cy=0.0, strike=0.0, length=100.0, n=8)
     f.update(bad)
