@@ -159,6 +159,14 @@ seas_status seas_net_get_elements(const seas_net *net, double *centroids, double
 /* Builds the selective H-matrix stack and the spectral tables on the device (Sec. 2.3.1, Sec. 2.3.2).
  * stats may be NULL. */
 seas_status seas_build_hmatrix(seas_net *net, const seas_hparams *hp, seas_op **op, seas_op_stats *stats);
+/* The part of the operator whose receivers lie on `faults` (n_faults indices): their spectral self effects and the
+ * H-matrix blocks of their rows, for sharding one scenario across GPUs by receiver faults (each GPU steps the same
+ * full slip-rate history -- gathered from the GPUs that own its parts -- and returns tau on its own faults).
+ * seas_stress_step then writes tau, and parts, only on the owned faults' elements; other entries of the output
+ * buffers are left as they were.  Not with SEAS_FLAG_STATIC_TAIL (SEAS_EINVAL).  No counterpart in the paper, which
+ * names the method inherently parallel. */
+seas_status seas_build_hmatrix_part(seas_net *net, const seas_hparams *hp, const int32_t *faults, int n_faults,
+                                    seas_op **op, seas_op_stats *stats);
 /* Per ordered fault pair (receiver a, source b): last lag of the window, [F][F] int32, -1 on the diagonal. */
 seas_status seas_op_pair_windows(const seas_op *op, int32_t *last_lag);
 /* Per fault f and mode n = 0..N_f: last lag W_f(n) of the spectral window (flattened fault after fault). */

@@ -176,7 +176,8 @@ struct seas_op {
     seas_hparams hp{};
     int children = 0;
     // spectral self effect
-    std::vector<FaultDev> faults_h;
+    std::vector<char> owned;         // per fault: 1 if its receivers belong to this operator (all unless partial)
+    std::vector<FaultDev> faults_h;  // the owned faults (the spectral self effect runs on these)
     std::vector<ModeDev> modes_h;
     std::vector<int32_t> mode_W;     // per fault, modes 0..N_f
     DArr<FaultDev> d_faults;
@@ -653,6 +654,10 @@ seas_status build_self(seas_op &op) {
     const long double pi = 3.141592653589793238462643383279502884L;
     for (int f = 0; f < net.F; ++f) {
         const int nf = net.faults[f].n_elem;
+        if (!op.owned[f]) {                    // another operator's fault: no self effect here
+            op.mode_W.insert(op.mode_W.end(), (size_t)nf + 1, 0);
+            continue;
+        }
         FaultDev fd{};
         fd.off = net.off[f];
         fd.nf = nf;
@@ -680,7 +685,7 @@ seas_status build_self(seas_op &op) {
             ModeDev md{};
             md.w_off = w_total;
             md.W = W;
-            md.fault = f;
+            md.fault = (int32_t)op.faults_h.size();
             md.n = n;
             op.modes_h.push_back(md);
             g_prefix.push_back(g_total);
@@ -793,6 +798,7 @@ seas_status build_interaction(seas_op &op) {
         for (int b = 0; b < net.F; ++b) {
             if (a == b) continue;
             op.pair_last[(size_t)a * net.F + b] = pair_last_lag(net, a, b, hp.eta_tmax, hp.max_steps, no_trunc);
+            if (!op.owned[a]) continue;        // rows of another operator
             traverse(trees[a], trees[b], hp.eta_h, dense, max_block, a * net.F + b, op.blocks_h, op.block_far,
                      op.block_pair);
         }
@@ -1166,7 +1172,22 @@ seas_status build_interaction(seas_op &op) {
 
 extern "C" seas_status seas_build_hmatrix(seas_net *net, const seas_hparams *hp, seas_op **out,
                                           seas_op_stats *stats) {
+    return seas_build_hmatrix_part(net, hp, nullptr, 0, out, stats);
+}
+
+extern "C" seas_status seas_build_hmatrix_part(seas_net *net, const seas_hparams *hp, const int32_t *faults,
+                                               int n_faults, seas_op **out, seas_op_stats *stats) {
     if (!net || !hp || !out) return fail(SEAS_EINVAL, "NULL argument");
+    std::vector<char> owned((size_t)net->F, faults ? 0 : 1);
+    if (faults) {
+        if (n_faults < 1) return fail(SEAS_EINVAL, "no owned faults");
+        for (int k = 0; k < n_faults; ++k) {
+            if (faults[k] < 0 || faults[k] >= net->F) return fail(SEAS_EINVAL, "fault %d out of range", faults[k]);
+            owned[(size_t)faults[k]] = 1;
+        }
+        if (hp->flags & SEAS_FLAG_STATIC_TAIL)
+            return fail(SEAS_EINVAL, "the static tail needs every fault's rows (no partial operator)");
+    }
     *out = nullptr;
     if (hp->leaf < 1 || hp->leaf > kMaxBlockSide) return fail(SEAS_EINVAL, "leaf must be in [1, %d]", kMaxBlockSide);
     if (!(hp->eta_h > 0)) return fail(SEAS_EINVAL, "eta_h must be > 0");
@@ -1186,6 +1207,7 @@ extern "C" seas_status seas_build_hmatrix(seas_net *net, const seas_hparams *hp,
     op->net = net;
     op->hp = *hp;
     op->tail = (hp->flags & SEAS_FLAG_STATIC_TAIL) && !(hp->flags & SEAS_FLAG_NO_TRUNC);
+    op->owned = owned;
     SEAS_TRY(build_self(*op));
     SEAS_TRY(build_interaction(*op));
     if (op->tail) SEAS_TRY(build_static(*op));
@@ -1276,6 +1298,7 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     StepArgs a{};
     a.N = net.N;
     a.F = net.F;
+    a.n_self = (int)op.faults_h.size();
     a.B = s.B;
     a.n_modes_total = op.n_modes_total;
     a.max_nf = op.max_nf;

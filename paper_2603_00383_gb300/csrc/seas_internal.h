@@ -163,7 +163,8 @@ struct DynDev {
 };
 
 struct StepArgs {
-    int N, F, B, n_modes_total;   // elements, faults, batch, sum over faults of (N_f + 1)
+    int N, F, B, n_modes_total;   // elements, faults, batch, sum over the owned faults of (N_f + 1)
+    int n_self;                   // faults with a spectral self effect in this operator (the owned ones)
     int max_nf;                   // largest N_f (shared memory of the FFT kernels)
     int64_t step;                 // tick of the step being evaluated (ring slots are tick mod depth)
     int64_t lag_max;              // largest lag with nonzero history: the oldest active member's step (<= step);

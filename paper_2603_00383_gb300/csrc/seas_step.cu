@@ -1636,7 +1636,7 @@ cudaError_t launch_fft_forward(const StepArgs &a, cudaStream_t s) {
     const size_t smem = (size_t)2 * a.max_nf * sizeof(double2);
     cudaError_t e = fft_smem((const void *)k_fft_forward, smem);
     if (e != cudaSuccess) return e;
-    k_fft_forward<<<dim3(a.F, a.B), kThreads, smem, s>>>(a);
+    k_fft_forward<<<dim3(a.n_self, a.B), kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1684,7 +1684,7 @@ cudaError_t launch_ifft_assemble(const StepArgs &a, double *tau, double *parts, 
     const size_t smem = (size_t)2 * a.max_nf * sizeof(double2);
     cudaError_t e = fft_smem((const void *)k_ifft_assemble, smem);
     if (e != cudaSuccess) return e;
-    k_ifft_assemble<<<dim3(a.F, a.B), kThreads, smem, s>>>(a, tau, parts);
+    k_ifft_assemble<<<dim3(a.n_self, a.B), kThreads, smem, s>>>(a, tau, parts);
     return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_
             "seas_scenario_admit", "seas_scenario_retire", "seas_scenario_member_step", "seas_ctx_get_memory",
             "seas_integrator_create", "seas_integrator_step", "seas_integrator_state", "seas_destroy_integrator",
             "seas_push_slip_rate_steps", "seas_integrator_step_gamma", "seas_integrator_step_adaptive",
-            "seas_scenario_graph_create", "seas_scenario_graph_step"]
+            "seas_scenario_graph_create", "seas_scenario_graph_step", "seas_build_hmatrix_part"]
 
 
 class SeasError(RuntimeError):
@@ -126,6 +126,7 @@ _SIGS = {
     "seas_integrator_step_adaptive": ([_VP, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int64)], C.c_int),
     "seas_scenario_graph_create": ([_VP, _VP, _VP, _VP], C.c_int),
     "seas_scenario_graph_step": ([_VP], C.c_int),
+    "seas_build_hmatrix_part": ([_VP, C.POINTER(seas_hparams), _VP, C.c_int, _PP, C.POINTER(seas_op_stats)], C.c_int),
 }
 
 
@@ -275,13 +276,19 @@ def seas_net_get_elements(net: Handle):
     return c, n
 
 
-def seas_build_hmatrix(net: Handle, hp: dict):
+def seas_build_hmatrix(net: Handle, hp: dict, owned=None):
     """hp keys: leaf, q_w, eta_h, aca_tol, eta_tmin, eta_tmax, eta_w, max_steps, precision, flags, max_block.
+    owned: receiver faults of a partial operator (seas_build_hmatrix_part), None for all.
     Returns (op handle, stats dict)."""
     p = _hparams(hp)
     h = C.c_void_p()
     st = seas_op_stats()
-    _check(lib().seas_build_hmatrix(net.ptr, C.byref(p), C.byref(h), C.byref(st)))
+    if owned is None:
+        _check(lib().seas_build_hmatrix(net.ptr, C.byref(p), C.byref(h), C.byref(st)))
+    else:
+        f = np.ascontiguousarray(np.asarray(owned, dtype=np.int32))
+        _check(lib().seas_build_hmatrix_part(net.ptr, C.byref(p), C.c_void_p(f.ctypes.data), len(f), C.byref(h),
+                                             C.byref(st)))
     stats = {name: getattr(st, name) for name, _ in seas_op_stats._fields_}
     return Handle(h, "op", net=net, N=net.N, F=net.F, max_steps=p.max_steps), stats
 
@@ -514,7 +521,8 @@ class Session:
     stream the library works on torch's current stream of `device` when torch is loaded (so that tensors the
     caller passes are ordered with the library's kernels), else on a stream of its own."""
 
-    def __init__(self, workload, batch: int = 1, device: int = 0, stream=None, hbm_budget: int = 0, **hp):
+    def __init__(self, workload, batch: int = 1, device: int = 0, stream=None, hbm_budget: int = 0, owned=None,
+                 **hp):
         if stream is None:
             import sys
             torch = sys.modules.get("torch")
@@ -525,7 +533,7 @@ class Session:
                                       workload.beta)
         params = dict(workload.hparams)
         params.update(hp)
-        self.op, self.stats = seas_build_hmatrix(self.net, params)
+        self.op, self.stats = seas_build_hmatrix(self.net, params, owned)
         self.scn = seas_scenario_create(self.op, batch)
 
     def close(self):
