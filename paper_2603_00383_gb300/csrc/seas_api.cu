@@ -1001,7 +1001,7 @@ seas_status build_interaction(seas_op &op) {
             const int64_t row_bytes = (int64_t)q2 * eb;
             // a run's rows, their z-row map (4 bytes a row) and its history slice fit one stage
             const int64_t max_rows =
-                std::max<int64_t>(1, (kStageBytes - 32 - (int64_t)q2 * x_cap) / (row_bytes + 4));
+                std::max<int64_t>(1, (kStageBytes - 64 - (int64_t)q2 * x_cap) / (row_bytes + 4));
             unsigned char *d = op.d_varena.p + off;
             gsrc.push_back(x.v);
             gdst.push_back(d);
@@ -1052,6 +1052,7 @@ seas_status build_interaction(seas_op &op) {
     SEAS_TRY(op.d_runs.upload(c, runs));
     SEAS_TRY(op.d_ztasks.upload(c, ztasks));
     SEAS_TRY(op.d_srcs.upload(c, srcs));
+    zmap.resize(zmap.size() + 4, 0);             // the bulk copies of a run's map round up to 16 bytes
     SEAS_TRY(op.d_zmap.upload(c, zmap));
     if (prec == kPrecFP16) SEAS_TRY(op.d_zscale.upload(c, zscale));
 
@@ -1322,6 +1323,7 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     a.vring = s.vring.p;
     a.xring = s.xring.p;
     a.prec = op.hp.precision;
+    a.xsplit = xsplit_of(op.hp.precision, s.B) ? 1 : 0;
     a.slip = s.slip.p;
     a.slip_prev = s.slip_prev.p;
     a.dring = s.dring.p;
@@ -1386,17 +1388,23 @@ seas_status scenario_alloc(seas_op *op, int batch, std::unique_ptr<seas_scn> &s)
     SEAS_TRY(s->faults.upload(c, ft));
     // a multiple of 4 elements (16-byte rows for 4- and 8-byte elements) with room for the 16-byte round-up of
     // history slices
-    s->ring_stride = (BN + 3) / 4 * 4 + 4;
-    SEAS_TRY(s->vring.alloc(c, (size_t)(op->ring * s->ring_stride)));
+    // (the split history of the tensor-core consumers is 8 scenarios wide whatever the batch)
+    const bool xsplit = xsplit_of(op->hp.precision, batch);
+    s->ring_stride = (std::max<int64_t>(BN, xsplit ? N * 8 : 0) + 3) / 4 * 4 + 4;
+    // the interaction kernel's bulk copies of history slices are widened to 16-byte bounds and to the padded
+    // column count of a block (at most 7 columns of 8 scenarios past the slice): a tail of kCopyTail bytes keeps
+    // the last slot's copies inside the allocation
+    SEAS_TRY(s->vring.alloc(c, (size_t)(op->ring * s->ring_stride + kCopyTail / 8)));
     if (op->hp.precision != kPrecFP64) {
         const int xb = op->hp.precision == kPrecDF64 ? 8 : 4;
-        SEAS_TRY(s->xring.alloc(c, (size_t)(op->ring * s->ring_stride * xb)));
+        SEAS_TRY(s->xring.alloc(c, (size_t)(op->ring * s->ring_stride * xb + kCopyTail)));
         SEAS_TRY(s->xring.zero(c->stream));
     }
     SEAS_TRY(s->partial.alloc(c, (size_t)(op->n_partial * batch)));
     {
         const int zb = op->hp.precision == kPrecBF16 || op->hp.precision == kPrecFP16 ? 4 : 8;
-        SEAS_TRY(s->zbuf.alloc(c, (size_t)std::max<int64_t>(16, op->z_rows * batch * zb)));
+        const int64_t zw = xsplit ? 8 : batch;        // z rows of the split layout: 8 (high, low) pairs
+        SEAS_TRY(s->zbuf.alloc(c, (size_t)(op->z_rows * zw * zb + kCopyTail)));   // widened copies, as above
         SEAS_TRY(s->zbuf.zero(c->stream));
     }
     SEAS_TRY(s->counter_err.alloc(c, 4));
@@ -1442,7 +1450,8 @@ extern "C" seas_status seas_scenario_create(seas_op *op, int batch, seas_scn **o
         for (size_t b = 0; b < op->blocks_h.size(); ++b) {
             if (!op->block_far[b]) continue;
             const int64_t q2 = pad_row(op->blocks_h[b].q, op->hp.precision);
-            if (q2 * eb + (q2 * batch * xb + 15) / 16 * 16 + 32 > kStageBytes)
+            const int xw = xsplit_of(op->hp.precision, batch) ? 8 : batch;
+            if (q2 * eb + (q2 * xw * xb + 15) / 16 * 16 + 16 + 48 > kStageBytes)
                 return fail(SEAS_EINVAL, "batch %d too large for blocks of %d columns (stage of %d bytes)", batch,
                             op->blocks_h[b].q, kStageBytes);
         }

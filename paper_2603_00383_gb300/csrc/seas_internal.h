@@ -21,8 +21,13 @@ constexpr int kStageBytes = 68 * 1024;  // one shared-memory stage of the intera
 constexpr int kStages = 3;              // stages in flight per CTA
 constexpr int kStageItems = 31;         // units per stage (one producer lane each)
 constexpr int64_t kTaskBytes = 1 << 20; // operator bytes per task (one deterministic partial sum)
+constexpr int kCopyTail = 1024;         // bytes past the history ring and z buffer that widened copies may read
 
 __host__ __device__ inline int pad2(int n) { return n + (n & 1); }
+
+// BF16 operators with batches of 5..8 run on the tensor-core consumers, whose B operands (history and z rows) are
+// stored pre-split into bfloat16 (high, low) pairs, 8 scenarios wide.
+__host__ __device__ inline bool xsplit_of(int prec, int batch) { return prec == 1 && batch > 4; }
 
 // Storage precision of the interaction operator (values of seas_hparams::precision).
 constexpr int kPrecFP64 = 0;   // double entries, FP64 arithmetic
@@ -179,8 +184,11 @@ struct StepArgs {
     const double2 *tw;            // FFT twiddles
     double *vring;                // [R][ring_stride]
     void *xring;                  // history in the operator's arithmetic: float2 (DF64) or float (BF16/FP16), same
-                                  // layout; NULL for FP64
+                                  // layout; NULL for FP64.  Split layout (xsplit): 32 bytes per element, the bfloat16
+                                  // high parts of scenarios 0..7 then their low parts (scenarios >= B zero)
     int prec;
+    int xsplit;                   // 1: BF16 operator with a batch of 5..8 (tensor-core consumers): history and z rows
+                                  // held as bfloat16 (high, low) pairs of their FP32 values, 8 scenarios wide
     double *slip, *slip_prev;     // [B][N]
     double2 *dring;               // spectral rings
     double2 *fmodes;              // [B][n_modes_total]

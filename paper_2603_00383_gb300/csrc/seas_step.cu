@@ -137,6 +137,13 @@ __global__ void k_push(StepArgs a_, const double *__restrict__ V, const double *
             const float hi = (float)v;
             reinterpret_cast<float2 *>(a.xring)[(int64_t)slot * a.ring_stride + i * a.B + b] =
                 make_float2(hi, (float)(v - (double)hi));
+        } else if (a.xsplit) {
+            // the FP32 value as bfloat16 high part + bfloat16 of the remainder (the tensor-core B operand)
+            __nv_bfloat16 *xr = reinterpret_cast<__nv_bfloat16 *>(a.xring) + ((int64_t)slot * a.ring_stride + i * 8) * 2;
+            const float f = (float)v;
+            const __nv_bfloat16 h = __float2bfloat16_rn(f);
+            xr[b] = h;
+            xr[8 + b] = __float2bfloat16_rn(f - __bfloat162float(h));
         } else if (a.prec != kPrecFP64) {
             reinterpret_cast<float *>(a.xring)[(int64_t)slot * a.ring_stride + i * a.B + b] = (float)v;
         }
@@ -331,7 +338,7 @@ template <int PREC, int BT, int PASS> struct InterLayout {
     static constexpr size_t red = info + kStages * sizeof(StageInfo);
     static constexpr size_t bars =
         red + (size_t)InterShape<PREC, BT, PASS>::NC * InterShape<PREC, BT, PASS>::RV * sizeof(double);
-    static constexpr size_t total = bars + 2 * kStages * sizeof(uint64_t);
+    static constexpr size_t total = bars + (2 * kStages + 1) * sizeof(uint64_t);   // full, empty, consumers
     static_assert(sizeof(StageInfo) % 8 == 0 && red % 8 == 0 && bars % 8 == 0, "8-byte alignment");
     static_assert(total <= 227 * 1024, "shared memory per CTA");
 };
@@ -382,8 +389,8 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Bounded wait (limit_ns of wall time, 2 s unless the scenario sets another, and at most 2^30 polls); false, with
-// the error word set, if the phase never completes.  Called by one thread per role, which then shares the outcome,
-// so an abort is uniform.
+// the error word set, if the phase never completes.  The producer's lane 0 waits and shares the outcome with its warp;
+// every lane of a consumer warp waits and the warp combines the outcomes, so an abort is uniform per warp.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
@@ -419,8 +426,27 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int NC>
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory"); }
+// Every consumer lane waits on a stage's full barrier itself; the warp goes on only if all its lanes saw it.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int *err, uint64_t limit_ns) {
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity, err, limit_ns));
+}
+
+// A warp is done with a stage: its lanes' shared-memory reads are ordered before lane 0's arrive (release) on the
+// stage's empty barrier, which counts one arrival per consumer warp.
+__device__ __forceinline__ void warp_release(uint64_t *bar) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
+
+// Meeting of all consumer warps (the task-end reduction through shared memory): an mbarrier counting one arrival per
+// warp, waited on with the same bound as the stages, so that a warp that left on an error cannot hang the others.
+// ph: this thread's phase bit of the barrier.
+__device__ __forceinline__ bool consumers_meet(uint64_t *bar, uint32_t &ph, int *err, uint64_t limit_ns) {
+    warp_release(bar);
+    const bool ok = warp_wait(bar, ph, err, limit_ns);
+    ph ^= 1u;
+    return ok;
+}
 
 // ------------------------------------------------------------------------------------------------------------
 // Arithmetic of each storage precision: stored element S, history element X, dot-product value Z, accumulator
@@ -616,15 +642,6 @@ __device__ __forceinline__ void edot(float2 &z, float2 v, float2 x) {
 __device__ __forceinline__ void edot(float &z, float v, float x) { z = fmaf(v, x, z); }
 
 // N values of 4 to 16 bytes each, N * size a multiple of 16, from a 16-byte aligned shared-memory address.
-template <typename X, int N>
-__device__ __forceinline__ void ld16(const X *p, X (&o)[N]) {
-    static_assert((N * sizeof(X)) % 16 == 0, "whole 16-byte words");
-    const uint4 *q = reinterpret_cast<const uint4 *>(p);
-    uint4 *d = reinterpret_cast<uint4 *>(o);
-#pragma unroll
-    for (int i = 0; i < (int)(N * sizeof(X) / 16); ++i) d[i] = q[i];
-}
-
 // [tensor-core consumers: begin]
 // ------------------------------------------------------------------------------------------------------------
 // Tensor-core consumers for BF16 storage with 8 scenarios: with B = 8 the interaction is a multi-right-hand-side
@@ -661,19 +678,6 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
 
 // B fragments (rows k = 2 tg + {0, 1} and 2 tg + 8 + {0, 1} of a 16 x 8 tile, column g) of four FP32 values,
 // split into hi and lo BF16 parts.
-__device__ __forceinline__ void split_b(const float (&v)[4], uint32_t (&hi)[2], uint32_t (&lo)[2]) {
-    __nv_bfloat16 h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        h[e] = __float2bfloat16_rn(v[e]);
-        l[e] = __float2bfloat16_rn(v[e] - __bfloat162float(h[e]));
-    }
-    hi[0] = pack_bf16(h[0], h[1]);
-    hi[1] = pack_bf16(h[2], h[3]);
-    lo[0] = pack_bf16(l[0], l[1]);
-    lo[1] = pack_bf16(l[2], l[3]);
-}
-
 // Zero the halves of A-fragment registers whose inner index (k = k0 + 2 tg + {0, 1}, and + 8 for registers 2, 3)
 // is not below kvalid: operand bytes past an item are not guaranteed to be finite numbers.
 __device__ __forceinline__ void mask_a_k(uint32_t (&a)[4], int tg, int kvalid) {
@@ -687,43 +691,26 @@ __device__ __forceinline__ void mask_a_k(uint32_t (&a)[4], int tg, int kvalid) {
 }
 
 // Splits the FP32 operand rows [rows][8] of one unit, in place, into packed BF16 (hi, lo) pairs laid out as MMA B
-// fragments: word 16 rp + n holds the hi parts of rows 2 rp and 2 rp + 1 of scenario n, word 16 rp + 8 + n their lo
-// parts (a missing odd last row counts as zero).  Each thread reads exactly the two words it writes, so the
-// transform needs no barrier inside; the caller's barrier publishes it.
-__device__ __forceinline__ void split_rows_inplace(unsigned char *area, int rows, int t, int nthreads) {
-    float *f = reinterpret_cast<float *>(area);
-    uint32_t *w = reinterpret_cast<uint32_t *>(area);
-    const int pairs = (rows + 1) >> 1;
-    for (int o = t; o < pairs * 8; o += nthreads) {
-        const int rp = o >> 3, n = o & 7;
-        const float v0 = f[16 * rp + n];
-        const float v1 = 2 * rp + 1 < rows ? f[16 * rp + 8 + n] : 0.f;
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
-        w[16 * rp + n] = pack_bf16(h0, h1);
-        w[16 * rp + 8 + n] = pack_bf16(l0, l1);
-    }
-}
-
-// Consumer warps of k_interaction<BF16, 8, PASS>.  Per stage: the barrier that opens it (and hands the previous
-// stage back to the producer), the split of the stage's FP32 operand rows into BF16 hi / lo fragments in place,
-// a second barrier, then the MMAs, which read their B fragments with one 32-bit shared load each.
+// Consumer warps of k_interaction<BF16, 8, PASS>.  B operand rows (history values of source columns, z values)
+// arrive split: 16 bytes of bfloat16 high parts of scenarios 0..7, then 16 bytes of low parts; one ldmatrix.trans
+// per 16-row K step yields both halves' fragments (rows past the unit's staged rows are clamped to its last row:
+// finite values, multiplied by A fragments masked to zero there).
 //   Pass 1: each (run, 16 rows) piece is one warp's Z tile over the run's source columns; its rows go to the z rows
-//   that the staged z-row map gives.
+//   that the staged z-row map gives, written split as well.
 //   Pass 2: the task's receivers form mt 16-row tiles; warp w owns tile w mod mtp in group w / mtp (mtp = mt
 //   rounded up to 1, 2, 4 or 8) and the stage's (unit, 16-row chunk) pieces are dealt round-robin to the groups; at
 //   the task's end the groups are added in a fixed order.  Blocks are at most 128 receivers wide here (scenario
 //   creation checks).
 template <int CW, int PASS>
 __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, unsigned char *stage_mem, double *red,
-                                            uint64_t *full, uint64_t *empty, int *sh_flag) {
+                                            uint64_t *full, uint64_t *empty) {
     constexpr int NC = CW * 32;
     constexpr int B8 = 8;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int g = lane >> 2, tg = lane & 3, mi = lane >> 3, rr = lane & 7;
-    float *zg = static_cast<float *>(a.zbuf);
+    uint32_t *zg = static_cast<uint32_t *>(a.zbuf);       // z rows: 4 words of high pairs, 4 of low pairs
     int cur = -1, mt = 1, mtp = 1, G = CW, grp = 0, tile = 0;
+    int ts = 0;                                            // pass 2: the stage's index within its task
     bool act = true;
     float2 acc[4];
     float dst[4], dsl[4];                                  // products with the hi and the lo parts of the operand
@@ -733,23 +720,18 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
         dst[v] = 0.f;
         dsl[v] = 0.f;
     }
+    // Warps run through the stages on their own: each waits for a stage, takes its share of the pieces (dealt from a
+    // start that rotates with the stage, so that no warp always gets the extra ones) and releases the stage; they
+    // meet only to add the groups of a finished task.  On the receiver side the rotation follows the stage's index
+    // within its task, which the task alone fixes: a group's sums, hence the result, do not depend on which CTA ran
+    // the task.
+    uint32_t mph = 0;
     for (int gi = 0;; ++gi) {
         const int slot = gi % kStages;
-        if (t == 0) *sh_flag = mbar_wait(&full[slot], (gi / kStages) & 1, a.err, a.wait_ns) ? 0 : 1;
-        consumer_sync<NC>();
-        if (*sh_flag) return;
-        if (t == 0 && gi > 0) mbar_arrive(&empty[(gi - 1) % kStages]);
+        if (!warp_wait(&full[slot], (gi / kStages) & 1, a.err, a.wait_ns)) return;
         const StageInfo &si = info[slot];
         if (si.task < 0) break;
         unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
-        if constexpr (PASS == 2) {
-            // B operand rows of every unit (z or history rows), split into fragments once per stage
-            for (int m = 0; m < si.n; ++m) {
-                const StageItem &it = si.it[m];
-                split_rows_inplace(base + it.x_off, it.k < 0 ? it.i1 - it.i0 : it.k, t, NC);
-            }
-            consumer_sync<NC>();
-        }
         if constexpr (PASS == 1) {
             const int q2 = pad_row(si.q, kPrecBF16);
             int u = 0;
@@ -757,10 +739,10 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
                 const StageItem &it = si.it[m];
                 const int rows = it.k;
                 const __nv_bfloat16 *V = reinterpret_cast<const __nv_bfloat16 *>(base + it.data_off);
-                const float *x = reinterpret_cast<const float *>(base + it.x_off);
+                const unsigned char *xr = base + it.x_off;                  // q2 split history rows
                 const int32_t *zm = reinterpret_cast<const int32_t *>(base + it.map_off);
                 const int pieces = (rows + 15) >> 4;
-                for (int pc = (warp - u % CW + CW) % CW; pc < pieces; pc += CW) {
+                for (int pc = (warp - (u + gi) % CW + CW) % CW; pc < pieces; pc += CW) {
                     const int r0 = pc * 16;
                     // four independent accumulator chains: (hi, lo) parts of x times (even, odd) K steps
                     float d[4][4] = {};
@@ -769,37 +751,46 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
                         uint32_t af[4];
                         ldsm_x4(af, V + (int64_t)arow * q2 + K0 + (mi >> 1) * 8);
                         if (q2 - K0 < 16) mask_a_k(af, tg, q2 - K0);
-                        // history rows past the slice (a last piece of 8 columns) count as zero
-                        float xv[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int j = K0 + 2 * tg + (e & 1) + (e >= 2 ? 8 : 0);
-                            xv[e] = j < q2 ? x[j * 8 + g] : 0.f;
-                        }
-                        uint32_t bh[2], bl[2];
-                        split_b(xv, bh, bl);
+                        // B: matrices (high, K0..K0+7), (high, K0+8..), (low, K0..), (low, K0+8..); columns past
+                        // the slice (a last piece of 8) read its last row, against A columns masked to zero
+                        uint32_t bf[4];
+                        const int brow = min(K0 + (mi & 1) * 8 + rr, q2 - 1);
+                        ldsm_x4_t(bf, xr + brow * 32 + (mi >> 1) * 16);
                         if (kk == 0) {
-                            mma_bf16(d[0], af, bh[0], bh[1]);
-                            mma_bf16(d[1], af, bl[0], bl[1]);
+                            mma_bf16(d[0], af, bf[0], bf[1]);
+                            mma_bf16(d[1], af, bf[2], bf[3]);
                         } else {
-                            mma_bf16(d[2], af, bh[0], bh[1]);
-                            mma_bf16(d[3], af, bl[0], bl[1]);
+                            mma_bf16(d[2], af, bf[0], bf[1]);
+                            mma_bf16(d[3], af, bf[2], bf[3]);
                         }
                     }
-                    // D fragment: v = 0, 1 -> row g, scenario 2 tg + v; v = 2, 3 -> row g + 8
+                    // D fragment: v = 0, 1 -> row g, scenarios 2 tg, 2 tg + 1; v = 2, 3 -> row g + 8.  Each z value
+                    // goes out split (scenarios >= B hold zero history, hence zero z)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const int row = r0 + g + (v >= 2 ? 8 : 0), col = 2 * tg + (v & 1);
-                        if (row < rows && col < a.B)
-                            zg[(int64_t)zm[row] * a.B + col] = (d[0][v] + d[1][v]) + (d[2][v] + d[3][v]);
+                    for (int h = 0; h < 2; ++h) {
+                        const int row = r0 + g + 8 * h;
+                        if (row < rows) {
+                            const float z0 = (d[0][2 * h] + d[1][2 * h]) + (d[2][2 * h] + d[3][2 * h]);
+                            const float z1 = (d[0][2 * h + 1] + d[1][2 * h + 1]) + (d[2][2 * h + 1] + d[3][2 * h + 1]);
+                            const __nv_bfloat16 h0 = __float2bfloat16_rn(z0), h1 = __float2bfloat16_rn(z1);
+                            const __nv_bfloat16 l0 = __float2bfloat16_rn(z0 - __bfloat162float(h0));
+                            const __nv_bfloat16 l1 = __float2bfloat16_rn(z1 - __bfloat162float(h1));
+                            uint32_t *zr = zg + (int64_t)zm[row] * 8;
+                            zr[tg] = pack_bf16(h0, h1);
+                            zr[4 + tg] = pack_bf16(l0, l1);
+                        }
                     }
                 }
                 u += pieces;
             }
+            warp_release(&empty[slot]);
         } else {
             const int p = si.p, p2 = pad_row(p, kPrecBF16);
+            const int flush = si.flush;
+            const int64_t part_off = si.part_off;
             if (si.task != cur) {
                 cur = si.task;
+                ts = 0;
                 mt = (p2 + 15) / 16;
                 mtp = mt <= 1 ? 1 : mt <= 2 ? 2 : mt <= 4 ? 4 : 8;
                 G = CW / mtp;
@@ -813,38 +804,41 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
                 const StageItem &it = si.it[m];
                 const int rows = it.k < 0 ? it.i1 - it.i0 : it.k;
                 const __nv_bfloat16 *S = reinterpret_cast<const __nv_bfloat16 *>(base + it.data_off);
-                // B operand rows (history values of dense items, z values of far items), split into fragments
-                const uint32_t *bw = reinterpret_cast<const uint32_t *>(base + it.x_off);
+                // B operand rows (history values of dense items, z values of far items), split
+                const unsigned char *br = base + it.x_off;
                 const int pieces = (rows + 15) >> 4;
                 if (act)
-                    for (int pc = (grp - u % G + G) % G; pc < pieces; pc += G) {
+                    for (int pc = (grp - (u + ts) % G + G) % G; pc < pieces; pc += G) {
                         const int k0 = pc * 16;
                         uint32_t af[4];
                         const int arow = min(k0 + (mi >> 1) * 8 + rr, rows - 1);   // rows past the unit: not read
                         ldsm_x4_t(af, S + (int64_t)arow * p2 + i0 + (mi & 1) * 8);
                         if (rows - k0 < 16) mask_a_k(af, tg, rows - k0);
-                        // row pairs past the unit's (rows + 1) / 2 are not read: zero
-                        const int rp = (k0 >> 1) + tg, pairs = (rows + 1) >> 1;
-                        const bool in0 = rp < pairs, in1 = rp + 4 < pairs;
-                        mma_bf16(dst, af, in0 ? bw[16 * rp + g] : 0u, in1 ? bw[16 * (rp + 4) + g] : 0u);
-                        mma_bf16(dsl, af, in0 ? bw[16 * rp + 8 + g] : 0u, in1 ? bw[16 * (rp + 4) + 8 + g] : 0u);
+                        // B: (high, k0..k0+7), (high, k0+8..), (low, k0..), (low, k0+8..); rows past the unit read
+                        // its last row, against A entries masked to zero
+                        uint32_t bf[4];
+                        const int brow = min(k0 + (mi & 1) * 8 + rr, rows - 1);
+                        ldsm_x4_t(bf, br + brow * 32 + (mi >> 1) * 16);
+                        mma_bf16(dst, af, bf[0], bf[1]);
+                        mma_bf16(dsl, af, bf[2], bf[3]);
                     }
                 u += pieces;
             }
+            warp_release(&empty[slot]);
+            ++ts;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {                      // compensated accumulation, once per stage
                 PTHalf<__nv_bfloat16>::kahan(acc[v], dst[v] + dsl[v]);
                 dst[v] = 0.f;
                 dsl[v] = 0.f;
             }
-            if (si.flush) {
+            if (flush) {
                 // D fragment: v = 0, 1 -> receiver row g, scenario 2 tg + v; v = 2, 3 -> row g + 8.  Groups added in
-                // a fixed order by the thread that owns each (receiver, scenario).
-                const int64_t part_off = si.part_off;
+                // a fixed order by the thread that owns each (receiver, scenario); a second meeting frees red.
 #pragma unroll
                 for (int v = 0; v < 4; ++v)
                     red[(warp * 32 + lane) * 4 + v] = act ? (double)acc[v].x - (double)acc[v].y : 0.0;
-                consumer_sync<NC>();
+                if (!consumers_meet(&empty[kStages], mph, a.err, a.wait_ns)) return;
                 for (int o = t; o < p2 * B8; o += NC) {
                     const int i = o >> 3, nn = o & 7, ti = i >> 4, ii = i & 15;
                     const int lo = (ii & 7) * 4 + (nn >> 1), reg = (ii >> 3) * 2 + (nn & 1);
@@ -854,6 +848,7 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
                         a.partial[(int64_t)nn * a.n_partial + part_off + i] = sum;
                     }
                 }
+                if (!consumers_meet(&empty[kStages], mph, a.err, a.wait_ns)) return;
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[v] = make_float2(0.f, 0.f);
                 cur = -1;
@@ -877,7 +872,12 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
     static_assert(sizeof(X) == sizeof(Z), "history and z values are staged alike");
     constexpr int SB = (int)sizeof(S);
     constexpr int XB = (int)sizeof(X);
-    constexpr int XA = 16 / XB;                     // history elements per 16 bytes
+    constexpr bool kSplitB = PREC == kPrecBF16 && BT == 8;   // split B rows (tensor-core consumers)
+    // History / z rows and z-row maps: one bulk copy per unit, except for DF64, whose consumers wait longer for bulk
+    // copies of these small slices than for warp-wide element copies (measured: 2.85 vs 1.67 ms for the receiver pass
+    // of the six-fault network at depth 2000; FP64 is the same either way and BF16 gains 30 %)
+    constexpr bool kBulkX = PREC != kPrecDF64;
+    constexpr int XA = 16 / XB;                               // history elements per 16 bytes
     extern __shared__ __align__(128) unsigned char smem_raw[];
     using LY = InterLayout<PREC, BT, PASS>;
     unsigned char *stage_mem = smem_raw;                                            // kStages x kStageBytes
@@ -898,9 +898,12 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
             sh_flag = 2;
         } else {
             for (int s = 0; s < kStages; ++s) {
-                mbar_init(&full[s], 1 + 32);       // lane 0's arrive (with the bulk bytes) + 32 cp.async arrivals
-                mbar_init(&empty[s], 1);
+                // the producer's arrive (with the transaction bytes), and with element copies each lane's arrive
+                // once its copies have landed
+                mbar_init(&full[s], kBulkX ? 1 : 1 + 32);
+                mbar_init(&empty[s], CW);          // one release per consumer warp
             }
+            mbar_init(&empty[kStages], CW);        // the consumers' meeting barrier
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
             sh_flag = *(volatile int *)a.err;      // an earlier launch already failed: do nothing
         }
@@ -950,10 +953,11 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                 if (lane == 0) t = atomicAdd(PASS == 1 ? a.counter + 2 : a.counter, 1);
                 t = __shfl_sync(0xffffffffu, t, 0);
                 if (t >= n_active) {
-                    if (lane == 0) info[slot].task = -1;
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&full[slot]);
-                    cp_async_arrive(&full[slot]);
+                    if (lane == 0) {
+                        info[slot].task = -1;
+                        mbar_arrive(&full[slot]);
+                    }
+                    if (!kBulkX) cp_async_arrive(&full[slot]);
                     return;
                 }
                 task = t;
@@ -972,18 +976,20 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
             if (!have && it + lane < ie) u = load(it + lane);
             const bool valid = it + lane < ie;
             const int w2 = PASS == 1 ? pad_row(q, PREC) : pad_row(p, PREC);     // operator row length
+            // Each unit's history / z rows and z-row map arrive in one bulk copy each, issued by the unit's lane and
+            // widened to 16-byte bounds (the consumers index past the skew; values past a unit's count are finite
+            // neighbours that multiply zero padding or are masked).  A row holds RW values of the history type: the
+            // batch, or 8 for the split rows of the tensor-core consumers (8 bfloat16 high parts, 8 low parts).
+            const int RW = kSplitB ? 8 : a.B;
             int data_bytes = 0, x_bytes = 0, nrow = 0;
             int map_bytes = 0;
             if (valid) {
                 nrow = u.k < 0 ? u.i1 - u.i0 : u.k;
                 data_bytes = SB * nrow * w2;
-                // the tensor-core consumers split B rows in pairs: room for an even count of 8-wide rows
-                constexpr bool kPairB = PREC == kPrecBF16 && BT == 8;
                 const int brows = PASS == 1 ? pad_row(q, PREC) : nrow;
-                const int span = kPairB ? (brows + 1) / 2 * 2 * 8 : brows * a.B;
-                x_bytes = (XB * span + 15) / 16 * 16;
+                x_bytes = (XB * brows * RW + 15) / 16 * 16 + 16;
                 if (PASS == 1) {                   // the run's z-row map follows its history slice
-                    map_bytes = (4 * nrow + 15) / 16 * 16;
+                    map_bytes = (4 * nrow + 15) / 16 * 16 + 16;
                     x_bytes += map_bytes;
                 }
             }
@@ -999,24 +1005,24 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                 if (lane == 0) {
                     atomicExch(a.err, 3);
                     info[slot].task = -1;
+                    mbar_arrive(&full[slot]);
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&full[slot]);
-                cp_async_arrive(&full[slot]);
+                if (!kBulkX) cp_async_arrive(&full[slot]);
                 return;
             }
             const bool in = lane < n;
-            int dincl = in ? data_bytes : 0, xincl = in ? x_bytes : 0, rincl = in ? nrow : 0;
+            int dincl = in ? data_bytes : 0, rincl = in ? nrow : 0;
             for (int o = 1; o < 32; o <<= 1) {
                 const int d = __shfl_up_sync(0xffffffffu, dincl, o);
-                const int x = __shfl_up_sync(0xffffffffu, xincl, o);
                 const int r = __shfl_up_sync(0xffffffffu, rincl, o);
                 if (lane >= o) {
                     dincl += d;
-                    xincl += x;
                     rincl += r;
                 }
             }
+            // the units' history / z areas follow the operator bytes in the same order: their inclusive sums are
+            // incl - dincl over the stage's lanes
+            const int xincl = incl - dincl;
             const int total_data = __shfl_sync(0xffffffffu, dincl, 31);
             const int total_rows = __shfl_sync(0xffffffffu, rincl, 31);
             StageInfo *si = &info[slot];
@@ -1033,70 +1039,79 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
             }
             const int data_off = dincl - (in ? data_bytes : 0);
             const int x_off = total_data + xincl - (in ? x_bytes : 0);
-            if (in)
-                si->it[lane] = StageItem{u.k, u.i0, u.i1, data_off, x_off, rincl, u.scale, x_off + x_bytes - map_bytes,
-                                         u.map};
+            const int map_off = x_off + x_bytes - map_bytes;
             unsigned char *dst = stage_mem + (size_t)slot * kStageBytes;
-            // source, count and span (count plus the zero tail that padding columns multiply) of each unit's
-            // history / z values
-            // The tensor-core consumers take their B rows 8 scenarios wide and in pairs: with a narrower batch the
-            // rows are spread to a stride of 8 (element copies) and every unused value is zero.
-            constexpr bool kPairRows = PREC == kPrecBF16 && BT == 8;
-            const bool spread = kPairRows && a.B != 8;
+            // source, count and span (count plus the tail that padding columns multiply) of each unit's history /
+            // z values
             const X *xsrc = nullptr;
-            int xcnt = 0, xspan = 0;
+            int xspan = 0;
             if (in) {
-                const int brows = PASS == 1 ? pad_row(q, PREC) : nrow;
-                xspan = kPairRows ? (brows + 1) / 2 * 2 * 8 : brows * a.B;
+                xspan = (PASS == 1 ? pad_row(q, PREC) : nrow) * RW;
                 if (PASS == 2 && u.k > 0) {
-                    xsrc = reinterpret_cast<const X *>(zbuf + u.map * a.B);
-                    xcnt = nrow * a.B;
+                    xsrc = reinterpret_cast<const X *>(zbuf + u.map * RW);
                 } else {
                     // lags past the step (whole tasks are switched on) read a slot not yet written: zeros
                     const int64_t back = (a.step - u.T) % a.ring;
                     const int slot_v = (int)(back < 0 ? back + a.ring : back);
                     const int e0 = c0 + (PASS == 1 ? 0 : u.i0);
-                    xsrc = xring + (int64_t)slot_v * a.ring_stride + (int64_t)e0 * a.B;
-                    xcnt = (PASS == 1 ? q : nrow) * a.B;
+                    xsrc = xring + (int64_t)slot_v * a.ring_stride + (int64_t)e0 * RW;
                 }
             }
-            // zero tails first (plain shared stores, published by lane 0's arrive below)
-            for (int m = 0; m < n; ++m) {
-                const int cnt = __shfl_sync(0xffffffffu, xcnt, m), span = __shfl_sync(0xffffffffu, xspan, m);
-                X *xd = reinterpret_cast<X *>(dst + __shfl_sync(0xffffffffu, x_off, m));
-                for (int c = (spread ? 0 : cnt) + lane; c < span; c += 32) xd[c] = X{};
+            // bulk copies: 16-byte aligned source and length; the skew (a multiple of the element size) moves the
+            // unit's view in the stage
+            const int32_t *msrc = PASS == 1 ? a.zmap + u.map : nullptr;
+            int xskew = 0, mskew = 0;
+            uint32_t xcopy = 0, mcopy = 0;
+            if (in) {
+                xskew = (int)(reinterpret_cast<uintptr_t>(xsrc) & 15);
+                if (PASS == 1) mskew = (int)(reinterpret_cast<uintptr_t>(msrc) & 15);
+                if (kBulkX) {
+                    xcopy = (uint32_t)((xskew + XB * xspan + 15) & ~15);
+                    if (PASS == 1) mcopy = (uint32_t)((mskew + 4 * nrow + 15) & ~15);
+                }
             }
+            if (in)
+                si->it[lane] = StageItem{u.k, u.i0, u.i1, data_off, x_off + xskew, rincl, u.scale, map_off + mskew,
+                                         u.map};
+            uint32_t tx = xcopy + mcopy;
+            for (int o = 16; o > 0; o >>= 1) tx += __shfl_xor_sync(0xffffffffu, tx, o);
             __syncwarp();
-            if (lane == 0) mbar_arrive_tx(&full[slot], (uint32_t)total_data);
+            if (lane == 0) mbar_arrive_tx(&full[slot], (uint32_t)total_data + tx);
             __syncwarp();
             // lane 0 holds unit `it`, the first of the n adjacent units: their operator bytes in one bulk copy
             if (lane == 0 && total_data > 0) bulk_g2s(dst, u.a, (uint32_t)total_data, &full[slot]);
-            for (int m = 0; m < n; ++m) {
-                const int cnt = __shfl_sync(0xffffffffu, xcnt, m);
-                const X *src = reinterpret_cast<const X *>(
-                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(xsrc), m));
-                X *xd = reinterpret_cast<X *>(dst + __shfl_sync(0xffffffffu, x_off, m));
-                if (spread) {
-                    for (int c = lane; c < cnt; c += 32) cp_async_elem<XB>(xd + (c / a.B) * 8 + c % a.B, src + c);
-                } else if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-                    const int n16 = cnt / XA;
-                    for (int c = lane; c < n16; c += 32) cp_async16(xd + c * XA, src + c * XA);
-                    for (int c = n16 * XA + lane; c < cnt; c += 32) cp_async_elem<XB>(xd + c, src + c);
-                } else {
-                    for (int c = lane; c < cnt; c += 32) cp_async_elem<XB>(xd + c, src + c);
-                }
-            }
-            if (PASS == 1) {
-                // z-row maps: 4-byte elements (their start in zmap need not be 16-byte aligned)
+            if (kBulkX) {
+                if (xcopy)
+                    bulk_g2s(dst + x_off, reinterpret_cast<const unsigned char *>(xsrc) - xskew, xcopy, &full[slot]);
+                if (mcopy)
+                    bulk_g2s(dst + map_off, reinterpret_cast<const unsigned char *>(msrc) - mskew, mcopy, &full[slot]);
+            } else {
+                // the warp copies each unit's slice (16 bytes a lane when the skew is zero) at the same skewed place
                 for (int m = 0; m < n; ++m) {
-                    const int rows = __shfl_sync(0xffffffffu, nrow, m);
-                    const int64_t mp = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)u.map, m);
-                    const int xo = __shfl_sync(0xffffffffu, x_off + x_bytes - map_bytes, m);
-                    int32_t *md = reinterpret_cast<int32_t *>(dst + xo);
-                    for (int c = lane; c < rows; c += 32) cp_async_elem<4>(md + c, a.zmap + mp + c);
+                    const int cnt = __shfl_sync(0xffffffffu, xspan, m);
+                    const int sk = __shfl_sync(0xffffffffu, xskew, m);
+                    const X *src = reinterpret_cast<const X *>(
+                        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(xsrc), m));
+                    X *xd = reinterpret_cast<X *>(dst + __shfl_sync(0xffffffffu, x_off, m) + sk);
+                    if (sk == 0) {
+                        const int n16 = cnt / XA;
+                        for (int c = lane; c < n16; c += 32) cp_async16(xd + c * XA, src + c * XA);
+                        for (int c = n16 * XA + lane; c < cnt; c += 32) cp_async_elem<XB>(xd + c, src + c);
+                    } else {
+                        for (int c = lane; c < cnt; c += 32) cp_async_elem<XB>(xd + c, src + c);
+                    }
                 }
+                if (PASS == 1) {
+                    for (int m = 0; m < n; ++m) {
+                        const int rows = __shfl_sync(0xffffffffu, nrow, m);
+                        const int64_t mp = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)u.map, m);
+                        int32_t *md = reinterpret_cast<int32_t *>(dst + __shfl_sync(0xffffffffu, map_off, m) +
+                                                                  __shfl_sync(0xffffffffu, mskew, m));
+                        for (int c = lane; c < rows; c += 32) cp_async_elem<4>(md + c, a.zmap + mp + c);
+                    }
+                }
+                cp_async_arrive(&full[slot]);
             }
-            cp_async_arrive(&full[slot]);
             it += n;
             // shift the descriptors of units it .. it + 31 down and fetch the tail now
             if (it < ie) {
@@ -1120,7 +1135,7 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
 
     // [tensor-core consumers: begin]
     if constexpr (PREC == kPrecBF16 && BT == 8) {
-        consume_mma<CW, PASS>(a, info, stage_mem, red, full, empty, &sh_flag);
+        consume_mma<CW, PASS>(a, info, stage_mem, red, full, empty);
         return;
     }
     // [tensor-core consumers: end]
@@ -1132,15 +1147,14 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
         // z = V^T x for every row of the stage's runs.  L lanes share a row, each summing at least four vectors
         // before the shuffle tree (the tree's adds run on the same pipe as the products); DF64 takes one lane per
         // row, its shuffle adds costing a dozen FP32 operations each.  The lanes of row slot rw start their sweep
-        // rw * L vectors further on, so the rows a warp reads fall in different shared-memory banks.  With a full
-        // batch (B == BT) the VE * BT history values of a vector are contiguous and are read with 16-byte loads.
+        // rw * L vectors further on, so the rows a warp reads fall in different shared-memory banks.  History values
+        // are read one by one (16-byte vector reads of them measured slower).
         Z *zout = reinterpret_cast<Z *>(a.zbuf);
+        // Warps run through the stages on their own (each waits for a stage and releases it); the row slots of a
+        // stage start at a warp that rotates with the stage, so that the short last sweep moves from warp to warp.
         for (int g = 0;; ++g) {
             const int slot = g % kStages;
-            if (t == 0) sh_flag = mbar_wait(&full[slot], (g / kStages) & 1, a.err, a.wait_ns) ? 0 : 1;
-            consumer_sync<NC>();
-            if (sh_flag) return;
-            if (t == 0 && g > 0) mbar_arrive(&empty[(g - 1) % kStages]);
+            if (!warp_wait(&full[slot], (g / kStages) & 1, a.err, a.wait_ns)) return;
             const StageInfo &sx = info[slot];
             if (sx.task < 0) break;
             const unsigned char *bx = stage_mem + (size_t)slot * kStageBytes;
@@ -1150,10 +1164,11 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
             const int q4 = PREC == kPrecDF64 ? 0 : qv >> 2;
             const int L = q4 >= 32 ? 32 : q4 >= 16 ? 16 : q4 >= 8 ? 8 : q4 >= 4 ? 4 : q4 >= 2 ? 2 : 1;
             const int subs = 32 / L, SA = CW * subs;
-            const int sl = lane % L, rw = lane / L, slotA = warp * subs + rw;
+            const int wr = (warp + g) % CW;                        // the warp's place in this stage
+            const int sl = lane % L, rw = lane / L, slotA = wr * subs + rw;
             const int rot = (rw * L) % qv;
-            const bool xvec = a.B == BT;
-            const int trips = (nz + SA - 1) / SA;                  // uniform over the warp
+            // sweeps that reach at least one of the warp's row slots (uniform over the warp)
+            const int trips = nz > wr * subs ? (nz - wr * subs + SA - 1) / SA : 0;
             int k = 0, zstart = 0;
             for (int r = 0; r < trips; ++r) {
                 const int f = slotA + r * SA;
@@ -1178,20 +1193,11 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                         if (uu >= qv) uu -= qv;
                         E v[VE];
                         VecLoad<PREC, VE>::ld(vr + uu * VE, v);
-                        if (xvec) {
-                            X xv[VE * BT];
-                            ld16(x + uu * VE * BT, xv);
 #pragma unroll
-                            for (int e = 0; e < VE; ++e)
+                        for (int e = 0; e < VE; ++e)
 #pragma unroll
-                                for (int bb = 0; bb < BT; ++bb) edot(z[bb], v[e], xv[e * BT + bb]);
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < VE; ++e)
-#pragma unroll
-                                for (int bb = 0; bb < BT; ++bb)
-                                    edot(z[bb], v[e], x[(uu * VE + e) * a.B + (bb < a.B ? bb : 0)]);
-                        }
+                            for (int bb = 0; bb < BT; ++bb)
+                                edot(z[bb], v[e], x[(uu * VE + e) * a.B + (bb < a.B ? bb : 0)]);
                     }
                 }
 #pragma unroll
@@ -1200,6 +1206,7 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                     if (act && sl == 0 && bb < a.B) zout[zrow * a.B + bb] = T::zscale(z[bb], sc);
                 }
             }
+            warp_release(&empty[slot]);
         }
         return;
     } else {
@@ -1218,18 +1225,23 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
         int cur = -1, P = 1, G = 1, vec = 0, grp = 0, nvt = 1;
         Acc acc[NVT][VE][BT];
         PAcc part[NVT][VE][BT];
+        // Warps run through the stages on their own; the groups' share of a stage's rows starts at a group that
+        // rotates (by whole warps) with the stage's index within its task (fixed by the task, so that the sums do not
+        // depend on which CTA ran it); all warps meet only for the task-end reduction.
+        uint32_t mph = 0;
+        int ts = 0;
         for (int g = 0;; ++g) {
             const int slot = g % kStages;
-            if (t == 0) sh_flag = mbar_wait(&full[slot], (g / kStages) & 1, a.err, a.wait_ns) ? 0 : 1;
-            consumer_sync<NC>();
-            if (sh_flag) return;
-            if (t == 0 && g > 0) mbar_arrive(&empty[(g - 1) % kStages]);
+            if (!warp_wait(&full[slot], (g / kStages) & 1, a.err, a.wait_ns)) return;
             const StageInfo &si = info[slot];
             const int task = si.task;
             if (task < 0) break;
             const int p = si.p, p2 = pad_row(p, PREC);
+            const int flush = si.flush;
+            const int64_t part_off = si.part_off;
             if (task != cur) {
                 cur = task;
+                ts = 0;
                 // P: threads per row, a power of two, so that groups tile the warps (P <= 32) or whole warps
                 // tile a group (P > 32)
                 const int pv = p2 / VE;
@@ -1253,8 +1265,10 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
             const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
             if (grp < G) {
                 const int nr = si.n_rows;
+                const int gpw = P >= 32 ? 1 : 32 / P;              // groups per warp
+                const int f0 = (int)((grp + (int64_t)ts * gpw) % G);
                 int k = 0, rstart = 0;
-                for (int f = grp; f < nr; f += G) {
+                for (int f = f0; f < nr; f += G) {
                     while (f >= si.it[k].row_end) {
                         rstart = si.it[k].row_end;
                         ++k;
@@ -1308,12 +1322,13 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                             }
                 }
             }
-            if (si.flush) {
-                const int64_t part_off = si.part_off;
+            warp_release(&empty[slot]);
+            ++ts;
+            if (flush) {
                 // column c = (vec + s P) VE + e; value v of a thread: vector s = v / (VE BT), element e = (v / BT) mod
                 // VE, scenario bb = v mod BT.  The G groups are reduced in a fixed order, RV values per round through
-                // shared memory; rounds past the task's vectors are skipped (uniform).  The barrier that opens the
-                // next interval protects red from the next writes.
+                // shared memory; rounds past the task's vectors are skipped (uniform).  Each round's reads are
+                // followed by a second meeting, which frees red for the next writes.
                 constexpr int NV = NVT * VE * BT;
                 const int nv = nvt * VE * BT;
                 if (G == 1) {
@@ -1367,7 +1382,7 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                         for (int j = 0; j < NV; ++j)
                             if (j < cnt) red[(warp * P + vv) * NV + base + j] = vals[j];
                     }
-                    consumer_sync<NC>();
+                    if (!consumers_meet(&empty[kStages], mph, a.err, a.wait_ns)) return;
                     if (t < P * NV) {
                         const int vt = t % P, v = t / P;
                         const int sv = v / (VE * BT), e = (v / BT) % VE, bb = v % BT;
@@ -1379,13 +1394,13 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                             a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
                         }
                     }
+                    if (!consumers_meet(&empty[kStages], mph, a.err, a.wait_ns)) return;
                 } else if (P <= 32) {
                     // the 32 / P groups of a warp by a shuffle tree, then the CW warp sums of each (column, value) by
                     // one of RV P threads
 #pragma unroll
                     for (int r0 = 0; r0 < NV; r0 += RV) {
                         if (r0 >= nv) break;
-                        if (r0 > 0) consumer_sync<NC>();
 #pragma unroll
                         for (int m = 0; m < RV; ++m) {
                             const int v = r0 + m;
@@ -1395,7 +1410,7 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                                 if (lane < P) red[(warp * 32 + lane) * RV + m] = x;
                             }
                         }
-                        consumer_sync<NC>();
+                        if (!consumers_meet(&empty[kStages], mph, a.err, a.wait_ns)) return;
                         if (t < RV * P) {
                             const int m = t / P, vv = t % P, v = r0 + m;
                             const int sv = v / (VE * BT), e = (v / BT) % VE, bb = v % BT;
@@ -1407,19 +1422,19 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                                 a.partial[(int64_t)bb * a.n_partial + part_off + c] = sum;
                             }
                         }
+                        if (!consumers_meet(&empty[kStages], mph, a.err, a.wait_ns)) return;
                     }
                 } else {
                     // 2 to 8 groups of whole warps: group 0 adds the others' values
 #pragma unroll
                     for (int r0 = 0; r0 < NV; r0 += RV) {
                         if (r0 >= nv) break;
-                        if (r0 > 0) consumer_sync<NC>();
 #pragma unroll
                         for (int m = 0; m < RV; ++m) {
                             const int v = r0 + m;
                             if (v < NV) red[t * RV + m] = T::to_d(acc[v / (VE * BT)][(v / BT) % VE][v % BT]);
                         }
-                        consumer_sync<NC>();
+                        if (!consumers_meet(&empty[kStages], mph, a.err, a.wait_ns)) return;
                         if (grp == 0) {
 #pragma unroll
                             for (int m = 0; m < RV; ++m) {
@@ -1433,6 +1448,7 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                                 }
                             }
                         }
+                        if (!consumers_meet(&empty[kStages], mph, a.err, a.wait_ns)) return;
                     }
                 }
                 cur = -1;
@@ -1535,8 +1551,15 @@ __global__ void __launch_bounds__(kThreads) k_reset_member(StepArgs a, int mb) {
     for (int64_t e = tid; e < (int64_t)a.ring * a.N; e += nt) {
         const int64_t slot = e / a.N, i = e - slot * a.N, o = slot * a.ring_stride + i * a.B + mb;
         a.vring[o] = 0.0;
-        if (a.prec == kPrecDF64) reinterpret_cast<float2 *>(a.xring)[o] = make_float2(0.f, 0.f);
-        else if (a.prec != kPrecFP64) reinterpret_cast<float *>(a.xring)[o] = 0.f;
+        if (a.prec == kPrecDF64) {
+            reinterpret_cast<float2 *>(a.xring)[o] = make_float2(0.f, 0.f);
+        } else if (a.xsplit) {
+            __nv_bfloat16 *xr = reinterpret_cast<__nv_bfloat16 *>(a.xring) + (slot * a.ring_stride + i * 8) * 2;
+            xr[mb] = __float2bfloat16_rn(0.f);
+            xr[8 + mb] = __float2bfloat16_rn(0.f);
+        } else if (a.prec != kPrecFP64) {
+            reinterpret_cast<float *>(a.xring)[o] = 0.f;
+        }
     }
     if (a.tail)
         for (int64_t e = tid; e < (int64_t)a.sring_depth * a.N; e += nt) {
