@@ -224,6 +224,23 @@ seas_status seas_scenario_set_wait_limit(seas_scn *scn, double seconds);
  * involved.  No counterpart in the paper. */
 seas_status seas_scenario_probe_wait(seas_scn *scn);
 
+/* Autotuner of the interaction kernel's launch shape: for each pass (0: source side, 1: receiver side) the number of
+ * consumer warps per CTA (8 or 16, where the library compiles both for this precision and batch) that runs the
+ * pass fastest on this scenario's operator, measured with CUDA events over `reps` launches of the pass (1..100,
+ * median; one untimed launch first) with every task of the operator active, as at full history depth.  The choice
+ * holds for the scenario's later steps; it changes no result beyond the summation order of the task reductions.
+ * The passes' per-step scratch is overwritten, so call it between steps.  cache_path (NULL: none) names a text file
+ * of earlier choices, one line per key (device name, SM count, precision, batch and the operator's work shape): a
+ * matching line is applied without timing (from_cache = 1), otherwise the new choice is appended.  SEAS_ESTATE with
+ * a captured graph (its kernels are fixed) or while kernel timing is on.  No counterpart in the paper. */
+typedef struct {
+    int consumer_warps[2];      /* chosen per pass */
+    int candidates[2][2];       /* counts compiled per pass (0: none; the first is the default) */
+    double ms[2][2];            /* median launch time of each candidate (0: not timed) */
+    int from_cache;
+} seas_tune;
+seas_status seas_scenario_autotune(seas_scn *scn, const char *cache_path, int reps, seas_tune *out);
+
 /* CUDA-graph stepping.  seas_scenario_graph_create captures one step of the scenario -- a push of the slip rate in
  * the caller's device buffer V ([batch][N], slip integrated) and a stress step into the device buffers tau
  * ([batch][N]) and parts (nullable, [3][batch][N]) -- as one graph of all its kernels (interaction passes on every

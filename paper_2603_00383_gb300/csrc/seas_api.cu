@@ -239,6 +239,7 @@ struct seas_scn {
     DArr<double2> dring, fmodes;
     DArr<int> counter_err;           // [0], [2]: task counters of the two interaction passes, [1]: device error word
     uint64_t wait_ns = 2000000000ull;   // bound of one device wait (seas_scenario_set_wait_limit)
+    int cw[2] = {0, 0};              // consumer warps of the interaction passes (seas_scenario_autotune; 0: default)
     int64_t ring_stride = 0;
     DArr<FaultDev> faults;           // fault table with spectral-ring offsets for this batch size
     int64_t dring_len = 0;
@@ -1153,6 +1154,27 @@ seas_status build_interaction(seas_op &op) {
         op.bytes_upto[x.T] += eb * (x.k < 0 ? (int64_t)b.q * b.p : (int64_t)x.k * (b.p + b.q));
     }
     for (size_t T = 1; T < op.bytes_upto.size(); ++T) op.bytes_upto[T] += op.bytes_upto[T - 1];
+    if (eb == 2) {
+        // 2-byte arenas: each unit's row chunks rotated once (chunk_at), for conflict-free shared-memory reads
+        std::vector<UnitRows> units;
+        units.reserve(items.size() + runs.size());
+        for (const TaskDev &t : tasks) {
+            const int nch = pad_row(op.blocks_h[t.block].p, prec) / 8;
+            for (int i = t.item_begin; i < t.item_end; ++i) {
+                const ItemDev &it = items[(size_t)i];
+                units.push_back(UnitRows{const_cast<void *>(it.a), it.k < 0 ? it.i1 - it.i0 : it.k, nch});
+            }
+        }
+        for (const TaskDev &t : ztasks) {
+            const int nch = pad_row(srcs[(size_t)t.block].q, prec) / 8;
+            for (int i = t.item_begin; i < t.item_end; ++i)
+                units.push_back(UnitRows{const_cast<void *>(runs[(size_t)i].v), runs[(size_t)i].rows, nch});
+        }
+        DArr<UnitRows> d_units;
+        SEAS_TRY(d_units.upload(c, units));
+        CUDA_TRY(launch_rotate_rows(d_units.p, (int)units.size(), c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
     SEAS_TRY(op.d_items.upload(c, items));
     SEAS_TRY(op.d_tasks.upload(c, tasks));
     SEAS_TRY(op.d_cover_ptr.upload(c, cover_ptr));
@@ -1304,6 +1326,8 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     a.n_modes_total = op.n_modes_total;
     a.max_nf = op.max_nf;
     a.step = step;
+    a.cw[0] = s.cw[0];
+    a.cw[1] = s.cw[1];
     int64_t lag_max = -1;            // the oldest active member's step
     for (int b = 0; b < s.B; ++b)
         if (s.active[b]) lag_max = std::max<int64_t>(lag_max, step - s.start[b]);
@@ -1723,6 +1747,132 @@ extern "C" seas_status seas_scenario_probe_wait(seas_scn *s) {
     CUDA_TRY(cudaSetDevice(c->device));
     const StepArgs a = step_args(*s, s->n > 0 ? s->n - 1 : 0);
     CUDA_TRY(launch_wait_probe(a, c->stream));
+    return SEAS_OK;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// autotuner: the consumer warp count of each interaction pass, by measurement
+// ------------------------------------------------------------------------------------------------------------
+
+namespace {
+
+// Key of a tuning choice: the device, the precision and batch, and the shape of the operator's work (units, tasks
+// and bytes of both passes), so that a cached choice is reused only for the same work on the same kind of GPU.
+std::string tune_key(const seas_scn &s) {
+    const seas_op &op = *s.op;
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, op.net->ctx->device);
+    std::string name = prop.name;
+    for (char &ch : name)
+        if (ch == ' ' || ch == '|') ch = '_';
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s|sm%d|prec%d|B%d|tasks%zu|ztasks%zu|items%zu|runs%zu|bytes%lld|steps%d", name.c_str(),
+             op.net->ctx->n_sms, op.hp.precision, s.B, op.task_T.size(), op.ztask_T.size(), op.d_items.n,
+             op.d_runs.n, (long long)op.stats.bytes_interaction, op.hp.max_steps);
+    return buf;
+}
+
+bool tune_lookup(const char *path, const std::string &key, int *cw) {
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool hit = false;
+    while (fgets(line, sizeof line, f)) {
+        const size_t n = key.size();
+        if (strncmp(line, key.c_str(), n) == 0 && line[n] == ' ') {
+            int a = 0, b = 0;
+            if (sscanf(line + n + 1, "%d %d", &a, &b) == 2 && (a == 8 || a == 16) && (b == 8 || b == 16)) {
+                cw[0] = a;                 // the last matching line wins
+                cw[1] = b;
+                hit = true;
+            }
+        }
+    }
+    fclose(f);
+    return hit;
+}
+
+}  // namespace
+
+extern "C" seas_status seas_scenario_autotune(seas_scn *s, const char *cache_path, int reps, seas_tune *out) {
+    if (!s || !out) return fail(SEAS_EINVAL, "NULL argument");
+    if (reps < 1 || reps > 100) return fail(SEAS_EINVAL, "reps %d outside [1, 100]", reps);
+    if (s->gexec) return fail(SEAS_ESTATE, "the scenario has a captured step: its kernels are fixed");
+    if (s->timing) return fail(SEAS_ESTATE, "kernel timing is on");
+    seas_op &op = *s->op;
+    seas_ctx *c = op.net->ctx;
+    CUDA_TRY(cudaSetDevice(c->device));
+    *out = seas_tune{};
+    for (int p = 0; p < 2; ++p) {
+        int opts[2] = {0, 0};
+        const int n = interaction_options(op.hp.precision, s->B, p + 1, opts);
+        for (int k = 0; k < n; ++k) out->candidates[p][k] = opts[k];
+    }
+    const std::string key = tune_key(*s);
+    int cached[2] = {0, 0};
+    if (cache_path && tune_lookup(cache_path, key, cached)) {
+        for (int p = 0; p < 2; ++p) {
+            const bool ok = cached[p] == out->candidates[p][0] || cached[p] == out->candidates[p][1];
+            s->cw[p] = ok ? cached[p] : 0;
+            out->consumer_warps[p] = ok ? cached[p] : out->candidates[p][0];
+        }
+        out->from_cache = 1;
+        return SEAS_OK;
+    }
+    // every task active at the deepest lag: the passes' work does not depend on the history's values, and their
+    // scratch (z rows, partial sums) is recomputed by the next step
+    StepArgs a = step_args(*s, s->n > 0 ? s->n - 1 : 0);
+    a.lag_max = op.ring - 1;
+    a.n_tasks_active = (int)op.task_T.size();
+    a.n_ztasks_active = (int)op.ztask_T.size();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        CUDA_TRY(ce);
+    }
+    for (int p = 0; p < 2 && ce == cudaSuccess; ++p) {
+        double best = 0;
+        for (int k = 0; k < 2 && ce == cudaSuccess; ++k) {
+            const int cw = out->candidates[p][k];
+            if (!cw) continue;
+            a.cw[p] = cw;
+            std::vector<float> t;
+            for (int r = 0; r <= reps && ce == cudaSuccess; ++r) {      // launch 0 is untimed
+                ce = cudaMemsetAsync(s->counter_err.p + (p == 0 ? 2 : 0), 0, sizeof(int), c->stream);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
+                if (ce == cudaSuccess) ce = launch_interaction(a, p + 1, c->stream);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
+                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0) t.push_back(ms);
+            }
+            if (ce != cudaSuccess) break;
+            std::sort(t.begin(), t.end());
+            out->ms[p][k] = t[t.size() / 2];
+            if (best == 0 || out->ms[p][k] < best) {
+                best = out->ms[p][k];
+                out->consumer_warps[p] = cw;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(ce);
+    // counters back to zero for the next step (its reduction would reset them too)
+    CUDA_TRY(cudaMemsetAsync(s->counter_err.p, 0, sizeof(int), c->stream));
+    CUDA_TRY(cudaMemsetAsync(s->counter_err.p + 2, 0, sizeof(int), c->stream));
+    SEAS_TRY(seas_scenario_check(s));
+    for (int p = 0; p < 2; ++p) s->cw[p] = out->consumer_warps[p];
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (!f) return fail(SEAS_EINVAL, "cannot append to tuning cache %s", cache_path);
+        fprintf(f, "%s %d %d %.6f %.6f %.6f %.6f\n", key.c_str(), s->cw[0], s->cw[1], out->ms[0][0], out->ms[0][1],
+                out->ms[1][0], out->ms[1][1]);
+        fclose(f);
+    }
     return SEAS_OK;
 }
 

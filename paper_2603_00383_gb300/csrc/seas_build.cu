@@ -318,6 +318,29 @@ __global__ void __launch_bounds__(kThreads) k_gather(const void *const *__restri
     for (int c = lane; c < n16; c += 32) d[c] = s[c];
 }
 
+// Chunk rotation of 2-byte operator units (chunk_at): one warp per unit, one row at a time, in place (a row's
+// chunks are all read before any is written).  Rows have at most 128 chunks (1024 columns).
+__global__ void __launch_bounds__(kThreads) k_rotate_rows(const UnitRows *__restrict__ units, int n) {
+    const int w = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const UnitRows u = units[w];
+    uint4 *base = static_cast<uint4 *>(u.p);
+    for (int r = 0; r < u.rows; ++r) {
+        uint4 *row = base + (int64_t)r * u.nch;
+        uint4 v[4];
+        for (int k = 0; k < 4; ++k) {
+            const int c = lane + 32 * k;
+            if (c < u.nch) v[k] = row[c];
+        }
+        __syncwarp();
+        for (int k = 0; k < 4; ++k) {
+            const int c = lane + 32 * k;
+            if (c < u.nch) row[chunk_at(c, r, u.nch)] = v[k];
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------------------------------------------------------
 // Spectral weights.  With m = n pi and rho = c_s t / L_f, the time integral of Eq. (non_replicant_kernel),
 //   G(rho) = c_s k_n int_0^t K(n, s) ds = (2/pi) int_0^{psi_m} cos^2(psi) sin(m rho sin psi) / sin(psi) dpsi,
@@ -436,6 +459,13 @@ cudaError_t launch_gather(const void *const *src, void *const *dst, const int32_
     if (n <= 0) return cudaSuccess;
     const int per = kThreads / 32;
     k_gather<<<(n + per - 1) / per, kThreads, 0, s>>>(src, dst, bytes, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rotate_rows(const UnitRows *units, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int per = kThreads / 32;
+    k_rotate_rows<<<(n + per - 1) / per, kThreads, 0, s>>>(units, n);
     return cudaGetLastError();
 }
 

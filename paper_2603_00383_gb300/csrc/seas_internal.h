@@ -42,6 +42,23 @@ __host__ __device__ inline int pad_row(int n, int prec) {
     return (n + e - 1) / e * e;
 }
 
+// Rows of 2-byte operator units (BF16, FP16) are stored with their 16-byte chunks rotated: logical chunk c of row r
+// (counted from the unit's first row) of a unit whose rows have nch chunks sits at chunk (c + rot) mod nch, rot =
+// (r / period) mod g with g = gcd(nch, 8) and period = 8 / g.  Then the same logical chunk of 8 consecutive rows falls
+// in 8 different 16-byte bank groups of shared memory whatever the row length, so the matrix loads of the tensor-core
+// consumers (8 rows, one chunk each) are conflict free.  The operator build applies it once; every consumer of a
+// 2-byte arena reads through it.
+__host__ __device__ inline int chunk_rot(int r, int nch) {
+    int g = nch & -nch;
+    if (g > 8) g = 8;
+    const int shift = g == 8 ? 0 : g == 4 ? 1 : g == 2 ? 2 : 3;   // log2(8 / g)
+    return (r >> shift) & (g - 1);
+}
+__host__ __device__ inline int chunk_at(int c, int r, int nch) {
+    const int q = c + chunk_rot(r, nch);
+    return q >= nch ? q - nch : q;
+}
+
 // One fault of the spectral self-effect path.
 struct FaultDev {
     int32_t off;        // first element (global index)
@@ -156,6 +173,12 @@ cudaError_t launch_pack(const BlockDev *blocks, const SliceGen *slices, const Sl
                         const int64_t *vdst_off, void *vdst, float *scales, int prec, cudaStream_t s);
 // dst[i] = src[i] for n runs of bytes[i] bytes (16-byte multiples, 16-byte aligned)
 cudaError_t launch_gather(const void *const *src, void *const *dst, const int32_t *bytes, int n, cudaStream_t s);
+// One operator unit of a 2-byte arena for the chunk rotation: its first row, rows and 16-byte chunks per row.
+struct UnitRows {
+    void *p;
+    int32_t rows, nch;
+};
+cudaError_t launch_rotate_rows(const UnitRows *units, int n, cudaStream_t s);
 cudaError_t launch_spectral_tables(const ModeDev *modes, int n_modes, const int64_t *g_prefix, int64_t n_g,
                                    const double *mode_L, double cs_dt, const double *gl_x, const double *gl_w,
                                    int gl_n, double *G, double *w, cudaStream_t s);
@@ -206,6 +229,7 @@ struct StepArgs {
     int n_ztasks_active;
     void *zbuf;                   // [z rows][B] in the arithmetic's dot type (double, float2 or float)
     int pass;                     // 1 or 2: which pass a launch of the interaction kernel runs
+    int cw[2];                    // consumer warps of pass 1 and 2 (0: the default of the precision and batch)
     const DynDev *dyn;            // non-null in a captured step: step, lag_max and task counts come from here
     double *partial;              // [B][n_partial]
     int64_t n_partial;
@@ -248,6 +272,9 @@ cudaError_t launch_push(const StepArgs &a, const double *V, const double *slip_i
 cudaError_t launch_fft_forward(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_interaction(const StepArgs &a, int pass, cudaStream_t s);   // pass 1, then pass 2
+// Consumer warp counts compiled for the interaction pass of a precision and batch (the default first); returns how
+// many (1 or 2) it wrote to cw.
+int interaction_options(int prec, int batch, int pass, int *cw);
 cudaError_t launch_reduce(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_static_tail(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_ifft_assemble(const StepArgs &a, double *tau, double *parts, cudaStream_t s);

@@ -197,7 +197,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_forward(StepArgs a_) {
 
 // Per-mode causal convolution (Eq. funcational_discretized_form):
 //   F_n = -(mu k_n / 2) sum_{T=0}^{min(W_f(n), step)} w_n^T D_n^{step - T},  k_n = pi n / L_f.
-// One warp per (mode, scenario); lanes stride the lags; the ring is mode-major so the lanes read contiguous slots.
+// One warp per (mode, scenario); lanes stride the lags, four lags a lane in flight (the loop is latency-bound:
+// windows run to ~2000 lags); the ring is mode-major so the lanes read contiguous slots.
 __global__ void __launch_bounds__(kThreads) k_modeconv(StepArgs a_) {
     StepArgs a = a_;
     apply_dyn(a);
@@ -213,6 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_modeconv(StepArgs a_) {
     const double *w = a.w + mo.w_off;
     const int slot0 = (int)(a.step % R);
     double re = 0.0, im = 0.0;
+#pragma unroll 4
     for (int T = lane; T <= Tmax; T += 32) {
         int s = slot0 - T;
         if (s < 0) s += R;
@@ -301,10 +303,17 @@ __global__ void __launch_bounds__(kThreads) k_ifft_assemble(StepArgs a_, double 
 // Threads of the interaction kernel for a batch width BT: CW consumer warps (16 while the accumulators are small
 // enough for 120 registers, which hides more shared-memory and pipe latency) plus one producer warp; RV values per
 // flush round keep the reduction buffer at 16 KB.
-template <int PREC, int BT, int PASS> struct InterShape {
-    // the tensor-core consumers (BF16, 8 scenarios) keep four accumulators per thread: 16 warps on the receiver
-    // side; on the source side, where a stage holds few pieces, 8 (fewer warps at each barrier)
+// The default count per (precision, batch width, pass); ALT: the other count (8 <-> 16) is compiled too, for the
+// autotuner (where 16 warps keep every instantiation within 120 registers: batch widths up to 4, and the BF16
+// tensor-core consumers).
+template <int PREC, int BT, int PASS> struct InterDefault {
+    // the tensor-core consumers (BF16, 8 scenarios): 16 warps on the receiver side; on the source side, where a
+    // stage holds few pieces, 8
     static constexpr int CW = BT <= 2 || (PREC == kPrecBF16 && BT == 8 && PASS == 2) ? 16 : 8;
+    static constexpr bool ALT = BT <= 4 || PREC == kPrecBF16;
+};
+template <int PREC, int BT, int PASS, int CWv> struct InterShape {
+    static constexpr int CW = CWv;
     static constexpr int NC = CW * 32;
     static constexpr int NT = NC + 32;
     static constexpr int RV = CW == 8 ? 8 : 4;
@@ -333,11 +342,11 @@ struct StageInfo {
 // Dynamic shared memory of the interaction kernel for batch width BT, in bytes from the start: the stages, their
 // descriptors, the flush buffer and the full/empty mbarriers.  The kernel and its launcher both use this, and the
 // kernel checks the end against the size it was launched with.
-template <int PREC, int BT, int PASS> struct InterLayout {
+template <int PREC, int BT, int PASS, int CWv> struct InterLayout {
     static constexpr size_t info = (size_t)kStages * kStageBytes;
     static constexpr size_t red = info + kStages * sizeof(StageInfo);
     static constexpr size_t bars =
-        red + (size_t)InterShape<PREC, BT, PASS>::NC * InterShape<PREC, BT, PASS>::RV * sizeof(double);
+        red + (size_t)InterShape<PREC, BT, PASS, CWv>::NC * InterShape<PREC, BT, PASS, CWv>::RV * sizeof(double);
     static constexpr size_t total = bars + (2 * kStages + 1) * sizeof(uint64_t);   // full, empty, consumers
     static_assert(sizeof(StageInfo) % 8 == 0 && red % 8 == 0 && bars % 8 == 0, "8-byte alignment");
     static_assert(total <= 227 * 1024, "shared memory per CTA");
@@ -628,6 +637,35 @@ template <int PREC, int BT> struct VecWidth {
     static constexpr int value = SB == 2 ? (BT <= 2 ? 8 : 4) : (BT <= 4 ? 2 : 1);
 };
 
+// The chunk rotation of 2-byte operator rows (chunk_at) with its row-length terms computed once: rot(r) is row r's
+// rotation, at(c, rot) the stored chunk of logical chunk c.  Same mapping as chunk_at.
+struct ChunkRot {
+    int nch, sh, gm;
+    __device__ __forceinline__ explicit ChunkRot(int n) : nch(n) {
+        int g = n & -n;
+        if (g > 8) g = 8;
+        sh = g == 8 ? 0 : g == 4 ? 1 : g == 2 ? 2 : 3;
+        gm = g - 1;
+    }
+    __device__ __forceinline__ int rot(int r) const { return (r >> sh) & gm; }
+    __device__ __forceinline__ int at(int c, int rt) const {
+        const int q = c + rt;
+        return q >= nch ? q - nch : q;
+    }
+};
+
+// Element offset of vector uu (VE elements) of a row with rotation rt: 2-byte operator rows are stored
+// chunk-rotated, 8-byte ones as they are.
+template <int PREC, int VE>
+__device__ __forceinline__ int vec_off(const ChunkRot &cr, int uu, int rt) {
+    if constexpr (PREC == kPrecBF16 || PREC == kPrecFP16) {
+        if constexpr (VE == 8) return cr.at(uu, rt) * 8;
+        else return cr.at(uu >> 1, rt) * 8 + (uu & 1) * 4;
+    } else {
+        return uu * VE;
+    }
+}
+
 // Multiply-accumulate of one converted operator value with one coefficient.
 __device__ __forceinline__ void emac(double &acc, double v, double c) { acc = fma(v, c, acc); }
 __device__ __forceinline__ void emac(DF &acc, float2 v, float2 c) { df_add(acc, df_prod(v, c)); }
@@ -713,13 +751,18 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
     int ts = 0;                                            // pass 2: the stage's index within its task
     bool act = true;
     float2 acc[4];
-    float dst[4], dsl[4];                                  // products with the hi and the lo parts of the operand
+    // products with the hi and the lo parts of the operand, in two sets that alternate from piece to piece (four
+    // independent MMA chains per warp)
+    float dst[4], dsl[4], dst2[4], dsl2[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         acc[v] = make_float2(0.f, 0.f);
         dst[v] = 0.f;
         dsl[v] = 0.f;
+        dst2[v] = 0.f;
+        dsl2[v] = 0.f;
     }
+    bool alt = false;
     // Warps run through the stages on their own: each waits for a stage, takes its share of the pieces (dealt from a
     // start that rotates with the stage, so that no warp always gets the extra ones) and releases the stage; they
     // meet only to add the groups of a finished task.  On the receiver side the rotation follows the stage's index
@@ -734,6 +777,7 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
         unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
         if constexpr (PASS == 1) {
             const int q2 = pad_row(si.q, kPrecBF16);
+            const ChunkRot cr(q2 / 8);
             int u = 0;
             for (int m = 0; m < si.n; ++m) {
                 const StageItem &it = si.it[m];
@@ -747,9 +791,13 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
                     // four independent accumulator chains: (hi, lo) parts of x times (even, odd) K steps
                     float d[4][4] = {};
                     const int arow = min(r0 + (mi & 1) * 8 + rr, rows - 1);     // rows past the run: not read
+                    const int art = cr.rot(arow);
                     for (int K0 = 0, kk = 0; K0 < q2; K0 += 16, kk ^= 1) {
                         uint32_t af[4];
-                        ldsm_x4(af, V + (int64_t)arow * q2 + K0 + (mi >> 1) * 8);
+                        // chunk K0 / 8 (+1) of the row, rotated; past the row (a last piece of 8 columns) its last
+                        // chunk, against B rows and A columns masked to zero
+                        const int ach = min(K0 / 8 + (mi >> 1), cr.nch - 1);
+                        ldsm_x4(af, V + (int64_t)arow * q2 + cr.at(ach, art) * 8);
                         if (q2 - K0 < 16) mask_a_k(af, tg, q2 - K0);
                         // B: matrices (high, K0..K0+7), (high, K0+8..), (low, K0..), (low, K0+8..); columns past
                         // the slice (a last piece of 8) read its last row, against A columns masked to zero
@@ -800,6 +848,10 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
             }
             int u = 0;
             const int i0 = tile * 16;
+            // the warp's receiver chunk (+1 for matrices 1 and 3) in every row; past the row (receivers >= p2) its
+            // last chunk: those receivers' sums are never written
+            const ChunkRot cr2(p2 / 8);
+            const int ach2 = min(i0 / 8 + (mi & 1), cr2.nch - 1);
             for (int m = 0; m < si.n; ++m) {
                 const StageItem &it = si.it[m];
                 const int rows = it.k < 0 ? it.i1 - it.i0 : it.k;
@@ -812,15 +864,21 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
                         const int k0 = pc * 16;
                         uint32_t af[4];
                         const int arow = min(k0 + (mi >> 1) * 8 + rr, rows - 1);   // rows past the unit: not read
-                        ldsm_x4_t(af, S + (int64_t)arow * p2 + i0 + (mi & 1) * 8);
+                        ldsm_x4_t(af, S + (int64_t)arow * p2 + cr2.at(ach2, cr2.rot(arow)) * 8);
                         if (rows - k0 < 16) mask_a_k(af, tg, rows - k0);
                         // B: (high, k0..k0+7), (high, k0+8..), (low, k0..), (low, k0+8..); rows past the unit read
                         // its last row, against A entries masked to zero
                         uint32_t bf[4];
                         const int brow = min(k0 + (mi & 1) * 8 + rr, rows - 1);
                         ldsm_x4_t(bf, br + brow * 32 + (mi >> 1) * 16);
-                        mma_bf16(dst, af, bf[0], bf[1]);
-                        mma_bf16(dsl, af, bf[2], bf[3]);
+                        if (alt) {
+                            mma_bf16(dst2, af, bf[0], bf[1]);
+                            mma_bf16(dsl2, af, bf[2], bf[3]);
+                        } else {
+                            mma_bf16(dst, af, bf[0], bf[1]);
+                            mma_bf16(dsl, af, bf[2], bf[3]);
+                        }
+                        alt = !alt;
                     }
                 u += pieces;
             }
@@ -828,10 +886,13 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
             ++ts;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {                      // compensated accumulation, once per stage
-                PTHalf<__nv_bfloat16>::kahan(acc[v], dst[v] + dsl[v]);
+                PTHalf<__nv_bfloat16>::kahan(acc[v], (dst[v] + dsl[v]) + (dst2[v] + dsl2[v]));
                 dst[v] = 0.f;
                 dsl[v] = 0.f;
+                dst2[v] = 0.f;
+                dsl2[v] = 0.f;
             }
+            alt = false;
             if (flush) {
                 // D fragment: v = 0, 1 -> receiver row g, scenario 2 tg + v; v = 2, 3 -> row g + 8.  Groups added in
                 // a fixed order by the thread that owns each (receiver, scenario); a second meeting frees red.
@@ -858,12 +919,12 @@ __device__ __forceinline__ void consume_mma(const StepArgs &a, StageInfo *info, 
 }
 
 // [tensor-core consumers: end]
-template <int PREC, int BT, int PASS>
-__global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interaction(StepArgs a_) {
+template <int PREC, int BT, int PASS, int CWv>
+__global__ void __launch_bounds__(InterShape<PREC, BT, PASS, CWv>::NT, 1) k_interaction(StepArgs a_) {
     StepArgs a = a_;
     apply_dyn(a);
-    constexpr int CW = InterShape<PREC, BT, PASS>::CW, NC = InterShape<PREC, BT, PASS>::NC;
-    constexpr int RV = InterShape<PREC, BT, PASS>::RV;
+    constexpr int CW = InterShape<PREC, BT, PASS, CWv>::CW, NC = InterShape<PREC, BT, PASS, CWv>::NC;
+    constexpr int RV = InterShape<PREC, BT, PASS, CWv>::RV;
     using T = PT<PREC>;
     using S = typename T::S;
     using X = typename T::X;
@@ -879,7 +940,7 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
     constexpr bool kBulkX = PREC != kPrecDF64;
     constexpr int XA = 16 / XB;                               // history elements per 16 bytes
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    using LY = InterLayout<PREC, BT, PASS>;
+    using LY = InterLayout<PREC, BT, PASS, CWv>;
     unsigned char *stage_mem = smem_raw;                                            // kStages x kStageBytes
     StageInfo *info = reinterpret_cast<StageInfo *>(smem_raw + LY::info);
     double *red = reinterpret_cast<double *>(smem_raw + LY::red);                  // [NC][RV]
@@ -1167,6 +1228,7 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
             const int wr = (warp + g) % CW;                        // the warp's place in this stage
             const int sl = lane % L, rw = lane / L, slotA = wr * subs + rw;
             const int rot = (rw * L) % qv;
+            const ChunkRot cr1(q2 * (int)sizeof(S) / 16);
             // sweeps that reach at least one of the warp's row slots (uniform over the warp)
             const int trips = nz > wr * subs ? (nz - wr * subs + SA - 1) / SA : 0;
             int k = 0, zstart = 0;
@@ -1188,11 +1250,12 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                     const X *x = reinterpret_cast<const X *>(bx + itm.x_off);
                     zrow = reinterpret_cast<const int32_t *>(bx + itm.map_off)[f - zstart];
                     if (PREC == kPrecFP16) sc = a.zscale[itm.map + (f - zstart)];
+                    const int rt1 = cr1.rot(f - zstart);
                     for (int i = sl; i < qv; i += L) {
                         int uu = i + rot;
                         if (uu >= qv) uu -= qv;
                         E v[VE];
-                        VecLoad<PREC, VE>::ld(vr + uu * VE, v);
+                        VecLoad<PREC, VE>::ld(vr + vec_off<PREC, VE>(cr1, uu, rt1), v);
 #pragma unroll
                         for (int e = 0; e < VE; ++e)
 #pragma unroll
@@ -1263,6 +1326,7 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                         }
             }
             const unsigned char *base = stage_mem + (size_t)slot * kStageBytes;
+            const ChunkRot cr2(p2 * (int)sizeof(S) / 16);
             if (grp < G) {
                 const int nr = si.n_rows;
                 const int gpw = P >= 32 ? 1 : 32 / P;              // groups per warp
@@ -1276,6 +1340,7 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                     const StageItem &itm = si.it[k];
                     const int r = f - rstart;
                     const S *rowp = reinterpret_cast<const S *>(base + itm.data_off) + (int64_t)r * p2;
+                    const int rt2 = cr2.rot(r);
                     E cv[BT];
                     if (itm.k < 0) {
                         const X *x = reinterpret_cast<const X *>(base + itm.x_off);
@@ -1298,7 +1363,7 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS>::NT, 1) k_interacti
                             const int uu = vec + s * P;
                             if (uu * VE < p2) {
                                 E v[VE];
-                                VecLoad<PREC, VE>::ld(rowp + uu * VE, v);
+                                VecLoad<PREC, VE>::ld(rowp + vec_off<PREC, VE>(cr2, uu, rt2), v);
 #pragma unroll
                                 for (int e = 0; e < VE; ++e)
 #pragma unroll
@@ -1590,18 +1655,39 @@ __global__ void k_wait_probe(StepArgs a) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
 }
 
-template <int PREC, int BT, int PASS>
-cudaError_t launch_interaction_pass(const StepArgs &a, cudaStream_t s) {
+template <int PREC, int BT, int PASS, int CWv>
+cudaError_t launch_interaction_cw(const StepArgs &a, cudaStream_t s) {
     // a captured step does not know its task counts at launch: every SM, CTAs without a task return
     const int n = a.dyn ? a.n_sms : PASS == 1 ? a.n_ztasks_active : a.n_tasks_active;
     if (n <= 0) return cudaSuccess;
-    const size_t smem = InterLayout<PREC, BT, PASS>::total;
-    cudaError_t e = cudaFuncSetAttribute(k_interaction<PREC, BT, PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const size_t smem = InterLayout<PREC, BT, PASS, CWv>::total;
+    cudaError_t e = cudaFuncSetAttribute(k_interaction<PREC, BT, PASS, CWv>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = n < a.n_sms ? n : a.n_sms;
-    k_interaction<PREC, BT, PASS><<<grid, InterShape<PREC, BT, PASS>::NT, smem, s>>>(a);
+    k_interaction<PREC, BT, PASS, CWv><<<grid, InterShape<PREC, BT, PASS, CWv>::NT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// The pass with the scenario's consumer warp count (a.cw[pass - 1]; 0 or a count not compiled: the default).
+template <int PREC, int BT, int PASS>
+cudaError_t launch_interaction_pass(const StepArgs &a, cudaStream_t s) {
+    using D = InterDefault<PREC, BT, PASS>;
+    constexpr int OTHER = D::CW == 8 ? 16 : 8;
+    const int want = a.cw[PASS - 1];
+    if constexpr (D::ALT) {
+        if (want == OTHER) return launch_interaction_cw<PREC, BT, PASS, OTHER>(a, s);
+    }
+    return launch_interaction_cw<PREC, BT, PASS, D::CW>(a, s);
+}
+
+template <int PREC, int BT, int PASS>
+int interaction_options_pass(int *cw) {
+    using D = InterDefault<PREC, BT, PASS>;
+    cw[0] = D::CW;
+    if (!D::ALT) return 1;
+    cw[1] = D::CW == 8 ? 16 : 8;
+    return 2;
 }
 
 // pass 1: z = V^T x of the far slices (source side); pass 2: the receivers' sums.  Pass 2 reads what pass 1 wrote,
@@ -1609,6 +1695,19 @@ cudaError_t launch_interaction_pass(const StepArgs &a, cudaStream_t s) {
 template <int PREC, int BT>
 cudaError_t launch_interaction_bt(const StepArgs &a, int pass, cudaStream_t s) {
     return pass == 1 ? launch_interaction_pass<PREC, BT, 1>(a, s) : launch_interaction_pass<PREC, BT, 2>(a, s);
+}
+
+template <int PREC, int BT>
+int interaction_options_bt(int pass, int *cw) {
+    return pass == 1 ? interaction_options_pass<PREC, BT, 1>(cw) : interaction_options_pass<PREC, BT, 2>(cw);
+}
+
+template <int PREC>
+int interaction_options_prec(int batch, int pass, int *cw) {
+    if (batch > 4) return interaction_options_bt<PREC, 8>(pass, cw);
+    if (batch > 2) return interaction_options_bt<PREC, 4>(pass, cw);
+    if (batch > 1) return interaction_options_bt<PREC, 2>(pass, cw);
+    return interaction_options_bt<PREC, 1>(pass, cw);
 }
 
 template <int PREC>
@@ -1668,6 +1767,15 @@ cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s) {
     dim3 grid((a.n_modes + kThreads / 32 - 1) / (kThreads / 32), a.B);
     k_modeconv<<<grid, kThreads, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+int interaction_options(int prec, int batch, int pass, int *cw) {
+    switch (prec) {
+        case kPrecDF64: return interaction_options_prec<kPrecDF64>(batch, pass, cw);
+        case kPrecBF16: return interaction_options_prec<kPrecBF16>(batch, pass, cw);
+        case kPrecFP16: return interaction_options_prec<kPrecFP16>(batch, pass, cw);
+        default: return interaction_options_prec<kPrecFP64>(batch, pass, cw);
+    }
 }
 
 cudaError_t launch_interaction(const StepArgs &a, int pass, cudaStream_t s) {

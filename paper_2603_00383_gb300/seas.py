@@ -31,7 +31,7 @@ EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_
             "seas_scenario_admit", "seas_scenario_retire", "seas_scenario_member_step", "seas_ctx_get_memory",
             "seas_integrator_create", "seas_integrator_step", "seas_integrator_state", "seas_destroy_integrator",
             "seas_push_slip_rate_steps", "seas_integrator_step_gamma", "seas_integrator_step_adaptive",
-            "seas_scenario_graph_create", "seas_scenario_graph_step", "seas_build_hmatrix_part"]
+            "seas_scenario_graph_create", "seas_scenario_graph_step", "seas_build_hmatrix_part", "seas_scenario_autotune"]
 
 
 class SeasError(RuntimeError):
@@ -75,6 +75,11 @@ class seas_friction(C.Structure):
 class seas_timing(C.Structure):
     _fields_ = [("launches", C.c_int64 * 7), ("ms", C.c_double * 7), ("interaction_bytes", C.c_int64),
                 ("steps", C.c_int64)]
+
+
+class seas_tune(C.Structure):
+    _fields_ = [("consumer_warps", C.c_int * 2), ("candidates", (C.c_int * 2) * 2), ("ms", (C.c_double * 2) * 2),
+                ("from_cache", C.c_int)]
 
 
 KERNEL_CLASSES = ["push", "fft_forward", "modeconv", "interaction", "reduce", "ifft_assemble", "interaction_source"]
@@ -127,6 +132,7 @@ _SIGS = {
     "seas_scenario_graph_create": ([_VP, _VP, _VP, _VP], C.c_int),
     "seas_scenario_graph_step": ([_VP], C.c_int),
     "seas_build_hmatrix_part": ([_VP, C.POINTER(seas_hparams), _VP, C.c_int, _PP, C.POINTER(seas_op_stats)], C.c_int),
+    "seas_scenario_autotune": ([_VP, C.c_char_p, C.c_int, C.POINTER(seas_tune)], C.c_int),
 }
 
 
@@ -471,6 +477,19 @@ def seas_scenario_set_wait_limit(scn: Handle, seconds: float):
 
 def seas_scenario_probe_wait(scn: Handle):
     _check(lib().seas_scenario_probe_wait(scn.ptr))
+
+
+def seas_scenario_autotune(scn: Handle, cache_path=None, reps: int = 5) -> dict:
+    """Consumer warps per interaction pass, picked by timing (seas_scenario_autotune); returns the choice, the
+    candidates and their median launch times per pass (source, receiver)."""
+    t = seas_tune()
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(lib().seas_scenario_autotune(scn.ptr, path, int(reps), C.byref(t)))
+    passes = ("source", "receiver")
+    return {"consumer_warps": {passes[p]: t.consumer_warps[p] for p in range(2)},
+            "ms": {passes[p]: {int(t.candidates[p][k]): t.ms[p][k] for k in range(2) if t.candidates[p][k]}
+                   for p in range(2)},
+            "from_cache": bool(t.from_cache)}
 
 
 def seas_scenario_check(scn: Handle):
