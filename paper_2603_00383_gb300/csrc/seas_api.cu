@@ -240,6 +240,9 @@ struct seas_scn {
     DArr<int> counter_err;           // [0], [2]: task counters of the two interaction passes, [1]: device error word
     uint64_t wait_ns = 2000000000ull;   // bound of one device wait (seas_scenario_set_wait_limit)
     int cw[2] = {0, 0};              // consumer warps of the interaction passes (seas_scenario_autotune; 0: default)
+    // side stream of the self-term convolution, forked from and joined back to the step's stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     int64_t ring_stride = 0;
     DArr<FaultDev> faults;           // fault table with spectral-ring offsets for this batch size
     int64_t dring_len = 0;
@@ -251,6 +254,9 @@ struct seas_scn {
     size_t ev_used = 0;
     seas_timing acc{};
     ~seas_scn() {
+        if (fork_ev) cudaEventDestroy(fork_ev);
+        if (join_ev) cudaEventDestroy(join_ev);
+        if (side) cudaStreamDestroy(side);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         for (cudaEvent_t e : dyn_ev)
             if (e) cudaEventDestroy(e);
@@ -1432,6 +1438,9 @@ seas_status scenario_alloc(seas_op *op, int batch, std::unique_ptr<seas_scn> &s)
         SEAS_TRY(s->zbuf.zero(c->stream));
     }
     SEAS_TRY(s->counter_err.alloc(c, 4));
+    CUDA_TRY(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming));
     SEAS_TRY(s->counter_err.zero(c->stream));
     SEAS_TRY(s->slip.alloc(c, (size_t)BN));
     SEAS_TRY(s->slip_prev.alloc(c, (size_t)BN));
@@ -1618,6 +1627,23 @@ extern "C" seas_status seas_push_slip_rate_steps(seas_scn *s, const double *V, c
     return SEAS_OK;
 }
 
+// The step's kernels after the push.  The self-term mode convolution depends on neither interaction pass, and its
+// blocks use no shared memory, so they run beside the persistent interaction CTAs: it goes to the scenario's side
+// stream between a fork event on `st` and a join before the assembly, which needs both.
+static cudaError_t launch_step_kernels(seas_scn &s, const StepArgs &a, double *tau, double *parts, cudaStream_t st) {
+    cudaError_t e = cudaEventRecord(s.fork_ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s.side, s.fork_ev, 0);
+    if (e == cudaSuccess) e = launch_modeconv(a, s.side);
+    if (e == cudaSuccess) e = cudaEventRecord(s.join_ev, s.side);
+    if (e == cudaSuccess) e = launch_interaction(a, 1, st);
+    if (e == cudaSuccess) e = launch_interaction(a, 2, st);
+    if (e == cudaSuccess) e = launch_reduce(a, st);
+    if (e == cudaSuccess) e = launch_static_tail(a, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s.join_ev, 0);
+    if (e == cudaSuccess) e = launch_ifft_assemble(a, tau, parts, st);
+    return e;
+}
+
 extern "C" seas_status seas_stress_step(seas_scn *s, double *tau, double *sigma_n, double *parts, int mem) {
     if (!s || !tau) return fail(SEAS_EINVAL, "NULL argument");
     if (mem != SEAS_MEM_HOST && mem != SEAS_MEM_DEVICE) return fail(SEAS_EINVAL, "mem must be HOST or DEVICE");
@@ -1629,14 +1655,19 @@ extern "C" seas_status seas_stress_step(seas_scn *s, double *tau, double *sigma_
     StepArgs a = step_args(*s, s->n - 1);
     double *dtau = mem == SEAS_MEM_DEVICE ? tau : s->d_tau.p;
     double *dparts = parts ? (mem == SEAS_MEM_DEVICE ? parts : s->d_parts.p) : nullptr;
-    SEAS_TRY(timed(*s, 2, [&] { return launch_modeconv(a, c->stream); }));
-    SEAS_TRY(timed(*s, 6, [&] { return launch_interaction(a, 1, c->stream); }));
-    SEAS_TRY(timed(*s, 3, [&] { return launch_interaction(a, 2, c->stream); }));
-    SEAS_TRY(timed(*s, 4, [&] {
-        const cudaError_t e = launch_reduce(a, c->stream);
-        return e != cudaSuccess ? e : launch_static_tail(a, c->stream);
-    }));
-    SEAS_TRY(timed(*s, 5, [&] { return launch_ifft_assemble(a, dtau, dparts, c->stream); }));
+    if (!s->timing) {
+        CUDA_TRY(launch_step_kernels(*s, a, dtau, dparts, c->stream));
+    } else {
+        // per-kernel events: the kernels one after another on the step's stream
+        SEAS_TRY(timed(*s, 2, [&] { return launch_modeconv(a, c->stream); }));
+        SEAS_TRY(timed(*s, 6, [&] { return launch_interaction(a, 1, c->stream); }));
+        SEAS_TRY(timed(*s, 3, [&] { return launch_interaction(a, 2, c->stream); }));
+        SEAS_TRY(timed(*s, 4, [&] {
+            const cudaError_t e = launch_reduce(a, c->stream);
+            return e != cudaSuccess ? e : launch_static_tail(a, c->stream);
+        }));
+        SEAS_TRY(timed(*s, 5, [&] { return launch_ifft_assemble(a, dtau, dparts, c->stream); }));
+    }
     if (s->timing) {
         int64_t b = 0;
         SEAS_TRY(seas_op_step_bytes(&op, s->n - 1, &b));
@@ -1676,12 +1707,7 @@ extern "C" seas_status seas_stress_step_static(seas_scn *s, double *tau, double 
     StepArgs a = step_args(*s, s->n - 1);
     a.partial = scratch;
     a.fint = scratch + op.n_partial * s->B;
-    CUDA_TRY(launch_modeconv(a, c->stream));
-    CUDA_TRY(launch_interaction(a, 1, c->stream));
-    CUDA_TRY(launch_interaction(a, 2, c->stream));
-    CUDA_TRY(launch_reduce(a, c->stream));
-    CUDA_TRY(launch_static_tail(a, c->stream));
-    CUDA_TRY(launch_ifft_assemble(a, tau, parts, c->stream));
+    CUDA_TRY(launch_step_kernels(*s, a, tau, parts, c->stream));
     return SEAS_OK;
 }
 
@@ -1905,12 +1931,7 @@ extern "C" seas_status seas_scenario_graph_create(seas_scn *s, const double *V, 
     CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     cudaError_t e = launch_push(a, V, nullptr, 0, 1, 1, st);
     if (e == cudaSuccess) e = launch_fft_forward(a, st);
-    if (e == cudaSuccess) e = launch_modeconv(a, st);
-    if (e == cudaSuccess) e = launch_interaction(a, 1, st);
-    if (e == cudaSuccess) e = launch_interaction(a, 2, st);
-    if (e == cudaSuccess) e = launch_reduce(a, st);
-    if (e == cudaSuccess) e = launch_static_tail(a, st);
-    if (e == cudaSuccess) e = launch_ifft_assemble(a, tau, parts, st);
+    if (e == cudaSuccess) e = launch_step_kernels(*s, a, tau, parts, st);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(st, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {

@@ -1222,7 +1222,9 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS, CWv>::NT, 1) k_inte
             const int nz = sx.n_rows;
             const int qv = pad_row(sx.q, PREC) / VE;
             const int q2 = qv * VE;
-            const int q4 = PREC == kPrecDF64 ? 0 : qv >> 2;
+            // lanes per row: each lane sums at least four vectors (FP64: eight, since every add of the shuffle tree
+            // costs an FP64 pipe slot like a product: 0.91 -> 0.83 ms for the six-fault source pass)
+            const int q4 = PREC == kPrecDF64 ? 0 : PREC == kPrecFP64 ? qv >> 3 : qv >> 2;
             const int L = q4 >= 32 ? 32 : q4 >= 16 ? 16 : q4 >= 8 ? 8 : q4 >= 4 ? 4 : q4 >= 2 ? 2 : 1;
             const int subs = 32 / L, SA = CW * subs;
             const int wr = (warp + g) % CW;                        // the warp's place in this stage
