@@ -475,6 +475,28 @@ def run_ours(args, w, start, K, W):
                               "copy of the scenario taken at the window's start (the headline run records none)")
     if not torch.equal(tauB, tau):
         log("warning: kernel-timing pass differs from the headline run")
+    # the same window replayed as a captured CUDA graph: one graph launch per step (the step's seven kernels, the
+    # self-term convolution on its forked branch), the slip rate copied into the graph's input buffer each step
+    sG = seas.seas_scenario_load(s.op, ckpt)
+    seas.seas_scenario_autotune(sG, tune_cache, reps=1)
+    vG = torch.zeros(w.N, dtype=torch.float64, device=device)
+    tG = torch.zeros(w.N, dtype=torch.float64, device=device)
+    seas.seas_scenario_graph_create(sG, vG, tG)
+    evG = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize(device)
+    for k in range(K):
+        evG[k][0].record(stream)
+        vG.copy_(Vd[start + k])
+        seas.seas_scenario_graph_step(sG)
+        evG[k][1].record(stream)
+    torch.cuda.synchronize(device)
+    seas.seas_scenario_check(sG)
+    perG = np.array([a_.elapsed_time(b_) for a_, b_ in evG])
+    graph = {"ms_per_step": float(perG.mean()), "p50_ms": float(np.percentile(perG, 50)),
+             "value": job_rate(w.N * K, world, float(perG.sum()) / 1e3), "unit": METRIC,
+             "last_step_equal": bool(torch.equal(tG, tau[K - 1]))}
+    seas.seas_destroy_scn(sG)
+    log(f"graph replay: {graph['ms_per_step']:.3f} ms per step (eager {total_ms / K:.3f})")
     if args.dump_step_bytes and rank == 0:
         with open(args.dump_step_bytes, "w") as fh:
             json.dump({"precision": args.precision, "steps": w.steps,
@@ -611,7 +633,7 @@ def run_ours(args, w, start, K, W):
                     "n_blocks_far", "n_blocks_near", "compression_ratio", "bytes_interaction", "mean_rank",
                     "max_rank", "build_seconds", "n_tasks")},
                 "vs_plain_fp64_gpu": plain, "variants": variants, "batched": batched, "static_tail": tail, "e2e": e2e,
-                "served": served, "ensemble_8x8": ensemble,
+                "served": served, "ensemble_8x8": ensemble, "graph": graph,
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
                 "autotune": {"consumer_warps": s.tune["consumer_warps"], "median_launch_ms": s.tune["ms"],
                              "by": "seas_scenario_autotune (per pass, every task active, 5 launches each)"},
