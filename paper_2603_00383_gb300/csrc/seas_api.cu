@@ -1438,7 +1438,11 @@ seas_status scenario_alloc(seas_op *op, int batch, std::unique_ptr<seas_scn> &s)
         SEAS_TRY(s->zbuf.zero(c->stream));
     }
     SEAS_TRY(s->counter_err.alloc(c, 4));
-    CUDA_TRY(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+    {
+        int least = 0, greatest = 0;                  // numerically greatest = lowest priority
+        CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CUDA_TRY(cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, least));
+    }
     CUDA_TRY(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming));
     SEAS_TRY(s->counter_err.zero(c->stream));
@@ -1631,11 +1635,13 @@ extern "C" seas_status seas_push_slip_rate_steps(seas_scn *s, const double *V, c
 // blocks use no shared memory, so they run beside the persistent interaction CTAs: it goes to the scenario's side
 // stream between a fork event on `st` and a join before the assembly, which needs both.
 static cudaError_t launch_step_kernels(seas_scn &s, const StepArgs &a, double *tau, double *parts, cudaStream_t st) {
+    // the source pass is enqueued first, so the persistent interaction CTAs take their SMs first and the
+    // convolution's blocks fill what is left beside them (the side stream has the lowest priority)
     cudaError_t e = cudaEventRecord(s.fork_ev, st);
+    if (e == cudaSuccess) e = launch_interaction(a, 1, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s.side, s.fork_ev, 0);
     if (e == cudaSuccess) e = launch_modeconv(a, s.side);
     if (e == cudaSuccess) e = cudaEventRecord(s.join_ev, s.side);
-    if (e == cudaSuccess) e = launch_interaction(a, 1, st);
     if (e == cudaSuccess) e = launch_interaction(a, 2, st);
     if (e == cudaSuccess) e = launch_reduce(a, st);
     if (e == cudaSuccess) e = launch_static_tail(a, st);

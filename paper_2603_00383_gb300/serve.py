@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import collections
 import math
+import os
 import time
 from dataclasses import dataclass, field
 
@@ -204,10 +205,15 @@ class GpuBackend:
     """Carries out a Scheduler's actions through the C ABI: one context (with its own torch stream) and operator per
     resident geometry, one scenario handle of ``batch`` members per group."""
 
-    def __init__(self, geometries, batch: int, device: int = 0, precision: int = 0, record: bool = False):
+    def __init__(self, geometries, batch: int, device: int = 0, precision: int = 0, record: bool = False,
+                 tune: bool = True):
+        import tempfile
         import torch
         from . import seas
         self.torch, self.seas = torch, seas
+        # the interaction's consumer warps per pass, tuned once per operator when it is built (off the serving clock)
+        # and applied to each of its groups from this cache file
+        self.tune_cache = os.path.join(tempfile.mkdtemp(prefix="seas_serve_tune_"), "choices.txt") if tune else None
         self.geoms = geometries
         self.batch = batch
         self.device = device
@@ -228,6 +234,10 @@ class GpuBackend:
         ctx = seas.seas_create(self.device, 0, st)
         net = seas.seas_build_network(ctx, w.faults, w.mu, w.cs, w.cp, w.beta)
         op, stats = seas.seas_build_hmatrix(net, dict(w.hparams, precision=self.precision))
+        if self.tune_cache:
+            probe = seas.seas_scenario_create(op, self.batch)
+            seas.seas_scenario_autotune(probe, self.tune_cache, reps=3)
+            seas.seas_destroy_scn(probe)
         self.build_seconds[g] = time.perf_counter() - t0
         self.ctx[g], self.net[g], self.op[g], self.stream[g] = ctx, net, op, st
 
@@ -247,6 +257,8 @@ class GpuBackend:
         torch, seas = self.torch, self.seas
         w = self.geoms[g]
         scn = seas.seas_scenario_create(self.op[g], self.batch)
+        if self.tune_cache:
+            seas.seas_scenario_autotune(scn, self.tune_cache, reps=1)          # the operator's choice, cached
         for m in range(self.batch):
             seas.seas_scenario_retire(scn, m)
         with torch.cuda.stream(self.stream[g]):
