@@ -202,9 +202,11 @@ __global__ void __launch_bounds__(kThreads) k_fft_forward(StepArgs a_) {
 __global__ void __launch_bounds__(kThreads) k_modeconv(StepArgs a_) {
     StepArgs a = a_;
     apply_dyn(a);
-    const int md = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    const int b = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // batches: one block per mode, one warp per scenario, so the warps read the mode's weights together (L1 hits
+    // after the first); one scenario: eight modes per block
+    const int md = a.B > 1 ? blockIdx.x : blockIdx.x * (kThreads / 32) + warp;
+    const int b = a.B > 1 ? warp : 0;
     if (md >= a.n_modes) return;
     const ModeDev mo = a.modes[md];
     const FaultDev fd = a.faults[mo.fault];
@@ -1844,8 +1846,8 @@ cudaError_t launch_fft_forward(const StepArgs &a, cudaStream_t s) {
 
 cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s) {
     if (a.n_modes == 0) return cudaSuccess;
-    dim3 grid((a.n_modes + kThreads / 32 - 1) / (kThreads / 32), a.B);
-    k_modeconv<<<grid, kThreads, 0, s>>>(a);
+    if (a.B > 1) k_modeconv<<<a.n_modes, 32 * a.B, 0, s>>>(a);
+    else k_modeconv<<<(a.n_modes + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
