@@ -25,7 +25,9 @@ What it computes, step by step, in plain FP64 NumPy (no blocking, no compression
 
 Windows (optional, off by default): mode-dependent self windows W_f(n) = ceil(T_end(n)/dt) with
 T_end(n) = eta_w L_f / c_s * Lcal(n) (Eq. mode_dependent_truncation) and per fault-pair interaction windows ending at
-ceil((1 + eta_Tmax) T_max / dt) (Sec. 2.3.2, "Truncation of elastodynamic time-window").  Static tail (flag 4,
+ceil((1 + eta_Tmax) T_max / dt) (Sec. 2.3.2, "Truncation of elastodynamic time-window"), or, with the
+cluster-level end truncation of Sec. 4.3 (flag 16), the same criterion per block of the H-matrix partition (the
+fault-wise cluster trees and the dual traversal restated in cluster_tree / hmatrix_blocks).  Static tail (flag 4,
 not in the paper, off by default): the history a window drops is added back as an elastostatic response, per mode
 c_n D_n^{m - W - 1} with c_n = (2/pi) Si(n pi) - sum_{T <= W} w_n^T, per fault pair A^static delta^{m - T_last - 1}.
 
@@ -184,15 +186,26 @@ def static_slice(net: Network, rows=None, cols=None) -> np.ndarray:
     return np.where(same, 0.0, A)
 
 
+def _element_hi(net: Network, pair_hi, rows=None) -> np.ndarray:
+    """Window ends per element pair [rows][N]: ``pair_hi`` given per fault pair [F][F] is broadcast to the elements
+    of each pair; given per element pair [N][N] (cluster-level windows) its rows are taken as they are."""
+    hi = np.asarray(pair_hi)
+    rows = np.arange(net.N) if rows is None else np.asarray(rows)
+    if hi.shape == (net.N, net.N):
+        return hi[rows]
+    fo = net.fault_of
+    return hi[fo[rows]][:, fo]
+
+
 def interaction_history(net: Network, V: np.ndarray, pair_hi=None, dtype=np.float64) -> np.ndarray:
     """f_int^n for every step n of V[steps][N] (Eq. fault-to-fault_interactions_discretized), all rows.
 
-    ``pair_hi`` (optional, [F][F] ints) limits the lags of receiver-fault a / source-fault b to T <= pair_hi[a][b]."""
+    ``pair_hi`` (optional, [F][F] or [N][N] ints) limits the lags of receiver-fault a / source-fault b (or of
+    receiver element i / source element j) to T <= pair_hi[a][b] (pair_hi[i][j])."""
     steps = V.shape[0]
     A = np.stack([interaction_slice(net, T, dtype=dtype) for T in range(steps)])
     if pair_hi is not None:
-        fo = net.fault_of
-        hi = np.asarray(pair_hi)[fo][:, fo]
+        hi = _element_hi(net, pair_hi)
         A = np.where(np.arange(steps)[:, None, None] <= hi[None, :, :], A, 0)
     Vd = V.astype(dtype)
     out = np.zeros((steps, net.N), dtype=dtype)
@@ -205,8 +218,7 @@ def interaction_rows(net: Network, V: np.ndarray, n: int, rows, pair_hi=None, ch
     """f_int^n at receiver ``rows`` only, for one step n, from the slip-rate history V[0..n][N]."""
     rows = np.asarray(rows)
     acc = np.zeros(rows.shape[0])
-    fo = net.fault_of
-    hi = None if pair_hi is None else np.asarray(pair_hi)[fo[rows]][:, fo]
+    hi = None if pair_hi is None else _element_hi(net, pair_hi, rows)
     for T0 in range(0, n + 1, chunk):
         Ts = np.arange(T0, min(n + 1, T0 + chunk))
         A = interaction_slice(net, Ts, rows=rows)               # [lags, rows, N]
@@ -254,6 +266,93 @@ def pair_windows(net: Network, eta_tmin: float, eta_tmax: float, max_steps: int,
             lag = math.ceil(t_end[a, b] / net.dt - 1e-9)
             last[a, b] = max_steps - 1 if no_trunc else min(lag, max_steps - 1)
     return t_init, t_end, last
+
+
+@dataclass
+class Cluster:
+    lo: int                   # first element (global index)
+    hi: int                   # one past the last element
+    centre: np.ndarray        # mean of the element centroids
+    radius: float             # largest centroid distance from the centre plus half an element
+    children: tuple = ()
+
+
+def cluster_tree(net: Network, f: int, leaf: int) -> Cluster:
+    """The binary cluster tree of fault f (Sec. 2.3.2, "Fault-wise hierarchical decomposition"): the root holds the
+    fault's elements in order; a cluster of more than ``leaf`` elements is cut into two halves of consecutive
+    elements, the left half taking the extra element of an odd count."""
+    def make(lo, hi):
+        pts = net.x[lo:hi]
+        c = pts.mean(axis=0)
+        r = float(np.max(np.hypot(*(pts - c).T) + 0.5 * net.ds[lo:hi]))
+        node = Cluster(lo, hi, c, r)
+        if hi - lo > leaf:
+            mid = lo + (hi - lo + 1) // 2
+            node.children = (make(lo, mid), make(mid, hi))
+        return node
+    return make(int(net.offset[f]), int(net.offset[f + 1]))
+
+
+def hmatrix_blocks(net: Network, a: int, b: int, leaf: int, eta_h: float, max_block: int, dense: bool = False):
+    """Leaf blocks of the dual-tree traversal of receiver fault a against source fault b (Sec. 2.3.2,
+    Eq. admissibility_condition): a cluster pair whose centre distance exceeds eta_H (r_A + r_B), and whose sides
+    are at most ``max_block``, is an admissible (far) block; a pair of two leaves that is not admissible is a near
+    block; any other pair is refined by cutting the cluster of larger radius (the receiver on a tie within 1e-12,
+    the non-leaf one when the other is a leaf).  ``dense``: nothing is admissible.  Returns
+    [(r0, p, c0, q, far)] with rows r0 .. r0 + p - 1 and columns c0 .. c0 + q - 1."""
+    out = []
+
+    def visit(A: Cluster, B: Cluster):
+        p, q = A.hi - A.lo, B.hi - B.lo
+        d = float(np.hypot(*(A.centre - B.centre)))
+        adm = (not dense) and d > eta_h * (A.radius + B.radius) and p <= max_block and q <= max_block
+        if adm or (not A.children and not B.children):
+            out.append((A.lo, p, B.lo, q, bool(adm)))
+            return
+        if not A.children:
+            cut_receiver = False
+        elif not B.children:
+            cut_receiver = True
+        else:
+            tie = abs(A.radius - B.radius) <= 1e-12 * max(A.radius, B.radius)
+            cut_receiver = tie or A.radius > B.radius
+        if cut_receiver:
+            for C in A.children:
+                visit(C, B)
+        else:
+            for C in B.children:
+                visit(A, C)
+
+    visit(cluster_tree(net, a, leaf), cluster_tree(net, b, leaf))
+    return out
+
+
+def cluster_windows(net: Network, leaf: int, eta_h: float, max_block: int, eta_tmax: float, max_steps: int,
+                    dense: bool = False, no_trunc: bool = False) -> np.ndarray:
+    """Cluster-level end truncation (Sec. 4.3, "Improvement of the algorithm"): the fault-pair criterion of
+    Sec. 2.3.2 applied to each block of the H-matrix partition instead of to the whole fault pair.  For a block of
+    receiver cluster A and source cluster B, T_max^AB is the largest distance from the two ends of A's segment to
+    the ends of B's elements over c_s, and every element pair of the block keeps lags
+    T <= min(ceil((1 + eta_Tmax) T_max^AB / dt - 1e-9), max_steps - 1) (every lag with ``no_trunc``).
+
+    Returns last_lag [N][N] (-1 between elements of one fault)."""
+    last = np.full((net.N, net.N), -1, dtype=np.int64)
+    for a in range(net.F):
+        for b in range(net.F):
+            if a == b:
+                continue
+            for r0, p, c0, q, _ in hmatrix_blocks(net, a, b, leaf, eta_h, max_block, dense):
+                e1r = net.e1[r0]
+                ends = np.stack([net.x[r0] - 0.5 * net.ds[r0] * e1r,
+                                 net.x[r0 + p - 1] + 0.5 * net.ds[r0 + p - 1] * e1r])
+                cols = slice(c0, c0 + q)
+                hb = 0.5 * net.ds[cols][:, None] * net.e1[cols]
+                src_ends = np.concatenate([net.x[cols] - hb, net.x[cols] + hb])
+                de = ends[:, None, :] - src_ends[None, :, :]
+                tmax = np.hypot(de[..., 0], de[..., 1]).max() / net.cs
+                lag = math.ceil((1.0 + eta_tmax) * tmax / net.dt - 1e-9)
+                last[r0:r0 + p, c0:c0 + q] = max_steps - 1 if no_trunc else min(lag, max_steps - 1)
+    return last
 
 
 # ----------------------------------------------------------------------------------------------------------------
@@ -431,8 +530,9 @@ def slip_from_rate(V: np.ndarray, dt: float) -> np.ndarray:
 def stress_history(net: Network, V: np.ndarray, hp: dict, slip=None):
     """tau^n for every step of V[steps][N]; returns (tau, rad, self, int), each [steps][N]  (Eq. superimposition2).
 
-    hp: operator parameters (eta_tmin, eta_tmax, eta_w, q_w, max_steps, flags); windows are applied unless
-    flags has NO_TRUNC (2).  With STATIC_TAIL (4) and windows, the history each window drops is added as a static
+    hp: operator parameters (eta_tmin, eta_tmax, eta_w, q_w, max_steps, flags; leaf, eta_h, max_block for
+    CLUSTER_TRUNC); windows are applied unless flags has NO_TRUNC (2); with CLUSTER_TRUNC (16) the interaction
+    windows end per H-matrix block (cluster_windows; DENSE (1) makes every block a leaf pair).  With STATIC_TAIL (4) and windows, the history each window drops is added as a static
     response: per mode, c_n D_n^{m - W_f(n) - 1} (SelfTables); per fault pair, A^static delta^{m - T_last - 1}, the
     elastostatic stress of the slip reached when the pair's window starts (static_slice)."""
     steps = V.shape[0]
@@ -450,6 +550,12 @@ def stress_history(net: Network, V: np.ndarray, hp: dict, slip=None):
         fself[:, o0:o1] = self_history(net, f, delta[:, o0:o1],
                                        SelfTables(n_f, net.length[f], net.dt, net.cs, W, tail=tail))
     _, _, last = pair_windows(net, hp.get("eta_tmin", 0.01), hp.get("eta_tmax", 0.01), max_steps, no_trunc)
+    if hp.get("flags", 0) & 16:
+        if tail:
+            raise ValueError("the static tail is defined for fault-pair windows only")
+        last = cluster_windows(net, int(hp.get("leaf", 32)), float(hp.get("eta_h", 2.0)),
+                               int(hp.get("max_block", 0)) or 64, hp.get("eta_tmax", 0.01), max_steps,
+                               dense=bool(hp.get("flags", 0) & 1), no_trunc=no_trunc)
     fint = interaction_history(net, V, pair_hi=last)
     if tail:
         fint += static_tail_history(net, delta, last)

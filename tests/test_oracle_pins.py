@@ -625,3 +625,132 @@ def test_adaptive_gamma_follows_the_rate():
     assert it.adaptive_gamma(0.5, 100) == 100
     it.V[-1] = np.full(net.N, 1.0)
     assert it.adaptive_gamma(0.5, 100) == 1
+
+
+# ------------------------------------------------ cluster trees, H-matrix partition, cluster-level windows ------
+
+def _random_net(seed=7):
+    rng = np.random.default_rng(seed)
+    faults = np.array([[0.0, 0.0, 0.1, 900.0, 37], [150.0, 700.0, -0.3, 700.0, 29],
+                       [1100.0, -250.0, 1.2, 500.0, 21]])
+    faults[:, :2] += rng.uniform(-20, 20, (3, 2))
+    return O.network(faults, MU, CS)
+
+
+@pytest.mark.parametrize("leaf,eta_h,max_block,dense", [(4, 2.0, 64, False), (8, 0.7, 8, False),
+                                                        (3, 1.5, 64, True)])
+def test_hmatrix_blocks_tile_each_fault_pair_once(leaf, eta_h, max_block, dense):
+    """P16a: the leaf blocks of each ordered fault pair cover every (receiver, source) element pair exactly once;
+    every far block satisfies the admissibility test (centre distance > eta_H (r_A + r_B), radii recomputed here
+    from the elements) and the side cap; every near block is a pair of leaves; the tree halves keep consecutive
+    elements with the extra one on the left."""
+    net = _random_net()
+    for f in range(net.F):
+        stack = [O.cluster_tree(net, f, leaf)]
+        while stack:
+            c = stack.pop()
+            if c.children:
+                l, r = c.children
+                assert (l.lo, l.hi, r.lo, r.hi) == (c.lo, c.lo + (c.hi - c.lo + 1) // 2, l.hi, c.hi)
+                stack += [l, r]
+            else:
+                assert 1 <= c.hi - c.lo <= leaf
+
+    def circle(lo, hi):
+        c = net.x[lo:hi].mean(axis=0)
+        return c, max(math.hypot(*(net.x[i] - c)) + net.ds[i] / 2 for i in range(lo, hi))
+
+    for a in range(net.F):
+        for b in range(net.F):
+            if a == b:
+                continue
+            cover = np.zeros((net.n_elem[a], net.n_elem[b]), dtype=int)
+            blocks = O.hmatrix_blocks(net, a, b, leaf, eta_h, max_block, dense)
+            for r0, p, c0, q, far in blocks:
+                cover[r0 - net.offset[a]:r0 - net.offset[a] + p, c0 - net.offset[b]:c0 - net.offset[b] + q] += 1
+                if far:
+                    (ca, ra), (cb, rb) = circle(r0, r0 + p), circle(c0, c0 + q)
+                    assert not dense and math.hypot(*(ca - cb)) > eta_h * (ra + rb) and max(p, q) <= max_block
+                else:
+                    assert p <= leaf and q <= leaf
+            assert (cover == 1).all()
+            if not dense:
+                assert any(b_[4] for b_ in blocks)
+
+
+def test_cluster_windows_of_two_collinear_faults_in_closed_form():
+    """P16b: two collinear faults of 1000 m on x in [0, 1000] and [4000, 5000], 16 elements each, leaf 8: with
+    eta_H = 6 neither the root pair (4000 < 6 x 1000) nor a half against a whole fault (4250, 3750 < 6 x 750) is
+    admissible, and the four pairs of halves are (3500 .. 4500 > 6 x 500).  Each block's window ends at
+    (1 + eta_Tmax) times the largest distance between the ends of its two half-segments over c_s, here the span
+    from the outer end of one half to the outer end of the other: 4000, 4500 or 5000 m; the fault-pair window
+    (5000 m) is the longest.  Distances along the line of sight make an end taken at a centroid (ds = 62.5 m) move
+    the window by two lags."""
+    net = O.network(np.array([[500.0, 0.0, 0.0, 1000.0, 16], [4500.0, 0.0, 0.0, 1000.0, 16]]), MU, CS)
+    eta_t = 0.3
+    W = O.cluster_windows(net, 8, 6.0, 64, eta_t, 10 ** 6)
+    lag = lambda d: math.ceil((1 + eta_t) * d / CS / net.dt - 1e-9)
+    assert [lag(d) for d in (4000.0, 4500.0, 5000.0)] == [167, 188, 208]
+    blocks = sorted(O.hmatrix_blocks(net, 0, 1, 8, 6.0, 64))
+    assert blocks == [(0, 8, 16, 8, True), (0, 8, 24, 8, True), (8, 8, 16, 8, True), (8, 8, 24, 8, True)]
+    exp = np.full((32, 32), -1)
+    L, R = slice(0, 8), slice(8, 16)
+    BL, BR = slice(16, 24), slice(24, 32)
+    exp[L, BL], exp[L, BR], exp[R, BL], exp[R, BR] = 188, 208, 167, 188
+    exp[BL, L], exp[BL, R], exp[BR, L], exp[BR, R] = 188, 167, 208, 188
+    np.testing.assert_array_equal(W, exp)
+    _, _, P = O.pair_windows(net, 0.01, eta_t, 10 ** 6)
+    assert P[0, 1] == P[1, 0] == 208
+    assert (O.cluster_windows(net, 8, 6.0, 64, eta_t, 180) == np.where(exp < 0, -1, np.minimum(exp, 179))).all()
+
+
+def test_cluster_windows_reduce_to_the_fault_pair_windows_for_one_block_per_pair():
+    """P16c: with eta_H so small that every root pair is admissible (and no side cap), each fault pair is one block
+    and the cluster-level windows are the fault-pair windows of Sec. 2.3.2, element for element."""
+    net = _random_net(3)
+    W = O.cluster_windows(net, 4, 1e-3, 10 ** 6, 0.01, 10 ** 6)
+    _, _, P = O.pair_windows(net, 0.01, 0.01, 10 ** 6)
+    np.testing.assert_array_equal(W, P[net.fault_of][:, net.fault_of])
+
+
+def test_cluster_windows_never_cut_before_the_whole_source_element_has_arrived():
+    """P16d: on a three-fault network with many blocks, each element pair's cluster-level window is no longer than
+    its fault-pair window and no shorter than the time for the S-wave from the far end of the source element to
+    reach the receiver centroid (brute force over element pairs)."""
+    net = _random_net(11)
+    W = O.cluster_windows(net, 4, 1.0, 16, 0.0, 10 ** 6)
+    _, _, P = O.pair_windows(net, 0.01, 0.0, 10 ** 6)
+    Pe = P[net.fault_of][:, net.fault_of]
+    other = net.fault_of[:, None] != net.fault_of[None, :]
+    assert (W[other] <= Pe[other]).all() and (W[other] < Pe[other]).mean() > 0.3
+    for i in range(net.N):
+        for j in range(net.N):
+            if not other[i, j]:
+                assert W[i, j] == -1
+                continue
+            far = max(math.hypot(*(net.x[i] - net.x[j] - s * 0.5 * net.ds[j] * net.e1[j])) for s in (-1, 1))
+            assert W[i, j] >= math.ceil(far / CS / net.dt - 1e-9)
+
+
+def test_interaction_with_element_windows_equals_a_brute_force_loop():
+    """P16e: with a window per element pair, f_int^n = -(mu / 2 c_s) sum_j sum_{T <= min(n, hi_ij)} A_ij^T V_j^{n-T}
+    written as plain loops, on two faults of five elements over 14 steps."""
+    net = O.network(np.array([[0.0, 0.0, 0.0, 50.0, 5], [10.0, 12.0, 0.4, 40.0, 5]]), MU, CS)
+    steps = 14
+    rng = np.random.default_rng(5)
+    V = rng.normal(size=(steps, net.N))
+    hi = rng.integers(0, steps, size=(net.N, net.N))
+    A = [O.interaction_slice(net, T) for T in range(steps)]
+    ref = np.zeros((steps, net.N))
+    for n in range(steps):
+        for i in range(net.N):
+            s = 0.0
+            for j in range(net.N):
+                for T in range(min(n, hi[i, j]) + 1):
+                    s += A[T][i, j] * V[n - T, j]
+            ref[n, i] = -(MU / (2 * CS)) * s
+    got = O.interaction_history(net, V, pair_hi=hi)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    rows = np.array([1, 6, 9])
+    np.testing.assert_allclose(O.interaction_rows(net, V, steps - 1, rows, pair_hi=hi), ref[-1, rows],
+                               rtol=1e-12, atol=1e-12 * np.abs(ref).max())
