@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the other storage precisions")
     ap.add_argument("--no-batched", action="store_true", help="skip the 8-scenario ensemble runs")
     ap.add_argument("--no-tail", action="store_true", help="skip the static-tail run")
+    ap.add_argument("--no-cluster", action="store_true", help="skip the cluster-level end truncation run")
     ap.add_argument("--no-oracle-rows", action="store_true", help="skip the oracle interaction rows (errors)")
     ap.add_argument("--dump-step-bytes", default=None, help="write the per-step algorithmic interaction bytes here")
     ap.add_argument("--served-seconds", type=float, default=15.0, help="wall time of the served run (0: skip)")
@@ -125,6 +126,13 @@ class OracleStepper:
 
     def interaction(self, rows, n):
         return self.O.interaction_rows(self.net, self.V, int(n), rows, pair_hi=self.last)
+
+    def interaction_cluster(self, rows, n):
+        """The same rows with the cluster-level end truncation (windows per block of the H-matrix partition)."""
+        hp = self.w.hparams
+        W = self.O.cluster_windows(self.net, int(hp["leaf"]), float(hp["eta_h"]), int(hp.get("max_block", 0)) or 64,
+                                   hp["eta_tmax"], hp["max_steps"], no_trunc=bool(hp.get("flags", 0) & 2))
+        return self.O.interaction_rows(self.net, self.V, int(n), rows, pair_hi=W)
 
 
 _WORKER = None
@@ -355,7 +363,7 @@ def run_ours(args, w, start, K, W):
     w.seed = rank_seed(rank)                                # independent scenario per rank
     # CPU oracle first (before any GPU work in this process): the CPU baseline and the interaction rows that every
     # storage precision is checked against
-    oracle, ref_int = None, None
+    oracle, ref_int, ref_int_cluster = None, None, None
     rows = oracle_rows(w)
     if rank == 0 and (args.cpu_sample > 0 or not args.no_oracle_rows):
         t0 = time.perf_counter()
@@ -372,6 +380,10 @@ def run_ours(args, w, start, K, W):
             t0 = time.perf_counter()
             ref_int = st.interaction(rows, w.steps - 1)
             log(f"oracle interaction rows {time.perf_counter() - t0:.1f} s")
+            if not args.no_cluster:
+                t0 = time.perf_counter()
+                ref_int_cluster = st.interaction_cluster(rows, w.steps - 1)
+                log(f"oracle interaction rows, cluster-level windows {time.perf_counter() - t0:.1f} s")
         del st
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
@@ -391,10 +403,11 @@ def run_ours(args, w, start, K, W):
         got = tau_win.cpu().numpy()[steps - start, elems]
         return rel(got, ref)
 
-    def int_err(parts_last, b=0):
-        if ref_int is None:
+    def int_err(parts_last, b=0, ref=None):
+        r = ref_int if ref is None else ref
+        if r is None:
             return None
-        return rel(parts_last[2, b * w.N + rows].cpu().numpy(), ref_int)
+        return rel(parts_last[2, b * w.N + rows].cpu().numpy(), r)
 
     # consumer warps per interaction pass picked by the library's autotuner for every measured scenario; copies of a
     # scenario (same operator and batch) take the choice from this run's cache file
@@ -584,6 +597,28 @@ def run_ours(args, w, start, K, W):
         s4.close()
         del r4
 
+    # cluster-level end truncation (Sec. 4.3): the headline operator with a window per H-matrix block
+    cluster = None
+    if not args.no_cluster:
+        s5 = session(head_code, flags=int(w.hparams.get("flags", 0)) | seas.SEAS_FLAG_CLUSTER_TRUNC)
+        r5 = measure(s5, Vd, 1, head_code)
+        cv = job_rate(w.N * K, world, r5["total_ms"] / 1e3)
+        cluster = {"value": cv, "unit": METRIC, "ms_per_step": r5["total_ms"] / K,
+                   "p50_ms": float(np.percentile(r5["per"], 50)), "speedup": cv / value,
+                   "bytes_interaction": s5.stats["bytes_interaction"],
+                   "bytes_vs_headline": s5.stats["bytes_interaction"] / s.stats["bytes_interaction"],
+                   "window_bytes_per_step": r5["roofline"]["algorithmic_bytes_per_launch"],
+                   "rel_l2_interaction_vs_oracle": int_err(r5["parts"], ref=ref_int_cluster),
+                   "rel_l2_interaction_vs_headline": rel(r5["parts"][2].cpu().numpy(), parts[2].cpu().numpy()),
+                   "rel_l2_tau_vs_headline": rel(r5["tau"].cpu().numpy(), tau.cpu().numpy()),
+                   "consumer_warps": s5.tune["consumer_warps"],
+                   "roofline": {k: r5["roofline"][k] for k in (
+                       "bound", "achieved", "peak", "unit", "frac", "mean_launch_ms", "pass_ms")}}
+        log(f"cluster-level truncation {cv / 1e6:.3f} M element-steps/s ({cv / value:.2f}x), "
+            f"{cluster['bytes_vs_headline']:.3f} of the operator bytes")
+        s5.close()
+        del r5
+
     # plain FP64 GPU path: every block dense (leaf blocks, exact windows), no compression, FP64 arithmetic
     plain = None
     if not args.no_plain:
@@ -632,7 +667,8 @@ def run_ours(args, w, start, K, W):
                 "operator": {k: stats[k] for k in (
                     "n_blocks_far", "n_blocks_near", "compression_ratio", "bytes_interaction", "mean_rank",
                     "max_rank", "build_seconds", "n_tasks")},
-                "vs_plain_fp64_gpu": plain, "variants": variants, "batched": batched, "static_tail": tail, "e2e": e2e,
+                "vs_plain_fp64_gpu": plain, "variants": variants, "batched": batched, "static_tail": tail,
+                "cluster_trunc": cluster, "e2e": e2e,
                 "served": served, "ensemble_8x8": ensemble, "graph": graph,
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
                 "autotune": {"consumer_warps": s.tune["consumer_warps"], "median_launch_ms": s.tune["ms"],

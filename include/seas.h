@@ -74,6 +74,14 @@ typedef int seas_status;
  * window end) but does not limit the number of pushes, so scenarios may run any number of steps (used by long-running
  * served requests).  Without it, a push past max_steps returns SEAS_ESTATE. */
 #define SEAS_FLAG_LAG_CAP 8
+/* SEAS_FLAG_CLUSTER_TRUNC: cluster-level end truncation, the extension Sec. 4.3 proposes.  The criterion of
+ * Sec. 2.3.2 is applied per block of the H-matrix partition instead of per fault pair: for the block of receiver
+ * cluster A and source cluster B, T_max^AB is the largest distance from the two ends of A's segment to the ends of
+ * B's elements over c_s, and the block keeps lags up to min(ceil((1 + eta_Tmax) T_max^AB / dt), max_steps - 1)
+ * (never longer than the fault pair's window).  Well-separated cluster pairs then store and evaluate fewer lags.
+ * Not with SEAS_FLAG_STATIC_TAIL (SEAS_EINVAL: the tail is defined per fault pair); ignored with
+ * SEAS_FLAG_NO_TRUNC. */
+#define SEAS_FLAG_CLUSTER_TRUNC 16
 
 /* storage precision and arithmetic of the interaction operator */
 #define SEAS_PREC_FP64 0   /* FP64 entries, FP64 arithmetic */
@@ -171,6 +179,14 @@ seas_status seas_build_hmatrix_part(seas_net *net, const seas_hparams *hp, const
 seas_status seas_op_pair_windows(const seas_op *op, int32_t *last_lag);
 /* Per fault f and mode n = 0..N_f: last lag W_f(n) of the spectral window (flattened fault after fault). */
 seas_status seas_op_mode_windows(const seas_op *op, int32_t *w);
+
+/* The operator's H-matrix blocks (the leaf blocks of the dual traversal of Sec. 2.3.2, in build order): row i of
+ * `blocks` ([cap][7] int32, host) is (r0, p, c0, q, far, first_lag, last_lag) for receivers r0 .. r0 + p - 1 and
+ * sources c0 .. c0 + q - 1; far = 1 for an admissible (low-rank) block; the block's window is
+ * first_lag .. last_lag (empty when first_lag > last_lag; first_lag is a lower bound: exactly-zero slices at the
+ * start of the window are not stored).  *n_blocks receives the count; at most cap rows are
+ * written (blocks may be NULL with cap = 0 to query the count). */
+seas_status seas_op_blocks(const seas_op *op, int32_t *blocks, int64_t cap, int64_t *n_blocks);
 
 /* Allocates the history ring buffers of `batch` (1..8) independent scenarios sharing the operator.  BF16 operators
  * with batches of 5..8 run on tensor-core consumers that tile at most 128 receivers per block (SEAS_EINVAL

@@ -532,9 +532,10 @@ def stress_history(net: Network, V: np.ndarray, hp: dict, slip=None):
 
     hp: operator parameters (eta_tmin, eta_tmax, eta_w, q_w, max_steps, flags; leaf, eta_h, max_block for
     CLUSTER_TRUNC); windows are applied unless flags has NO_TRUNC (2); with CLUSTER_TRUNC (16) the interaction
-    windows end per H-matrix block (cluster_windows; DENSE (1) makes every block a leaf pair).  With STATIC_TAIL (4) and windows, the history each window drops is added as a static
-    response: per mode, c_n D_n^{m - W_f(n) - 1} (SelfTables); per fault pair, A^static delta^{m - T_last - 1}, the
-    elastostatic stress of the slip reached when the pair's window starts (static_slice)."""
+    windows end per H-matrix block (cluster_windows; DENSE (1) makes every block a leaf pair).  With STATIC_TAIL
+    (4) and windows, the history each window drops is added as a static response: per mode,
+    c_n D_n^{m - W_f(n) - 1} (SelfTables); per fault pair, A^static delta^{m - T_last - 1}, the elastostatic stress
+    of the slip reached when the pair's window starts (static_slice)."""
     steps = V.shape[0]
     no_trunc = bool(hp.get("flags", 0) & 2)
     tail = bool(hp.get("flags", 0) & 4) and not no_trunc

@@ -207,6 +207,7 @@ struct seas_op {
     DArr<int32_t> d_cover_ptr, d_cover_blk, d_blk_task_ptr, d_blk_task_T;
     DArr<int64_t> d_blk_part;
     std::vector<int32_t> pair_last;  // [F][F]
+    std::vector<int32_t> block_lo, block_hi;  // window of each block (first and last lag)
     std::vector<int64_t> bytes_upto; // stored interaction bytes with lag <= T
     int ring = 1;
     // static tail (SEAS_FLAG_STATIC_TAIL)
@@ -583,6 +584,28 @@ int32_t pair_last_lag(const seas_net &net, int a, int b, double eta_tmax, int ma
     return (int32_t)std::min<double>(lag, max_steps - 1);
 }
 
+// Cluster-level end truncation (Sec. 4.3): the fault-pair criterion above applied to one block.  The receiver and
+// source clusters are straight runs of consecutive elements, so the largest distance between a point of one and a
+// point of the other is reached between segment ends: T_max^AB = the largest of the four distances between the
+// outer ends of the block's first and last receiver elements and of its first and last source elements, over c_s.
+int32_t cluster_last_lag(const seas_net &net, const BlockDev &b, double eta_tmax, int max_steps) {
+    auto ends = [&](int first, int last, double *ex, double *ey) {
+        const double h0 = 0.5 * net.ds[first], h1 = 0.5 * net.ds[last];
+        ex[0] = net.x[first] - h0 * net.e1x[first];
+        ey[0] = net.y[first] - h0 * net.e1y[first];
+        ex[1] = net.x[last] + h1 * net.e1x[last];
+        ey[1] = net.y[last] + h1 * net.e1y[last];
+    };
+    double rx[2], ry[2], sx[2], sy[2];
+    ends(b.r0, b.r0 + b.p - 1, rx, ry);
+    ends(b.c0, b.c0 + b.q - 1, sx, sy);
+    double dmax = 0.0;
+    for (int u = 0; u < 2; ++u)
+        for (int v = 0; v < 2; ++v) dmax = std::max(dmax, std::hypot(rx[u] - sx[v], ry[u] - sy[v]));
+    const double lag = std::ceil((1.0 + eta_tmax) * (dmax / net.med.cs) / net.dt - 1e-9);
+    return (int32_t)std::min<double>(lag, max_steps - 1);
+}
+
 // Conservative first lag of a block: one less than floor(min segment distance / (c_s dt)).  Exactly-zero slices
 // found while building are dropped as well, so the stored window starts at the exact first nonzero lag.
 int32_t block_first_lag(const seas_net &net, const BlockDev &b) {
@@ -812,9 +835,11 @@ seas_status build_interaction(seas_op &op) {
     const int nb = (int)op.blocks_h.size();
     std::vector<int32_t> lo(nb), hi(nb);
     int32_t Tmin = INT32_MAX, Tmax = -1;
+    const bool cluster_trunc = (hp.flags & SEAS_FLAG_CLUSTER_TRUNC) && !no_trunc;
     for (int b = 0; b < nb; ++b) {
         lo[b] = block_first_lag(net, op.blocks_h[b]);
         hi[b] = op.pair_last[op.block_pair[b]];
+        if (cluster_trunc) hi[b] = std::min(hi[b], cluster_last_lag(net, op.blocks_h[b], hp.eta_tmax, hp.max_steps));
         if (lo[b] <= hi[b]) {
             Tmin = std::min(Tmin, lo[b]);
             Tmax = std::max(Tmax, hi[b]);
@@ -823,6 +848,8 @@ seas_status build_interaction(seas_op &op) {
         else op.stats.n_blocks_near++;
     }
     op.ring = std::max<int32_t>(1, Tmax + 1);
+    op.block_lo = lo;
+    op.block_hi = hi;
     SEAS_TRY(op.d_blocks.upload(c, op.blocks_h));
 
     GeomDev g{net.d_x.p, net.d_e1.p, net.d_n.p, net.d_ds.p, net.med.cs, net.dt, -net.med.mu / (2.0 * net.med.cs)};
@@ -1226,8 +1253,11 @@ extern "C" seas_status seas_build_hmatrix_part(seas_net *net, const seas_hparams
     if (hp->max_steps < 1 || hp->max_steps > (1 << 22)) return fail(SEAS_EINVAL, "max_steps in [1, 2^22]");
     if (hp->precision < kPrecFP64 || hp->precision > kPrecDF64)
         return fail(SEAS_EINVAL, "precision %d not available", hp->precision);
-    if (hp->flags & ~(SEAS_FLAG_DENSE | SEAS_FLAG_NO_TRUNC | SEAS_FLAG_STATIC_TAIL | SEAS_FLAG_LAG_CAP))
+    if (hp->flags & ~(SEAS_FLAG_DENSE | SEAS_FLAG_NO_TRUNC | SEAS_FLAG_STATIC_TAIL | SEAS_FLAG_LAG_CAP |
+                      SEAS_FLAG_CLUSTER_TRUNC))
         return fail(SEAS_EINVAL, "unsupported flags 0x%x", hp->flags);
+    if ((hp->flags & SEAS_FLAG_CLUSTER_TRUNC) && (hp->flags & SEAS_FLAG_STATIC_TAIL))
+        return fail(SEAS_EINVAL, "the static tail is defined for fault-pair windows (no SEAS_FLAG_CLUSTER_TRUNC)");
     if (hp->max_block != 0 && hp->max_block < hp->leaf) return fail(SEAS_EINVAL, "max_block must be >= leaf");
     seas_ctx *c = net->ctx;
     CUDA_TRY(cudaSetDevice(c->device));
@@ -1297,6 +1327,24 @@ extern "C" seas_status seas_plan_hmatrix(const seas_fault *faults, int n_faults,
 extern "C" seas_status seas_op_pair_windows(const seas_op *op, int32_t *last_lag) {
     if (!op || !last_lag) return fail(SEAS_EINVAL, "NULL argument");
     std::copy(op->pair_last.begin(), op->pair_last.end(), last_lag);
+    return SEAS_OK;
+}
+
+extern "C" seas_status seas_op_blocks(const seas_op *op, int32_t *blocks, int64_t cap, int64_t *n_blocks) {
+    if (!op || (!blocks && cap > 0)) return fail(SEAS_EINVAL, "NULL argument");
+    const int64_t nb = (int64_t)op->blocks_h.size();
+    if (n_blocks) *n_blocks = nb;
+    for (int64_t i = 0; i < std::min(cap, nb); ++i) {
+        const BlockDev &b = op->blocks_h[(size_t)i];
+        int32_t *r = blocks + 7 * i;
+        r[0] = b.r0;
+        r[1] = b.p;
+        r[2] = b.c0;
+        r[3] = b.q;
+        r[4] = op->block_far[(size_t)i];
+        r[5] = op->block_lo[(size_t)i];
+        r[6] = op->block_hi[(size_t)i];
+    }
     return SEAS_OK;
 }
 

@@ -19,19 +19,20 @@ SEAS_OK = 0
 SEAS_EINVAL, SEAS_ENOMEM, SEAS_ECUDA, SEAS_ESTATE, SEAS_EBUSY, SEAS_ETIMEOUT, SEAS_EIO = -1, -2, -3, -4, -5, -6, -7
 SEAS_MEM_HOST, SEAS_MEM_DEVICE = 0, 1
 SEAS_FLAG_DENSE, SEAS_FLAG_NO_TRUNC, SEAS_FLAG_STATIC_TAIL, SEAS_FLAG_LAG_CAP = 1, 2, 4, 8
+SEAS_FLAG_CLUSTER_TRUNC = 16
 SEAS_PREC_FP64, SEAS_PREC_BF16, SEAS_PREC_FP16S, SEAS_PREC_DF64 = 0, 1, 2, 3
 
 EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_get_elements", "seas_build_hmatrix",
-            "seas_op_pair_windows", "seas_op_mode_windows", "seas_scenario_create", "seas_push_slip_rate",
-            "seas_stress_step", "seas_scenario_step", "seas_sync", "seas_strerror", "seas_last_error",
-            "seas_scenario_save", "seas_scenario_load", "seas_destroy_scn", "seas_destroy_op", "seas_destroy_net",
-            "seas_destroy_ctx", "seas_plan_hmatrix", "seas_scenario_set_timing", "seas_scenario_get_timing",
-            "seas_op_step_bytes", "seas_scenario_check", "seas_stress_step_static",
-            "seas_measure_fp64_peak", "seas_scenario_set_wait_limit", "seas_scenario_probe_wait",
-            "seas_scenario_admit", "seas_scenario_retire", "seas_scenario_member_step", "seas_ctx_get_memory",
-            "seas_integrator_create", "seas_integrator_step", "seas_integrator_state", "seas_destroy_integrator",
-            "seas_push_slip_rate_steps", "seas_integrator_step_gamma", "seas_integrator_step_adaptive",
-            "seas_scenario_graph_create", "seas_scenario_graph_step", "seas_build_hmatrix_part", "seas_scenario_autotune"]
+            "seas_op_pair_windows", "seas_op_mode_windows", "seas_op_blocks", "seas_scenario_create",
+            "seas_push_slip_rate", "seas_stress_step", "seas_scenario_step", "seas_sync", "seas_strerror",
+            "seas_last_error", "seas_scenario_save", "seas_scenario_load", "seas_destroy_scn", "seas_destroy_op",
+            "seas_destroy_net", "seas_destroy_ctx", "seas_plan_hmatrix", "seas_scenario_set_timing",
+            "seas_scenario_get_timing", "seas_op_step_bytes", "seas_scenario_check", "seas_stress_step_static",
+            "seas_measure_fp64_peak", "seas_scenario_set_wait_limit", "seas_scenario_probe_wait", "seas_scenario_admit",
+            "seas_scenario_retire", "seas_scenario_member_step", "seas_ctx_get_memory", "seas_integrator_create",
+            "seas_integrator_step", "seas_integrator_state", "seas_destroy_integrator", "seas_push_slip_rate_steps",
+            "seas_integrator_step_gamma", "seas_integrator_step_adaptive", "seas_scenario_graph_create",
+            "seas_scenario_graph_step", "seas_build_hmatrix_part", "seas_scenario_autotune"]
 
 
 class SeasError(RuntimeError):
@@ -94,6 +95,7 @@ _SIGS = {
     "seas_build_hmatrix": ([_VP, C.POINTER(seas_hparams), _PP, C.POINTER(seas_op_stats)], C.c_int),
     "seas_op_pair_windows": ([_VP, _VP], C.c_int),
     "seas_op_mode_windows": ([_VP, _VP], C.c_int),
+    "seas_op_blocks": ([_VP, _VP, C.c_int64, _VP], C.c_int),
     "seas_scenario_create": ([_VP, C.c_int, _PP], C.c_int),
     "seas_push_slip_rate": ([_VP, _VP, _VP, C.c_int, C.c_int], C.c_int),
     "seas_stress_step": ([_VP, _VP, _VP, _VP, C.c_int], C.c_int),
@@ -302,6 +304,15 @@ def seas_build_hmatrix(net: Handle, hp: dict, owned=None):
 def seas_op_pair_windows(op: Handle) -> np.ndarray:
     out = np.zeros((op.F, op.F), dtype=np.int32)
     _check(lib().seas_op_pair_windows(op.ptr, out.ctypes.data))
+    return out
+
+
+def seas_op_blocks(op: Handle) -> np.ndarray:
+    """The operator's blocks, [n, 7] int32 rows (r0, p, c0, q, far, first_lag, last_lag)."""
+    n = C.c_int64(0)
+    _check(lib().seas_op_blocks(op.ptr, None, 0, C.byref(n)))
+    out = np.zeros((n.value, 7), dtype=np.int32)
+    _check(lib().seas_op_blocks(op.ptr, out.ctypes.data, n.value, C.byref(n)))
     return out
 
 
@@ -547,13 +558,18 @@ class Session:
             torch = sys.modules.get("torch")
             if torch is not None and torch.cuda.is_available():
                 stream = torch.cuda.current_stream(device)
-        self.ctx = seas_create(device, hbm_budget, stream)
-        self.net = seas_build_network(self.ctx, workload.faults, workload.mu, workload.cs, workload.cp,
-                                      workload.beta)
-        params = dict(workload.hparams)
-        params.update(hp)
-        self.op, self.stats = seas_build_hmatrix(self.net, params, owned)
-        self.scn = seas_scenario_create(self.op, batch)
+        self.ctx = self.net = self.op = self.scn = None
+        try:
+            self.ctx = seas_create(device, hbm_budget, stream)
+            self.net = seas_build_network(self.ctx, workload.faults, workload.mu, workload.cs, workload.cp,
+                                          workload.beta)
+            params = dict(workload.hparams)
+            params.update(hp)
+            self.op, self.stats = seas_build_hmatrix(self.net, params, owned)
+            self.scn = seas_scenario_create(self.op, batch)
+        except BaseException:
+            self.close()
+            raise
 
     def close(self):
         for fn, h in ((seas_destroy_scn, "scn"), (seas_destroy_op, "op"), (seas_destroy_net, "net"),

@@ -35,6 +35,7 @@ FLAG_DENSE = 1          # every block stored dense (admissibility never satisfie
 FLAG_NO_TRUNC = 2       # no causal end truncation of pair windows, full spectral windows
 FLAG_STATIC_TAIL = 4    # add the elastostatic response of truncated history (default off)
 FLAG_LAG_CAP = 8        # max_steps caps the windows but not the number of steps
+FLAG_CLUSTER_TRUNC = 16 # interaction windows end per H-matrix block (cluster-level end truncation)
 
 PREC_FP64 = 0
 PREC_BF16 = 1

@@ -28,7 +28,8 @@ def test_static_step_matches_stress_step(case):
         w, batch, hp = synth.two_fault_128(), 2, dict(flags=seas.SEAS_FLAG_NO_TRUNC, eta_h=2.0, leaf=32, aca_tol=1e-6)
         first, count = w.steps // 2, 2
     elif case == "tiny_dense":
-        w, batch, hp = synth.tiny(3, n_faults=3, steps=60), 1, dict(flags=seas.SEAS_FLAG_DENSE | seas.SEAS_FLAG_NO_TRUNC)
+        w, batch = synth.tiny(3, n_faults=3, steps=60), 1
+        hp = dict(flags=seas.SEAS_FLAG_DENSE | seas.SEAS_FLAG_NO_TRUNC)
         first, count = w.steps // 2, 2
     else:
         w, batch, hp = synth.two_fault_128(), 1, dict(flags=0, eta_h=2.0, leaf=32, aca_tol=1e-6)
