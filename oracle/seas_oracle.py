@@ -31,6 +31,9 @@ fault-wise cluster trees and the dual traversal restated in cluster_tree / hmatr
 not in the paper, off by default): the history a window drops is added back as an elastostatic response, per mode
 c_n D_n^{m - W - 1} with c_n = (2/pi) Si(n pi) - sum_{T <= W} w_n^T, per fault pair A^static delta^{m - T_last - 1}.
 
+Half-space (App. B): image_faults doubles each surface-breaking fault across the traction-free surface and
+continues the slip evenly; half_space_stress_history is the functional of that doubled network on the real rows.
+
 Parity status: every function here is pinned by tests/test_oracle_pins.py (closed forms, special cases, printed
 numbers, brute force in extended precision).
 """
@@ -582,3 +585,54 @@ def static_tail_history(net: Network, delta: np.ndarray, last) -> np.ndarray:
                 continue
             out[lag:, ra] += delta[: steps - lag, rb] @ As[ra, rb].T
     return -(net.mu / (2 * net.cs)) * out
+
+
+# ----------------------------------------------------------------------------------------------------------------
+# traction-free surface by the method of images
+# ----------------------------------------------------------------------------------------------------------------
+
+
+def image_faults(faults: np.ndarray):
+    """Method of images for a traction-free surface (App. B; Sec. 4.2 names image methods for simple geometries).
+
+    Every fault's start end c - (L/2) e'_1 lies on the surface; the faults are parallel with e'_1 pointing into the
+    medium, and the surface is the line through their start ends normal to e'_1.  Reflection across that line maps
+    each fault onto its own continuation beyond the start end.  Continuing the slip evenly, delta(-z) = delta(z)
+    with z the distance from the surface, makes the anti-plane displacement even in z, so its z-derivative, and with
+    it the shear traction on the surface, vanishes; the full-space functional of the doubled network then gives the
+    half-space stress on the real elements.
+
+    Returns (doubled, mirror, real): doubled[f] = (start end x, y, phi, 2 L_f, 2 N_f); mirror[k] = the real element
+    whose slip rate element k of the doubled network carries (on fault f: N_f + j and N_f - 1 - j both carry real
+    element j); real[i] = the element of the doubled network at real element i (N_f + j)."""
+    faults = np.asarray(faults, dtype=np.float64)
+    e1 = np.stack([np.cos(faults[:, 2]), np.sin(faults[:, 2])], axis=1)
+    start = faults[:, :2] - 0.5 * faults[:, 3:4] * e1
+    scale = float(faults[:, 3].max())
+    if np.any(e1 @ e1[0] < 1.0 - 1e-12):
+        raise ValueError("the faults of a half-space network are parallel, with the same orientation")
+    if np.any(np.abs((start - start[0]) @ e1[0]) > 1e-9 * scale):
+        raise ValueError("every fault's start end lies on the one free surface")
+    doubled = np.column_stack([start, faults[:, 2], 2.0 * faults[:, 3], 2 * faults[:, 4]])
+    mirror, real = [], []
+    o_real = 0
+    o_doubled = 0
+    for f in range(faults.shape[0]):
+        n = int(faults[f, 4])
+        j = np.arange(n)
+        mirror.append(np.concatenate([o_real + j[::-1], o_real + j]))
+        real.append(o_doubled + n + j)
+        o_real += n
+        o_doubled += 2 * n
+    return doubled, np.concatenate(mirror), np.concatenate(real)
+
+
+def half_space_stress_history(faults: np.ndarray, mu: float, cs: float, V: np.ndarray, hp: dict,
+                              beta: float = 0.5):
+    """(tau, rad, self, int) on the real elements of a half-space network, each [steps][N]: stress_history of the
+    doubled network of image_faults with the slip rate V[steps][N] continued evenly across the surface.  The
+    windows are those of the doubled faults (a self window on the 2 L_f fault, as in App. B)."""
+    doubled, mirror, real = image_faults(faults)
+    net2 = network(doubled, mu, cs, beta)
+    parts = stress_history(net2, V[:, mirror], hp)
+    return tuple(p[:, real] for p in parts)

@@ -754,3 +754,74 @@ def test_interaction_with_element_windows_equals_a_brute_force_loop():
     rows = np.array([1, 6, 9])
     np.testing.assert_allclose(O.interaction_rows(net, V, steps - 1, rows, pair_hi=hi), ref[-1, rows],
                                rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+# ------------------------------------------------------------------ traction-free surface, method of images ------
+
+def _surface_fault(x0, depth, n, phi=-math.pi / 2):
+    e1 = np.array([math.cos(phi), math.sin(phi)])
+    return [x0 + 0.5 * depth * e1[0], 0.5 * depth * e1[1], phi, depth, n]
+
+
+def test_half_space_static_limit_is_the_stress_of_the_segment_and_its_image():
+    """P17a: a fault from the free surface y = 0 down to depth D slips uniformly by delta at step 0.  With the
+    static tail after the self windows, the half-space self term is its elastostatic limit, which the method of
+    images makes the full-space stress of the segment and its mirror image, i.e. screw dislocations +delta at depth
+    -D (the image's far end) and -delta at depth D (textbook field, independent of the oracle's kernels).  The
+    spectral series of a slip box converges like 1/N (checked at 32 and 64 real elements, receivers between 0.05 D
+    and 0.8 D); the fault alone in a full space (dislocations at 0 and D) is off by more than the stress itself, and
+    an odd continuation of the slip would be too."""
+    D = 1000.0
+    errs = []
+    for n in (32, 64):
+        faults = np.array([_surface_fault(0.0, D, n)])
+        doubled, _, _ = O.image_faults(faults)
+        net2 = O.network(doubled, MU, CS)
+        steps = int(O.mode_windows(2 * n, 2 * D, net2.dt, CS, 0.25, 0, 10 ** 6).max()) + 5
+        V = np.zeros((steps, n))
+        V[0] = 1.0 / net2.dt
+        fs = O.half_space_stress_history(faults, MU, CS, V, dict(eta_w=0.25, q_w=0, flags=4, max_steps=steps))[2]
+        net = O.network(faults, MU, CS)
+        down = np.array([0.0, -1.0])
+        ref = _dislocation_traction(net.x, net.nrm, -D * down, 1.0) + _dislocation_traction(net.x, net.nrm,
+                                                                                               D * down, -1.0)
+        alone = _dislocation_traction(net.x, net.nrm, np.zeros(2), 1.0) + _dislocation_traction(net.x, net.nrm,
+                                                                                                D * down, -1.0)
+        z = -net.x[:, 1]
+        sel = (z > 0.05 * D) & (z < 0.8 * D)
+        scale = np.abs(ref[sel]).max()
+        errs.append(np.abs(fs[-1, sel] - ref[sel]).max() / scale)
+        assert np.abs(fs[-1, sel] - alone[sel]).max() / scale > 1.0
+    assert errs[1] < 0.05 and errs[0] / errs[1] > 1.6, errs
+
+
+def test_half_space_response_is_even_across_the_surface():
+    """P17b: on two parallel faults breaking the surface (different depths and element counts), the full-space
+    tau of the doubled network under the evenly continued slip rate is itself even: each image element carries the
+    stress of its real partner, self and interaction parts alike."""
+    faults = np.array([_surface_fault(0.0, 300.0, 12), _surface_fault(140.0, 200.0, 10)])
+    doubled, mirror, real = O.image_faults(faults)
+    net2 = O.network(doubled, MU, CS)
+    steps = 70
+    V = np.random.default_rng(3).lognormal(size=(steps, 22))
+    tau, _, fs, fi = O.stress_history(net2, V[:, mirror], dict(max_steps=steps, flags=2))
+    partner = np.concatenate([net2.offset[f] + np.arange(2 * n)[::-1] for f, n in enumerate(faults[:, 4].astype(int))])
+    for part in (tau, fs, fi):
+        np.testing.assert_allclose(part[:, partner], part, rtol=1e-11, atol=1e-11 * np.abs(part).max())
+    assert np.abs(fi).max() > 1e-3 * np.abs(fs).max()
+    got = O.half_space_stress_history(faults, MU, CS, V, dict(max_steps=steps, flags=2))[0]
+    np.testing.assert_array_equal(got, tau[:, real])
+
+
+def test_image_faults_maps_and_rejects_networks_off_one_surface():
+    """P17c: the index maps of a three-element fault, and the geometry checks (parallel faults, start ends on one
+    line normal to them)."""
+    doubled, mirror, real = O.image_faults(np.array([_surface_fault(0.0, 30.0, 3), _surface_fault(50.0, 20.0, 2)]))
+    assert mirror.tolist() == [2, 1, 0, 0, 1, 2, 4, 3, 3, 4] and real.tolist() == [3, 4, 5, 8, 9]
+    np.testing.assert_allclose(doubled[0], [0.0, 0.0, -math.pi / 2, 60.0, 6], atol=1e-12)
+    with pytest.raises(ValueError):
+        O.image_faults(np.array([_surface_fault(0.0, 30.0, 3), _surface_fault(50.0, 20.0, 2, phi=-1.2)]))
+    bad = np.array([_surface_fault(0.0, 30.0, 3), _surface_fault(50.0, 20.0, 2)])
+    bad[1, 1] -= 5.0
+    with pytest.raises(ValueError):
+        O.image_faults(bad)
