@@ -95,12 +95,27 @@ typedef struct seas_net seas_net;
 typedef struct seas_op seas_op;
 typedef struct seas_scn seas_scn;
 
-/* One planar fault: centre (m), strike phi (rad), length L (m), number of elements N_f (>= 1). */
+/* One planar fault: centre (m), strike phi (rad), length L (m), number of elements N_f (>= 1), flags
+ * (SEAS_FAULT_*, 0 for a fault in the full space). */
 typedef struct {
     double cx, cy, strike_rad, length;
     int32_t n_elem;
-    int32_t reserved;
+    int32_t flags;
 } seas_fault;
+
+/* SEAS_FAULT_SURFACE_START: a traction-free surface passes through the fault's start end c - (L/2) e'_1, normal to
+ * the fault, with the medium on the e'_1 side (a fault breaking the surface, as the single-fault verification of
+ * App. B).  The library applies the method of images: each fault is continued by its mirror image beyond the start
+ * end (a fault of 2 L_f and 2 N_f elements, the doubled domain of App. B) whose slip rate is the real one continued
+ * evenly across the surface, delta(-z) = delta(z) (which makes the shear traction on the surface vanish), and the
+ * full-space functional of the doubled network is evaluated; the image half's receivers are computed and dropped.
+ * Either every fault of a network carries the flag or none does; flagged faults must be parallel with the same
+ * orientation and have their start ends on one line normal to them (the common surface), else SEAS_EINVAL.
+ * Every vector the caller passes or receives (V, slip, tau, sigma_n, parts, the integrator's state) holds the real
+ * elements only, N = sum N_f; the self windows are those of the doubled faults (L -> 2 L_f, N_f -> 2 N_f), and the
+ * operator queries (seas_plan_hmatrix, seas_op_blocks, seas_op_mode_windows) report the doubled network: its fault
+ * f holds elements 2 off_f .. 2 off_f + 2 N_f - 1, of which 2 off_f + N_f + j is real element off_f + j. */
+#define SEAS_FAULT_SURFACE_START 1
 
 /* Homogeneous medium: shear modulus mu (Pa), shear speed c_s (m/s), P speed c_p (recorded; unused in mode III),
  * and beta in dt = beta * min ds / c_s (the paper uses 1/2). */

@@ -158,6 +158,12 @@ struct seas_net {
     seas_medium med{};
     double dt = 0.0;
     int N = 0, F = 0;
+    // SEAS_FAULT_SURFACE_START (method of images): the network holds the doubled faults; the caller's vectors hold
+    // the N_io real elements, io_map[i] = the real element of element i (-1 - j where i is the image of j)
+    bool images = false;
+    int N_io = 0;
+    std::vector<int32_t> io_map;
+    DArr<int32_t> d_io_map;
     std::vector<int> off;                       // F + 1
     std::vector<double> x, y, e1x, e1y, nx, ny, ds;
     std::vector<int> fault_of;
@@ -366,13 +372,60 @@ double seg_point_dist(double px, double py, double ax, double ay, double bx, dou
 
 namespace {
 
+// Method of images (App. B): every fault's start end lies on one traction-free surface normal to the parallel
+// faults.  Each fault is replaced by its continuation across the surface, centred at the start end, of twice the
+// length and element count; element N_f + j of the doubled fault is real element j, element N_f - 1 - j its image.
+seas_status image_faults(const seas_fault *faults, int n_faults, std::vector<seas_fault> &doubled) {
+    int flagged = 0;
+    for (int f = 0; f < n_faults; ++f) {
+        if (faults[f].flags & ~SEAS_FAULT_SURFACE_START)
+            return fail(SEAS_EINVAL, "fault %d: unknown flags 0x%x", f, faults[f].flags);
+        flagged += (faults[f].flags & SEAS_FAULT_SURFACE_START) ? 1 : 0;
+    }
+    if (flagged == 0) return SEAS_OK;
+    if (flagged != n_faults)
+        return fail(SEAS_EINVAL, "%d of %d faults on the free surface: with images every fault starts on it", flagged,
+                    n_faults);
+    const double c0 = std::cos(faults[0].strike_rad), s0 = std::sin(faults[0].strike_rad);
+    double scale = 0.0;
+    for (int f = 0; f < n_faults; ++f) scale = std::max(scale, std::fabs(faults[f].length));
+    const double x0 = faults[0].cx - 0.5 * faults[0].length * c0, y0 = faults[0].cy - 0.5 * faults[0].length * s0;
+    doubled.assign(faults, faults + n_faults);
+    for (int f = 0; f < n_faults; ++f) {
+        const seas_fault &F = faults[f];
+        const double c1 = std::cos(F.strike_rad), s1 = std::sin(F.strike_rad);
+        if (c1 * c0 + s1 * s0 < 1.0 - 1e-12)
+            return fail(SEAS_EINVAL, "fault %d is not parallel to fault 0 with the same orientation (images)", f);
+        const double xs = F.cx - 0.5 * F.length * c1, ys = F.cy - 0.5 * F.length * s1;
+        if (std::fabs((xs - x0) * c0 + (ys - y0) * s0) > 1e-9 * scale)
+            return fail(SEAS_EINVAL, "fault %d: its start end is off the free surface through fault 0's", f);
+        if (F.n_elem > (1 << 30)) return fail(SEAS_EINVAL, "fault %d: n_elem too large", f);
+        doubled[f].cx = xs;
+        doubled[f].cy = ys;
+        doubled[f].length = 2.0 * F.length;
+        doubled[f].n_elem = 2 * F.n_elem;
+        doubled[f].flags = 0;
+    }
+    return SEAS_OK;
+}
+
 // Host geometry of a network (validation, centroids, frames, dt); no device work.
-seas_status make_geometry(const seas_fault *faults, int n_faults, const seas_medium *med, seas_net &net) {
-    if (!faults || !med) return fail(SEAS_EINVAL, "NULL argument");
+seas_status make_geometry(const seas_fault *faults_in, int n_faults, const seas_medium *med, seas_net &net) {
+    if (!faults_in || !med) return fail(SEAS_EINVAL, "NULL argument");
     if (n_faults < 1) return fail(SEAS_EINVAL, "n_faults must be >= 1");
     if (!(is_fin(med->mu) && med->mu > 0 && is_fin(med->cs) && med->cs > 0 && is_fin(med->beta) && med->beta > 0 &&
           is_fin(med->cp)))
         return fail(SEAS_EINVAL, "medium: mu, cs, beta must be finite and > 0");
+    for (int f = 0; f < n_faults; ++f) {
+        const seas_fault &F = faults_in[f];
+        if (!(is_fin(F.cx) && is_fin(F.cy) && is_fin(F.strike_rad) && is_fin(F.length) && F.length > 0))
+            return fail(SEAS_EINVAL, "fault %d: non-finite or non-positive geometry", f);
+        if (F.n_elem < 1) return fail(SEAS_EINVAL, "fault %d: n_elem %d < 1", f, F.n_elem);
+    }
+    std::vector<seas_fault> doubled;
+    SEAS_TRY(image_faults(faults_in, n_faults, doubled));
+    net.images = !doubled.empty();
+    const seas_fault *faults = net.images ? doubled.data() : faults_in;
     int64_t N = 0;
     for (int f = 0; f < n_faults; ++f) {
         const seas_fault &F = faults[f];
@@ -411,6 +464,17 @@ seas_status make_geometry(const seas_fault *faults, int n_faults, const seas_med
         net.off[f + 1] = net.off[f] + F.n_elem;
     }
     net.dt = med->beta * min_ds / med->cs;
+    net.N_io = net.images ? net.N / 2 : net.N;
+    if (net.images) {
+        net.io_map.resize((size_t)net.N);
+        for (int f = 0; f < n_faults; ++f) {
+            const int n = faults_in[f].n_elem, o = net.off[f], o_io = net.off[f] / 2;
+            for (int j = 0; j < n; ++j) {
+                net.io_map[(size_t)(o + n + j)] = o_io + j;
+                net.io_map[(size_t)(o + n - 1 - j)] = -1 - (o_io + j);
+            }
+        }
+    }
     // A receiver centroid on (or numerically at) another fault's element makes the kernel singular.
     for (int a = 0; a < n_faults; ++a) {
         for (int b = 0; b < n_faults; ++b) {
@@ -450,6 +514,7 @@ extern "C" seas_status seas_build_network(seas_ctx *c, const seas_fault *faults,
     SEAS_TRY(net->d_e1.upload(c, he));
     SEAS_TRY(net->d_n.upload(c, hn));
     SEAS_TRY(net->d_ds.upload(c, net->ds));
+    if (net->images) SEAS_TRY(net->d_io_map.upload(c, net->io_map));
     c->children++;
     *out = net.release();
     return SEAS_OK;
@@ -459,20 +524,22 @@ extern "C" seas_status seas_net_get_info(const seas_net *net, seas_net_info *inf
     if (!net || !info) return fail(SEAS_EINVAL, "NULL argument");
     info->dt = net->dt;
     info->n_faults = net->F;
-    info->n_elem = net->N;
+    info->n_elem = net->N_io;
     return SEAS_OK;
 }
 
 extern "C" seas_status seas_net_get_elements(const seas_net *net, double *centroids, double *normals) {
     if (!net) return fail(SEAS_EINVAL, "NULL network");
-    for (int i = 0; i < net->N; ++i) {
+    for (int k = 0; k < net->N; ++k) {
+        const int i = net->images ? net->io_map[(size_t)k] : k;   // the caller's real elements only
+        if (i < 0) continue;
         if (centroids) {
-            centroids[2 * i] = net->x[i];
-            centroids[2 * i + 1] = net->y[i];
+            centroids[2 * i] = net->x[k];
+            centroids[2 * i + 1] = net->y[k];
         }
         if (normals) {
-            normals[2 * i] = net->nx[i];
-            normals[2 * i + 1] = net->ny[i];
+            normals[2 * i] = net->nx[k];
+            normals[2 * i + 1] = net->ny[k];
         }
     }
     return SEAS_OK;
@@ -1374,6 +1441,8 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     seas_net &net = *op.net;
     StepArgs a{};
     a.N = net.N;
+    a.io_map = net.images ? net.d_io_map.p : nullptr;
+    a.N_io = net.N_io;
     a.F = net.F;
     a.n_self = (int)op.faults_h.size();
     a.B = s.B;
@@ -1649,7 +1718,7 @@ extern "C" seas_status seas_push_slip_rate_steps(seas_scn *s, const double *V, c
                 return fail(SEAS_ESTATE, "push %lld of member %d beyond max_steps %d",
                             (long long)(s->n - s->start[b] + gamma - 1), b, op.hp.max_steps);
     CUDA_TRY(cudaSetDevice(c->device));
-    const int64_t BN = (int64_t)s->B * op.net->N;
+    const int64_t BN = (int64_t)s->B * op.net->N_io;     // the caller's elements
     const double *dV = V, *dS = slip;
     if (mem == SEAS_MEM_HOST) {
         for (int64_t i = 0; i < BN; ++i)
@@ -1705,7 +1774,7 @@ extern "C" seas_status seas_stress_step(seas_scn *s, double *tau, double *sigma_
     seas_op &op = *s->op;
     seas_ctx *c = op.net->ctx;
     CUDA_TRY(cudaSetDevice(c->device));
-    const int64_t BN = (int64_t)s->B * op.net->N;
+    const int64_t BN = (int64_t)s->B * op.net->N_io;     // the caller's elements
     StepArgs a = step_args(*s, s->n - 1);
     double *dtau = mem == SEAS_MEM_DEVICE ? tau : s->d_tau.p;
     double *dparts = parts ? (mem == SEAS_MEM_DEVICE ? parts : s->d_parts.p) : nullptr;
@@ -1799,7 +1868,7 @@ int scenario_view(const seas_scn *s, ScnView *v) {
     v->stream = op.net->ctx->stream;
     v->device = op.net->ctx->device;
     v->B = s->B;
-    v->N = op.net->N;
+    v->N = op.net->N_io;
     v->dt = op.net->dt;
     v->rad = op.net->med.mu / (2.0 * op.net->med.cs);
     v->n = s->n;

@@ -194,6 +194,11 @@ struct StepArgs {
     int N, F, B, n_modes_total;   // elements, faults, batch, sum over the owned faults of (N_f + 1)
     int n_self;                   // faults with a spectral self effect in this operator (the owned ones)
     int max_nf;                   // largest N_f (shared memory of the FFT kernels)
+    // caller's vectors (V, slip in; tau, parts out) with a free surface (method of images): N_io real elements per
+    // scenario, io_map[i] = the real element of element i, -1 - j for the image of real element j; NULL otherwise
+    // (the caller's layout is the network's, N per scenario)
+    const int32_t *io_map;
+    int N_io;
     int64_t step;                 // tick of the step being evaluated (ring slots are tick mod depth)
     int64_t lag_max;              // largest lag with nonzero history: the oldest active member's step (<= step);
                                   // members admitted later have zero history before their first tick

@@ -130,8 +130,14 @@ __global__ void k_push(StepArgs a_, const double *__restrict__ V, const double *
     const int slot = (int)(a.step % a.ring);
     double *vr = a.vring + (int64_t)slot * a.ring_stride;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < BN; e += (int64_t)gridDim.x * blockDim.x) {
-        const double v = V[e];
         const int64_t b = e / a.N, i = e - b * a.N;
+        // the caller's element: itself, or with a free surface the real element whose rate an image carries
+        int64_t ue = e;
+        if (a.io_map) {
+            const int m = a.io_map[i];
+            ue = b * a.N_io + (m >= 0 ? m : -1 - m);
+        }
+        const double v = V[ue];
         vr[i * a.B + b] = v;                           // ring layout [slot][element][scenario]
         if (a.prec == kPrecDF64) {
             const float hi = (float)v;
@@ -150,7 +156,7 @@ __global__ void k_push(StepArgs a_, const double *__restrict__ V, const double *
         const double base = replace_last || j > 1 ? a.slip_prev[e] : a.slip[e];
         double s;
         if (slip_in) {
-            s = gamma == 1 ? slip_in[e] : base + (slip_in[e] - base) * ((double)j / (double)gamma);
+            s = gamma == 1 ? slip_in[ue] : base + (slip_in[ue] - base) * ((double)j / (double)gamma);
         } else {
             s = __dadd_rn(base, __dmul_rn(v, (double)j * a.dt));   // delta^n = delta^{n-1} + dt V^n
         }
@@ -272,18 +278,24 @@ __global__ void __launch_bounds__(kThreads) k_ifft_assemble(StepArgs a_, double 
     const int slot = (int)(a.step % a.ring);
     const double *V = a.vring + (int64_t)slot * a.ring_stride;
     const double *fi = a.fint + (int64_t)b * a.N + fd.off;
-    double *t = tau + (int64_t)b * a.N + fd.off;
+    // the caller's layout: [B][N], or with a free surface [B][N_io] holding the real elements only
+    const int64_t BNo = a.io_map ? (int64_t)a.B * a.N_io : BN;
     for (int m = threadIdx.x; m < N; m += blockDim.x) {
+        int64_t o = (int64_t)b * a.N + fd.off + m;
+        if (a.io_map) {
+            const int u = a.io_map[fd.off + m];
+            if (u < 0) continue;                       // an image element: computed, not returned
+            o = (int64_t)b * a.N_io + u;
+        }
         const double2 zz = z[m >> 1];
         const double fs = 2.0 * ((m & 1) ? zz.y : zz.x);
         const double rad = a.rad * V[(int64_t)(fd.off + m) * a.B + b];
         const double f = fi[m];
-        t[m] = rad + fs + f;
+        tau[o] = rad + fs + f;
         if (parts) {
-            const int64_t o = (int64_t)b * a.N + fd.off + m;
             parts[o] = rad;
-            parts[BN + o] = fs;
-            parts[2 * BN + o] = f;
+            parts[BNo + o] = fs;
+            parts[2 * BNo + o] = f;
         }
     }
 }

@@ -20,6 +20,7 @@ SEAS_EINVAL, SEAS_ENOMEM, SEAS_ECUDA, SEAS_ESTATE, SEAS_EBUSY, SEAS_ETIMEOUT, SE
 SEAS_MEM_HOST, SEAS_MEM_DEVICE = 0, 1
 SEAS_FLAG_DENSE, SEAS_FLAG_NO_TRUNC, SEAS_FLAG_STATIC_TAIL, SEAS_FLAG_LAG_CAP = 1, 2, 4, 8
 SEAS_FLAG_CLUSTER_TRUNC = 16
+SEAS_FAULT_SURFACE_START = 1
 SEAS_PREC_FP64, SEAS_PREC_BF16, SEAS_PREC_FP16S, SEAS_PREC_DF64 = 0, 1, 2, 3
 
 EXPORTED = ["seas_create", "seas_build_network", "seas_net_get_info", "seas_net_get_elements", "seas_build_hmatrix",
@@ -43,7 +44,7 @@ class SeasError(RuntimeError):
 
 class seas_fault(C.Structure):
     _fields_ = [("cx", C.c_double), ("cy", C.c_double), ("strike_rad", C.c_double), ("length", C.c_double),
-                ("n_elem", C.c_int32), ("reserved", C.c_int32)]
+                ("n_elem", C.c_int32), ("flags", C.c_int32)]
 
 
 class seas_medium(C.Structure):
@@ -214,11 +215,20 @@ def seas_create(device: int = 0, hbm_budget: int = 0, stream=None) -> Handle:
 
 
 def _faults(faults):
+    """faults: [F, 5] (cx, cy, strike_rad, length, n_elem) or [F, 6] with SEAS_FAULT_* flags in the last column."""
     faults = np.asarray(faults, dtype=np.float64)
     arr = (seas_fault * len(faults))()
-    for i, (cx, cy, s, L, n) in enumerate(faults):
-        arr[i] = seas_fault(cx, cy, s, L, int(n), 0)
+    for i, row in enumerate(faults):
+        cx, cy, s, L, n = row[:5]
+        arr[i] = seas_fault(cx, cy, s, L, int(n), int(row[5]) if row.shape[0] > 5 else 0)
     return faults, arr
+
+
+def _network_n_elem(faults) -> list:
+    """Elements per fault of the network the library builds: twice N_f for faults on a free surface (method of
+    images), whose operator queries report the doubled faults."""
+    flags = faults[:, 5].astype(int) if faults.shape[1] > 5 else np.zeros(len(faults), dtype=int)
+    return [int(n) * (2 if f & SEAS_FAULT_SURFACE_START else 1) for n, f in zip(faults[:, 4], flags)]
 
 
 def _hparams(hp: dict) -> seas_hparams:
@@ -241,7 +251,7 @@ def seas_plan_hmatrix(faults, mu: float, cs: float, cp: float, beta: float, hp: 
                                    C.byref(dt)))
     blocks = np.zeros((nb.value, 6), dtype=np.int32)
     last = np.zeros((F, F), dtype=np.int32)
-    nel = [int(n) for n in faults[:, 4]]
+    nel = _network_n_elem(faults)
     mw = np.zeros(sum(n + 1 for n in nel), dtype=np.int32)
     _check(lib().seas_plan_hmatrix(arr, F, C.byref(med), C.byref(p), blocks.ctypes.data, nb.value, C.byref(nb),
                                    last.ctypes.data, mw.ctypes.data, C.byref(dt)))
@@ -260,7 +270,7 @@ def seas_ctx_get_memory(ctx: Handle):
 
 
 def seas_build_network(ctx: Handle, faults, mu: float, cs: float, cp: float = 6000.0, beta: float = 0.5) -> Handle:
-    """faults: [F, 5] array (cx, cy, strike_rad, length, n_elem)."""
+    """faults: [F, 5] array (cx, cy, strike_rad, length, n_elem), or [F, 6] with SEAS_FAULT_* flags."""
     faults, arr = _faults(faults)
     med = seas_medium(mu, cs, cp, beta)
     h = C.c_void_p()
@@ -268,7 +278,7 @@ def seas_build_network(ctx: Handle, faults, mu: float, cs: float, cp: float = 60
     info = seas_net_info()
     _check(lib().seas_net_get_info(h, C.byref(info)))
     return Handle(h, "net", ctx=ctx, N=info.n_elem, F=info.n_faults, dt=info.dt,
-                  n_elem=[int(n) for n in faults[:, 4]])
+                  n_elem_net=_network_n_elem(faults))
 
 
 def seas_net_get_info(net: Handle) -> dict:
@@ -317,7 +327,7 @@ def seas_op_blocks(op: Handle) -> np.ndarray:
 
 
 def seas_op_mode_windows(op: Handle) -> list:
-    n_elem = op.net.n_elem
+    n_elem = op.net.n_elem_net
     flat = np.zeros(sum(n + 1 for n in n_elem), dtype=np.int32)
     _check(lib().seas_op_mode_windows(op.ptr, flat.ctypes.data))
     out, o = [], 0
