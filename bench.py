@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 8-scenario ensemble runs")
     ap.add_argument("--no-tail", action="store_true", help="skip the static-tail run")
     ap.add_argument("--no-cluster", action="store_true", help="skip the cluster-level end truncation run")
+    ap.add_argument("--no-surface", action="store_true", help="skip the free-surface (method of images) run")
     ap.add_argument("--no-oracle-rows", action="store_true", help="skip the oracle interaction rows (errors)")
     ap.add_argument("--dump-step-bytes", default=None, help="write the per-step algorithmic interaction bytes here")
     ap.add_argument("--served-seconds", type=float, default=15.0, help="wall time of the served run (0: skip)")
@@ -619,6 +620,27 @@ def run_ours(args, w, start, K, W):
         s5.close()
         del r5
 
+    # a fault breaking a traction-free surface (method of images), the shape of App. B's single-fault check: the
+    # self term of the doubled 3200-element fault per step (no interaction), the deepest K steps of 2000
+    surface = None
+    if not args.no_surface:
+        ws = synth.surface_fault_1600(steps=w.steps)
+        Vs = torch.from_numpy(ws.slip_rate(0, 0, ws.steps)).to(device)
+        ss = seas.Session(ws, device=local, stream=stream.cuda_stream)
+        s0 = ws.steps - K
+        advance(seas, torch, ss.scn, Vs, 0, s0, device)
+        ms_s, per_s, _, _ = timed_run(seas, torch, ss.scn, Vs, s0, K, dist, device)
+        seas.seas_scenario_check(ss.scn)
+        ms_s = max_over_ranks(dist, ms_s, device)
+        surface = {"workload": ws.name, "elements": ws.N, "elements_with_images": 2 * ws.N, "steps": ws.steps,
+                   "timed_window": [s0, s0 + K], "value": job_rate(ws.N * K, world, ms_s / 1e3), "unit": METRIC,
+                   "ms_per_step": ms_s / K, "p50_ms": float(np.percentile(per_s, 50)),
+                   "bytes_self": ss.stats["bytes_self"],
+                   "parity": "against the oracle's doubled network at 64 and 2 x 40 elements (GPU tests)"}
+        log(f"surface fault {surface['value'] / 1e6:.3f} M element-steps/s, {ms_s / K:.3f} ms per step")
+        ss.close()
+        del Vs
+
     # plain FP64 GPU path: every block dense (leaf blocks, exact windows), no compression, FP64 arithmetic
     plain = None
     if not args.no_plain:
@@ -668,7 +690,7 @@ def run_ours(args, w, start, K, W):
                     "n_blocks_far", "n_blocks_near", "compression_ratio", "bytes_interaction", "mean_rank",
                     "max_rank", "build_seconds", "n_tasks")},
                 "vs_plain_fp64_gpu": plain, "variants": variants, "batched": batched, "static_tail": tail,
-                "cluster_trunc": cluster, "e2e": e2e,
+                "cluster_trunc": cluster, "surface_fault": surface, "e2e": e2e,
                 "served": served, "ensemble_8x8": ensemble, "graph": graph,
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
                 "autotune": {"consumer_warps": s.tune["consumer_warps"], "median_launch_ms": s.tune["ms"],

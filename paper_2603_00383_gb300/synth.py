@@ -12,6 +12,8 @@ Workloads (shapes follow the paper's benchmarks; the paper's own data are not us
 * ``six_fault_3072``  -- six non-intersecting faults of 256..768 elements (3072 in total, 20 m elements) placed at
   random in a 40 x 40 km box (the paper's ~3e3-DOF scale, abstract and Sec. 3.1).
 * ``paper_two_fault`` -- the exact two-fault geometry printed in Sec. 3.1 (centroids, lengths, normals; Table 1).
+* ``surface_fault_1600`` -- one fault breaking a traction-free surface, 40 km deep, 1600 elements (doubled to
+  3200 by the method of images), the shape of the paper's single-fault verification (App. B).
 * ``tiny``            -- 2..3 faults of 4..16 elements for brute-force checks.
 * ``ensemble``        -- random networks for batched / served runs (2..12 faults, 500..6000 elements).
 
@@ -63,7 +65,7 @@ class Workload:
     """One synthetic stress-transfer workload: network, medium, operator parameters and slip-rate statistics."""
 
     name: str
-    faults: np.ndarray                 # [F, 5]: cx, cy, strike_rad, length, n_elem
+    faults: np.ndarray                 # [F, 5]: cx, cy, strike_rad, length, n_elem (+ fault flags, optional)
     mu: float = 32e9
     cs: float = 3464.0
     cp: float = 6000.0
@@ -242,7 +244,21 @@ def ensemble_network(geom_id: int, seed: int = SEED) -> Workload:
                     hparams=_hp(leaf=32, eta_h=2.0, aca_tol=1e-6, max_steps=steps))
 
 
-WORKLOADS = {"two_fault_128": two_fault_128, "six_fault_3072": six_fault_3072, "paper_two_fault": paper_two_fault}
+FAULT_SURFACE_START = 1   # mirror of the C header's SEAS_FAULT_SURFACE_START (a fault flag; an input)
+
+
+def surface_fault_1600(steps: int = 2000, n_real: int = 1600, depth: float = 40000.0) -> Workload:
+    """The shape of the single-fault verification of App. B: one vertical fault from the free surface (y = 0) down
+    to 40 km, 1600 elements of 25 m, which the library doubles across the surface to an 80 km fault of 3200
+    elements (method of images); self windows with eta_w = 2 and q_w = N_elts / 2 = 1600 on the doubled fault."""
+    fault = (0.0, -0.5 * depth, -0.5 * math.pi, depth, n_real, FAULT_SURFACE_START)
+    return Workload("surface_fault_1600", np.array([fault]), steps=steps,
+                    hparams=dict(leaf=32, eta_h=2.0, aca_tol=1e-6, eta_tmin=0.01, eta_tmax=0.01, eta_w=2.0,
+                                 q_w=n_real, max_steps=steps))
+
+
+WORKLOADS = {"two_fault_128": two_fault_128, "six_fault_3072": six_fault_3072, "paper_two_fault": paper_two_fault,
+             "surface_fault_1600": surface_fault_1600}
 
 
 def served_network(geom_id: int, seed: int = SEED, n_lo: int = 256, n_hi: int = 8000, max_steps: int = 1000,
