@@ -187,6 +187,8 @@ struct seas_op {
     std::vector<ModeDev> modes_h;
     std::vector<int32_t> mode_W;     // per fault, modes 0..N_f
     DArr<FaultDev> d_faults;
+    DArr<int32_t> d_big;             // owned faults whose FFTs run on a thread-block cluster
+    int n_big = 0;
     DArr<ModeDev> d_modes;
     DArr<double> d_w;
     DArr<double2> d_tw;
@@ -763,6 +765,26 @@ seas_status build_self(seas_op &op) {
         if ((int)rp.size() > kMaxStages) return fail(SEAS_EINVAL, "fault %d: FFT plan too deep", f);
         fd.nstages = (int)rp.size();
         for (size_t s = 0; s < rp.size(); ++s) fd.radix[s] = rp[s];
+        // large faults: a four-step factorisation N_f = n1 n2 with both factors multiples of the cluster size,
+        // n1 the one nearest sqrt(N_f) (the FFT then spreads over kFftCluster SMs)
+        if (nf >= kFftClusterMin) {
+            int best = 0;
+            for (int n1 = kFftCluster; n1 <= nf / kFftCluster; n1 += kFftCluster)
+                if (nf % n1 == 0 && (nf / n1) % kFftCluster == 0 &&
+                    (best == 0 || std::fabs(n1 - std::sqrt((double)nf)) < std::fabs(best - std::sqrt((double)nf))))
+                    best = n1;
+            if (best > 0) {
+                const std::vector<int> p1 = radix_plan(best), p2 = radix_plan(nf / best);
+                if ((int)p1.size() <= kMaxStages && (int)p2.size() <= kMaxStages) {
+                    fd.n1 = best;
+                    fd.n2 = nf / best;
+                    fd.nst1 = (int)p1.size();
+                    fd.nst2 = (int)p2.size();
+                    for (size_t s = 0; s < p1.size(); ++s) fd.radix1[s] = p1[s];
+                    for (size_t s = 0; s < p2.size(); ++s) fd.radix2[s] = p2[s];
+                }
+            }
+        }
         fd.tw_off = (int64_t)tw.size();
         for (int k = 0; k < nf; ++k) {
             const long double ang = -2 * pi * k / nf;
@@ -798,6 +820,11 @@ seas_status build_self(seas_op &op) {
         op.max_nf = std::max(op.max_nf, nf);
     }
     SEAS_TRY(op.d_faults.upload(c, op.faults_h));
+    std::vector<int32_t> big;
+    for (size_t k = 0; k < op.faults_h.size(); ++k)
+        if (op.faults_h[k].n1 > 0) big.push_back((int32_t)k);
+    op.n_big = (int)big.size();
+    if (!big.empty()) SEAS_TRY(op.d_big.upload(c, big));
     SEAS_TRY(op.d_modes.upload(c, op.modes_h));
     SEAS_TRY(op.d_tw.upload(c, tw));
     SEAS_TRY(op.d_w.alloc(c, (size_t)w_total));
@@ -1445,6 +1472,9 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     a.N_io = net.N_io;
     a.F = net.F;
     a.n_self = (int)op.faults_h.size();
+    a.big = op.d_big.p;
+    a.n_big = op.n_big;
+    a.n_small = a.n_self - op.n_big;
     a.B = s.B;
     a.n_modes_total = op.n_modes_total;
     a.max_nf = op.max_nf;

@@ -12,6 +12,8 @@ namespace seas {
 constexpr int kThreads = 256;       // threads per CTA of every kernel
 constexpr int kMaxFFT = 7168;       // largest N_f: two N_f-point complex buffers fit in shared memory
 constexpr int kMaxStages = 16;      // radix stages of one FFT plan
+constexpr int kFftCluster = 8;      // CTAs of the thread-block cluster that runs one large fault's FFT
+constexpr int kFftClusterMin = 2048;  // N_f from which a fault's FFTs run on a cluster (when N_f factors suitably)
 constexpr int kMaxBlockSide = 1024; // rows / columns of one H-matrix block (4 accumulator rows per thread)
 constexpr int kRowsPerThread = kMaxBlockSide / kThreads;
 constexpr int kItemRows = 256;      // rows of one pass-2 item (bounds its staged history / z rows)
@@ -71,6 +73,10 @@ struct FaultDev {
     int32_t nstages;
     int32_t radix[kMaxStages];
     double kfac;        // -(mu / 2) * pi / L_f, so that F_n = kfac * n * sum_T w_n^T D_n^{t-T}
+    // four-step plan of a large fault's FFT on a cluster of kFftCluster CTAs: N_f = n1 n2, both multiples of
+    // kFftCluster (n1 = 0: the fault's FFTs run on one CTA)
+    int32_t n1, n2, nst1, nst2;
+    int32_t radix1[kMaxStages], radix2[kMaxStages];
 };
 
 // One spectral mode n >= 1 of one fault.
@@ -199,6 +205,9 @@ struct StepArgs {
     // (the caller's layout is the network's, N per scenario)
     const int32_t *io_map;
     int N_io;
+    // faults whose FFTs run on a thread-block cluster (indices into faults), and how many run on one CTA
+    const int32_t *big;
+    int n_big, n_small;
     int64_t step;                 // tick of the step being evaluated (ring slots are tick mod depth)
     int64_t lag_max;              // largest lag with nonzero history: the oldest active member's step (<= step);
                                   // members admitted later have zero history before their first tick

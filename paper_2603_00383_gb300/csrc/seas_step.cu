@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cooperative_groups.h>
+
 #include <atomic>
 #include <type_traits>
 
@@ -37,78 +39,112 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
 // ------------------------------------------------------------------------------------------------------------
-// Self-sorting (Stockham) mixed-radix FFT of N points held in shared memory, radices 2, 3, 4, 5, 7, 11, 13, 17, 19,
-// 23 (the odd primes as plain R-point DFTs).  Stage with radix R after sub-transforms of size Ns: butterfly j takes
-// src[j + r N/R] (r < R), twiddles it by
+// Self-sorting (Stockham) mixed-radix FFTs of N points held in shared memory, radices 2, 3, 4, 5, 7, 11, 13, 17, 19,
+// 23 (the odd primes as plain R-point DFTs); nb independent transforms stored one after another.  Stage with radix R
+// after sub-transforms of size Ns: butterfly j takes src[j + r N/R] (r < R), twiddles it by
 // W_{Ns R}^{r (j mod Ns)}, takes an R-point DFT and writes dst[(j / Ns) Ns R + (j mod Ns) + t Ns].
-// tw[k] = e^{-2 pi i k / N}; the inverse (unnormalised) uses conjugate twiddles.  Returns the buffer holding the
-// result.  All threads of the CTA must call it.
+// tw[k ts] = e^{-2 pi i k / N} (ts = 1 for the fault's own table; a factor of the fault's N_f reads that table with
+// stride N_f / N); the inverse (unnormalised) uses conjugate twiddles.  Returns the buffer holding the result.
+// All threads of the CTA must call it; wsh is shared scratch of kFftRadixMax entries (the DFT constants of the
+// odd-prime radices >= 7, read there as broadcasts instead of held in registers: with them in registers every
+// stage of the kernel was compiled at the register limit with spills).
 // ------------------------------------------------------------------------------------------------------------
+constexpr int kFftRadixMax = 23;
+
 template <int R>
 __device__ __forceinline__ void fft_stage(const double2 *__restrict__ src, double2 *__restrict__ dst, int N, int Ns,
-                                          const double2 *__restrict__ tw, bool inverse) {
+                                          const double2 *__restrict__ tw, int ts, int nb, bool inverse,
+                                          double2 *wsh) {
     const int NR = N / R;
     const int tstride = N / (Ns * R);
     // R-point DFT constants W_R^m, m < R (conjugated for the inverse)
-    double2 wr[R];
+    constexpr bool kShared = R >= 7;
+    double2 wr[kShared ? 1 : R];
+    if constexpr (kShared) {
+        for (int m = threadIdx.x; m < R; m += blockDim.x) {
+            const double2 w = tw[m * NR * ts];
+            wsh[m] = inverse ? cconj(w) : w;
+        }
+        __syncthreads();
+    } else {
 #pragma unroll
-    for (int m = 0; m < R; ++m) {
-        double2 w = tw[m * NR];
-        wr[m] = inverse ? cconj(w) : w;
+        for (int m = 0; m < R; ++m) {
+            const double2 w = tw[m * NR * ts];
+            wr[m] = inverse ? cconj(w) : w;
+        }
     }
-    for (int j = threadIdx.x; j < NR; j += blockDim.x) {
+    for (int jt = threadIdx.x; jt < nb * NR; jt += blockDim.x) {
+        const int sub = jt / NR, j = jt - sub * NR;       // sub-transform, butterfly within it
+        const double2 *__restrict__ sv = src + sub * N;
+        double2 *__restrict__ dv = dst + sub * N;
         const int k = j % Ns;
         double2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            double2 x = src[j + r * NR];
+            double2 x = sv[j + r * NR];
             if (r > 0) {
-                double2 w = tw[k * r * tstride];
+                double2 w = tw[k * r * tstride * ts];
                 x = cmul(x, inverse ? cconj(w) : w);
             }
             v[r] = x;
         }
         const int d = (j / Ns) * Ns * R + k;
         if (R == 2) {
-            dst[d] = cadd(v[0], v[1]);
-            dst[d + Ns] = csub(v[0], v[1]);
+            dv[d] = cadd(v[0], v[1]);
+            dv[d + Ns] = csub(v[0], v[1]);
         } else if (R == 4) {
             // W_4 = -i (forward), +i (inverse)
             const double2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
             const double2 b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
             const double2 jb1 = inverse ? make_double2(-b1.y, b1.x) : make_double2(b1.y, -b1.x);
-            dst[d] = cadd(a0, b0);
-            dst[d + Ns] = cadd(a1, jb1);
-            dst[d + 2 * Ns] = csub(a0, b0);
-            dst[d + 3 * Ns] = csub(a1, jb1);
+            dv[d] = cadd(a0, b0);
+            dv[d + Ns] = cadd(a1, jb1);
+            dv[d + 2 * Ns] = csub(a0, b0);
+            dv[d + 3 * Ns] = csub(a1, jb1);
         } else {
+            if constexpr (kShared) {
+                // one output at a time (the R inputs stay in registers), constants W_R^{r t mod R} from shared
+#pragma unroll 1
+                for (int t = 0; t < R; ++t) {
+                    double2 acc = v[0];
+                    int idx = 0;
 #pragma unroll
-            for (int t = 0; t < R; ++t) {
-                double2 acc = v[0];
+                    for (int r = 1; r < R; ++r) {
+                        idx += t;
+                        if (idx >= R) idx -= R;
+                        acc = cadd(acc, cmul(v[r], wsh[idx]));
+                    }
+                    dv[d + t * Ns] = acc;
+                }
+            } else {
 #pragma unroll
-                for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], wr[(r * t) % R]));
-                dst[d + t * Ns] = acc;
+                for (int t = 0; t < R; ++t) {
+                    double2 acc = v[0];
+#pragma unroll
+                    for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], wr[(r * t) % R]));
+                    dv[d + t * Ns] = acc;
+                }
             }
         }
     }
 }
 
 __device__ double2 *fft_stockham(double2 *src, double2 *dst, int N, const int *radix, int nstages,
-                                 const double2 *__restrict__ tw, bool inverse) {
+                                 const double2 *__restrict__ tw, int ts, int nb, bool inverse, double2 *wsh) {
     int Ns = 1;
     for (int st = 0; st < nstages; ++st) {
         const int R = radix[st];
         switch (R) {
-            case 2: fft_stage<2>(src, dst, N, Ns, tw, inverse); break;
-            case 3: fft_stage<3>(src, dst, N, Ns, tw, inverse); break;
-            case 4: fft_stage<4>(src, dst, N, Ns, tw, inverse); break;
-            case 5: fft_stage<5>(src, dst, N, Ns, tw, inverse); break;
-            case 7: fft_stage<7>(src, dst, N, Ns, tw, inverse); break;
-            case 11: fft_stage<11>(src, dst, N, Ns, tw, inverse); break;
-            case 13: fft_stage<13>(src, dst, N, Ns, tw, inverse); break;
-            case 17: fft_stage<17>(src, dst, N, Ns, tw, inverse); break;
-            case 19: fft_stage<19>(src, dst, N, Ns, tw, inverse); break;
-            default: fft_stage<23>(src, dst, N, Ns, tw, inverse); break;
+            case 2: fft_stage<2>(src, dst, N, Ns, tw, ts, nb, inverse, wsh); break;
+            case 3: fft_stage<3>(src, dst, N, Ns, tw, ts, nb, inverse, wsh); break;
+            case 4: fft_stage<4>(src, dst, N, Ns, tw, ts, nb, inverse, wsh); break;
+            case 5: fft_stage<5>(src, dst, N, Ns, tw, ts, nb, inverse, wsh); break;
+            case 7: fft_stage<7>(src, dst, N, Ns, tw, ts, nb, inverse, wsh); break;
+            case 11: fft_stage<11>(src, dst, N, Ns, tw, ts, nb, inverse, wsh); break;
+            case 13: fft_stage<13>(src, dst, N, Ns, tw, ts, nb, inverse, wsh); break;
+            case 17: fft_stage<17>(src, dst, N, Ns, tw, ts, nb, inverse, wsh); break;
+            case 19: fft_stage<19>(src, dst, N, Ns, tw, ts, nb, inverse, wsh); break;
+            default: fft_stage<23>(src, dst, N, Ns, tw, ts, nb, inverse, wsh); break;
         }
         __syncthreads();
         double2 *tmp = src;
@@ -166,6 +202,25 @@ __global__ void k_push(StepArgs a_, const double *__restrict__ V, const double *
     }
 }
 
+// The padded real transform from the half-length complex one: X_k = E_k + e^{-2 pi i k/M} O_k with
+// E_k = (Z_k + conj Z_{N-k}) / 2, O_k = (Z_k - conj Z_{N-k}) / (2i); zc = conj Z_{N-k}, pk = e^{-2 pi i k/M}.
+__device__ __forceinline__ double2 real_post(double2 zk, double2 zc, double2 pk) {
+    const double2 E = make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y));
+    const double2 dd = csub(zk, zc);
+    const double2 O = make_double2(0.5 * dd.y, -0.5 * dd.x);
+    return cadd(E, cmul(pk, O));
+}
+
+// The inverse: Z_k = E_k + i O_k from the modes F_k (F_0 = 0) and conj F_{N-k}, pk = e^{-2 pi i k/M}.
+__device__ __forceinline__ double2 real_pre(const double2 *__restrict__ Fm, int k, int N, double2 pk) {
+    const double2 A = k == 0 ? make_double2(0.0, 0.0) : Fm[k];
+    const double2 Bc = cconj(Fm[N - k]);
+    const double2 E = make_double2(0.5 * (A.x + Bc.x), 0.5 * (A.y + Bc.y));
+    const double2 dd = cmul(csub(A, Bc), cconj(pk));
+    const double2 O = make_double2(0.5 * dd.x, 0.5 * dd.y);
+    return make_double2(E.x - O.y, E.y + O.x);
+}
+
 // Spectral coefficients of the zero-padded slip (Eq. functional_no_replication): D_k = (1/M) sum_{j<N_f}
 // delta_j e^{-2 pi i k j / M}, M = 2 N_f, k = 0..N_f, from one N_f-point complex FFT of z_j = x_{2j} + i x_{2j+1}
 // (x = delta padded with zeros): X_k = E_k + e^{-2 pi i k/M} O_k, E_k = (Z_k + conj Z_{N-k})/2,
@@ -175,6 +230,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_forward(StepArgs a_) {
     apply_dyn(a);
     extern __shared__ double2 smem[];
     const FaultDev &fd = a.faults[blockIdx.x];
+    if (fd.n1 > 0) return;                             // a large fault: its FFT runs on a cluster
     const int b = blockIdx.y;
     const int N = fd.nf;
     double2 *b0 = smem, *b1 = smem + N;
@@ -186,17 +242,12 @@ __global__ void __launch_bounds__(kThreads) k_fft_forward(StepArgs a_) {
     __syncthreads();
     const double2 *tw = a.tw + fd.tw_off;
     const double2 *post = tw + N;
-    double2 *Z = fft_stockham(b0, b1, N, fd.radix, fd.nstages, tw, false);
+    double2 *Z = fft_stockham(b0, b1, N, fd.radix, fd.nstages, tw, 1, 1, false, smem + 2 * a.max_nf);
     const double invM = 1.0 / (2.0 * N);
     const int slot = (int)(a.step % fd.ring);
     double2 *ring = a.dring + fd.dring_off + (int64_t)b * (N + 1) * fd.ring + slot;
     for (int k = threadIdx.x; k <= N; k += blockDim.x) {
-        const double2 zk = Z[k == N ? 0 : k];
-        const double2 zc = cconj(Z[k == 0 ? 0 : N - k]);
-        const double2 E = make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y));
-        const double2 dd = csub(zk, zc);
-        const double2 O = make_double2(0.5 * dd.y, -0.5 * dd.x);
-        const double2 X = cadd(E, cmul(post[k], O));
+        const double2 X = real_post(Z[k == N ? 0 : k], cconj(Z[k == 0 ? 0 : N - k]), post[k]);
         ring[(int64_t)k * fd.ring] = make_double2(X.x * invM, X.y * invM);
     }
 }
@@ -249,6 +300,29 @@ __global__ void __launch_bounds__(kThreads) k_modeconv(StepArgs a_) {
     }
 }
 
+// Element m of fault fd in scenario b: tau = radiation damping + self (fs) + interaction, and the three parts, in
+// the caller's layout: [B][N], or with a free surface [B][N_io] holding the real elements only.
+__device__ __forceinline__ void assemble_out(const StepArgs &a, const FaultDev &fd, int b, int m, double fs,
+                                            const double *__restrict__ V, double *__restrict__ tau,
+                                            double *__restrict__ parts) {
+    int64_t o = (int64_t)b * a.N + fd.off + m;
+    int64_t BNo = (int64_t)a.B * a.N;
+    if (a.io_map) {
+        const int u = a.io_map[fd.off + m];
+        if (u < 0) return;                             // an image element: computed, not returned
+        o = (int64_t)b * a.N_io + u;
+        BNo = (int64_t)a.B * a.N_io;
+    }
+    const double rad = a.rad * V[(int64_t)(fd.off + m) * a.B + b];
+    const double f = a.fint[(int64_t)b * a.N + fd.off + m];
+    tau[o] = rad + fs + f;
+    if (parts) {
+        parts[o] = rad;
+        parts[BNo + o] = fs;
+        parts[2 * BNo + o] = f;
+    }
+}
+
 // Inverse transform and assembly: f_self,j = sum_{n=-N_f+1}^{N_f} F_n e^{2 pi i n j / M} (F_{-n} = conj F_n,
 // F_0 = 0), kept for j < N_f, from one N_f-point inverse complex FFT; then
 // tau = -(mu / 2 c_s) V + f_self + f_int (Eq. superimposition2).
@@ -258,45 +332,140 @@ __global__ void __launch_bounds__(kThreads) k_ifft_assemble(StepArgs a_, double 
     apply_dyn(a);
     extern __shared__ double2 smem[];
     const FaultDev &fd = a.faults[blockIdx.x];
+    if (fd.n1 > 0) return;                             // a large fault: its FFT runs on a cluster
     const int b = blockIdx.y;
     const int N = fd.nf;
     double2 *b0 = smem, *b1 = smem + N;
     const double2 *Fm = a.fmodes + (int64_t)b * a.n_modes_total + fd.mode_off;
     const double2 *tw = a.tw + fd.tw_off;
     const double2 *post = tw + N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const double2 A = k == 0 ? make_double2(0.0, 0.0) : Fm[k];
-        const double2 Bc = cconj(Fm[N - k]);
-        const double2 E = make_double2(0.5 * (A.x + Bc.x), 0.5 * (A.y + Bc.y));
-        const double2 dd = cmul(csub(A, Bc), cconj(post[k]));
-        const double2 O = make_double2(0.5 * dd.x, 0.5 * dd.y);
-        b0[k] = make_double2(E.x - O.y, E.y + O.x);      // Z_k = E_k + i O_k
+    for (int k = threadIdx.x; k < N; k += blockDim.x) b0[k] = real_pre(Fm, k, N, post[k]);
+    __syncthreads();
+    const double2 *z = fft_stockham(b0, b1, N, fd.radix, fd.nstages, tw, 1, 1, true, smem + 2 * a.max_nf);
+    const double *V = a.vring + (int64_t)(a.step % a.ring) * a.ring_stride;
+    for (int m = threadIdx.x; m < N; m += blockDim.x) {
+        const double2 zz = z[m >> 1];
+        assemble_out(a, fd, b, m, 2.0 * ((m & 1) ? zz.y : zz.x), V, tau, parts);
+    }
+}
+
+// Large faults (N_f = n1 n2, both multiples of kFftCluster): the FFTs run on a thread-block cluster of
+// kFftCluster CTAs, one per SM, because one SM's FP64 pipe (2 FMA per clock) bounds a one-CTA transform of a few
+// thousand points at ~0.1 ms.  Four-step factorisation: with j = n2' n1 + n2 (n2' = n2 of the plan) and
+// k = k1 + n1 k2,  Z_k = sum_{n2} W_{n2'}^{n2 k2} [W_N^{n2 k1} sum_{n1} W_{n1'}^{n1 k1} z_j]: CTA r transforms the
+// columns n2 in [r c2, (r + 1) c2) (c2 = n2' / C) and keeps them, twiddled, in its shared memory; after a cluster
+// barrier it gathers the rows k1 in [r c1, (r + 1) c1) from all CTAs' shared memory (distributed shared memory)
+// and transforms them.  Each CTA then holds Z_k for its rows; the forward pass reads conj Z_{N-k} from the CTA
+// holding row (n1' - k1) mod n1'.
+namespace cg = cooperative_groups;
+
+struct FftCl {
+    int N, N1, N2, c1, c2, chunk, r;
+    double2 *Y, *w0, *w1, *wsh;
+};
+
+__device__ __forceinline__ FftCl fft_cl_setup(const FaultDev &fd, double2 *smem, int r) {
+    FftCl q;
+    q.N = fd.nf;
+    q.N1 = fd.n1;
+    q.N2 = fd.n2;
+    q.c1 = q.N1 / kFftCluster;
+    q.c2 = q.N2 / kFftCluster;
+    q.chunk = q.N / kFftCluster;
+    q.r = r;
+    q.Y = smem;
+    q.w0 = smem + q.chunk;
+    q.w1 = smem + 2 * q.chunk;
+    q.wsh = smem + 3 * q.chunk;
+    return q;
+}
+
+// Columns (already in w0 as [c2][n1']) -> twiddled Y; cluster barrier; rows gathered into w0 ([c1][n2']) and
+// transformed.  Returns the buffer holding Z_{k1 + n1' k2} at [p][k2], k1 = r c1 + p.
+__device__ const double2 *fft_cl_run(cg::cluster_group &cl, const FaultDev &fd, const FftCl &q,
+                                     const double2 *__restrict__ tw, bool inverse) {
+    const double2 *A = fft_stockham(q.w0, q.w1, q.N1, fd.radix1, fd.nst1, tw, q.N2, q.c2, inverse, q.wsh);
+    for (int t = threadIdx.x; t < q.chunk; t += blockDim.x) {
+        const int c = t / q.N1, k1 = t - c * q.N1;
+        const double2 w = tw[(q.r * q.c2 + c) * k1];                 // W_N^{n2 k1}
+        q.Y[t] = cmul(A[t], inverse ? cconj(w) : w);
+    }
+    cl.sync();
+    for (int t = threadIdx.x; t < q.chunk; t += blockDim.x) {
+        const int p = t / q.N2, n2 = t - p * q.N2;
+        const double2 *Yr = cl.map_shared_rank(q.Y, n2 / q.c2);
+        q.w0[t] = Yr[(n2 % q.c2) * q.N1 + q.r * q.c1 + p];
     }
     __syncthreads();
-    const double2 *z = fft_stockham(b0, b1, N, fd.radix, fd.nstages, tw, true);
-    const int64_t BN = (int64_t)a.B * a.N;
-    const int slot = (int)(a.step % a.ring);
-    const double *V = a.vring + (int64_t)slot * a.ring_stride;
-    const double *fi = a.fint + (int64_t)b * a.N + fd.off;
-    // the caller's layout: [B][N], or with a free surface [B][N_io] holding the real elements only
-    const int64_t BNo = a.io_map ? (int64_t)a.B * a.N_io : BN;
-    for (int m = threadIdx.x; m < N; m += blockDim.x) {
-        int64_t o = (int64_t)b * a.N + fd.off + m;
-        if (a.io_map) {
-            const int u = a.io_map[fd.off + m];
-            if (u < 0) continue;                       // an image element: computed, not returned
-            o = (int64_t)b * a.N_io + u;
-        }
-        const double2 zz = z[m >> 1];
-        const double fs = 2.0 * ((m & 1) ? zz.y : zz.x);
-        const double rad = a.rad * V[(int64_t)(fd.off + m) * a.B + b];
-        const double f = fi[m];
-        tau[o] = rad + fs + f;
-        if (parts) {
-            parts[o] = rad;
-            parts[BNo + o] = fs;
-            parts[2 * BNo + o] = f;
-        }
+    return fft_stockham(q.w0, q.w1, q.N2, fd.radix2, fd.nst2, tw, q.N1, q.c1, inverse, q.wsh);
+}
+
+__global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads) k_fft_forward_cl(StepArgs a_) {
+    StepArgs a = a_;
+    apply_dyn(a);
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double2 smem[];
+    const FaultDev &fd = a.faults[a.big[blockIdx.x / kFftCluster]];
+    const FftCl q = fft_cl_setup(fd, smem, (int)cl.block_rank());
+    const int b = blockIdx.y, N = q.N;
+    const double2 *tw = a.tw + fd.tw_off;
+    const double *x = a.slip + (int64_t)b * a.N + fd.off;
+    for (int t = threadIdx.x; t < q.chunk; t += blockDim.x) {      // z_j = x_2j + i x_2j+1, j = n2' n1 + n2
+        const int c = t / q.N1, n1 = t - c * q.N1;
+        const int j = q.N2 * n1 + q.r * q.c2 + c;
+        const int e = 2 * j, o = 2 * j + 1;
+        q.w0[t] = make_double2(e < N ? x[e] : 0.0, o < N ? x[o] : 0.0);
+    }
+    __syncthreads();
+    const double2 *Z = fft_cl_run(cl, fd, q, tw, false);
+    cl.sync();
+    const double2 *post = tw + N;
+    const double invM = 1.0 / (2.0 * N);
+    const int slot = (int)(a.step % fd.ring);
+    double2 *ring = a.dring + fd.dring_off + (int64_t)b * (N + 1) * fd.ring + slot;
+    const int count = q.chunk + (q.r == 0 ? 1 : 0);                // rank 0 also writes k = N_f (from Z_0)
+    for (int t = threadIdx.x; t < count; t += blockDim.x) {
+        const int tt = t == q.chunk ? 0 : t;
+        const int p = tt / q.N2, k2 = tt - p * q.N2;
+        const int k1 = q.r * q.c1 + p;
+        const int k = t == q.chunk ? N : k1 + q.N1 * k2;
+        // N - k mod N = (n1' - k1) + n1' (n2' - 1 - k2) for k1 > 0, n1' ((n2' - k2) mod n2') for k1 = 0
+        const int k1p = k1 == 0 ? 0 : q.N1 - k1;
+        const int k2p = k1 == 0 ? (q.N2 - k2) % q.N2 : q.N2 - 1 - k2;
+        const double2 *Zr = cl.map_shared_rank(Z, k1p / q.c1);
+        const double2 X = real_post(Z[tt], cconj(Zr[(k1p % q.c1) * q.N2 + k2p]), post[k]);
+        ring[(int64_t)k * fd.ring] = make_double2(X.x * invM, X.y * invM);
+    }
+    cl.sync();                                                     // others read this CTA's rows until here
+}
+
+__global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads)
+    k_ifft_assemble_cl(StepArgs a_, double *__restrict__ tau, double *__restrict__ parts) {
+    StepArgs a = a_;
+    apply_dyn(a);
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double2 smem[];
+    const FaultDev &fd = a.faults[a.big[blockIdx.x / kFftCluster]];
+    const FftCl q = fft_cl_setup(fd, smem, (int)cl.block_rank());
+    const int b = blockIdx.y, N = q.N;
+    const double2 *tw = a.tw + fd.tw_off;
+    const double2 *post = tw + N;
+    const double2 *Fm = a.fmodes + (int64_t)b * a.n_modes_total + fd.mode_off;
+    for (int t = threadIdx.x; t < q.chunk; t += blockDim.x) {
+        const int c = t / q.N1, n1 = t - c * q.N1;
+        const int j = q.N2 * n1 + q.r * q.c2 + c;
+        q.w0[t] = real_pre(Fm, j, N, post[j]);
+    }
+    __syncthreads();
+    const double2 *z = fft_cl_run(cl, fd, q, tw, true);
+    cl.sync();                                                     // every CTA has gathered its rows
+    const double *V = a.vring + (int64_t)(a.step % a.ring) * a.ring_stride;
+    for (int t = threadIdx.x; t < q.chunk; t += blockDim.x) {
+        const int p = t / q.N2, k2 = t - p * q.N2;
+        const int k = q.r * q.c1 + p + q.N1 * k2;                    // z_k carries elements 2k and 2k + 1
+        const double2 zz = z[t];
+        if (2 * k < N) assemble_out(a, fd, b, 2 * k, 2.0 * zz.x, V, tau, parts);
+        if (2 * k + 1 < N) assemble_out(a, fd, b, 2 * k + 1, 2.0 * zz.y, V, tau, parts);
     }
 }
 
@@ -1848,12 +2017,27 @@ static cudaError_t fft_smem(const void *fn, size_t smem) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+static size_t fft_cl_smem(const StepArgs &a) {
+    return (size_t)(3 * (a.max_nf / kFftCluster) + kFftRadixMax) * sizeof(double2);
+}
+
 cudaError_t launch_fft_forward(const StepArgs &a, cudaStream_t s) {
-    const size_t smem = (size_t)2 * a.max_nf * sizeof(double2);
-    cudaError_t e = fft_smem((const void *)k_fft_forward, smem);
-    if (e != cudaSuccess) return e;
-    k_fft_forward<<<dim3(a.n_self, a.B), kThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (a.n_small > 0) {
+        const size_t smem = (size_t)(2 * a.max_nf + kFftRadixMax) * sizeof(double2);
+        e = fft_smem((const void *)k_fft_forward, smem);
+        if (e != cudaSuccess) return e;
+        k_fft_forward<<<dim3(a.n_self, a.B), kThreads, smem, s>>>(a);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && a.n_big > 0) {
+        const size_t smem = fft_cl_smem(a);
+        e = fft_smem((const void *)k_fft_forward_cl, smem);
+        if (e != cudaSuccess) return e;
+        k_fft_forward_cl<<<dim3(a.n_big * kFftCluster, a.B), kThreads, smem, s>>>(a);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t launch_modeconv(const StepArgs &a, cudaStream_t s) {
@@ -1906,11 +2090,22 @@ cudaError_t launch_static_tail(const StepArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_ifft_assemble(const StepArgs &a, double *tau, double *parts, cudaStream_t s) {
-    const size_t smem = (size_t)2 * a.max_nf * sizeof(double2);
-    cudaError_t e = fft_smem((const void *)k_ifft_assemble, smem);
-    if (e != cudaSuccess) return e;
-    k_ifft_assemble<<<dim3(a.n_self, a.B), kThreads, smem, s>>>(a, tau, parts);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (a.n_small > 0) {
+        const size_t smem = (size_t)(2 * a.max_nf + kFftRadixMax) * sizeof(double2);
+        e = fft_smem((const void *)k_ifft_assemble, smem);
+        if (e != cudaSuccess) return e;
+        k_ifft_assemble<<<dim3(a.n_self, a.B), kThreads, smem, s>>>(a, tau, parts);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && a.n_big > 0) {
+        const size_t smem = fft_cl_smem(a);
+        e = fft_smem((const void *)k_ifft_assemble_cl, smem);
+        if (e != cudaSuccess) return e;
+        k_ifft_assemble_cl<<<dim3(a.n_big * kFftCluster, a.B), kThreads, smem, s>>>(a, tau, parts);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace seas
