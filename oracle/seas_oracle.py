@@ -555,8 +555,6 @@ def stress_history(net: Network, V: np.ndarray, hp: dict, slip=None):
                                        SelfTables(n_f, net.length[f], net.dt, net.cs, W, tail=tail))
     _, _, last = pair_windows(net, hp.get("eta_tmin", 0.01), hp.get("eta_tmax", 0.01), max_steps, no_trunc)
     if hp.get("flags", 0) & 16:
-        if tail:
-            raise ValueError("the static tail is defined for fault-pair windows only")
         last = cluster_windows(net, int(hp.get("leaf", 32)), float(hp.get("eta_h", 2.0)),
                                int(hp.get("max_block", 0)) or 64, hp.get("eta_tmax", 0.01), max_steps,
                                dense=bool(hp.get("flags", 0) & 1), no_trunc=no_trunc)
@@ -570,10 +568,21 @@ def static_tail_history(net: Network, delta: np.ndarray, last) -> np.ndarray:
     """Interaction part of the static tail at every step m: -(mu / 2 c_s) sum over source faults b != fault(i) of
     sum_{j in b} A_ij^static delta_j^{m - T_last(a, b) - 1}, where the pair's window still reaches back to step 0
     nothing is added (the dropped lags T > T_last carry A^T ~ dt A^static, and dt sum_{T > T_last} V^{m-T} is that
-    slip)."""
+    slip).  ``last`` per fault pair [F][F], or per element pair [N][N] (cluster-level windows: each element pair's
+    own window end T_last(i, j) in place of the pair's)."""
     steps = delta.shape[0]
     As = static_slice(net)
     out = np.zeros((steps, net.N))
+    if np.asarray(last).shape == (net.N, net.N) and net.N != net.F:
+        L = np.asarray(last)
+        other = net.fault_of[:, None] != net.fault_of[None, :]
+        for i in range(net.N):
+            for lag in np.unique(L[i][other[i]]):
+                cols = np.nonzero(other[i] & (L[i] == lag))[0]
+                lag = int(lag) + 1
+                if lag < steps:
+                    out[lag:, i] += delta[: steps - lag, cols] @ As[i, cols]
+        return -(net.mu / (2 * net.cs)) * out
     for a in range(net.F):
         ra = slice(net.offset[a], net.offset[a + 1])
         for b in range(net.F):

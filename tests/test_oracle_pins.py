@@ -825,3 +825,32 @@ def test_image_faults_maps_and_rejects_networks_off_one_surface():
     bad[1, 1] -= 5.0
     with pytest.raises(ValueError):
         O.image_faults(bad)
+
+
+def test_static_tail_with_cluster_windows_restores_the_dropped_history():
+    """P16f: the static tail with a window per element pair (cluster-level truncation).  Slip rate only at step 0:
+    once every block's window has passed the plain truncated sum is zero and the tail alone is left; it tends to the
+    untruncated sum as the pair-level tail does (P14b), and before any window has ended it adds nothing.  Broadcast
+    to element pairs, the fault-pair windows give the fault-pair tail (up to summation order)."""
+    net = _two_small_faults()
+    steps = 700
+    V = np.zeros((steps, net.N))
+    V[0] = np.linspace(1.0, 2.0, net.N)
+    hp = dict(eta_tmin=0.01, eta_tmax=0.01, eta_w=1.5, q_w=0, max_steps=steps, leaf=2, eta_h=0.5, max_block=4)
+    full = O.stress_history(net, V, dict(hp, flags=2))[3]
+    trunc = O.stress_history(net, V, dict(hp, flags=16))[3]
+    tail = O.stress_history(net, V, dict(hp, flags=16 | 4))[3]
+    W = O.cluster_windows(net, 2, 0.5, 4, 0.01, steps)
+    other = net.fault_of[:, None] != net.fault_of[None, :]
+    _, _, P = O.pair_windows(net, 0.01, 0.01, steps)
+    assert len(np.unique(W[other])) > 2 and (W[other] < P[net.fault_of][:, net.fault_of][other]).any()
+    m0 = int(W.max()) + 1
+    assert np.all(trunc[m0:] == 0)
+    e = [np.linalg.norm(tail[m] - full[m]) / np.linalg.norm(full[m]) for m in (300, 690)]
+    assert e[0] < 0.05 and e[1] < e[0] / 4 and e[1] < 1e-2
+    first = int(W[other].min()) + 1
+    assert np.all(tail[:first] == trunc[:first])
+    delta = O.slip_from_rate(V, net.dt)
+    pair_tail = O.static_tail_history(net, delta, P)
+    np.testing.assert_allclose(O.static_tail_history(net, delta, P[net.fault_of][:, net.fault_of]), pair_tail,
+                               rtol=1e-13, atol=1e-13 * np.abs(pair_tail).max())
