@@ -588,13 +588,14 @@ def run_ours(args, w, start, K, W):
         del V8d
 
     # the flagged static tail (elastostatic response of the history the windows drop) on the headline operator
-    tail = None
+    tail, tail_tau = None, None
     if not args.no_tail:
         s4 = session(head_code, flags=int(w.hparams.get("flags", 0)) | seas.SEAS_FLAG_STATIC_TAIL)
         r4 = measure(s4, Vd, 1, head_code)
         tv = job_rate(w.N * K, world, r4["total_ms"] / 1e3)
         tail = {"value": tv, "unit": METRIC, "ms_per_step": r4["total_ms"] / K, "cost_vs_headline": value / tv - 1,
                 "tail_share_of_tau": rel(r4["tau"].cpu().numpy(), tau.cpu().numpy())}
+        tail_tau = r4["tau"].cpu().numpy()
         s4.close()
         del r4
 
@@ -619,6 +620,17 @@ def run_ours(args, w, start, K, W):
             f"{cluster['bytes_vs_headline']:.3f} of the operator bytes")
         s5.close()
         del r5
+        if tail_tau is not None:
+            # with the static tail per block: against the fault-pair windows with their tail
+            s6 = session(head_code, flags=int(w.hparams.get("flags", 0)) | seas.SEAS_FLAG_CLUSTER_TRUNC
+                         | seas.SEAS_FLAG_STATIC_TAIL)
+            r6 = measure(s6, Vd, 1, head_code)
+            cluster["with_static_tail"] = {
+                "value": job_rate(w.N * K, world, r6["total_ms"] / 1e3), "unit": METRIC,
+                "ms_per_step": r6["total_ms"] / K,
+                "rel_l2_tau_vs_pair_windows_with_tail": rel(r6["tau"].cpu().numpy(), tail_tau)}
+            s6.close()
+            del r6
 
     # a fault breaking a traction-free surface (method of images), the shape of App. B's single-fault check: the
     # self term of the doubled 3200-element fault per step (no interaction), the deepest K steps of 2000

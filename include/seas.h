@@ -67,7 +67,8 @@ typedef int seas_status;
 /* SEAS_FLAG_STATIC_TAIL (not in the paper, which truncates): add back, as an elastostatic response, the history each
  * window drops.  Per spectral mode: (S_n - sum_{T<=W} w_n^T) D_n^{n-W-1}, S_n = (2/pi) Si(n pi) the weights' static
  * limit; per ordered fault pair whose window ends at T_last: A^static delta^{n-T_last-1}, A^static the t -> infinity
- * limit of the kernel over dt (Eq. primitives), delta the slip.  FP64 in every precision.  Costs a dense N x N FP64
+ * limit of the kernel over dt (Eq. primitives), delta the slip (per block, with the block's T_last, under
+ * SEAS_FLAG_CLUSTER_TRUNC).  FP64 in every precision.  Costs a dense N x N FP64
  * static operator and a slip ring per scenario; ignored with SEAS_FLAG_NO_TRUNC (nothing is dropped). */
 #define SEAS_FLAG_STATIC_TAIL 4
 /* SEAS_FLAG_LAG_CAP: max_steps caps every window (lags 0 .. max_steps - 1 are kept, older history is dropped like a
@@ -79,8 +80,8 @@ typedef int seas_status;
  * cluster A and source cluster B, T_max^AB is the largest distance from the two ends of A's segment to the ends of
  * B's elements over c_s, and the block keeps lags up to min(ceil((1 + eta_Tmax) T_max^AB / dt), max_steps - 1)
  * (never longer than the fault pair's window).  Well-separated cluster pairs then store and evaluate fewer lags.
- * Not with SEAS_FLAG_STATIC_TAIL (SEAS_EINVAL: the tail is defined per fault pair); ignored with
- * SEAS_FLAG_NO_TRUNC. */
+ * With SEAS_FLAG_STATIC_TAIL the tail adds, per block, the static response of the slip at the block's own window
+ * end.  Ignored with SEAS_FLAG_NO_TRUNC. */
 #define SEAS_FLAG_CLUSTER_TRUNC 16
 
 /* storage precision and arithmetic of the interaction operator */

@@ -221,6 +221,7 @@ struct seas_op {
     // static tail (SEAS_FLAG_STATIC_TAIL)
     bool tail = false;
     DArr<double> d_smat;             // [N][N] -(mu / 2 c_s) A^static
+    DArr<int32_t> d_block_last;      // with cluster-level windows: each block's last lag
     DArr<int32_t> d_pair_last;
     seas_op_stats stats{};
 };
@@ -903,6 +904,7 @@ seas_status build_static(seas_op &op) {
         }
     SEAS_TRY(op.d_smat.upload(c, m));
     SEAS_TRY(op.d_pair_last.upload(c, op.pair_last));
+    if (op.hp.flags & SEAS_FLAG_CLUSTER_TRUNC) SEAS_TRY(op.d_block_last.upload(c, op.block_hi));
     return SEAS_OK;
 }
 
@@ -1350,8 +1352,6 @@ extern "C" seas_status seas_build_hmatrix_part(seas_net *net, const seas_hparams
     if (hp->flags & ~(SEAS_FLAG_DENSE | SEAS_FLAG_NO_TRUNC | SEAS_FLAG_STATIC_TAIL | SEAS_FLAG_LAG_CAP |
                       SEAS_FLAG_CLUSTER_TRUNC))
         return fail(SEAS_EINVAL, "unsupported flags 0x%x", hp->flags);
-    if ((hp->flags & SEAS_FLAG_CLUSTER_TRUNC) && (hp->flags & SEAS_FLAG_STATIC_TAIL))
-        return fail(SEAS_EINVAL, "the static tail is defined for fault-pair windows (no SEAS_FLAG_CLUSTER_TRUNC)");
     if (hp->max_block != 0 && hp->max_block < hp->leaf) return fail(SEAS_EINVAL, "max_block must be >= leaf");
     seas_ctx *c = net->ctx;
     CUDA_TRY(cudaSetDevice(c->device));
@@ -1542,6 +1542,7 @@ StepArgs step_args(seas_scn &s, int64_t step) {
     a.sring = s.sring.p;
     a.smat = op.d_smat.p;
     a.pair_last = op.d_pair_last.p;
+    a.block_last = op.d_block_last.p;
     return a;
 }
 

@@ -261,6 +261,7 @@ struct StepArgs {
     double *sring;                // [sring_depth][N][B]: slip after each push
     const double *smat;           // [N][N]: -(mu / 2 c_s) A^static, receiver-major (same-fault entries unused)
     const int32_t *pair_last;     // [F][F]: last lag of each ordered fault pair's window
+    const int32_t *block_last;    // with cluster-level windows: last lag of each block (NULL: the pair's)
 };
 
 // Allocation-free stepping (seas_stress_step_static): scratch in a static device array of this many doubles.

@@ -1787,8 +1787,9 @@ __global__ void __launch_bounds__(InterShape<PREC, BT, PASS, CWv>::NT, 1) k_inte
 
 // Static tail of the interaction (flag SEAS_FLAG_STATIC_TAIL, not in the paper): for receiver e on fault a and each
 // source fault b whose window ends at lag T_last(a, b) < step, f_int[e] += sum_{j in b} smat[e][j] delta_j^{step -
-// T_last - 1}: the dropped lags T > T_last carry A^T ~ dt A^static, and dt times their slip rates is that slip.  One
-// warp per receiver element, lanes over the source columns, a fixed shuffle tree: deterministic.
+// T_last - 1}: the dropped lags T > T_last carry A^T ~ dt A^static, and dt times their slip rates is that slip.  With
+// cluster-level windows the same per block covering e, with the block's T_last.  One warp per receiver element,
+// lanes over the source columns, a fixed shuffle tree: deterministic.
 __global__ void __launch_bounds__(kThreads) k_static_tail(StepArgs a_) {
     StepArgs a = a_;
     apply_dyn(a);
@@ -1802,19 +1803,28 @@ __global__ void __launch_bounds__(kThreads) k_static_tail(StepArgs a_) {
     double sum[kMaxBatch];
 #pragma unroll
     for (int bb = 0; bb < kMaxBatch; ++bb) sum[bb] = 0.0;
-    for (int fb = 0; fb < a.F; ++fb) {
-        if (fb == fa) continue;
-        const int64_t back = (int64_t)a.pair_last[fa * a.F + fb] + 1;
-        if (a.lag_max < back) continue;                 // no member's window has passed yet
-        const int64_t src = a.step - back;
-        const double *sl = a.sring + (src % a.sring_depth) * BN;
-        const int j0 = a.faults[fb].off, j1 = j0 + a.faults[fb].nf;
+    // source columns j0 .. j1 - 1 whose window ends at lag back - 1
+    auto add = [&](int j0, int j1, int64_t back) {
+        if (a.lag_max < back) return;                   // no member's window has passed yet
+        const double *sl = a.sring + ((a.step - back) % a.sring_depth) * BN;
         for (int j = j0 + lane; j < j1; j += 32) {
             const double m = row[j];
 #pragma unroll
             for (int bb = 0; bb < kMaxBatch; ++bb)
                 if (bb < a.B) sum[bb] = fma(m, sl[(int64_t)j * a.B + bb], sum[bb]);
         }
+    };
+    if (a.block_last) {
+        // cluster-level windows: every block covering the receiver, with its own window end
+        for (int c = a.cover_ptr[e]; c < a.cover_ptr[e + 1]; ++c) {
+            const int blk = a.cover_blk[c];
+            const BlockDev &bd = a.blocks[blk];
+            add(bd.c0, bd.c0 + bd.q, (int64_t)a.block_last[blk] + 1);
+        }
+    } else {
+        for (int fb = 0; fb < a.F; ++fb)
+            if (fb != fa)
+                add(a.faults[fb].off, a.faults[fb].off + a.faults[fb].nf, (int64_t)a.pair_last[fa * a.F + fb] + 1);
     }
 #pragma unroll
     for (int bb = 0; bb < kMaxBatch; ++bb) {
