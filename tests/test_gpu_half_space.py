@@ -126,3 +126,30 @@ def test_surface_networks_off_one_surface_are_rejected():
         with pytest.raises(seas.SeasError) as e:
             seas.Session(w)
         assert e.value.status == seas.SEAS_EINVAL
+
+
+def test_surface_faults_in_an_eight_scenario_bf16_batch():
+    """The tensor-core BF16 path with 8 scenarios on two parallel surface faults: member b pushed (1 + b / 8) times
+    the rates gets that multiple of the oracle's half-space stress (the functional is linear): self and radiation
+    parts in FP64 within 1e-10, the BF16 interaction within the BF16 bound of the parity tests (5e-3)."""
+    steps = 200
+    faults = np.array([surface_fault(0.0, 400.0, 48), surface_fault(150.0, 300.0, 32)])
+    hp = dict(max_steps=steps, leaf=8, eta_h=1.0, eta_tmax=0.01)
+    w = synth.Workload("surface2_b8", faults, mu=MU, cs=CS, steps=steps, hparams=hp)
+    V = w.slip_rate(0, 0, steps)
+    scale = 1.0 + np.arange(8) / 8.0
+    P = np.zeros((steps, 3, 8, w.N))
+    p = np.zeros(3 * 8 * w.N)
+    t = np.zeros(8 * w.N)
+    with seas.Session(w, batch=8, precision=seas.SEAS_PREC_BF16) as s:
+        for n in range(steps):
+            seas.seas_push_slip_rate(s.scn, np.concatenate([c * V[n] for c in scale]))
+            seas.seas_stress_step(s.scn, t, parts=p)
+            P[n] = p.reshape(3, 8, w.N)
+    ref = O.half_space_stress_history(faults[:, :5], MU, CS, V, hp)
+    worst = [0.0, 0.0, 0.0]
+    for b, c in enumerate(scale):
+        for k in range(3):
+            worst[k] = max(worst[k], rel(P[:, k, b], c * ref[k + 1]))
+    print(f"surface faults, BF16 x 8: worst member rel-L2 rad/self/int {worst}")
+    assert worst[0] <= 1e-10 and worst[1] <= 1e-10 and worst[2] <= 5e-3

@@ -99,3 +99,48 @@ def test_receiver_on_another_fault_is_rejected():
     with pytest.raises(seas.SeasError) as e:
         seas.seas_plan_hmatrix(faults, 32e9, 3464.0, 6000.0, 0.5, dict(max_steps=10, leaf=4))
     assert e.value.status == seas.SEAS_EINVAL
+
+
+def _surface_fault(x0, depth, n, phi=-0.5 * math.pi):
+    e1 = (math.cos(phi), math.sin(phi))
+    return [x0 + 0.5 * depth * e1[0], 0.5 * depth * e1[1], phi, depth, n, seas.SEAS_FAULT_SURFACE_START]
+
+
+def test_plan_of_a_surface_network_is_the_oracles_doubled_network():
+    """Faults breaking a free surface (method of images): the host plan is that of the doubled network the oracle
+    builds (image_faults): the same dt, mode windows of 2 N_f + 1 modes per fault, and the same block partition as
+    the oracle's dual traversal of the doubled faults."""
+    faults = np.array([_surface_fault(0.0, 400.0, 48), _surface_fault(150.0, 300.0, 32)])
+    hp = dict(max_steps=300, leaf=8, eta_h=1.0)
+    pl = seas.seas_plan_hmatrix(faults, 32e9, 3464.0, 6000.0, 0.5, hp)
+    doubled, mirror, real = O.image_faults(faults[:, :5])
+    net2 = O.network(doubled, 32e9, 3464.0)
+    assert pl["dt"] == pytest.approx(net2.dt, rel=1e-15)
+    assert [len(m) for m in pl["mode_windows"]] == [97, 65]
+    for f, n in enumerate((96, 64)):
+        W = O.mode_windows(n, doubled[f, 3], net2.dt, 3464.0, 1.5, 0, 300)
+        np.testing.assert_array_equal(pl["mode_windows"][f], W)
+    ref = set()
+    for a in range(2):
+        for b in range(2):
+            if a != b:
+                ref |= {tuple(int(v) for v in blk[:4]) for blk in O.hmatrix_blocks(net2, a, b, 8, 1.0, 64)}
+    assert {tuple(int(v) for v in r[:4]) for r in pl["blocks"]} == ref
+
+
+@pytest.mark.parametrize("bad", ["tilted", "off_surface", "mixed", "unknown_flag"])
+def test_surface_networks_off_one_surface_are_rejected_on_the_host(bad):
+    ok = _surface_fault(0.0, 100.0, 8)
+    other = _surface_fault(60.0, 100.0, 8)
+    if bad == "tilted":
+        other = _surface_fault(60.0, 100.0, 8, phi=-1.3)
+    elif bad == "off_surface":
+        other[1] -= 10.0
+    elif bad == "mixed":
+        other[5] = 0
+    else:
+        other[5] = 2
+    seas.seas_plan_hmatrix(np.array([ok]), 32e9, 3464.0, 6000.0, 0.5, dict(max_steps=4))
+    with pytest.raises(seas.SeasError) as e:
+        seas.seas_plan_hmatrix(np.array([ok, other]), 32e9, 3464.0, 6000.0, 0.5, dict(max_steps=4))
+    assert e.value.status == seas.SEAS_EINVAL
