@@ -281,13 +281,27 @@ def max_over_ranks(dist, x, device):
     return float(t.item())
 
 
-def advance(seas, torch, scn, Vd, n0, n1, device):
-    """Untimed steps n0 .. n1 - 1 (device-resident inputs)."""
+def advance(seas, torch, scn, Vd, n0, n1, device, sample_every=0):
+    """Untimed steps n0 .. n1 - 1 (device-resident inputs).  With sample_every > 0, every sample_every-th step is
+    also bracketed by CUDA events (its own synchronize), and {step: ms} is returned: the step time as the history
+    deepens."""
     t = torch.zeros(Vd.shape[1], dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    by_depth = {}
     for n in range(n0, n1):
+        sample = sample_every > 0 and n > 0 and n % sample_every == 0
+        if sample:
+            torch.cuda.synchronize(device)
+            a.record(stream)
         seas.seas_push_slip_rate(scn, Vd[n])
         seas.seas_stress_step(scn, t)
+        if sample:
+            b.record(stream)
+            b.synchronize()
+            by_depth[n] = a.elapsed_time(b)
     torch.cuda.synchronize(device)
+    return by_depth
 
 
 def nvtx_push(name):
@@ -462,8 +476,8 @@ def run_ours(args, w, start, K, W):
     head_code, head_dtype = PRECISIONS[args.precision]
     s = session(head_code)
     t0 = time.perf_counter()
-    advance(seas, torch, s.scn, Vd, 0, start, device)
-    log(f"advance {start} steps: {time.perf_counter() - t0:.1f} s")
+    by_depth = advance(seas, torch, s.scn, Vd, 0, start, device, sample_every=max(1, w.steps // 10))
+    log(f"advance {start} steps: {time.perf_counter() - t0:.1f} s; ms per step by depth {by_depth}")
     ckpt_dir = tempfile.mkdtemp(prefix="seas_bench_")
     ckpt = os.path.join(ckpt_dir, "window_start.ckpt")
     seas.seas_scenario_save(s.scn, ckpt)
@@ -692,7 +706,9 @@ def run_ours(args, w, start, K, W):
         stats = s.stats
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": total_ms / K, "p50_ms": float(np.percentile(per, 50)),
-                "p99_ms": float(np.percentile(per, 99)), "higher_is_better": True, "scaling": "weak",
+                "p99_ms": float(np.percentile(per, 99)),
+                "ms_by_history_depth": {str(k): v for k, v in by_depth.items()},
+                "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": head_dtype, "data": "synthetic",
                 "config": dict(config_of(w, start, K), precision=args.precision,
                                window_algorithmic_bytes_per_step=window_bytes),
