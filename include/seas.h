@@ -312,9 +312,10 @@ const char *seas_strerror(seas_status s);
 const char *seas_last_error(void);
 
 /* Host-only planning (no device work): the block partition, windows and time step the operator build would use.
- * blocks (nullable): [cap][6] int32 rows (r0, p, c0, q, far, first_lag) -- receiver rows [r0, r0 + p), source
- * columns [c0, c0 + q), far = 1 for an admissible (low-rank) block, first_lag = conservative first nonzero lag;
- * *n_blocks receives the total count even when it exceeds cap.  pair_last (nullable): [F][F] last lags.
+ * blocks (nullable): [cap][7] int32 rows (r0, p, c0, q, far, first_lag, last_lag) -- receiver rows [r0, r0 + p),
+ * source columns [c0, c0 + q), far = 1 for an admissible (low-rank) block, first_lag = conservative first nonzero
+ * lag, last_lag = the block's window end (its fault pair's, or its own with SEAS_FLAG_CLUSTER_TRUNC); *n_blocks
+ * receives the total count even when it exceeds cap.  pair_last (nullable): [F][F] last lags.
  * mode_windows (nullable): W_f(n), n = 0..N_f, fault after fault.  dt (nullable). */
 seas_status seas_plan_hmatrix(const seas_fault *faults, int n_faults, const seas_medium *medium,
                               const seas_hparams *hp, int32_t *blocks, int64_t cap, int64_t *n_blocks,

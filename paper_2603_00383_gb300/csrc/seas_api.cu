@@ -1386,26 +1386,29 @@ extern "C" seas_status seas_plan_hmatrix(const seas_fault *faults, int n_faults,
     std::vector<std::vector<Cluster>> trees(net.F);
     for (int f = 0; f < net.F; ++f) build_tree(net, f, net.off[f], net.off[f + 1], hp->leaf, trees[f]);
     std::vector<BlockDev> bl;
-    std::vector<int32_t> far, pairs;
+    std::vector<int32_t> far, pairs, pl((size_t)net.F * net.F, -1);
     for (int a = 0; a < net.F; ++a)
         for (int b = 0; b < net.F; ++b) {
             if (a == b) continue;
-            if (pair_last)
-                pair_last[a * net.F + b] = pair_last_lag(net, a, b, hp->eta_tmax, hp->max_steps, no_trunc);
+            pl[(size_t)a * net.F + b] = pair_last_lag(net, a, b, hp->eta_tmax, hp->max_steps, no_trunc);
+            if (pair_last) pair_last[a * net.F + b] = pl[(size_t)a * net.F + b];
             traverse(trees[a], trees[b], hp->eta_h, dense, max_block, a * net.F + b, bl, far, pairs);
         }
+    const bool cluster_trunc = (hp->flags & SEAS_FLAG_CLUSTER_TRUNC) && !no_trunc;
     if (pair_last)
         for (int a = 0; a < net.F; ++a) pair_last[a * net.F + a] = -1;
     if (n_blocks) *n_blocks = (int64_t)bl.size();
     if (blocks)
         for (int64_t i = 0; i < std::min<int64_t>(cap, (int64_t)bl.size()); ++i) {
-            int32_t *r = blocks + 6 * i;
+            int32_t *r = blocks + 7 * i;
             r[0] = bl[i].r0;
             r[1] = bl[i].p;
             r[2] = bl[i].c0;
             r[3] = bl[i].q;
             r[4] = far[i];
             r[5] = block_first_lag(net, bl[i]);
+            r[6] = pl[(size_t)pairs[i]];
+            if (cluster_trunc) r[6] = std::min(r[6], cluster_last_lag(net, bl[i], hp->eta_tmax, hp->max_steps));
         }
     if (mode_windows) {
         int64_t o = 0;

@@ -240,7 +240,8 @@ def _hparams(hp: dict) -> seas_hparams:
 
 
 def seas_plan_hmatrix(faults, mu: float, cs: float, cp: float, beta: float, hp: dict) -> dict:
-    """Host-only plan: blocks [n, 6] (r0, p, c0, q, far, first_lag), pair_last [F, F], mode windows per fault, dt."""
+    """Host-only plan: blocks [n, 7] (r0, p, c0, q, far, first_lag, last_lag), pair_last [F, F], mode windows per
+    fault, dt."""
     faults, arr = _faults(faults)
     med = seas_medium(mu, cs, cp, beta)
     p = _hparams(hp)
@@ -249,7 +250,7 @@ def seas_plan_hmatrix(faults, mu: float, cs: float, cp: float, beta: float, hp: 
     F = len(faults)
     _check(lib().seas_plan_hmatrix(arr, F, C.byref(med), C.byref(p), None, 0, C.byref(nb), None, None,
                                    C.byref(dt)))
-    blocks = np.zeros((nb.value, 6), dtype=np.int32)
+    blocks = np.zeros((nb.value, 7), dtype=np.int32)
     last = np.zeros((F, F), dtype=np.int32)
     nel = _network_n_elem(faults)
     mw = np.zeros(sum(n + 1 for n in nel), dtype=np.int32)

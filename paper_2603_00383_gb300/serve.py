@@ -429,9 +429,7 @@ def estimate_bytes(geometries, batch: int, precision: int):
     for w in geometries:
         p = seas.seas_plan_hmatrix(w.faults, w.mu, w.cs, w.cp, w.beta, dict(w.hparams, precision=precision))
         blocks, last = p["blocks"], p["pair_last"]
-        off = np.concatenate([[0], np.cumsum(w.faults[:, 4].astype(int))])
-        fault_of = np.repeat(np.arange(w.n_faults), np.diff(off))
-        lags = np.array([max(0, last[fault_of[b[0]], fault_of[b[2]]] - b[5] + 1) for b in blocks])
+        lags = np.maximum(0, blocks[:, 6].astype(np.int64) - blocks[:, 5] + 1)
         entries = int(np.sum(blocks[:, 1].astype(np.int64) * blocks[:, 3] * lags))
         W = max(int(max(x.max() for x in p["mode_windows"])), 1)
         ring = max(int(last.max()) + 1, 1)

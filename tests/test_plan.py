@@ -28,7 +28,7 @@ def test_partition_covers_every_cross_fault_pair_once(make, hp):
     pl, p = plan(w, **hp)
     net = O.network(w.faults, w.mu, w.cs)
     cover = np.zeros((net.N, net.N), dtype=np.int32)
-    for r0, pp, c0, q, far, _ in pl["blocks"]:
+    for r0, pp, c0, q, far, _, _ in pl["blocks"]:
         cover[r0:r0 + pp, c0:c0 + q] += 1
         assert net.fault_of[r0] == net.fault_of[r0 + pp - 1] != net.fault_of[c0] == net.fault_of[c0 + q - 1]
         ca, ra = circle(net, r0, r0 + pp)
@@ -76,7 +76,7 @@ def test_block_first_lag_never_after_the_first_nonzero_lag():
     pl, _ = plan(w, leaf=2, eta_h=1.0, flags=0)
     net = O.network(w.faults, w.mu, w.cs)
     A = np.stack([O.interaction_slice(net, T) for T in range(200)])
-    for r0, pp, c0, q, far, first in pl["blocks"]:
+    for r0, pp, c0, q, far, first, _ in pl["blocks"]:
         nz = np.nonzero(np.any(A[:, r0:r0 + pp, c0:c0 + q] != 0, axis=(1, 2)))[0]
         if len(nz):
             assert first <= nz[0] <= first + 2
@@ -144,3 +144,30 @@ def test_surface_networks_off_one_surface_are_rejected_on_the_host(bad):
     with pytest.raises(seas.SeasError) as e:
         seas.seas_plan_hmatrix(np.array([ok, other]), 32e9, 3464.0, 6000.0, 0.5, dict(max_steps=4))
     assert e.value.status == seas.SEAS_EINVAL
+
+
+@pytest.mark.parametrize("leaf,eta_h,max_block,dense", [(8, 2.0, 0, False), (4, 1.0, 16, False), (6, 2.0, 0, True)])
+def test_plan_block_windows_equal_the_oracle(leaf, eta_h, max_block, dense):
+    """The plan's last lag of every block: the fault pair's window without the flag, the oracle's cluster-level
+    window (Sec. 4.3 reading) with SEAS_FLAG_CLUSTER_TRUNC, as integers; the partition equals the oracle's."""
+    faults = np.array([[0.0, 0.0, 0.1, 400.0, 40], [60.0, 300.0, -0.3, 320.0, 32], [450.0, -150.0, 1.2, 240.0, 24]])
+    hp = dict(max_steps=260, leaf=leaf, eta_h=eta_h, max_block=max_block, eta_tmax=0.05,
+              flags=seas.SEAS_FLAG_DENSE if dense else 0)
+    net = O.network(faults, 32e9, 3464.0)
+    _, _, P = O.pair_windows(net, 0.01, 0.05, 260)
+    W = O.cluster_windows(net, leaf, eta_h, max_block or 64, 0.05, 260, dense=dense)
+    ref = set()
+    for a in range(net.F):
+        for b in range(net.F):
+            if a != b:
+                ref |= {tuple(int(v) for v in blk)
+                        for blk in O.hmatrix_blocks(net, a, b, leaf, eta_h, max_block or 64, dense)}
+    for cluster in (False, True):
+        p = dict(hp, flags=hp["flags"] | (seas.SEAS_FLAG_CLUSTER_TRUNC if cluster else 0))
+        pl = seas.seas_plan_hmatrix(faults, 32e9, 3464.0, 6000.0, 0.5, p)
+        assert {tuple(int(v) for v in r[:5]) for r in pl["blocks"]} == ref
+        expect = W if cluster else P[net.fault_of][:, net.fault_of]
+        for r0, pp, c0, q, far, first, last in pl["blocks"]:
+            assert (expect[r0:r0 + pp, c0:c0 + q] == last).all()
+    assert (W[net.fault_of[:, None] != net.fault_of[None, :]] < P[net.fault_of][:, net.fault_of][
+        net.fault_of[:, None] != net.fault_of[None, :]]).any()
