@@ -434,11 +434,12 @@ seas_status make_geometry(const seas_fault *faults_in, int n_faults, const seas_
         const seas_fault &F = faults[f];
         if (!(is_fin(F.cx) && is_fin(F.cy) && is_fin(F.strike_rad) && is_fin(F.length) && F.length > 0))
             return fail(SEAS_EINVAL, "fault %d: non-finite or non-positive geometry", f);
+        const char *with = net.images ? " (with its image across the free surface)" : "";
         if (F.n_elem < 1 || F.n_elem > kMaxFFT)
-            return fail(SEAS_EINVAL, "fault %d: n_elem %d outside [1, %d]", f, F.n_elem, kMaxFFT);
+            return fail(SEAS_EINVAL, "fault %d: n_elem %d%s outside [1, %d]", f, F.n_elem, with, kMaxFFT);
         if (!is_fft_size(F.n_elem))
-            return fail(SEAS_EINVAL, "fault %d: n_elem %d has a prime factor > 23 (FFT radices are the primes <= 23)", f,
-                        F.n_elem);
+            return fail(SEAS_EINVAL, "fault %d: n_elem %d%s has a prime factor > 23 (FFT radices are the primes <= 23)",
+                        f, F.n_elem, with);
         N += F.n_elem;
     }
     if (N > (1 << 24)) return fail(SEAS_EINVAL, "too many elements (%lld)", (long long)N);
