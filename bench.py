@@ -128,6 +128,10 @@ class OracleStepper:
     def interaction(self, rows, n):
         return self.O.interaction_rows(self.net, self.V, int(n), rows, pair_hi=self.last)
 
+    def self_part(self, rows0, n):
+        """The spectral self part at receivers ``rows0`` of fault 0 at step n."""
+        return self.O.self_rows(self.net, 0, self.delta[: n + 1, : self.n0], int(n), self.tab0, rows0)
+
     def interaction_cluster(self, rows, n):
         """The same rows with the cluster-level end truncation (windows per block of the H-matrix partition)."""
         hp = self.w.hparams
@@ -378,8 +382,9 @@ def run_ours(args, w, start, K, W):
     w.seed = rank_seed(rank)                                # independent scenario per rank
     # CPU oracle first (before any GPU work in this process): the CPU baseline and the interaction rows that every
     # storage precision is checked against
-    oracle, ref_int, ref_int_cluster = None, None, None
+    oracle, ref_int, ref_int_cluster, ref_self = None, None, None, None
     rows = oracle_rows(w)
+    rows0 = np.linspace(0, int(w.faults[0, 4]) - 1, 8).astype(int)          # receivers of fault 0 (self part)
     if rank == 0 and (args.cpu_sample > 0 or not args.no_oracle_rows):
         t0 = time.perf_counter()
         st = OracleStepper(w)
@@ -394,7 +399,8 @@ def run_ours(args, w, start, K, W):
         if not args.no_oracle_rows:
             t0 = time.perf_counter()
             ref_int = st.interaction(rows, w.steps - 1)
-            log(f"oracle interaction rows {time.perf_counter() - t0:.1f} s")
+            ref_self = st.self_part(rows0, w.steps - 1)
+            log(f"oracle interaction and self rows {time.perf_counter() - t0:.1f} s")
             if not args.no_cluster:
                 t0 = time.perf_counter()
                 ref_int_cluster = st.interaction_cluster(rows, w.steps - 1)
@@ -489,6 +495,8 @@ def run_ours(args, w, start, K, W):
     value = job_rate(w.N * K, world, total_ms / 1e3)
     err_tau = tau_err(tau)
     err_int = int_err(parts)
+    err_self = None if ref_self is None else rel(parts[1, rows0].cpu().numpy(), ref_self)
+    err_rad = rel(parts[0].cpu().numpy(), -(w.mu / (2 * w.cs)) * V[w.steps - 1])
     log(f"headline {value / 1e6:.3f} M element-steps/s, p50 {np.percentile(per, 50):.3f} ms")
 
     sB = seas.seas_scenario_load(s.op, ckpt)
@@ -713,7 +721,9 @@ def run_ours(args, w, start, K, W):
                 "config": dict(config_of(w, start, K), precision=args.precision,
                                window_algorithmic_bytes_per_step=window_bytes),
                 "rel_l2_tau_vs_oracle": err_tau, "rel_l2_interaction_vs_oracle": err_int,
-                "oracle_rows": {"interaction": [int(r) for r in rows], "step": w.steps - 1},
+                "rel_l2_self_vs_oracle": err_self, "rel_l2_radiation_vs_oracle": err_rad,
+                "oracle_rows": {"interaction": [int(r) for r in rows], "self": [int(r) for r in rows0],
+                                "step": w.steps - 1},
                 "operator": {k: stats[k] for k in (
                     "n_blocks_far", "n_blocks_near", "compression_ratio", "bytes_interaction", "mean_rank",
                     "max_rank", "build_seconds", "n_tasks")},
